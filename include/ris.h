@@ -1,0 +1,183 @@
+/*
+ * ris.h — C ABI of the GB300 (sm_103a) TDDFT-ris engine.
+ *
+ * The engine evaluates the minimal-auxiliary-basis ("ris") response kernel
+ * of arXiv:2511.18233 and its explicit nuclear derivatives:
+ *
+ *   - the ris two-electron kernel, Eq. (g_modified) of Sec. 2.2:
+ *       g^ris_{pq,sr} = sum_AB (pq|A)(M^-1)_AB(B|sr) - c_x sum_AB (pr|A)(M^-1)_AB(B|sq),
+ *     M_AB = (A|B), with separate Coulomb-fitting (J) and exchange-fitting (K)
+ *     auxiliary sets (Sec. 2.2; Sec. 4 uses s+p for J and s for K);
+ *   - the Casida problem, Eqs. (casida), (A_matrix), (B_matrix), with the pure
+ *     XC kernel dropped (Eq. (ris)); closed-shell singlet, so
+ *       A_ia,jb = (e_a - e_i) d_ij d_ab + 2 (ia|jb)_J - c_x (ij|ab)_K,
+ *       B_ia,jb = 2 (ia|jb)_J - c_x (ib|ja)_K;
+ *     TDA is the same path with Y = 0 (Sec. 3);
+ *   - the integral-derivative terms <g^{ris,(xi)}; Gamma_II> and
+ *     <g^{ris,(xi)}; Gamma_IJ>/(E_J - E_I) of Eqs. (gI_xi_ris) and
+ *     (gIJ_xi_ris), with the RI derivative formula closing Sec. 2.2 and
+ *     Gamma_IJ = {R_I^S,R_J^S} + {L_I^A,L_J^A} (Appendix A).
+ *
+ * The gradient returned is the derivative of the pair energy
+ *     E_IJ = 1/2 [R_I (A+B) R_J + L_I (A-B) L_J],  R = X+Y, L = X-Y,
+ * with respect to the nuclear coordinates at fixed MO coefficients, orbital
+ * energies and amplitudes; g_I = dE_II/dR (Eq. (gradient)) and the
+ * derivative coupling g_IJ = (dE_IJ/dR)/(omega_J - omega_I) (Eq. (fo-nacme)).
+ *
+ * Conventions
+ *   - Units: bohr and Hartree; gradients in Hartree/bohr, couplings in 1/bohr.
+ *   - Every shell is one uncontracted cartesian primitive, each component
+ *     normalised to <chi|chi> = 1; components in lexicographic order
+ *     (p: x,y,z; d: xx,xy,xz,yy,yz,zz).  AO functions are numbered shell by
+ *     shell in the order given.
+ *   - All matrices are row-major.  Amplitudes are [nstate][nocc][nvir] (the
+ *     transpose of the paper's vir x occ X_ai).
+ *   - Array arguments may be host or device pointers.  A device pointer must
+ *     live on the context's device; it is read or written in stream order on
+ *     the context's stream.  The library tells the two apart with
+ *     cudaPointerGetAttributes.
+ *
+ * Ownership and errors
+ *   - The caller owns every argument buffer; the context copies what it keeps
+ *     and owns all device memory it allocates.
+ *   - Every call returns a ris_status.  On error the outputs are untouched and
+ *     ris_last_error() returns a message.  Calls made out of order
+ *     (aux -> B -> excite -> gradient/nac) return RIS_ERR_STATE.
+ *   - One context per stream; contexts share no state.
+ */
+#ifndef RIS_H_
+#define RIS_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ris_ctx ris_ctx;
+
+typedef enum {
+  RIS_OK = 0,
+  RIS_ERR_ARG = -1,            /* invalid argument */
+  RIS_ERR_OOM = -2,            /* device allocation failed or over mem_budget */
+  RIS_ERR_METRIC_NOT_PD = -3,  /* auxiliary metric not positive definite */
+  RIS_ERR_NOT_CONVERGED = -4,  /* Davidson hit max_iter */
+  RIS_ERR_CUDA = -5,           /* CUDA runtime error */
+  RIS_ERR_TIMEOUT = -6,        /* a host wait exceeded its limit */
+  RIS_ERR_STATE = -7,          /* call order violated */
+  RIS_ERR_DEGENERATE = -8      /* |omega_J - omega_I| too small for a coupling */
+} ris_status;
+
+enum { RIS_FP64 = 0, RIS_MIXED = 1 };
+
+typedef struct {
+  int precision;      /* RIS_FP64 or RIS_MIXED */
+  int rpa;            /* 0: TDA (Y = 0), 1: full RPA (X, Y) */
+  double cx;          /* fraction of exact exchange c_x (Eq. g_integral); default 0.25 */
+  double conv_tol;    /* Davidson residual 2-norm per state; default 1e-10 */
+  int max_iter;       /* Davidson iterations; default 100 */
+  int max_subspace;   /* Davidson subspace size before restart; 0 = automatic */
+  double screen_thr;  /* shell-pair screening threshold; default 1e-14 */
+  size_t mem_budget;  /* device bytes the context may hold; 0 = no limit */
+  int occ_block;      /* occupied-orbital block for streamed B builds; 0 = all */
+  void* cuda_stream;  /* cudaStream_t to run on; NULL = the context makes one */
+  int device;         /* CUDA device ordinal */
+} ris_options;
+
+typedef struct {
+  int atom;        /* index into the coordinate array */
+  int l;           /* angular momentum: AO 0..2, auxiliary 0..1 */
+  double exponent; /* Gaussian exponent (bohr^-2) */
+} ris_shell;
+
+/* Fill *opt with the defaults listed above. */
+ris_status ris_options_default(ris_options* opt);
+
+/* Create a context on opt->device.  *out receives the handle. */
+ris_status ris_create(ris_ctx** out, const ris_options* opt);
+
+/*
+ * Geometry and basis (Sec. 2.2: the ris auxiliary set is one Gaussian per
+ * angular-momentum component per atom).  coords: [natm][3] bohr.  ao: the AO
+ * shells; auxJ / auxK: Coulomb- and exchange-fitting auxiliary shells.
+ * Builds the screened shell-pair list, the three-centre integrals (mu nu|P)
+ * and the metric Cholesky factor M = L L^T of each auxiliary set.
+ * Invalidates any earlier B tensors and excitations.
+ * Errors: RIS_ERR_ARG (bad shell, l out of range, atom index out of range),
+ * RIS_ERR_METRIC_NOT_PD (singular metric, e.g. duplicate atoms).
+ */
+ris_status ris_build_aux(ris_ctx* ctx, int natm, const double* coords, int nshell,
+                         const ris_shell* ao, int nJ, const ris_shell* auxJ, int nK,
+                         const ris_shell* auxK);
+
+/*
+ * MO data and the B tensors B^X_{pq,R} = sum_P (pq|P) (L_X^-T)_PR (RI of
+ * Eq. (g_modified)): B^J over the ov block and B^K over the oo and vv blocks
+ * (plus ov for RPA).  C: [nao][nmo] row-major, occupied columns first;
+ * mo_energy: [nmo].  nmo must equal nao; 0 < nocc < nmo.
+ */
+ris_status ris_build_B(ris_ctx* ctx, int nao, int nmo, int nocc, const double* C,
+                       const double* mo_energy);
+
+/*
+ * Lowest nstates excitation energies by Davidson on the ris A (TDA) or on the
+ * Casida problem (RPA), Eq. (casida).  omega: [nstates] Hartree.  X, Y:
+ * [nstates][nocc][nvir] or NULL (Y is written only for RPA).  Normalisation:
+ * sum X^2 = 1 (TDA), sum X^2 - Y^2 = 1 (RPA); each state's sign makes its
+ * largest-magnitude X element positive.
+ * Errors: RIS_ERR_NOT_CONVERGED after max_iter (outputs untouched).
+ */
+ris_status ris_excite(ris_ctx* ctx, int nstates, double* omega, double* X, double* Y);
+
+/*
+ * Excited-state gradients g_I = dE_II/dR (Eq. (gI_xi_ris), integral-derivative
+ * term) for the n states listed in states[] (0-based).  If X_in is NULL the
+ * amplitudes of the last ris_excite are used and states index them;
+ * otherwise X_in (and Y_in for RPA, NULL for TDA) hold nx states
+ * [nx][nocc][nvir] and states index those.  grad: [n][natm][3] Hartree/bohr.
+ */
+ris_status ris_gradient(ris_ctx* ctx, int n, const int* states, int nx, const double* X_in,
+                        const double* Y_in, double* grad);
+
+/*
+ * Derivative couplings g_IJ = (dE_IJ/dR)/(omega_J - omega_I) (Eqs. (fo-nacme),
+ * (gIJ_xi_ris), integral-derivative term) for npair pairs [npair][2].
+ * Amplitudes as in ris_gradient; omega_in: [nx] energies for X_in (NULL with
+ * X_in NULL).  nac: [npair][natm][3] 1/bohr; numerator (dE_IJ/dR, same
+ * shape) may be NULL.  Returns RIS_ERR_DEGENERATE if |omega_J - omega_I| <
+ * 1e-8 for a pair (the numerator is still written when requested).
+ */
+ris_status ris_nac(ris_ctx* ctx, int npair, const int* pairs, int nx, const double* X_in,
+                   const double* Y_in, const double* omega_in, double* nac, double* numerator);
+
+/* Sizes of the current problem (any pointer may be NULL). */
+ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int* nauxJ,
+                        int* nauxK, int* npairs_screened);
+
+/*
+ * Stage timings of the last calls in milliseconds, measured with CUDA events
+ * on the context's stream: [0] aux, [1] B, [2] excite, [3] gradient/nac
+ * derivative kernels, [4] number of A-products of the last excite,
+ * [5] Davidson iterations of the last excite.  n: entries to copy (<= 16).
+ */
+ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n);
+
+/*
+ * Test hook: Boys function F_m(T) = int_0^1 t^{2m} e^{-T t^2} dt as used by
+ * the integral kernels (the Coulomb integrals of Eq. (g_modified) reduce to
+ * it).  n values; m[i] in 0..9; all three arrays are DEVICE pointers on the
+ * current device.  Synchronises the device; returns 0 or a ris_status.
+ */
+int ris_debug_boys(int n, const int* m, const double* T, double* out);
+
+/* Message of the last error on this context ("" if none). */
+const char* ris_last_error(const ris_ctx* ctx);
+
+/* Free the context and everything it owns.  NULL is ignored. */
+void ris_destroy(ris_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIS_H_ */

@@ -218,20 +218,20 @@ class RisOracle:
     # -- four-index RI blocks as operators
     def _coul(self, U, V, ov1, ov2, Minv):
         """sum U_ia V_jb (ia|A) Minv_AB (B|jb) with separate 3c tensors per side."""
-        u = np.einsum("ia,iaP->P", U, ov1)
-        v = np.einsum("jb,jbP->P", V, ov2)
+        u = np.tensordot(U, ov1, axes=([0, 1], [0, 1]))
+        v = np.tensordot(V, ov2, axes=([0, 1], [0, 1]))
         return u @ Minv @ v
 
     def apply_A(self, X: np.ndarray) -> np.ndarray:
         """TDA A applied to X [n][nocc][nvir] (Eq. A_matrix with the ris kernel)."""
         out = np.empty_like(X)
-        cvv = np.einsum("abQ,QP->abP", self.vvK, self.MKinv)
+        cvv = np.tensordot(self.vvK, self.MKinv, axes=([2], [0]))  # [a][b][P]
         for k in range(X.shape[0]):
             x = X[k]
-            w = self.MJinv @ np.einsum("jb,jbP->P", x, self.ovJ)
-            coul = np.einsum("iaP,P->ia", self.ovJ, w)
-            t = np.einsum("jb,abP->jaP", x, cvv)
-            exch = np.einsum("ijP,jaP->ia", self.ooK, t)
+            w = self.MJinv @ np.tensordot(x, self.ovJ, axes=([0, 1], [0, 1]))
+            coul = np.tensordot(self.ovJ, w, axes=([2], [0]))
+            t = np.tensordot(x, cvv, axes=([1], [1]))                 # [j][a][P]
+            exch = np.tensordot(self.ooK, t, axes=([1, 2], [0, 2]))   # [i][a]
             out[k] = self.de * x + 2.0 * coul - self.cx * exch
         return out
 
@@ -337,15 +337,17 @@ class RisOracle:
 
     def _xk(self, U, V, oo, vv, Minv):
         """sum U_ia V_jb (ij|A) Minv_AB (B|ab)."""
-        t = np.einsum("ia,abQ->ibQ", U, vv)          # [i][b][Q]
-        t = np.einsum("ibQ,jb->ijQ", t, V)
-        return np.einsum("ijP,PQ,ijQ->", oo, Minv, t)
+        t = np.tensordot(U, vv, axes=([1], [0]))          # [i][b][Q]
+        t = np.tensordot(t, V, axes=([1], [1]))           # [i][Q][j]
+        u = np.tensordot(oo, Minv, axes=([2], [0]))       # [i][j][Q]
+        return float(np.einsum("ijQ,iQj->", u, t))
 
     def _bk(self, U, V, ov1, ov2, Minv):
         """sum U_ia V_jb (ib|A) Minv_AB (B|ja)."""
-        t = np.einsum("ia,jaQ->ijQ", U, ov2)
-        t2 = np.einsum("jb,ibP->ijP", V, ov1)
-        return np.einsum("ijP,PQ,ijQ->", t2, Minv, t)
+        t = np.tensordot(U, ov2, axes=([1], [1]))         # [i][j][Q]  (sum_a U_ia (ja|Q))
+        t2 = np.tensordot(V, ov1, axes=([1], [1]))        # [j][i][P]  (sum_b V_jb (ib|P))
+        u = np.tensordot(t2, Minv, axes=([2], [0]))       # [j][i][Q]
+        return float(np.einsum("jiQ,ijQ->", u, t))
 
     def _kernel_ApB(self, U, V):
         return (4.0 * self._coul(U, V, self.ovJ, self.ovJ, self.MJinv)

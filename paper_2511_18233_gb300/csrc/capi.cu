@@ -1,0 +1,210 @@
+// extern "C" boundary of the TDDFT-ris engine (declared in include/ris.h).
+#include <string.h>
+
+#include <memory>
+
+#include "engine.cuh"
+
+struct ris_ctx {
+  ris::Engine eng;
+};
+
+namespace {
+
+template <class F>
+ris_status guarded(ris_ctx* ctx, F&& f) {
+  if (!ctx) return RIS_ERR_ARG;
+  try {
+    RIS_CUDA(cudaSetDevice(ctx->eng.device));
+    f();
+    ctx->eng.err.clear();
+    return RIS_OK;
+  } catch (const ris::Error& e) {
+    ctx->eng.err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    ctx->eng.err = e.what();
+    return RIS_ERR_ARG;
+  }
+}
+
+struct StageTimer {
+  ris::Engine& e;
+  int slot;
+  StageTimer(ris::Engine& e_, int s) : e(e_), slot(s) { RIS_CUDA(cudaEventRecord(e.ev0, e.st)); }
+  void stop() {
+    RIS_CUDA(cudaEventRecord(e.ev1, e.st));
+    RIS_CUDA(cudaEventSynchronize(e.ev1));
+    float ms = 0.f;
+    RIS_CUDA(cudaEventElapsedTime(&ms, e.ev0, e.ev1));
+    e.stats[slot] = ms;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+ris_status ris_options_default(ris_options* opt) {
+  if (!opt) return RIS_ERR_ARG;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = RIS_FP64;
+  opt->rpa = 0;
+  opt->cx = 0.25;
+  opt->conv_tol = 1e-10;
+  opt->max_iter = 100;
+  opt->max_subspace = 0;
+  opt->screen_thr = 1e-14;
+  opt->mem_budget = 0;
+  opt->occ_block = 0;
+  opt->cuda_stream = nullptr;
+  opt->device = 0;
+  return RIS_OK;
+}
+
+ris_status ris_create(ris_ctx** out, const ris_options* opt) {
+  if (!out) return RIS_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<ris_ctx> c(new (std::nothrow) ris_ctx());
+  if (!c) return RIS_ERR_OOM;
+  ris_options o;
+  ris_options_default(&o);
+  if (opt) o = *opt;
+  if (o.precision != RIS_FP64 && o.precision != RIS_MIXED) return RIS_ERR_ARG;
+  if (!(o.conv_tol > 0) || o.max_iter <= 0 || !(o.screen_thr >= 0)) return RIS_ERR_ARG;
+  c->eng.opt = o;
+  c->eng.device = o.device;
+  ris_status s = guarded(c.get(), [&] {
+    if (o.cuda_stream) {
+      c->eng.st = (cudaStream_t)o.cuda_stream;
+      c->eng.own_stream = false;
+    } else {
+      RIS_CUDA(cudaStreamCreateWithFlags(&c->eng.st, cudaStreamNonBlocking));
+      c->eng.own_stream = true;
+    }
+    RIS_CUDA(cudaEventCreate(&c->eng.ev0));
+    RIS_CUDA(cudaEventCreate(&c->eng.ev1));
+  });
+  if (s != RIS_OK) return s;
+  *out = c.release();
+  return RIS_OK;
+}
+
+ris_status ris_build_aux(ris_ctx* ctx, int natm, const double* coords, int nshell,
+                         const ris_shell* ao, int nJ, const ris_shell* auxJ, int nK,
+                         const ris_shell* auxK) {
+  return guarded(ctx, [&] {
+    StageTimer t(ctx->eng, 0);
+    ctx->eng.build_aux(natm, coords, nshell, ao, nJ, auxJ, nK, auxK);
+    t.stop();
+  });
+}
+
+ris_status ris_build_B(ris_ctx* ctx, int nao, int nmo, int nocc, const double* C,
+                       const double* mo_energy) {
+  return guarded(ctx, [&] {
+    StageTimer t(ctx->eng, 1);
+    ctx->eng.build_B(nao, nmo, nocc, C, mo_energy);
+    t.stop();
+  });
+}
+
+ris_status ris_excite(ris_ctx* ctx, int nstates, double* omega, double* X, double* Y) {
+  return guarded(ctx, [&] {
+    StageTimer t(ctx->eng, 2);
+    ctx->eng.excite(nstates, omega, X, Y);
+    t.stop();
+  });
+}
+
+ris_status ris_gradient(ris_ctx* ctx, int n, const int* states, int nx, const double* X_in,
+                        const double* Y_in, double* grad) {
+  return guarded(ctx, [&] {
+    ris::Engine& e = ctx->eng;
+    RIS_REQUIRE(n >= 1 && states && grad, RIS_ERR_ARG, "bad gradient arguments");
+    StageTimer t(e, 3);
+    std::vector<int> pairs(2 * n);
+    for (int k = 0; k < n; k++) pairs[2 * k] = pairs[2 * k + 1] = states[k];
+    ris::DBuf out;
+    out.ensure((size_t)n * e.natm * 3);
+    e.pair_derivs(n, pairs.data(), nx, X_in, Y_in, out.p);
+    RIS_CUDA(cudaMemcpyAsync(grad, out.p, sizeof(double) * n * e.natm * 3, cudaMemcpyDefault, e.st));
+    t.stop();
+  });
+}
+
+ris_status ris_nac(ris_ctx* ctx, int npair, const int* pairs, int nx, const double* X_in,
+                   const double* Y_in, const double* omega_in, double* nac, double* numerator) {
+  bool degenerate = false;
+  ris_status s = guarded(ctx, [&] {
+    ris::Engine& e = ctx->eng;
+    RIS_REQUIRE(npair >= 1 && pairs && nac, RIS_ERR_ARG, "bad coupling arguments");
+    std::vector<double> om;
+    if (X_in) {
+      RIS_REQUIRE(omega_in, RIS_ERR_ARG, "omega_in is required with X_in");
+      om.resize(nx);
+      RIS_CUDA(cudaMemcpy(om.data(), omega_in, sizeof(double) * nx, cudaMemcpyDefault));
+    } else {
+      RIS_REQUIRE(e.stage >= 3, RIS_ERR_STATE, "no amplitudes: call ris_excite or pass X_in");
+      om = e.h_omega;
+      nx = e.nstates;
+    }
+    std::vector<double> den(npair);
+    for (int g = 0; g < npair; g++) {
+      const int I = pairs[2 * g], J = pairs[2 * g + 1];
+      RIS_REQUIRE(I >= 0 && I < nx && J >= 0 && J < nx, RIS_ERR_ARG, "state index out of range");
+      den[g] = om[J] - om[I];
+      if (!(fabs(den[g]) >= 1e-8)) degenerate = true;
+    }
+    StageTimer t(e, 3);
+    const size_t per = (size_t)e.natm * 3;
+    ris::DBuf num, res, dd;
+    num.ensure(npair * per);
+    res.ensure(npair * per);
+    dd.ensure(npair);
+    e.pair_derivs(npair, pairs, nx, X_in, Y_in, num.p);
+    if (numerator)
+      RIS_CUDA(cudaMemcpyAsync(numerator, num.p, sizeof(double) * npair * per, cudaMemcpyDefault, e.st));
+    if (!degenerate) {
+      RIS_CUDA(cudaMemcpyAsync(dd.p, den.data(), sizeof(double) * npair, cudaMemcpyHostToDevice, e.st));
+      ris::divide_pairs(res.p, num.p, dd.p, npair, (int)per, e.st);
+      RIS_CUDA(cudaMemcpyAsync(nac, res.p, sizeof(double) * npair * per, cudaMemcpyDefault, e.st));
+    }
+    t.stop();
+  });
+  if (s == RIS_OK && degenerate) {
+    ctx->eng.err = "|omega_J - omega_I| < 1e-8 for a requested pair";
+    return RIS_ERR_DEGENERATE;
+  }
+  return s;
+}
+
+ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int* nauxJ,
+                        int* nauxK, int* npairs) {
+  if (!ctx) return RIS_ERR_ARG;
+  const ris::Engine& e = ctx->eng;
+  if (natm) *natm = e.natm;
+  if (nao) *nao = e.ao.nfun;
+  if (nocc) *nocc = e.nocc;
+  if (nauxJ) *nauxJ = e.nJ;
+  if (nauxK) *nauxK = e.nK;
+  if (npairs) *npairs = e.pl.npair;
+  return RIS_OK;
+}
+
+ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n) {
+  if (!ctx || !out || n < 0 || n > 16) return RIS_ERR_ARG;
+  for (int i = 0; i < n; i++) out[i] = ctx->eng.stats[i];
+  return RIS_OK;
+}
+
+const char* ris_last_error(const ris_ctx* ctx) { return ctx ? ctx->eng.err.c_str() : "null context"; }
+
+void ris_destroy(ris_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->eng.device);
+  if (ctx->eng.st) cudaStreamSynchronize(ctx->eng.st);
+  delete ctx;
+}
+
+}  // extern "C"

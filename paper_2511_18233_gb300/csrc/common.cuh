@@ -1,0 +1,46 @@
+// Common definitions for the TDDFT-ris sm_103a library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/ris.h"
+
+namespace ris {
+
+// Highest angular momenta handled by the integral kernels.
+constexpr int kMaxLAO = 2;   // AO shells up to d
+constexpr int kMaxLAux = 1;  // auxiliary shells up to p
+// Boys table: F_m(k*dT) for m <= kBoysM, k*dT <= kBoysTmax.
+constexpr int kBoysM = 16;
+constexpr double kBoysDT = 0.05;
+constexpr double kBoysTmax = 40.0;
+constexpr int kBoysNT = 801;  // kBoysTmax/kBoysDT + 1
+constexpr int kBoysTaylor = 8;
+
+struct Error {
+  ris_status code;
+  std::string msg;
+};
+
+#define RIS_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw ::ris::Error{RIS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define RIS_CHECK_LAUNCH() RIS_CUDA(cudaGetLastError())
+
+#define RIS_REQUIRE(cond, code, text)                    \
+  do {                                                   \
+    if (!(cond)) throw ::ris::Error{code, std::string(text)}; \
+  } while (0)
+
+__host__ __device__ inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace ris

@@ -1,0 +1,1029 @@
+// TDDFT-ris engine: basis setup, metric factorisation, B tensors, Davidson
+// excitation energies and the explicit nuclear derivatives of the ris pair
+// energies.
+//
+// Notation (closed-shell singlet; i,j occupied, a,b virtual, P,Q auxiliary):
+//   B^X_{pq,R} = sum_P (pq|P) (L_X^-T)_PR,  M_X = L_X L_X^T      (Eq. g_modified)
+//   c^X_{pq,P} = sum_R B^X_{pq,R} (L_X^-1)_RP = sum_Q (pq|Q)(M_X^-1)_QP
+//   (A X)_ia = (e_a - e_i) X_ia + 2 sum_R B^J_ia,R (B^J_R . X)
+//              - c_x sum_R sum_jb B^K_ij,R X_jb B^K_ab,R        (Eq. A_matrix)
+//   E_IJ = 1/2 [R_I (A+B) R_J + L_I (A-B) L_J], R = X+Y, L = X-Y  (Appendix A)
+// The derivative of E_IJ at fixed C, eps and amplitudes follows the RI
+// derivative formula closing Sec. 2.2:
+//   dE_IJ/dxi = sum (mu nu|P)^xi Gamma_{mu nu,P} - sum_PQ (P|Q)^xi Omega_PQ
+// with the three-index density Gamma of the pair, in the AO basis:
+//   Coulomb (J set):  Gamma = 2 (D_I c_J + D_J c_I),  D_s = C_o R_s C_v^T,
+//                     c_s = M_J^-1 (T^J . D_s),     Omega = 2 c_I c_J^T
+//   exchange (K set), for each (U,V) in {(R_I,R_J),(L_I,L_J)} with weight
+//   -c_x/2:  Gamma += C_o G^oo_P C_o^T + (U C_v^T)^T c^oo_P (V C_v^T),
+//            G^oo_P = U c^vv_P V^T,  Omega += sum_ij c^oo_ij,P G^oo_ij,Q
+//   and, for RPA, the (ib|ja) term with weights -c_x/2 (R,R) and +c_x/2 (L,L):
+//            Gamma += C_o (U c^ov_P^T V + V c^ov_P^T U) C_v^T,
+//            Omega += sum_ib c^ov_ib,P (U c^ov_Q^T V)_ib.
+// The bra derivative tensor D^x_{mu nu,P} = (d_x mu nu|P) is contracted with
+// the symmetrised Gamma; the auxiliary-centre and metric derivatives follow
+// from translational invariance.
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <set>
+
+#include "engine.cuh"
+
+namespace ris {
+
+void DBuf::ensure(size_t count) {
+  if (p && count <= n) return;
+  release();
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    n = 0;
+    throw Error{RIS_ERR_OOM, "device allocation of " + std::to_string(count * 8) + " bytes failed"};
+  }
+  n = count;
+}
+void DBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  n = 0;
+}
+
+static void free_shells(ShellSet& s) {
+  int** ip[] = {&s.atom, &s.l, &s.off, &s.jmap, &s.kmap, &s.fun_atom, &s.d_by_l[0], &s.d_by_l[1]};
+  for (auto q : ip)
+    if (*q) {
+      cudaFree(*q);
+      *q = nullptr;
+    }
+  double** dp[] = {&s.ex, &s.nbase};
+  for (auto q : dp)
+    if (*q) {
+      cudaFree(*q);
+      *q = nullptr;
+    }
+}
+
+Engine::~Engine() {
+  free_shells(ao);
+  free_shells(aux);
+  free_pairs(pl);
+  if (d_jU) cudaFree(d_jU);
+  if (d_kU) cudaFree(d_kU);
+  if (d_info) cudaFree(d_info);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (own_stream && st) cudaStreamDestroy(st);
+}
+
+template <class T>
+static T* upload(const std::vector<T>& v, cudaStream_t st) {
+  T* d = nullptr;
+  RIS_CUDA(cudaMalloc(&d, sizeof(T) * std::max<size_t>(v.size(), 1)));
+  if (!v.empty())
+    RIS_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  return d;
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy n doubles from a user pointer (host or device) into device memory.
+static void copy_in(double* dst, const double* src, size_t n, cudaStream_t st) {
+  RIS_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                           is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           st));
+}
+static void copy_out(double* dst, const double* src, size_t n, cudaStream_t st) {
+  RIS_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                           is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           st));
+}
+
+static void make_shells(ShellSet& s, const std::vector<int>& atom, const std::vector<int>& l,
+                        const std::vector<double>& ex, const std::vector<int>* jmap,
+                        const std::vector<int>* kmap, cudaStream_t st) {
+  free_shells(s);
+  s.n = (int)atom.size();
+  s.h_atom = atom;
+  s.h_l = l;
+  s.h_ex = ex;
+  s.h_off.assign(s.n, 0);
+  std::vector<double> nb(s.n);
+  std::vector<int> fa;
+  int o = 0;
+  for (int i = 0; i < s.n; i++) {
+    s.h_off[i] = o;
+    o += ncart(l[i]);
+    for (int c = 0; c < ncart(l[i]); c++) fa.push_back(atom[i]);
+    nb[i] = pow(2.0 * ex[i] / M_PI, 0.75) * pow(4.0 * ex[i], 0.5 * l[i]);
+  }
+  s.nfun = o;
+  s.atom = upload(atom, st);
+  s.l = upload(l, st);
+  s.off = upload(s.h_off, st);
+  s.ex = upload(ex, st);
+  s.nbase = upload(nb, st);
+  s.fun_atom = upload(fa, st);
+  if (jmap) {
+    s.h_jmap = *jmap;
+    s.jmap = upload(*jmap, st);
+  }
+  if (kmap) {
+    s.h_kmap = *kmap;
+    s.kmap = upload(*kmap, st);
+  }
+  for (int L = 0; L <= kMaxLAux; L++) {
+    s.by_l[L].clear();
+    for (int i = 0; i < s.n; i++)
+      if (l[i] == L) s.by_l[L].push_back(i);
+    s.d_by_l[L] = upload(s.by_l[L], st);
+  }
+}
+
+// ------------------------------------------------------------------ small kernels
+__global__ void k_gather_sq(const double* __restrict__ src, int lds, const int* __restrict__ map,
+                            int n, double* __restrict__ dst) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int i = t / n, j = t % n;
+  dst[t] = src[(size_t)map[i] * lds + map[j]];
+}
+
+__global__ void k_orb_diff(const double* __restrict__ eps, int nocc, int nvir, double* __restrict__ de) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nocc * nvir) return;
+  de[t] = eps[nocc + t % nvir] - eps[t / nvir];
+}
+
+// out[b][R][a] = in[b][a][R]  (per b: transpose of an nvir x nR block)
+__global__ void k_transpose_last2(const double* __restrict__ in, int nb, int na, int nr,
+                                  double* __restrict__ out) {
+  __shared__ double tile[32][33];
+  const int b = blockIdx.z;
+  const int a0 = blockIdx.y * 32, r0 = blockIdx.x * 32;
+  const double* src = in + (size_t)b * na * nr;
+  double* dst = out + (size_t)b * na * nr;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int a = a0 + k, r = r0 + threadIdx.x;
+    tile[k][threadIdx.x] = (a < na && r < nr) ? src[(size_t)a * nr + r] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = r0 + k, a = a0 + threadIdx.x;
+    if (r < nr && a < na) dst[(size_t)r * na + a] = tile[threadIdx.x][k];
+  }
+}
+static void transpose_last2(const double* in, int nb, int na, int nr, double* out, cudaStream_t st) {
+  dim3 g(cdiv(nr, 32), cdiv(na, 32), nb);
+  k_transpose_last2<<<g, dim3(32, 8), 0, st>>>(in, nb, na, nr, out);
+  RIS_CHECK_LAUNCH();
+}
+
+__global__ void k_add_diag(const double* __restrict__ de, const double* __restrict__ X, long long nov,
+                           int nvec, double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nov * nvec) return;
+  out[t] += de[t % nov] * X[t];
+}
+
+// indices of the k smallest de (ties: smaller index first), one CTA
+__global__ void __launch_bounds__(1024) k_lowest(const double* __restrict__ de, int n, int k,
+                                                 int* __restrict__ idx) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  __shared__ double lastv;
+  __shared__ int lasti;
+  if (threadIdx.x == 0) {
+    lastv = -1e308;
+    lasti = -1;
+  }
+  __syncthreads();
+  for (int r = 0; r < k; r++) {
+    double best = 1e308;
+    int besti = 0x7fffffff;
+    const double lv = lastv;
+    const int li = lasti;
+    for (int i = threadIdx.x; i < n; i += 1024) {
+      const double v = de[i];
+      const bool after = (v > lv) || (v == lv && i > li);
+      if (after && (v < best || (v == best && i < besti))) {
+        best = v;
+        besti = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, besti, o);
+      if (ov < best || (ov == best && oi < besti)) {
+        best = ov;
+        besti = oi;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      bv[threadIdx.x >> 5] = best;
+      bi[threadIdx.x >> 5] = besti;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      best = bv[threadIdx.x];
+      besti = bi[threadIdx.x];
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, besti, o);
+        if (ov < best || (ov == best && oi < besti)) {
+          best = ov;
+          besti = oi;
+        }
+      }
+      if (threadIdx.x == 0) {
+        idx[r] = besti;
+        lastv = best;
+        lasti = besti;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_unit_rows(const int* __restrict__ idx, int k, long long n, double* __restrict__ V) {
+  const int r = blockIdx.x;
+  if (r >= k) return;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) V[(size_t)r * n + i] = (i == idx[r]) ? 1.0 : 0.0;
+}
+
+// R[k] = AX[k] - w[k] X[k]
+__global__ void k_residual(const double* __restrict__ AX, const double* __restrict__ X,
+                           const double* __restrict__ w, long long n, int ns, double* __restrict__ R) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ns) return;
+  R[t] = AX[t] - w[t / n] * X[t];
+}
+
+// T[j] = R[u_j] / (de - w[u_j]), |denominator| floored at 1e-8
+__global__ void k_precond(const double* __restrict__ R, const double* __restrict__ de,
+                          const double* __restrict__ w, const int* __restrict__ u, long long n, int nt,
+                          double* __restrict__ T) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nt) return;
+  const int j = (int)(t / n);
+  const long long i = t % n;
+  const int s = u[j];
+  double den = de[i] - w[s];
+  if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+  T[t] = R[(size_t)s * n + i] / den;
+}
+
+__global__ void k_scale_rows(double* __restrict__ X, long long n, int nrow, const double* __restrict__ nrm2) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nrow) return;
+  const double s = nrm2[t / n];
+  X[t] *= s > 0 ? 1.0 / sqrt(s) : 0.0;
+}
+
+// Cholesky of the Gram matrix G (nt x nt, unit diagonal expected) with
+// dropping of (near-)dependent rows; P[i][c] such that the kept rows
+// Tnew_i = sum_c P[i][c] T_c are orthonormal.  *nkeep = number kept.
+__global__ void k_cholqr_small(const double* __restrict__ G, int nt, double drop, double* __restrict__ P,
+                               int* __restrict__ nkeep, double* __restrict__ work) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* R = work;        // nt x nt upper factor over kept columns
+  int* keep = (int*)(work + nt * nt);
+  int r = 0;
+  for (int j = 0; j < nt; j++) {
+    // R[i][j] for kept i
+    double d = G[j * nt + j];
+    for (int q = 0; q < r; q++) {
+      const int i = keep[q];
+      double s = G[i * nt + j];
+      for (int q2 = 0; q2 < q; q2++) s -= R[keep[q2] * nt + i] * R[keep[q2] * nt + j];
+      R[i * nt + j] = s / R[i * nt + i];
+      d -= R[i * nt + j] * R[i * nt + j];
+    }
+    if (d > drop * G[j * nt + j] && d > 0) {
+      R[j * nt + j] = sqrt(d);
+      keep[r++] = j;
+    }
+  }
+  // P = R^{-T} restricted to kept: row q of P gives Tnew_q
+  for (int i = 0; i < nt * nt; i++) P[i] = 0.0;
+  for (int q = 0; q < r; q++) {
+    // solve R^T y = e_q over kept indices (forward substitution)
+    double y[64];
+    for (int s = 0; s < r; s++) {
+      double acc = (s == q) ? 1.0 : 0.0;
+      for (int s2 = 0; s2 < s; s2++) acc -= R[keep[s2] * nt + keep[s]] * y[s2];
+      y[s] = acc / R[keep[s] * nt + keep[s]];
+    }
+    for (int s = 0; s < r; s++) P[q * nt + keep[s]] = y[s];
+  }
+  *nkeep = r;
+}
+
+__global__ void k_diag_set(double* __restrict__ H, int ld, int m, const double* __restrict__ w) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  const int i = t / m, j = t % m;
+  H[(size_t)i * ld + j] = i == j ? w[i] : 0.0;
+}
+
+__global__ void k_mirror(double* __restrict__ H, int ld, int m0, int m1) {
+  // for i in [m0, m1), j in [0, m0): H[j][i] = H[i][j]
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (m1 - m0) * m0) return;
+  const int i = m0 + t / m0, j = t % m0;
+  H[(size_t)j * ld + i] = H[(size_t)i * ld + j];
+}
+
+// Sign of each row so that its largest-magnitude element is positive
+// (ties: smallest index); the same sign is applied to Y when given.
+__global__ void k_phase(double* __restrict__ X, double* __restrict__ Y, long long n) {
+  __shared__ double bv[32];
+  __shared__ long long bi[32];
+  __shared__ double sgn;
+  double* x = X + (size_t)blockIdx.x * n;
+  double best = -1.0;
+  long long besti = 0x7fffffffffffffffLL;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = fabs(x[i]);
+    if (v > best || (v == best && i < besti)) {
+      best = v;
+      besti = i;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const long long oi = __shfl_xor_sync(0xffffffffu, besti, o);
+    if (ov > best || (ov == best && oi < besti)) {
+      best = ov;
+      besti = oi;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    bv[threadIdx.x >> 5] = best;
+    bi[threadIdx.x >> 5] = besti;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+      if (bv[w] > bv[0] || (bv[w] == bv[0] && bi[w] < bi[0])) {
+        bv[0] = bv[w];
+        bi[0] = bi[w];
+      }
+    sgn = x[bi[0]] < 0 ? -1.0 : 1.0;
+  }
+  __syncthreads();
+  if (sgn < 0) {
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+      x[i] = -x[i];
+      if (Y) Y[(size_t)blockIdx.x * n + i] = -Y[(size_t)blockIdx.x * n + i];
+    }
+  }
+}
+
+__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ y, double* __restrict__ z) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) z[t] = a * x[t] + (y ? b * y[t] : 0.0);
+}
+static void axpby(long long n, double a, const double* x, double b, const double* y, double* z,
+                  cudaStream_t st) {
+  if (n <= 0) return;
+  k_axpby<<<cdiv(n, 256), 256, 0, st>>>(n, a, x, b, y, z);
+  RIS_CHECK_LAUNCH();
+}
+
+// Gamma[mu][nu][jU[P]] += f (DI[mu][nu] cJ[P] + DJ[mu][nu] cI[P])
+__global__ void k_gamma_J(const double* __restrict__ DI, const double* __restrict__ DJ,
+                          const double* __restrict__ cI, const double* __restrict__ cJ,
+                          const int* __restrict__ jU, int nao, int nJ, int nU, double f,
+                          double* __restrict__ G) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nao * nao * nJ) return;
+  const int P = (int)(t % nJ);
+  const long long mn = t / nJ;
+  G[mn * nU + jU[P]] += f * (DI[mn] * cJ[P] + DJ[mn] * cI[P]);
+}
+
+// Omega[jU[P]][jU[Q]] = f cI[P] cJ[Q]   (whole matrix zeroed first by caller)
+__global__ void k_omega_J(const double* __restrict__ cI, const double* __restrict__ cJ,
+                          const int* __restrict__ jU, int nJ, int nU, double f, double* __restrict__ O) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nJ * nJ) return;
+  const int P = t / nJ, Q = t % nJ;
+  O[(size_t)jU[P] * nU + jU[Q]] += f * cI[P] * cJ[Q];
+}
+
+// W_V[nu][k] = C_o[nu][k] (k < o), Q[k-o][nu] (k >= o)
+__global__ void k_build_W(const double* __restrict__ C, int nmo, const double* __restrict__ Q,
+                          int nao, int nocc, double* __restrict__ W) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nao * 2 * nocc) return;
+  const int nu = t / (2 * nocc), k = t % (2 * nocc);
+  W[t] = k < nocc ? C[(size_t)nu * nmo + k] : Q[(size_t)(k - nocc) * nao + nu];
+}
+
+// W[x][mu][P] = sum_nu D[x][mu][nu][P] * (G[mu][nu][P] + G[nu][mu][P]) / 2
+__global__ void __launch_bounds__(128) k_contract(const double* __restrict__ D,
+                                                  const double* __restrict__ G, int nao, int nU,
+                                                  double* __restrict__ W) {
+  const int mu = blockIdx.x;
+  const size_t plane = (size_t)nao * nao * nU;
+  for (int P = threadIdx.x; P < nU; P += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int nu = 0; nu < nao; nu++) {
+      const size_t a = ((size_t)mu * nao + nu) * nU + P;
+      const size_t b = ((size_t)nu * nao + mu) * nU + P;
+      const double g = 0.5 * (G[a] + G[b]);
+      s0 += D[a] * g;
+      s1 += D[plane + a] * g;
+      s2 += D[2 * plane + a] * g;
+    }
+    W[((size_t)0 * nao + mu) * nU + P] = s0;
+    W[((size_t)1 * nao + mu) * nU + P] = s1;
+    W[((size_t)2 * nao + mu) * nU + P] = s2;
+  }
+}
+
+// grad[A][x] = 2 sum_{mu in A, P} W - 2 sum_{P in A, mu} W
+//              - sum_{P in A, Q} (O[P][Q] + O[Q][P]) dM[x][P][Q]
+__global__ void __launch_bounds__(128) k_grad_reduce(const double* __restrict__ W,
+                                                     const double* __restrict__ O,
+                                                     const double* __restrict__ dM,
+                                                     const int* __restrict__ ao_atom,
+                                                     const int* __restrict__ ax_atom, int nao,
+                                                     int nU, double* __restrict__ grad) {
+  __shared__ double red[3][128];
+  const int A = blockIdx.x;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (long long t = threadIdx.x; t < (long long)nao * nU; t += 128) {
+    const int mu = (int)(t / nU), P = (int)(t % nU);
+    const double f = (ao_atom[mu] == A ? 2.0 : 0.0) - (ax_atom[P] == A ? 2.0 : 0.0);
+    if (f != 0.0)
+      for (int x = 0; x < 3; x++) s[x] += f * W[((size_t)x * nao + mu) * nU + P];
+  }
+  for (long long t = threadIdx.x; t < (long long)nU * nU; t += 128) {
+    const int P = (int)(t / nU), Q = (int)(t % nU);
+    if (ax_atom[P] != A) continue;
+    const double o = O[(size_t)P * nU + Q] + O[(size_t)Q * nU + P];
+    for (int x = 0; x < 3; x++) s[x] -= o * dM[(size_t)x * nU * nU + t];
+  }
+  for (int x = 0; x < 3; x++) red[x][threadIdx.x] = s[x];
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int x = 0; x < 3; x++) red[x][threadIdx.x] += red[x][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) grad[A * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_divide_pairs(double* __restrict__ out, const double* __restrict__ num,
+                               const double* __restrict__ den, int npair, int per) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npair * per) return;
+  out[t] = num[t] / den[t / per];
+}
+
+void divide_pairs(double* out, const double* num, const double* den, int npair, int per,
+                  cudaStream_t st) {
+  k_divide_pairs<<<cdiv((long long)npair * per, 256), 256, 0, st>>>(out, num, den, npair, per);
+  RIS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ setup
+void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_shell* aos, int nJs,
+                       const ris_shell* auxJ, int nKs, const ris_shell* auxK) {
+  RIS_REQUIRE(natm_ > 0 && nshell > 0 && nJs > 0 && nKs > 0, RIS_ERR_ARG, "empty input");
+  RIS_REQUIRE(coords && aos && auxJ && auxK, RIS_ERR_ARG, "null pointer");
+  std::vector<double> hxyz(3 * (size_t)natm_);
+  RIS_CUDA(cudaMemcpy(hxyz.data(), coords, sizeof(double) * 3 * natm_, cudaMemcpyDefault));
+  for (double v : hxyz) RIS_REQUIRE(std::isfinite(v), RIS_ERR_ARG, "non-finite coordinate");
+  auto check = [&](const ris_shell* s, int n, int lmax, const char* what) {
+    for (int i = 0; i < n; i++) {
+      RIS_REQUIRE(s[i].atom >= 0 && s[i].atom < natm_, RIS_ERR_ARG,
+                  std::string(what) + ": atom index out of range");
+      RIS_REQUIRE(s[i].l >= 0 && s[i].l <= lmax, RIS_ERR_ARG,
+                  std::string(what) + ": angular momentum out of range");
+      RIS_REQUIRE(s[i].exponent > 0 && std::isfinite(s[i].exponent), RIS_ERR_ARG,
+                  std::string(what) + ": bad exponent");
+    }
+  };
+  check(aos, nshell, kMaxLAO, "AO shell");
+  check(auxJ, nJs, kMaxLAux, "J auxiliary shell");
+  check(auxK, nKs, kMaxLAux, "K auxiliary shell");
+  stage = 0;
+  have_D = false;
+  natm = natm_;
+  xyz.ensure(3 * (size_t)natm);
+  RIS_CUDA(cudaMemcpyAsync(xyz.p, hxyz.data(), sizeof(double) * 3 * natm, cudaMemcpyHostToDevice, st));
+  // AO shells
+  {
+    std::vector<int> a(nshell), l(nshell);
+    std::vector<double> e(nshell);
+    for (int i = 0; i < nshell; i++) {
+      a[i] = aos[i].atom;
+      l[i] = aos[i].l;
+      e[i] = aos[i].exponent;
+    }
+    make_shells(ao, a, l, e, nullptr, nullptr, st);
+  }
+  // union auxiliary set: K shells first, then J shells not already present
+  {
+    std::vector<int> a, l, jm, km;
+    std::vector<double> e;
+    std::vector<int> joff(nJs), koff(nKs);
+    int o = 0;
+    for (int i = 0; i < nJs; i++) {
+      joff[i] = o;
+      o += ncart(auxJ[i].l);
+    }
+    nJ = o;
+    o = 0;
+    for (int i = 0; i < nKs; i++) {
+      koff[i] = o;
+      o += ncart(auxK[i].l);
+    }
+    nK = o;
+    auto same = [](const ris_shell& x, const ris_shell& y) {
+      return x.atom == y.atom && x.l == y.l && x.exponent == y.exponent;
+    };
+    std::vector<bool> used(nJs, false);
+    for (int i = 0; i < nKs; i++) {
+      a.push_back(auxK[i].atom);
+      l.push_back(auxK[i].l);
+      e.push_back(auxK[i].exponent);
+      km.push_back(koff[i]);
+      int jj = -1;
+      for (int j = 0; j < nJs; j++)
+        if (!used[j] && same(auxJ[j], auxK[i])) {
+          jj = j;
+          break;
+        }
+      if (jj >= 0) used[jj] = true;
+      jm.push_back(jj >= 0 ? joff[jj] : -1);
+    }
+    for (int j = 0; j < nJs; j++)
+      if (!used[j]) {
+        a.push_back(auxJ[j].atom);
+        l.push_back(auxJ[j].l);
+        e.push_back(auxJ[j].exponent);
+        jm.push_back(joff[j]);
+        km.push_back(-1);
+      }
+    make_shells(aux, a, l, e, &jm, &km, st);
+    nU = aux.nfun;
+    h_jU.assign(nJ, -1);
+    h_kU.assign(nK, -1);
+    for (int s = 0; s < aux.n; s++)
+      for (int c = 0; c < ncart(l[s]); c++) {
+        if (jm[s] >= 0) h_jU[jm[s] + c] = aux.h_off[s] + c;
+        if (km[s] >= 0) h_kU[km[s] + c] = aux.h_off[s] + c;
+      }
+    if (d_jU) cudaFree(d_jU);
+    if (d_kU) cudaFree(d_kU);
+    d_jU = upload(h_jU, st);
+    d_kU = upload(h_kU, st);
+  }
+  // screened pair list; the estimate is scaled by the largest auxiliary
+  // potential |V_P| <= N_P 2 pi / g (times g^-1/2 for p)
+  double vmax = 0.0;
+  for (int s = 0; s < aux.n; s++) {
+    const double g = aux.h_ex[s];
+    const double nb = pow(2.0 * g / M_PI, 0.75) * pow(4.0 * g, 0.5 * aux.h_l[s]);
+    vmax = std::max(vmax, nb * 2.0 * M_PI / g * (aux.h_l[s] ? 1.0 / sqrt(g) : 1.0));
+  }
+  build_pairs(ao, xyz.p, opt.screen_thr / std::max(vmax, 1e-300), pl, nullptr, st);
+  // integrals
+  const int nao_ = ao.nfun;
+  TJ.ensure((size_t)nao_ * nao_ * nJ);
+  TK.ensure((size_t)nao_ * nao_ * nK);
+  RIS_CUDA(cudaMemsetAsync(TJ.p, 0, sizeof(double) * (size_t)nao_ * nao_ * nJ, st));
+  RIS_CUDA(cudaMemsetAsync(TK.p, 0, sizeof(double) * (size_t)nao_ * nao_ * nK, st));
+  int3c(ao, aux, pl, xyz.p, nJ, nK, TJ.p, TK.p, st);
+  MU.ensure((size_t)nU * nU);
+  dMU.ensure(3 * (size_t)nU * nU);
+  int2c(aux, xyz.p, MU.p, dMU.p, st);
+  // metric factors
+  if (!d_info) RIS_CUDA(cudaMalloc(&d_info, sizeof(int) * 2));
+  LJinv.ensure((size_t)nJ * nJ);
+  LKinv.ensure((size_t)nK * nK);
+  w1.ensure((size_t)std::max(nJ, nK) * std::max(nJ, nK));
+  for (int set = 0; set < 2; set++) {
+    const int n = set == 0 ? nJ : nK;
+    const int* map = set == 0 ? d_jU : d_kU;
+    k_gather_sq<<<cdiv(n * n, 256), 256, 0, st>>>(MU.p, nU, map, n, w1.p);
+    RIS_CHECK_LAUNCH();
+    cholesky(w1.p, n, d_info + set, st);
+    tri_inverse(w1.p, set == 0 ? LJinv.p : LKinv.p, n, st);
+  }
+  int info[2];
+  RIS_CUDA(cudaMemcpyAsync(info, d_info, sizeof(info), cudaMemcpyDeviceToHost, st));
+  RIS_CUDA(cudaStreamSynchronize(st));
+  RIS_REQUIRE(info[0] == 0 && info[1] == 0, RIS_ERR_METRIC_NOT_PD,
+              "auxiliary metric is not positive definite (pivot " +
+                  std::to_string(info[0] ? info[0] : info[1]) + ")");
+  nao = nao_;
+  stage = 1;
+}
+
+void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const double* eps_in) {
+  RIS_REQUIRE(stage >= 1, RIS_ERR_STATE, "ris_build_B before ris_build_aux");
+  RIS_REQUIRE(nao_ == ao.nfun, RIS_ERR_ARG, "nao does not match the AO basis");
+  RIS_REQUIRE(nmo_ == nao_, RIS_ERR_ARG, "nmo must equal nao");
+  RIS_REQUIRE(nocc_ > 0 && nocc_ < nmo_, RIS_ERR_ARG, "need 0 < nocc < nmo");
+  RIS_REQUIRE(Cin && eps_in, RIS_ERR_ARG, "null pointer");
+  stage = 1;
+  nmo = nmo_;
+  nocc = nocc_;
+  nvir = nmo - nocc;
+  const int o = nocc, v = nvir, n = nao;
+  const long long nov = (long long)o * v;
+  C.ensure((size_t)n * nmo);
+  eps.ensure(nmo);
+  de.ensure(nov);
+  copy_in(C.p, Cin, (size_t)n * nmo, st);
+  copy_in(eps.p, eps_in, nmo, st);
+  k_orb_diff<<<cdiv(nov, 256), 256, 0, st>>>(eps.p, o, v, de.p);
+  RIS_CHECK_LAUNCH();
+  const double* Co = C.p;
+  const double* Cv = C.p + o;
+  // Coulomb: H[i][nu][P] = sum_mu C_mu,i T[mu][nu][P]; B[i][a][P]; B L^-T
+  w2.ensure((size_t)o * n * std::max(nJ, nK));
+  dgemm(true, false, o, n * nJ, n, 1.0, Co, nmo, TJ.p, n * nJ, 0.0, w2.p, n * nJ, st);
+  w3.ensure((size_t)nov * std::max(nJ, nK));
+  {
+    GemmBatch bt;
+    bt.nb1 = o;
+    bt.sB1 = (long long)n * nJ;
+    bt.sC1 = (long long)v * nJ;
+    dgemm(true, false, v, nJ, n, 1.0, Cv, nmo, w2.p, nJ, 0.0, w3.p, nJ, st, bt);
+  }
+  BJ.ensure((size_t)nov * nJ);
+  dgemm(false, true, (int)nov, nJ, nJ, 1.0, w3.p, nJ, LJinv.p, nJ, 0.0, BJ.p, nJ, st);
+  // exchange: oo and ov from C_o^T T^K, vv from C_v^T T^K
+  dgemm(true, false, o, n * nK, n, 1.0, Co, nmo, TK.p, n * nK, 0.0, w2.p, n * nK, st);
+  {
+    GemmBatch bt;
+    bt.nb1 = o;
+    bt.sB1 = (long long)n * nK;
+    bt.sC1 = (long long)o * nK;
+    dgemm(true, false, o, nK, n, 1.0, Co, nmo, w2.p, nK, 0.0, w3.p, nK, st, bt);
+  }
+  BKoo.ensure((size_t)o * o * nK);
+  dgemm(false, true, o * o, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, BKoo.p, nK, st);
+  cKoo.ensure((size_t)o * o * nK);
+  dgemm(false, false, o * o, nK, nK, 1.0, BKoo.p, nK, LKinv.p, nK, 0.0, cKoo.p, nK, st);
+  if (opt.rpa) {
+    GemmBatch bt;
+    bt.nb1 = o;
+    bt.sB1 = (long long)n * nK;
+    bt.sC1 = (long long)v * nK;
+    dgemm(true, false, v, nK, n, 1.0, Cv, nmo, w2.p, nK, 0.0, w3.p, nK, st, bt);
+    w4.ensure((size_t)nov * nK);
+    dgemm(false, true, (int)nov, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // [i][a][R]
+    cKov.ensure((size_t)nov * nK);
+    dgemm(false, false, (int)nov, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKov.p, nK, st);
+    BKovR.ensure((size_t)nov * nK);
+    transpose_last2(w4.p, 1, (int)nov, nK, BKovR.p, st);  // [R][ia]
+  }
+  w2.ensure((size_t)v * n * nK);
+  dgemm(true, false, v, n * nK, n, 1.0, Cv, nmo, TK.p, n * nK, 0.0, w2.p, n * nK, st);
+  w3.ensure((size_t)v * v * nK);
+  {
+    GemmBatch bt;
+    bt.nb1 = v;
+    bt.sB1 = (long long)n * nK;
+    bt.sC1 = (long long)v * nK;
+    dgemm(true, false, v, nK, n, 1.0, Cv, nmo, w2.p, nK, 0.0, w3.p, nK, st, bt);
+  }
+  w4.ensure((size_t)v * v * nK);
+  dgemm(false, true, v * v, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // B[a][b][R]
+  cKvv.ensure((size_t)v * v * nK);
+  dgemm(false, false, v * v, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKvv.p, nK, st);
+  BKvvD.ensure((size_t)v * v * nK);
+  transpose_last2(w4.p, v, v, nK, BKvvD.p, st);  // [b][R][a]
+  stage = 2;
+}
+
+// ------------------------------------------------------------------ A products
+// out[n] = A X[n] for TDA (Eq. A_matrix with the ris kernel)
+void Engine::apply_A_tda(const double* Xin, int nvec, double* out) {
+  const int o = nocc, v = nvir;
+  const long long nov = (long long)o * v;
+  w5.ensure((size_t)nvec * std::max(nJ, 1));
+  dgemm(false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
+  dgemm(false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
+  w6.ensure((size_t)nvec * o * nK * v);
+  {
+    GemmBatch bt;
+    bt.nb1 = nvec;
+    bt.sA1 = nov;
+    bt.sC1 = (long long)o * nK * v;
+    dgemm(false, false, o, nK * v, v, 1.0, Xin, v, BKvvD.p, nK * v, 0.0, w6.p, nK * v, st, bt);
+  }
+  {
+    GemmBatch bt;
+    bt.nb1 = nvec;
+    bt.sB1 = (long long)o * nK * v;
+    bt.sC1 = nov;
+    dgemm(false, false, o, v, o * nK, -opt.cx, BKoo.p, o * nK, w6.p, v, 1.0, out, v, st, bt);
+  }
+  k_add_diag<<<cdiv(nov * nvec, 256), 256, 0, st>>>(de.p, Xin, nov, nvec, out);
+  RIS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ Davidson (TDA)
+void Engine::davidson_tda(int ns) {
+  const long long n = (long long)nocc * nvir;
+  const int nb0 = (int)std::min<long long>(n, ns + std::min(ns, 8));
+  int maxsp = opt.max_subspace > 0 ? opt.max_subspace : std::max(nb0 + 2 * ns, 8 * ns);
+  maxsp = (int)std::min<long long>(std::min(maxsp, 256), n);
+  RIS_REQUIRE(maxsp >= nb0, RIS_ERR_ARG, "max_subspace smaller than the initial block");
+  const int kkeep = std::min(2 * ns, 64);
+  DBuf V, AV, Hs, S, w, Xr, AXr, Rr, T, Cc, G, Pm, ework, tmp;
+  V.ensure((size_t)maxsp * n);
+  AV.ensure((size_t)maxsp * n);
+  Hs.ensure((size_t)maxsp * maxsp);
+  S.ensure((size_t)64 * maxsp);
+  w.ensure(64);
+  Xr.ensure((size_t)ns * n);
+  AXr.ensure((size_t)ns * n);
+  Rr.ensure((size_t)ns * n);
+  T.ensure((size_t)ns * n);
+  tmp.ensure((size_t)std::max(ns, kkeep) * n);
+  Cc.ensure((size_t)ns * maxsp);
+  G.ensure((size_t)ns * ns);
+  Pm.ensure((size_t)ns * ns + 64);
+  ework.ensure(eig_work_size(maxsp));
+  int* d_idx = nullptr;
+  RIS_CUDA(cudaMalloc(&d_idx, sizeof(int) * (std::max(nb0, ns) + 8)));
+  struct Guard {
+    int* p;
+    ~Guard() { cudaFree(p); }
+  } guard{d_idx};
+  k_lowest<<<1, 1024, 0, st>>>(de.p, (int)n, nb0, d_idx);
+  RIS_CHECK_LAUNCH();
+  k_unit_rows<<<nb0, 256, 0, st>>>(d_idx, nb0, n, V.p);
+  RIS_CHECK_LAUNCH();
+  apply_A_tda(V.p, nb0, AV.p);
+  int nprod = nb0;
+  int m = nb0;
+  dgemm(false, true, m, m, (int)n, 1.0, V.p, (int)n, AV.p, (int)n, 0.0, Hs.p, maxsp, st);
+  std::vector<double> rn(ns);
+  bool converged = false;
+  int it = 0;
+  const double drop = 1e-10;
+  for (it = 0; it < opt.max_iter; it++) {
+    const int nk = std::min(m, std::max(ns, kkeep));
+    sym_eig_lowest(Hs.p, maxsp, m, nk, w.p, S.p, ework.p, st);
+    dgemm(false, false, ns, (int)n, m, 1.0, S.p, m, V.p, (int)n, 0.0, Xr.p, (int)n, st);
+    dgemm(false, false, ns, (int)n, m, 1.0, S.p, m, AV.p, (int)n, 0.0, AXr.p, (int)n, st);
+    k_residual<<<cdiv(n * ns, 256), 256, 0, st>>>(AXr.p, Xr.p, w.p, n, ns, Rr.p);
+    RIS_CHECK_LAUNCH();
+    row_norms(Rr.p, ns, n, G.p, st);
+    RIS_CUDA(cudaMemcpyAsync(rn.data(), G.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> u;
+    for (int k = 0; k < ns; k++)
+      if (!(sqrt(rn[k]) <= opt.conv_tol)) u.push_back(k);
+    if (u.empty()) {
+      converged = true;
+      break;
+    }
+    int nt = (int)u.size();
+    RIS_CUDA(cudaMemcpyAsync(d_idx, u.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
+    k_precond<<<cdiv(n * nt, 256), 256, 0, st>>>(Rr.p, de.p, w.p, d_idx, n, nt, T.p);
+    RIS_CHECK_LAUNCH();
+    if (m + nt > maxsp) {  // restart with the lowest Ritz vectors
+      const int keep = std::min(nk, maxsp - nt);
+      dgemm(false, false, keep, (int)n, m, 1.0, S.p, m, V.p, (int)n, 0.0, tmp.p, (int)n, st);
+      RIS_CUDA(cudaMemcpyAsync(V.p, tmp.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, st));
+      dgemm(false, false, keep, (int)n, m, 1.0, S.p, m, AV.p, (int)n, 0.0, tmp.p, (int)n, st);
+      RIS_CUDA(cudaMemcpyAsync(AV.p, tmp.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, st));
+      k_diag_set<<<cdiv(keep * keep, 256), 256, 0, st>>>(Hs.p, maxsp, keep, w.p);
+      RIS_CHECK_LAUNCH();
+      m = keep;
+    }
+    // two rounds of (project out V, orthonormalise within the block)
+    int nkeep = nt;
+    for (int pass = 0; pass < 2 && nkeep > 0; pass++) {
+      dgemm(false, true, nt, m, (int)n, 1.0, T.p, (int)n, V.p, (int)n, 0.0, Cc.p, m, st);
+      dgemm(false, false, nt, (int)n, m, -1.0, Cc.p, m, V.p, (int)n, 1.0, T.p, (int)n, st);
+      row_norms(T.p, nt, n, G.p, st);
+      k_scale_rows<<<cdiv(n * nt, 256), 256, 0, st>>>(T.p, n, nt, G.p);
+      RIS_CHECK_LAUNCH();
+      dgemm(false, true, nt, nt, (int)n, 1.0, T.p, (int)n, T.p, (int)n, 0.0, G.p, nt, st);
+      k_cholqr_small<<<1, 32, 0, st>>>(G.p, nt, drop, Pm.p, (int*)(Pm.p + nt * nt), Cc.p);
+      RIS_CHECK_LAUNCH();
+      RIS_CUDA(cudaMemcpyAsync(&nkeep, Pm.p + nt * nt, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RIS_CUDA(cudaStreamSynchronize(st));
+      if (nkeep == 0) break;
+      dgemm(false, false, nkeep, (int)n, nt, 1.0, Pm.p, nt, T.p, (int)n, 0.0, tmp.p, (int)n, st);
+      RIS_CUDA(cudaMemcpyAsync(T.p, tmp.p, sizeof(double) * nkeep * n, cudaMemcpyDeviceToDevice, st));
+      nt = nkeep;
+    }
+    if (nkeep == 0) break;
+    RIS_CUDA(cudaMemcpyAsync(V.p + (size_t)m * n, T.p, sizeof(double) * nt * n,
+                             cudaMemcpyDeviceToDevice, st));
+    apply_A_tda(T.p, nt, AV.p + (size_t)m * n);
+    nprod += nt;
+    dgemm(false, true, nt, m + nt, (int)n, 1.0, V.p + (size_t)m * n, (int)n, AV.p, (int)n, 0.0,
+          Hs.p + (size_t)m * maxsp, maxsp, st);
+    k_mirror<<<cdiv((long long)nt * m + 1, 256), 256, 0, st>>>(Hs.p, maxsp, m, m + nt);
+    RIS_CHECK_LAUNCH();
+    m += nt;
+  }
+  stats[4] = nprod;
+  stats[5] = it;
+  RIS_REQUIRE(converged, RIS_ERR_NOT_CONVERGED,
+              "Davidson did not converge in " + std::to_string(it) + " iterations");
+  k_phase<<<ns, 256, 0, st>>>(Xr.p, nullptr, n);
+  RIS_CHECK_LAUNCH();
+  nstates = ns;
+  omega.ensure(ns);
+  X.ensure((size_t)ns * n);
+  RIS_CUDA(cudaMemcpyAsync(omega.p, w.p, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
+  RIS_CUDA(cudaMemcpyAsync(X.p, Xr.p, sizeof(double) * ns * n, cudaMemcpyDeviceToDevice, st));
+}
+
+void Engine::excite(int ns, double* om, double* Xo, double* Yo) {
+  RIS_REQUIRE(stage >= 2, RIS_ERR_STATE, "ris_excite before ris_build_B");
+  const long long n = (long long)nocc * nvir;
+  RIS_REQUIRE(ns >= 1 && ns <= 32 && ns <= n, RIS_ERR_ARG, "nstates out of range (1..32)");
+  RIS_REQUIRE(om, RIS_ERR_ARG, "omega is NULL");
+  stage = 2;
+  if (opt.rpa)
+    davidson_rpa(ns);
+  else
+    davidson_tda(ns);
+  h_omega.resize(ns);
+  RIS_CUDA(cudaMemcpyAsync(h_omega.data(), omega.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+  copy_out(om, omega.p, ns, st);
+  if (Xo) copy_out(Xo, X.p, (size_t)ns * n, st);
+  if (Yo && opt.rpa) copy_out(Yo, Y.p, (size_t)ns * n, st);
+  RIS_CUDA(cudaStreamSynchronize(st));
+  stage = 3;
+}
+
+void Engine::davidson_rpa(int) {
+  throw Error{RIS_ERR_ARG, "RPA excitations are not available in this build"};
+}
+
+// ------------------------------------------------------------------ derivatives
+void Engine::ensure_D() {
+  if (have_D) return;
+  const size_t plane = (size_t)nao * nao * nU;
+  D.ensure(3 * plane);
+  RIS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * 3 * plane, st));
+  int3c_deriv(ao, aux, pl, xyz.p, D.p, st);
+  have_D = true;
+}
+
+void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in,
+                         const double* Y_in, double* out) {
+  RIS_REQUIRE(stage >= 2, RIS_ERR_STATE, "derivatives before ris_build_B");
+  RIS_REQUIRE(npair >= 1 && pairs, RIS_ERR_ARG, "no pairs");
+  const int o = nocc, v = nvir, nn = nao;
+  const long long nov = (long long)o * v;
+  const double* Xa;
+  const double* Ya = nullptr;
+  DBuf xin, yin;
+  if (X_in) {
+    RIS_REQUIRE(nx >= 1, RIS_ERR_ARG, "nx must be positive with X_in");
+    xin.ensure((size_t)nx * nov);
+    copy_in(xin.p, X_in, (size_t)nx * nov, st);
+    Xa = xin.p;
+    if (Y_in) {
+      yin.ensure((size_t)nx * nov);
+      copy_in(yin.p, Y_in, (size_t)nx * nov, st);
+      Ya = yin.p;
+    }
+  } else {
+    RIS_REQUIRE(stage >= 3, RIS_ERR_STATE, "no amplitudes: call ris_excite or pass X_in");
+    nx = nstates;
+    Xa = X.p;
+    if (opt.rpa) Ya = Y.p;
+  }
+  for (int g = 0; g < npair; g++)
+    for (int q = 0; q < 2; q++)
+      RIS_REQUIRE(pairs[2 * g + q] >= 0 && pairs[2 * g + q] < nx, RIS_ERR_ARG,
+                  "state index out of range");
+  const bool rpa = Ya != nullptr;
+  ensure_D();
+  // unique states
+  std::vector<int> su;
+  std::map<int, int> slot;
+  for (int g = 0; g < 2 * npair; g++)
+    if (!slot.count(pairs[g])) {
+      slot[pairs[g]] = (int)su.size();
+      su.push_back(pairs[g]);
+    }
+  const int nsu = (int)su.size();
+  // per state: R, L, D^R = C_o R C_v^T, c^J, Q_R = R C_v^T, Q_L = L C_v^T
+  DBuf Rs, Ls, DR, cJ, QR, QL, t1;
+  Rs.ensure((size_t)nsu * nov);
+  Ls.ensure((size_t)nsu * nov);
+  for (int s = 0; s < nsu; s++) {
+    const double* xs = Xa + (size_t)su[s] * nov;
+    const double* ys = rpa ? Ya + (size_t)su[s] * nov : nullptr;
+    axpby(nov, 1.0, xs, 1.0, ys, Rs.p + s * nov, st);
+    axpby(nov, 1.0, xs, -1.0, ys, Ls.p + s * nov, st);
+  }
+  DR.ensure((size_t)nsu * nn * nn);
+  t1.ensure((size_t)nn * v);
+  cJ.ensure((size_t)nsu * nJ);
+  w5.ensure((size_t)nsu * nJ);
+  QR.ensure((size_t)nsu * o * nn);
+  QL.ensure((size_t)nsu * o * nn);
+  const double* Co = C.p;
+  const double* Cv = C.p + o;
+  for (int s = 0; s < nsu; s++) {
+    dgemm(false, false, nn, v, o, 1.0, Co, nmo, Rs.p + s * nov, v, 0.0, t1.p, v, st);
+    dgemm(false, true, nn, nn, v, 1.0, t1.p, v, Cv, nmo, 0.0, DR.p + (size_t)s * nn * nn, nn, st);
+    dgemm(false, true, o, nn, v, 1.0, Rs.p + s * nov, v, Cv, nmo, 0.0, QR.p + (size_t)s * o * nn, nn, st);
+    dgemm(false, true, o, nn, v, 1.0, Ls.p + s * nov, v, Cv, nmo, 0.0, QL.p + (size_t)s * o * nn, nn, st);
+  }
+  // u_s = R_s . B^J (nJ), c_s = u_s L^-1 (row vector)
+  dgemm(false, false, nsu, nJ, (int)nov, 1.0, Rs.p, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
+  dgemm(false, false, nsu, nJ, nJ, 1.0, w5.p, nJ, LJinv.p, nJ, 0.0, cJ.p, nJ, st);
+  // per pair
+  const size_t gsz = (size_t)nn * nn * nU;
+  DBuf Gam, Om, Wc, Z, Goo, M1, WV, Wt, gtmp;
+  Gam.ensure(gsz);
+  Om.ensure((size_t)nU * nU);
+  Wc.ensure(3 * (size_t)nn * nU);
+  Z.ensure((size_t)o * v * nK);
+  Goo.ensure((size_t)o * o * nK);
+  M1.ensure((size_t)nn * 2 * o * nK);
+  WV.ensure((size_t)nn * 2 * o);
+  const double cx = opt.cx;
+  for (int g = 0; g < npair; g++) {
+    const int sI = slot[pairs[2 * g]], sJ = slot[pairs[2 * g + 1]];
+    RIS_CUDA(cudaMemsetAsync(Gam.p, 0, sizeof(double) * gsz, st));
+    RIS_CUDA(cudaMemsetAsync(Om.p, 0, sizeof(double) * nU * nU, st));
+    // Coulomb
+    k_gamma_J<<<cdiv((long long)nn * nn * nJ, 256), 256, 0, st>>>(
+        DR.p + (size_t)sI * nn * nn, DR.p + (size_t)sJ * nn * nn, cJ.p + (size_t)sI * nJ,
+        cJ.p + (size_t)sJ * nJ, d_jU, nn, nJ, nU, 2.0, Gam.p);
+    RIS_CHECK_LAUNCH();
+    k_omega_J<<<cdiv(nJ * nJ, 256), 256, 0, st>>>(cJ.p + (size_t)sI * nJ, cJ.p + (size_t)sJ * nJ,
+                                                   d_jU, nJ, nU, 2.0, Om.p);
+    RIS_CHECK_LAUNCH();
+    // exchange (ij|ab) for (R_I,R_J) and (L_I,L_J), each with weight -c_x/2;
+    // with Y = 0 both combinations coincide, so one pass with -c_x.
+    const int ncomb = rpa ? 2 : 1;
+    for (int cmb = 0; cmb < ncomb; cmb++) {
+      const double f = rpa ? -0.5 * cx : -cx;
+      const double* U = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sI * nov;
+      const double* Vv = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sJ * nov;
+      const double* QU = (cmb == 0 ? QR.p : QL.p) + (size_t)sI * o * nn;
+      const double* QV = (cmb == 0 ? QR.p : QL.p) + (size_t)sJ * o * nn;
+      // Z[j][b][P] = sum_a U[j][a] c^vv[a][b][P]
+      dgemm(false, false, o, v * nK, v, 1.0, U, v, cKvv.p, v * nK, 0.0, Z.p, v * nK, st);
+      // G[j][k][P] = sum_b V[k][b] Z[j][b][P]
+      {
+        GemmBatch bt;
+        bt.nb1 = o;
+        bt.sB1 = (long long)v * nK;
+        bt.sC1 = (long long)o * nK;
+        dgemm(false, false, o, nK, v, 1.0, Vv, v, Z.p, nK, 0.0, Goo.p, nK, st, bt);
+      }
+      // M1[mu][0:o][P] = C_o G ; M1[mu][o:2o][P] = Q_U^T c^oo
+      dgemm(false, false, nn, o * nK, o, 1.0, Co, nmo, Goo.p, o * nK, 0.0, M1.p, 2 * o * nK, st);
+      dgemm(true, false, nn, o * nK, o, 1.0, QU, nn, cKoo.p, o * nK, 0.0, M1.p + (size_t)o * nK,
+            2 * o * nK, st);
+      k_build_W<<<cdiv(nn * 2 * o, 256), 256, 0, st>>>(C.p, nmo, QV, nn, o, WV.p);
+      RIS_CHECK_LAUNCH();
+      // Gamma[mu][nu][P<nK] += f sum_k W_V[nu][k] M1[mu][k][P]
+      {
+        GemmBatch bt;
+        bt.nb1 = nn;
+        bt.sB1 = 2LL * o * nK;
+        bt.sC1 = (long long)nn * nU;
+        dgemm(false, false, nn, nK, 2 * o, f, WV.p, 2 * o, M1.p, nK, 1.0, Gam.p, nU, st, bt);
+      }
+      // Omega[P][Q] += f sum_ij c^oo_ij,P G_ij,Q   (K functions are union 0..nK-1)
+      dgemm(true, false, nK, nK, o * o, f, cKoo.p, nK, Goo.p, nK, 1.0, Om.p, nU, st);
+    }
+    if (rpa) throw Error{RIS_ERR_ARG, "RPA derivatives are not available in this build"};
+    k_contract<<<nn, 128, 0, st>>>(D.p, Gam.p, nn, nU, Wc.p);
+    RIS_CHECK_LAUNCH();
+    k_grad_reduce<<<natm, 128, 0, st>>>(Wc.p, Om.p, dMU.p, ao.fun_atom, aux.fun_atom, nn, nU,
+                                        out + (size_t)g * natm * 3);
+    RIS_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace ris

@@ -1,0 +1,84 @@
+// TDDFT-ris engine state and stages.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "ints.cuh"
+#include "la.cuh"
+
+namespace ris {
+
+// Device buffer owned by the context.
+struct DBuf {
+  double* p = nullptr;
+  size_t n = 0;
+  void ensure(size_t count);
+  void release();
+  ~DBuf() { release(); }
+};
+
+struct Engine {
+  ris_options opt{};
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int stage = 0;  // 0 created, 1 aux built, 2 B built, 3 excited
+
+  // geometry / basis
+  int natm = 0;
+  DBuf xyz;
+  ShellSet ao, aux;   // aux = union of the J and K sets, K functions first
+  int nJ = 0, nK = 0, nU = 0;
+  std::vector<int> h_jU, h_kU;  // J / K function -> union function
+  int* d_jU = nullptr;
+  int* d_kU = nullptr;
+  PairList pl;
+  DBuf TJ, TK;              // (mu nu|P) [mu][nu][P] per set
+  DBuf MU, dMU;             // union metric and d/dP_x
+  DBuf LJinv, LKinv;        // inverse Cholesky factors
+  DBuf D;                   // derivative integrals [3][mu][nu][P_U]
+  bool have_D = false;
+  int* d_info = nullptr;
+
+  // MO data
+  int nao = 0, nmo = 0, nocc = 0, nvir = 0;
+  DBuf C, eps, de;
+  DBuf BJ;        // [ov][RJ]
+  DBuf BKoo;      // [i][j][R]
+  DBuf BKvvD;     // [b][R][a] (Davidson layout)
+  DBuf BKovR;     // [R][i][a] (RPA)
+  DBuf cKoo, cKvv, cKov;  // fitting coefficients c = B L^-1, [p][q][P]
+
+  // excitations
+  int nstates = 0;
+  DBuf omega, X, Y;
+  std::vector<double> h_omega;
+
+  // work
+  DBuf w1, w2, w3, w4, w5, w6, w7, w8;
+  double stats[16] = {0};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  ~Engine();
+  void build_aux(int natm, const double* coords, int nshell, const ris_shell* ao,
+                 int nJs, const ris_shell* auxJ, int nKs, const ris_shell* auxK);
+  void build_B(int nao, int nmo, int nocc, const double* C, const double* mo_energy);
+  void excite(int nstates, double* omega, double* X, double* Y);
+  // numerators dE_IJ/dR for pairs, [npair][natm][3] into out (host or device)
+  void pair_derivs(int npair, const int* pairs, int nx, const double* X_in, const double* Y_in,
+                   double* out_dev);
+  void ensure_D();
+
+  // helpers
+  void apply_A_tda(const double* Xin, int nvec, double* out);
+  void apply_ApB_AmB(const double* Zin, int nvec, double* outP, double* outM);
+  void davidson_tda(int ns);
+  void davidson_rpa(int ns);
+};
+
+// out[g][k] = num[g][k] / den[g]
+void divide_pairs(double* out, const double* num, const double* den, int npair, int per,
+                  cudaStream_t st);
+
+}  // namespace ris

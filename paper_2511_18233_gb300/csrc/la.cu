@@ -1,0 +1,473 @@
+// Dense FP64 linear algebra on the device.
+//
+// * dgemm: tiled FP64 GEMM (64x64 block tile, 4x4 per thread), batched over
+//   two strided levels, transposes folded into the tile loads.
+// * cholesky / tri_inverse: the metric factor M = L L^T of Eq. (g_modified)
+//   and L^{-1}; left-looking, one CTA (the metric is at most a few thousand
+//   functions for one molecule of the ris basis).
+// * sym_eig_lowest: lowest k eigenpairs of a small symmetric matrix (the
+//   Davidson subspace problem), one CTA: Householder reduction to
+//   tridiagonal form, Sturm-sequence bisection for the eigenvalues, inverse
+//   iteration for the eigenvectors of the tridiagonal matrix, Gram-Schmidt
+//   inside clusters of close eigenvalues, back-transformation.
+#include <math.h>
+
+#include "la.cuh"
+
+namespace ris {
+
+// ------------------------------------------------------------------ GEMM
+constexpr int kBM = 64, kBN = 64, kBK = 16;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha,
+                                               const double* __restrict__ A, int lda,
+                                               const double* __restrict__ B, int ldb, double beta,
+                                               double* __restrict__ C, int ldc, GemmBatch bt) {
+  const int bz = blockIdx.z;
+  const int b1 = bz / bt.nb2, b2 = bz % bt.nb2;
+  A += b1 * bt.sA1 + b2 * bt.sA2;
+  B += b1 * bt.sB1 + b2 * bt.sB2;
+  C += b1 * bt.sC1 + b2 * bt.sC2;
+  __shared__ double As[kBK][kBM + 1];
+  __shared__ double Bs[kBK][kBN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int row0 = blockIdx.y * kBM, col0 = blockIdx.x * kBN;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; r++)
+#pragma unroll
+    for (int c = 0; c < 4; c++) acc[r][c] = 0.0;
+  for (int k0 = 0; k0 < k; k0 += kBK) {
+#pragma unroll
+    for (int e = tid; e < kBM * kBK; e += 256) {
+      int i, kk;
+      if (!TA) {
+        i = e / kBK;
+        kk = e % kBK;
+      } else {
+        kk = e / kBM;
+        i = e % kBM;
+      }
+      const int gi = row0 + i, gk = k0 + kk;
+      double v = 0.0;
+      if (gi < m && gk < k) v = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
+      As[kk][i] = v;
+    }
+#pragma unroll
+    for (int e = tid; e < kBN * kBK; e += 256) {
+      int j, kk;
+      if (!TB) {
+        kk = e / kBN;
+        j = e % kBN;
+      } else {
+        j = e / kBK;
+        kk = e % kBK;
+      }
+      const int gj = col0 + j, gk = k0 + kk;
+      double v = 0.0;
+      if (gj < n && gk < k) v = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk++) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; c++) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    const int gi = row0 + ty + 16 * r;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const int gj = col0 + tx + 16 * c;
+      if (gj >= n) continue;
+      double* p = C + (size_t)gi * ldc + gj;
+      *p = beta == 0.0 ? alpha * acc[r][c] : fma(alpha, acc[r][c], beta * *p);
+    }
+  }
+}
+
+void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const double* A, int lda,
+           const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t st,
+           const GemmBatch& bt) {
+  if (m <= 0 || n <= 0) return;
+  const int nb = bt.nb1 * bt.nb2;
+  if (nb <= 0) return;
+  RIS_REQUIRE(nb <= 65535, RIS_ERR_ARG, "dgemm: batch too large");
+  dim3 grid(cdiv(n, kBN), cdiv(m, kBM), nb);
+  if (k <= 0) {  // C = beta C
+    RIS_REQUIRE(beta == 0.0, RIS_ERR_ARG, "dgemm: k = 0 with beta != 0");
+  }
+  if (!transA && !transB)
+    k_dgemm<false, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else if (!transA && transB)
+    k_dgemm<false, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else if (transA && !transB)
+    k_dgemm<true, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else
+    k_dgemm<true, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  RIS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ reductions
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// ------------------------------------------------------------------ Cholesky
+__global__ void __launch_bounds__(1024) k_cholesky(double* A, int n, int* info) {
+  __shared__ double red[33];
+  __shared__ double piv;
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; j++) {
+    double part = 0.0;
+    for (int k = tid; k < j; k += 1024) part += A[(size_t)j * n + k] * A[(size_t)j * n + k];
+    const double s = block_sum<1024>(part, red);
+    if (tid == 0) {
+      const double d = A[(size_t)j * n + j] - s;
+      if (!(d > 0.0)) {
+        bad = j + 1;
+      } else {
+        piv = sqrt(d);
+        A[(size_t)j * n + j] = piv;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double pj = piv;
+    for (int i = j + 1 + tid; i < n; i += 1024) {
+      double acc = A[(size_t)i * n + j];
+      for (int k = 0; k < j; k++) acc -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+      A[(size_t)i * n + j] = acc / pj;
+    }
+    __syncthreads();
+  }
+  if (!bad) {
+    for (size_t e = tid; e < (size_t)n * n; e += 1024) {
+      const int i = (int)(e / n), j = (int)(e % n);
+      if (j > i) A[e] = 0.0;
+    }
+  }
+  if (tid == 0) *info = bad;
+}
+
+void cholesky(double* A, int n, int* d_info, cudaStream_t st) {
+  k_cholesky<<<1, 1024, 0, st>>>(A, n, d_info);
+  RIS_CHECK_LAUNCH();
+}
+
+__global__ void k_tri_inverse(const double* __restrict__ L, double* __restrict__ X, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int i = 0; i < j; i++) X[(size_t)i * n + j] = 0.0;
+  X[(size_t)j * n + j] = 1.0 / L[(size_t)j * n + j];
+  for (int i = j + 1; i < n; i++) {
+    double acc = 0.0;
+    for (int k = j; k < i; k++) acc += L[(size_t)i * n + k] * X[(size_t)k * n + j];
+    X[(size_t)i * n + j] = -acc / L[(size_t)i * n + i];
+  }
+}
+
+void tri_inverse(const double* L, double* Linv, int n, cudaStream_t st) {
+  k_tri_inverse<<<cdiv(n, 32), 32, 0, st>>>(L, Linv, n);
+  RIS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ eigensolver
+constexpr int kEigT = 512;
+
+size_t eig_work_size(int m) { return (size_t)m * m + 5 * (size_t)m + 64 + 64 * (size_t)m * 6; }
+
+__device__ int sturm_count(const double* d, const double* e, int m, double x) {
+  int c = 0;
+  double q = d[0] - x;
+  if (q < 0) c++;
+  for (int i = 1; i < m; i++) {
+    if (q == 0.0) q = -1e-300;
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (q < 0) c++;
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(kEigT) k_sym_eig(const double* __restrict__ H, int ldH, int m, int k,
+                                                   double* __restrict__ w, double* __restrict__ V,
+                                                   double* __restrict__ work) {
+  __shared__ double red[33];
+  __shared__ double sh_alpha, sh_tau;
+  double* A = work;
+  double* d = A + (size_t)m * m;
+  double* e = d + m;
+  double* p = e + m;
+  double* tau = p + m;
+  double* lam = tau + 2 * (size_t)m;  // 64
+  double* Z = lam + 64;               // k x m
+  double* DL = Z + (size_t)64 * m;
+  double* DD = DL + (size_t)64 * m;
+  double* DU = DD + (size_t)64 * m;
+  double* DU2 = DU + (size_t)64 * m;
+  double* PIV = DU2 + (size_t)64 * m;
+  const int tid = threadIdx.x;
+  for (size_t i = tid; i < (size_t)m * m; i += kEigT) A[i] = H[(i / m) * ldH + i % m];
+  __syncthreads();
+  // symmetrise
+  for (size_t ij = tid; ij < (size_t)m * m; ij += kEigT) {
+    const int i = (int)(ij / m), j = (int)(ij % m);
+    if (j < i) {
+      const double s = 0.5 * (A[(size_t)i * m + j] + A[(size_t)j * m + i]);
+      A[(size_t)i * m + j] = s;
+      A[(size_t)j * m + i] = s;
+    }
+  }
+  __syncthreads();
+  // --- Householder tridiagonalisation
+  for (int c = 0; c + 2 < m; c++) {
+    double part = 0.0;
+    for (int i = c + 1 + tid; i < m; i += kEigT) part += A[(size_t)i * m + c] * A[(size_t)i * m + c];
+    const double s = block_sum<kEigT>(part, red);
+    if (tid == 0) {
+      const double x0 = A[(size_t)(c + 1) * m + c];
+      const double nrm = sqrt(s);
+      d[c] = A[(size_t)c * m + c];
+      if (nrm == 0.0) {
+        sh_alpha = 0.0;
+        sh_tau = 0.0;
+      } else {
+        const double alpha = x0 >= 0.0 ? -nrm : nrm;
+        const double v0 = x0 - alpha;
+        const double vn2 = s - x0 * x0 + v0 * v0;
+        A[(size_t)(c + 1) * m + c] = v0;
+        sh_alpha = alpha;
+        sh_tau = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+      }
+      e[c] = sh_alpha;
+      tau[c] = sh_tau;
+    }
+    __syncthreads();
+    const double t = sh_tau;
+    if (t == 0.0) continue;
+    // p = t * A_sub v, using symmetry for coalesced reads
+    for (int i = c + 1 + tid; i < m; i += kEigT) {
+      double acc = 0.0;
+      for (int j = c + 1; j < m; j++) acc += A[(size_t)j * m + i] * A[(size_t)j * m + c];
+      p[i] = t * acc;
+    }
+    __syncthreads();
+    part = 0.0;
+    for (int i = c + 1 + tid; i < m; i += kEigT) part += p[i] * A[(size_t)i * m + c];
+    const double K = 0.5 * t * block_sum<kEigT>(part, red);
+    for (int i = c + 1 + tid; i < m; i += kEigT) p[i] -= K * A[(size_t)i * m + c];
+    __syncthreads();
+    const int ms = m - c - 1;
+    for (size_t ij = tid; ij < (size_t)ms * ms; ij += kEigT) {
+      const int i = c + 1 + (int)(ij / ms), j = c + 1 + (int)(ij % ms);
+      A[(size_t)i * m + j] -= A[(size_t)i * m + c] * p[j] + p[i] * A[(size_t)j * m + c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (m >= 2) {
+      d[m - 2] = A[(size_t)(m - 2) * m + m - 2];
+      e[m - 2] = A[(size_t)(m - 1) * m + m - 2];
+      tau[m - 2] = 0.0;
+    }
+    d[m - 1] = A[(size_t)(m - 1) * m + m - 1];
+    e[m - 1] = 0.0;
+    tau[m - 1] = 0.0;
+  }
+  __syncthreads();
+  // --- bisection (thread j -> eigenvalue j)
+  double glo = 0.0, ghi = 0.0;
+  for (int i = 0; i < m; i++) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    const double lo = d[i] - r, hi = d[i] + r;
+    if (i == 0 || lo < glo) glo = lo;
+    if (i == 0 || hi > ghi) ghi = hi;
+  }
+  const double tnorm = fmax(fmax(fabs(glo), fabs(ghi)), 1e-300);
+  if (tid < k) {
+    double lo = glo - 1e-12 * tnorm, hi = ghi + 1e-12 * tnorm;
+    for (int it = 0; it < 200; it++) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (sturm_count(d, e, m, mid) > tid)
+        hi = mid;
+      else
+        lo = mid;
+    }
+    lam[tid] = 0.5 * (lo + hi);
+  }
+  __syncthreads();
+  // --- inverse iteration: thread j factors T - lam_j I by Gaussian
+  //     elimination with partial pivoting (unit lower L, upper U with two
+  //     super-diagonals) and applies three solves to a fixed start vector.
+  if (tid < k) {
+    const int j = tid;
+    double* z = Z + (size_t)j * m;
+    double* dl = DL + (size_t)j * m;
+    double* dd = DD + (size_t)j * m;
+    double* du = DU + (size_t)j * m;
+    double* du2 = DU2 + (size_t)j * m;
+    double* piv = PIV + (size_t)j * m;
+    const double lj = lam[j];
+    const double tiny = 1e-15 * tnorm;
+    for (int i = 0; i < m; i++) {
+      dd[i] = d[i] - lj;
+      dl[i] = i + 1 < m ? e[i] : 0.0;
+      du[i] = i + 1 < m ? e[i] : 0.0;
+      du2[i] = 0.0;
+      piv[i] = 0.0;
+    }
+    for (int i = 0; i + 1 < m; i++) {
+      if (fabs(dd[i]) >= fabs(dl[i])) {
+        if (dd[i] == 0.0) dd[i] = tiny;
+        const double f = dl[i] / dd[i];
+        dl[i] = f;
+        dd[i + 1] -= f * du[i];
+      } else {
+        const double f = dd[i] / dl[i];
+        dd[i] = dl[i];
+        dl[i] = f;
+        const double tmp = du[i];
+        du[i] = dd[i + 1];
+        dd[i + 1] = tmp - f * dd[i + 1];
+        if (i + 2 < m) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du[i + 1];
+        }
+        piv[i] = 1.0;
+      }
+    }
+    if (dd[m - 1] == 0.0) dd[m - 1] = tiny;
+    for (int i = 0; i < m; i++) z[i] = 1.0 + 0.01 * (double)(i % 7);
+    for (int it = 0; it < 3; it++) {
+      for (int i = 0; i + 1 < m; i++) {
+        if (piv[i] == 0.0) {
+          z[i + 1] -= dl[i] * z[i];
+        } else {
+          const double t0 = z[i];
+          z[i] = z[i + 1];
+          z[i + 1] = t0 - dl[i] * z[i];
+        }
+      }
+      z[m - 1] /= dd[m - 1];
+      if (m >= 2) z[m - 2] = (z[m - 2] - du[m - 2] * z[m - 1]) / dd[m - 2];
+      for (int i = m - 3; i >= 0; i--) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / dd[i];
+      double nrm = 0.0;
+      for (int i = 0; i < m; i++) nrm += z[i] * z[i];
+      nrm = 1.0 / sqrt(nrm);
+      for (int i = 0; i < m; i++) z[i] *= nrm;
+    }
+  }
+  __syncthreads();
+  // --- Gram-Schmidt within clusters of close eigenvalues
+  const double gap_tol = 1e-7 * tnorm;
+  for (int j = 1; j < k; j++) {
+    for (int i = 0; i < j; i++) {
+      if (fabs(lam[j] - lam[i]) > gap_tol) continue;
+      double part = 0.0;
+      for (int q = tid; q < m; q += kEigT) part += Z[(size_t)i * m + q] * Z[(size_t)j * m + q];
+      const double s = block_sum<kEigT>(part, red);
+      for (int q = tid; q < m; q += kEigT) Z[(size_t)j * m + q] -= s * Z[(size_t)i * m + q];
+      __syncthreads();
+      part = 0.0;
+      for (int q = tid; q < m; q += kEigT) part += Z[(size_t)j * m + q] * Z[(size_t)j * m + q];
+      const double nn = block_sum<kEigT>(part, red);
+      for (int q = tid; q < m; q += kEigT) Z[(size_t)j * m + q] /= sqrt(nn);
+      __syncthreads();
+    }
+  }
+  // --- back-transformation x = H_0 ... H_{m-3} z  (apply H_{m-3} first)
+  for (int c = m - 3; c >= 0; c--) {
+    const double t = tau[c];
+    if (t == 0.0) continue;
+    // one warp per eigenvector
+    const int wid = tid >> 5, lane = tid & 31;
+    for (int j = wid; j < k; j += kEigT / 32) {
+      double* z = Z + (size_t)j * m;
+      double part = 0.0;
+      for (int i = c + 1 + lane; i < m; i += 32) part += A[(size_t)i * m + c] * z[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      const double f = t * part;
+      for (int i = c + 1 + lane; i < m; i += 32) z[i] -= f * A[(size_t)i * m + c];
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < k; j += kEigT) w[j] = lam[j];
+  for (size_t i = tid; i < (size_t)k * m; i += kEigT) V[i] = Z[i];
+}
+
+void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
+                    cudaStream_t st) {
+  RIS_REQUIRE(k >= 1 && k <= 64 && k <= m, RIS_ERR_ARG, "sym_eig_lowest: bad k");
+  k_sym_eig<<<1, kEigT, 0, st>>>(H, ldH, m, k, w, V, work);
+  RIS_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------------ utilities
+__global__ void k_fill(double* x, double v, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+void fill(double* x, double v, size_t n, cudaStream_t st) {
+  if (!n) return;
+  k_fill<<<(unsigned)std::min<size_t>(cdiv(n, 256), 152 * 8), 256, 0, st>>>(x, v, n);
+  RIS_CHECK_LAUNCH();
+}
+
+__global__ void k_row_dot(const double* __restrict__ V, long long ncol, const double* __restrict__ x,
+                          double* __restrict__ out) {
+  __shared__ double red[33];
+  const double* v = V + (size_t)blockIdx.x * ncol;
+  const double* y = x ? x : v;
+  double part = 0.0;
+  for (long long i = threadIdx.x; i < ncol; i += 256) part += v[i] * y[i];
+  const double s = block_sum<256>(part, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+void row_norms(const double* X, int nrow, long long ncol, double* out, cudaStream_t st) {
+  if (nrow <= 0) return;
+  k_row_dot<<<nrow, 256, 0, st>>>(X, ncol, nullptr, out);
+  RIS_CHECK_LAUNCH();
+}
+void gemv_rows(const double* V, int nrow, long long ncol, const double* x, double* out,
+               cudaStream_t st) {
+  if (nrow <= 0) return;
+  k_row_dot<<<nrow, 256, 0, st>>>(V, ncol, x, out);
+  RIS_CHECK_LAUNCH();
+}
+
+}  // namespace ris

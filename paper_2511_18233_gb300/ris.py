@@ -1,0 +1,206 @@
+"""Thin ctypes binding of the sm_103a TDDFT-ris library (include/ris.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Arrays may be numpy arrays (host) or CUDA torch tensors (device);
+the library tells them apart.  There is no CPU fallback: if the library
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libris.so")
+
+RIS_OK = 0
+STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC_NOT_PD",
+          -4: "RIS_ERR_NOT_CONVERGED", -5: "RIS_ERR_CUDA", -6: "RIS_ERR_TIMEOUT",
+          -7: "RIS_ERR_STATE", -8: "RIS_ERR_DEGENERATE"}
+FP64, MIXED = 0, 1
+
+EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
+           "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
+           "ris_last_error", "ris_destroy"]
+
+
+class RisError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("rpa", ctypes.c_int), ("cx", ctypes.c_double),
+                ("conv_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("max_subspace", ctypes.c_int), ("screen_thr", ctypes.c_double),
+                ("mem_budget", ctypes.c_size_t), ("occ_block", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+class Shell(ctypes.Structure):
+    _fields_ = [("atom", ctypes.c_int), ("l", ctypes.c_int), ("exponent", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libris.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i, d = ctypes.c_int, ctypes.c_double
+    L.ris_options_default.argtypes = [ctypes.POINTER(Options)]
+    L.ris_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Options)]
+    L.ris_build_aux.argtypes = [P, i, P, i, P, i, P, i, P]
+    L.ris_build_B.argtypes = [P, i, i, i, P, P]
+    L.ris_excite.argtypes = [P, i, P, P, P]
+    L.ris_gradient.argtypes = [P, i, P, i, P, P, P]
+    L.ris_nac.argtypes = [P, i, P, i, P, P, P, P, P]
+    L.ris_get_dims.argtypes = [P] + [ctypes.POINTER(i)] * 6
+    L.ris_get_stats.argtypes = [P, ctypes.POINTER(d), i]
+    L.ris_debug_boys.argtypes = [i, P, P, P]
+    L.ris_last_error.argtypes = [P]
+    L.ris_last_error.restype = ctypes.c_char_p
+    L.ris_destroy.argtypes = [P]
+    for f in EXPORTS:
+        if f not in ("ris_last_error", "ris_destroy"):
+            getattr(L, f).restype = ctypes.c_int
+    L.ris_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _ptr(a) -> Optional[int]:
+    """Raw address of a numpy array or torch tensor (contiguous, float64/int32)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _shells(arr) -> ctypes.Array:
+    n = len(arr)
+    out = (Shell * n)()
+    for k in range(n):
+        out[k].atom = int(arr["atom"][k])
+        out[k].l = int(arr["l"][k])
+        out[k].exponent = float(arr["exp"][k])
+    return out
+
+
+def options(**kw) -> Options:
+    o = Options()
+    load().ris_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """One ris_ctx (one CUDA stream).  Methods mirror the C ABI."""
+
+    def __init__(self, **opts):
+        self.L = load()
+        self.opt = options(**opts)
+        h = ctypes.c_void_p()
+        self._check(self.L.ris_create(ctypes.byref(h), ctypes.byref(self.opt)), None)
+        self.h = h
+        self.natm = self.nocc = self.nvir = 0
+
+    def _check(self, st: int, h=...):
+        if st != RIS_OK:
+            hh = self.h if h is ... else h
+            msg = self.L.ris_last_error(hh).decode() if hh else ""
+            raise RisError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ris_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_aux(self, coords, shells, aux_j, aux_k):
+        c = np.ascontiguousarray(coords, dtype=np.float64) if isinstance(coords, np.ndarray) else coords
+        s, j, k = _shells(shells), _shells(aux_j), _shells(aux_k)
+        self.natm = int(c.shape[0])
+        self._check(self.L.ris_build_aux(self.h, self.natm, _ptr(c), len(s), ctypes.addressof(s),
+                                         len(j), ctypes.addressof(j), len(k), ctypes.addressof(k)))
+
+    def build_B(self, C, mo_energy, nocc: int):
+        if isinstance(C, np.ndarray):
+            C = np.ascontiguousarray(C, dtype=np.float64)
+            mo_energy = np.ascontiguousarray(mo_energy, dtype=np.float64)
+        nao, nmo = C.shape
+        self.nocc, self.nvir = int(nocc), int(nmo - nocc)
+        self._check(self.L.ris_build_B(self.h, nao, nmo, int(nocc), _ptr(C), _ptr(mo_energy)))
+
+    def excite(self, nstates: int, out=None):
+        """Returns (omega, X[, Y]) as numpy arrays, or fills `out` (omega, X, Y)
+        tensors/arrays in place (host or device)."""
+        rpa = bool(self.opt.rpa)
+        if out is None:
+            om = np.zeros(nstates)
+            X = np.zeros((nstates, self.nocc, self.nvir))
+            Y = np.zeros_like(X) if rpa else None
+        else:
+            om, X, Y = out
+        self._check(self.L.ris_excite(self.h, int(nstates), _ptr(om), _ptr(X), _ptr(Y)))
+        return (om, X, Y) if rpa else (om, X)
+
+    def gradient(self, states: Sequence[int], X=None, Y=None, out=None):
+        st = np.ascontiguousarray(states, dtype=np.int32)
+        nx = 0 if X is None else int(X.shape[0])
+        g = np.zeros((len(st), self.natm, 3)) if out is None else out
+        self._check(self.L.ris_gradient(self.h, len(st), _ptr(st), nx, _ptr(X), _ptr(Y), _ptr(g)))
+        return g
+
+    def nac(self, pairs, X=None, Y=None, omega=None, out=None, numerator=None):
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        nx = 0 if X is None else int(X.shape[0])
+        n = np.zeros((len(pr), self.natm, 3)) if out is None else out
+        self._check(self.L.ris_nac(self.h, len(pr), _ptr(pr), nx, _ptr(X), _ptr(Y), _ptr(omega),
+                                   _ptr(n), _ptr(numerator)))
+        return n
+
+    def dims(self):
+        v = [ctypes.c_int() for _ in range(6)]
+        self._check(self.L.ris_get_dims(self.h, *[ctypes.byref(x) for x in v]))
+        keys = ["natm", "nao", "nocc", "nauxJ", "nauxK", "npairs"]
+        return {k: x.value for k, x in zip(keys, v)}
+
+    def stats(self):
+        out = (ctypes.c_double * 16)()
+        self._check(self.L.ris_get_stats(self.h, out, 16))
+        keys = ["aux_ms", "B_ms", "excite_ms", "deriv_ms", "n_products", "n_iter"]
+        return {k: out[i] for i, k in enumerate(keys)}
+
+
+def debug_boys(m, T):
+    """F_m(T) from the library's device Boys function (torch CUDA tensors)."""
+    import torch
+    m_t = torch.as_tensor(np.asarray(m, dtype=np.int32), device="cuda")
+    T_t = torch.as_tensor(np.asarray(T, dtype=np.float64), device="cuda")
+    out = torch.empty_like(T_t)
+    st = load().ris_debug_boys(int(T_t.numel()), m_t.data_ptr(), T_t.data_ptr(), out.data_ptr())
+    if st != 0:
+        raise RisError(st, "ris_debug_boys failed")
+    return out.cpu().numpy()

@@ -1,0 +1,173 @@
+"""Parity of the sm_103a library (through its C ABI) against the FP64 oracle.
+
+Tolerances (FP64 path):
+  * integrals / metric-derived quantities and gradients/couplings computed
+    from the same amplitudes: max|diff| / max|ref| <= 1e-9 per result array;
+  * excitation energies: relative 1e-9 (the Davidson eigenvalue error is
+    quadratic in the residual, <= 1e-10 here, so rounding dominates);
+  * amplitudes: |diff| <= 2 r/gap with r the residual tolerance (1e-10) and
+    gap the distance to the nearest other eigenvalue (first-order
+    perturbation bound), floored at 1e-9.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_18233_gb300 import synth
+
+gpu = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ris_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_18233_gb300 import build, ris
+    build.build()
+    return ris
+
+
+def _ctx(ris_mod, mol, **opt):
+    c = ris_mod.Context(**opt)
+    c.build_aux(mol.coords, mol.shells, mol.aux_j, mol.aux_k)
+    c.build_B(mol.C, mol.mo_energy, mol.nocc)
+    return c
+
+
+@pytest.fixture(scope="module")
+def small(oracle):
+    mol = synth.workload(0)
+    orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy,
+                           mol.nocc)
+    w, X = orc.tda_dense(6)
+    return mol, orc, w, X
+
+
+@gpu
+def test_boys_function(ris_mod, oracle):
+    rng = np.random.default_rng(0)
+    T = np.concatenate([np.linspace(0, 45, 700), rng.uniform(0, 60, 300), [0.0, 1e-12, 39.999, 40.0, 40.001, 300.0]])
+    m = rng.integers(0, 10, size=T.size).astype(np.int32)
+    got = ris_mod.debug_boys(m, T)
+    ref = np.array([oracle.boys(int(a), float(b)) for a, b in zip(m, T)])
+    np.testing.assert_allclose(got, ref, rtol=2e-14, atol=0)
+
+
+@gpu
+def test_excitation_energies_small(ris_mod, small):
+    mol, orc, w, X = small
+    c = _ctx(ris_mod, mol)
+    om, Xg = c.excite(5)
+    np.testing.assert_allclose(om, w[:5], rtol=1e-9)
+    gaps = np.array([min(abs(w[k] - w[j]) for j in range(6) if j != k) for k in range(5)])
+    for k in range(5):
+        tol = max(2 * 1e-10 / gaps[k], 1e-9)
+        assert np.max(np.abs(Xg[k] - X[k])) <= tol
+    st = c.stats()
+    assert st["n_products"] > 0 and st["excite_ms"] > 0
+
+
+@gpu
+def test_gradients_and_nac_small(ris_mod, small):
+    mol, orc, w, X = small
+    c = _ctx(ris_mod, mol)
+    Xin = np.ascontiguousarray(X[:5])
+    g = c.gradient(range(5), X=Xin)
+    ref = orc.gradients(range(5), X[:5])
+    assert _rel(g, ref) <= 1e-9
+    # translation sum rule
+    assert np.max(np.abs(g.sum(axis=1))) <= 1e-10 * np.max(np.abs(g))
+    nac = c.nac([(0, 1), (1, 0), (2, 4)], X=Xin, omega=np.ascontiguousarray(w[:5]))
+    nref = orc.nacs([(0, 1), (1, 0), (2, 4)], w[:5], X[:5])
+    assert _rel(nac, nref) <= 1e-9
+
+
+@gpu
+def test_full_pipeline_small(ris_mod, small):
+    """excite -> gradient -> nac with the library's own amplitudes."""
+    mol, orc, w, X = small
+    c = _ctx(ris_mod, mol)
+    om, Xg = c.excite(5)
+    g = c.gradient(range(5))
+    ref = orc.gradients(range(5), Xg)
+    assert _rel(g, ref) <= 1e-9
+    nac = c.nac([(0, 1)])
+    nref = orc.nacs([(0, 1)], om, Xg)
+    assert _rel(nac, nref) <= 1e-9
+
+
+@gpu
+def test_random_amplitudes_and_device_pointers(ris_mod, small):
+    import torch
+    mol, orc, w, X = small
+    c = _ctx(ris_mod, mol)
+    Xr = synth.random_amplitudes(3, mol.nocc, mol.nvir, seed=5)
+    pairs = [(0, 1), (2, 2), (1, 2)]
+    ref = orc.pair_energy_derivs(pairs, Xr)
+    num = np.zeros((3, mol.natm, 3))
+    c.nac(pairs, X=Xr, omega=np.array([0.1, 0.2, 0.3]), numerator=num)
+    assert _rel(num, ref) <= 1e-9
+    # the same call with device buffers
+    Xd = torch.as_tensor(Xr, device="cuda")
+    od = torch.tensor([0.1, 0.2, 0.3], dtype=torch.float64, device="cuda")
+    nd = torch.zeros((3, mol.natm, 3), dtype=torch.float64, device="cuda")
+    numd = torch.zeros_like(nd)
+    c.nac(pairs, X=Xd, omega=od, out=nd, numerator=numd)
+    np.testing.assert_array_equal(numd.cpu().numpy(), num)
+
+
+@gpu
+@pytest.mark.slow
+def test_chain_c20h22_parity(ris_mod, oracle):
+    """The 42-atom chain with s+p Coulomb auxiliaries: 10 states, spot-checked
+    gradients and adjacent couplings on sampled atoms."""
+    mol = synth.workload(1)
+    orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy,
+                           mol.nocc)
+    w, X, _ = orc.tda_davidson(11, tol=1e-11)
+    c = _ctx(ris_mod, mol)
+    om, Xg = c.excite(10)
+    np.testing.assert_allclose(om, w[:10], rtol=1e-9)
+    Xin = np.ascontiguousarray(X[:10])
+    g = c.gradient(range(10), X=Xin)
+    atoms = [0, 19, 33]
+    ref = orc.gradients([0, 4, 9], X[:10], atoms=atoms)
+    for k, s in enumerate([0, 4, 9]):
+        assert _rel(g[s, atoms], ref[k, atoms]) <= 1e-9
+    pairs = [(s, s + 1) for s in range(9)]
+    nac = c.nac(pairs, X=Xin, omega=np.ascontiguousarray(w[:10]))
+    nref = orc.nacs([(0, 1), (5, 6)], w[:10], X[:10], atoms=atoms)
+    assert _rel(nac[0, atoms], nref[0, atoms]) <= 1e-9
+    assert _rel(nac[5, atoms], nref[1, atoms]) <= 1e-9
+    assert np.max(np.abs(g.sum(axis=1))) <= 1e-10 * np.max(np.abs(g))
+
+
+@gpu
+def test_error_paths(ris_mod, small):
+    mol = small[0]
+    c = ris_mod.Context()
+    with pytest.raises(ris_mod.RisError) as e:
+        c.build_B(mol.C, mol.mo_energy, mol.nocc)
+    assert e.value.code == -7
+    bad = mol.shells.copy()
+    bad["l"][0] = 3
+    with pytest.raises(ris_mod.RisError) as e:
+        c.build_aux(mol.coords, bad, mol.aux_j, mol.aux_k)
+    assert e.value.code == -1
+    # two auxiliary functions on top of each other: singular metric
+    dup = np.concatenate([mol.aux_j, mol.aux_j[:1]])
+    with pytest.raises(ris_mod.RisError) as e:
+        c.build_aux(mol.coords, mol.shells, dup, mol.aux_k)
+    assert e.value.code == -3
+    c2 = _ctx(ris_mod, mol)
+    with pytest.raises(ris_mod.RisError) as e:
+        c2.gradient([0])
+    assert e.value.code == -7
+    om, X = c2.excite(3)
+    with pytest.raises(ris_mod.RisError) as e:
+        c2.nac([(0, 0)])
+    assert e.value.code == -8
