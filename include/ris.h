@@ -130,6 +130,15 @@ ris_status ris_build_B(ris_ctx* ctx, int nao, int nmo, int nocc, const double* C
 ris_status ris_excite(ris_ctx* ctx, int nstates, double* omega, double* X, double* Y);
 
 /*
+ * The response operator applied to nvec vectors (the Davidson product of
+ * Eqs. (A_matrix)/(B_matrix) with the ris kernel): TDA: out = A X; RPA
+ * (rpa option set): out = (A+B) X followed by out2 = (A-B) X.
+ * X, out, out2: [nvec][nocc][nvir]; out2 must be NULL for TDA.
+ * Requires ris_build_B.
+ */
+ris_status ris_apply(ris_ctx* ctx, int nvec, const double* X, double* out, double* out2);
+
+/*
  * Excited-state gradients g_I = dE_II/dR (Eq. (gI_xi_ris), integral-derivative
  * term) for the n states listed in states[] (0-based).  If X_in is NULL the
  * amplitudes of the last ris_excite are used and states index them;

@@ -117,6 +117,10 @@ ris_status ris_excite(ris_ctx* ctx, int nstates, double* omega, double* X, doubl
   });
 }
 
+ris_status ris_apply(ris_ctx* ctx, int nvec, const double* X, double* out, double* out2) {
+  return guarded(ctx, [&] { ctx->eng.apply(nvec, X, out, out2); });
+}
+
 ris_status ris_gradient(ris_ctx* ctx, int n, const int* states, int nx, const double* X_in,
                         const double* Y_in, double* grad) {
   return guarded(ctx, [&] {

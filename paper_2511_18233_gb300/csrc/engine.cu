@@ -316,17 +316,17 @@ __global__ void k_cholqr_small(const double* __restrict__ G, int nt, double drop
       keep[r++] = j;
     }
   }
-  // P = R^{-T} restricted to kept: row q of P gives Tnew_q
+  // P = R^{-T} over the kept indices: Tnew_s = sum_q (R^{-T})_sq T_keep[q].
+  // Column q of R^{-T} solves R^T y = e_q (forward substitution).
   for (int i = 0; i < nt * nt; i++) P[i] = 0.0;
   for (int q = 0; q < r; q++) {
-    // solve R^T y = e_q over kept indices (forward substitution)
     double y[64];
     for (int s = 0; s < r; s++) {
       double acc = (s == q) ? 1.0 : 0.0;
       for (int s2 = 0; s2 < s; s2++) acc -= R[keep[s2] * nt + keep[s]] * y[s2];
       y[s] = acc / R[keep[s] * nt + keep[s]];
     }
-    for (int s = 0; s < r; s++) P[q * nt + keep[s]] = y[s];
+    for (int s = 0; s < r; s++) P[s * nt + keep[q]] = y[s];
   }
   *nkeep = r;
 }
@@ -742,6 +742,30 @@ void Engine::apply_A_tda(const double* Xin, int nvec, double* out) {
   }
   k_add_diag<<<cdiv(nov * nvec, 256), 256, 0, st>>>(de.p, Xin, nov, nvec, out);
   RIS_CHECK_LAUNCH();
+}
+
+void Engine::apply(int nvec, const double* Xh, double* out, double* out2) {
+  RIS_REQUIRE(stage >= 2, RIS_ERR_STATE, "ris_apply before ris_build_B");
+  RIS_REQUIRE(nvec >= 1 && Xh && out, RIS_ERR_ARG, "bad ris_apply arguments");
+  RIS_REQUIRE((out2 != nullptr) == (opt.rpa != 0), RIS_ERR_ARG, "out2 must be given exactly for RPA");
+  const size_t n = (size_t)nvec * nocc * nvir;
+  DBuf x, y, z;
+  x.ensure(n);
+  y.ensure(n);
+  copy_in(x.p, Xh, n, st);
+  if (opt.rpa) {
+    z.ensure(n);
+    apply_ApB_AmB(x.p, nvec, y.p, z.p);
+    copy_out(out2, z.p, n, st);
+  } else {
+    apply_A_tda(x.p, nvec, y.p);
+  }
+  copy_out(out, y.p, n, st);
+  RIS_CUDA(cudaStreamSynchronize(st));
+}
+
+void Engine::apply_ApB_AmB(const double*, int, double*, double*) {
+  throw Error{RIS_ERR_ARG, "RPA products are not available in this build"};
 }
 
 // ------------------------------------------------------------------ Davidson (TDA)

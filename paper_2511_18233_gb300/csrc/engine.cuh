@@ -69,6 +69,7 @@ struct Engine {
   void pair_derivs(int npair, const int* pairs, int nx, const double* X_in, const double* Y_in,
                    double* out_dev);
   void ensure_D();
+  void apply(int nvec, const double* X, double* out, double* out2);
 
   // helpers
   void apply_A_tda(const double* Xin, int nvec, double* out);

@@ -61,23 +61,33 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
 }
 
 static std::vector<double> make_boys_table() {
+  // composite 32-point Gauss-Legendre on 32 panels of [0,1]; the integrand
+  // t^{2m} e^{-T t^2} is evaluated once per node for all m; Kahan summation.
   std::vector<double> gx, gw;
   gauss_legendre(32, gx, gw);
-  const int panels = 32;
+  const int panels = 32, nq = 32 * panels;
+  std::vector<double> tq(nq), wq(nq), ex(nq);
+  for (int pnl = 0; pnl < panels; pnl++) {
+    const double a = (double)pnl / panels, b = (double)(pnl + 1) / panels;
+    for (int i = 0; i < 32; i++) {
+      tq[pnl * 32 + i] = 0.5 * (b - a) * gx[i] + 0.5 * (a + b);
+      wq[pnl * 32 + i] = 0.5 * (b - a) * gw[i];
+    }
+  }
   std::vector<double> tab((size_t)kBoysNT * (kBoysM + 1));
   for (int k = 0; k < kBoysNT; k++) {
-    double T = k * kBoysDT;
+    const double T = k * kBoysDT;
+    for (int q = 0; q < nq; q++) ex[q] = wq[q] * exp(-T * tq[q] * tq[q]);
     for (int m = 0; m <= kBoysM; m++) {
-      long double s = 0.0L;
-      for (int pnl = 0; pnl < panels; pnl++) {
-        double a = (double)pnl / panels, b = (double)(pnl + 1) / panels;
-        for (int i = 0; i < 32; i++) {
-          double t = 0.5 * (b - a) * gx[i] + 0.5 * (a + b);
-          s += (long double)(0.5 * (b - a) * gw[i]) * powl((long double)t, 2 * m) *
-               expl(-(long double)T * t * t);
-        }
+      double s = 0.0, comp = 0.0;
+      for (int q = 0; q < nq; q++) {
+        const double y = ex[q] - comp;
+        const double t = s + y;
+        comp = (t - s) - y;
+        s = t;
+        ex[q] *= tq[q] * tq[q];  // next m
       }
-      tab[(size_t)k * (kBoysM + 1) + m] = (double)s;
+      tab[(size_t)k * (kBoysM + 1) + m] = s;
     }
   }
   return tab;

@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(1024) k_cholesky(double* A, int n, int* info) 
     for (int k = tid; k < j; k += 1024) part += A[(size_t)j * n + k] * A[(size_t)j * n + k];
     const double s = block_sum<1024>(part, red);
     if (tid == 0) {
-      const double d = A[(size_t)j * n + j] - s;
-      if (!(d > 0.0)) {
+      const double ajj = A[(size_t)j * n + j];
+      const double d = ajj - s;
+      if (!(d > 1e-13 * ajj)) {  // (numerically) singular or indefinite
         bad = j + 1;
       } else {
         piv = sqrt(d);

@@ -18,7 +18,7 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
 
 // In place lower Cholesky of an n x n row-major SPD matrix (upper part is
 // zeroed).  Writes 0 to *info on success, or j+1 if the j-th pivot is not
-// positive.
+// above 1e-13 times the diagonal element (singular or indefinite matrix).
 void cholesky(double* A, int n, int* d_info, cudaStream_t st);
 // Linv = L^{-1} for lower-triangular L (n x n, row-major).
 void tri_inverse(const double* L, double* Linv, int n, cudaStream_t st);

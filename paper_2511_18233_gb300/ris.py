@@ -23,6 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
+           "ris_apply",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
 
@@ -63,6 +64,7 @@ def load(path: str = LIB_PATH):
     L.ris_build_aux.argtypes = [P, i, P, i, P, i, P, i, P]
     L.ris_build_B.argtypes = [P, i, i, i, P, P]
     L.ris_excite.argtypes = [P, i, P, P, P]
+    L.ris_apply.argtypes = [P, i, P, P, P]
     L.ris_gradient.argtypes = [P, i, P, i, P, P, P]
     L.ris_nac.argtypes = [P, i, P, i, P, P, P, P, P]
     L.ris_get_dims.argtypes = [P] + [ctypes.POINTER(i)] * 6
@@ -165,6 +167,15 @@ class Context:
             om, X, Y = out
         self._check(self.L.ris_excite(self.h, int(nstates), _ptr(om), _ptr(X), _ptr(Y)))
         return (om, X, Y) if rpa else (om, X)
+
+    def apply(self, X, out=None, out2=None):
+        """TDA: A X.  RPA: ((A+B) X, (A-B) X)."""
+        rpa = bool(self.opt.rpa)
+        if out is None:
+            out = np.zeros_like(X)
+            out2 = np.zeros_like(X) if rpa else None
+        self._check(self.L.ris_apply(self.h, int(X.shape[0]), _ptr(X), _ptr(out), _ptr(out2)))
+        return (out, out2) if rpa else out
 
     def gradient(self, states: Sequence[int], X=None, Y=None, out=None):
         st = np.ascontiguousarray(states, dtype=np.int32)

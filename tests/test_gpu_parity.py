@@ -58,6 +58,16 @@ def test_boys_function(ris_mod, oracle):
 
 
 @gpu
+def test_apply_A_small(ris_mod, small):
+    mol, orc, w, X = small
+    c = _ctx(ris_mod, mol)
+    Xr = synth.random_amplitudes(4, mol.nocc, mol.nvir, seed=9)
+    got = c.apply(Xr)
+    ref = orc.apply_A(Xr)
+    assert _rel(got, ref) <= 1e-12
+
+
+@gpu
 def test_excitation_energies_small(ris_mod, small):
     mol, orc, w, X = small
     c = _ctx(ris_mod, mol)
