@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the sm_103a TDDFT-ris engine.
+
+One step = one evaluation at one geometry of the C20H22 chain workload
+(42 atoms, 512 AOs, nocc 71, 102 J / 42 K auxiliary functions): screened
+three-centre integrals and metric Cholesky, B tensors, Davidson for the 10
+lowest TDA-ris states, gradients of all 10 states and the 9 couplings
+between adjacent states.  Metric: evaluations per second.
+
+* value: device-resident inputs (coordinates, MO coefficients, orbital
+  energies as CUDA tensors), outputs into CUDA tensors, each step timed with
+  CUDA events on the library's stream; L2 flushed (512 MB write) between
+  steps, outside the timed events.
+* e2e: the same evaluation through host (numpy) buffers, host<->device copies
+  inside the timed region, wall clock.
+* roofline: the kernel class with the largest share of the timed region
+  (per-class CUDA events inside the library).
+* cpu_baseline / --impl reference: the FP64 oracle on the host cores on a
+  bounded sample of the same workload (setup, Davidson, the derivative of
+  two pair energies w.r.t. one atom), extrapolated to the full evaluation.
+
+Multi-GPU: replicas only (each rank evaluates its own copy; no collective
+in the data path); value = evaluations of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ris grad+NAC evals/s"
+WORKLOAD = "C20H22 chain, 42 atoms, nao 512, TDA-ris 10 states, 10 gradients + 9 adjacent NACs"
+NSTATES = 10
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.samples = []
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = np.array([num(s[0]) for s in self.samples])
+        util = np.array([num(s[3]) for s in self.samples])
+        load = sm[util > 0] if np.any(util > 0) else sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [n for k, n in enumerate(names) if any(s[4 + k].lower() == "active" for s in self.samples)]
+        return {"sm_mhz": float(np.nanmedian(load)), "sm_max_mhz": float(np.nanmax([num(s[1]) for s in self.samples])),
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ oracle leg
+def oracle_sample(mol, reps=1):
+    """Time the oracle on a bounded sample; returns (evals/s, seconds used,
+    sample description, omega, sample derivative)."""
+    from oracle import ris_oracle
+    ris_oracle.build()
+    t0 = time.perf_counter()
+    orc = ris_oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy,
+                               mol.nocc)
+    t1 = time.perf_counter()
+    w, X, _ = orc.tda_davidson(NSTATES, tol=1e-10)
+    t2 = time.perf_counter()
+    pairs = [(0, 0), (0, 1)]
+    d = orc.pair_energy_derivs(pairs, X, atoms=[0])
+    t3 = time.perf_counter()
+    npair_full = NSTATES + (NSTATES - 1)
+    t_full = (t1 - t0) + (t2 - t1) + (t3 - t2) / len(pairs) * npair_full * mol.natm
+    sample = (f"oracle setup + Davidson({NSTATES}) + d/dR of {len(pairs)} pair energies for 1 of "
+              f"{mol.natm} atoms; derivative time extrapolated to {npair_full} pairs x {mol.natm} atoms")
+    return 1.0 / t_full, t3 - t0, sample, w, X, d
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2511_18233_gb300 import synth
+    mol = synth.workload(1)
+    vals, used = [], 0.0
+    for it in range(args.warmup + args.steps):
+        v, t, sample, *_ = oracle_sample(mol)
+        used += t
+        if it >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2511_18233_gb300 import build, ris, synth
+    build.build()
+    mol = synth.workload(1)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(mol)  # before any CUDA work of the library
+
+    stream = torch.cuda.Stream()
+    prec = ris.FP64 if args.precision == "fp64" else ris.MIXED
+    ctx = ris.Context(device=local, precision=prec, cuda_stream=stream.cuda_stream, profile=1)
+    dev = f"cuda:{local}"
+    coords_d = torch.as_tensor(mol.coords, device=dev)
+    C_d = torch.as_tensor(mol.C, device=dev)
+    eps_d = torch.as_tensor(mol.mo_energy, device=dev)
+    nov = mol.nocc * mol.nvir
+    om_d = torch.zeros(NSTATES, dtype=torch.float64, device=dev)
+    X_d = torch.zeros((NSTATES, mol.nocc, mol.nvir), dtype=torch.float64, device=dev)
+    g_d = torch.zeros((NSTATES, mol.natm, 3), dtype=torch.float64, device=dev)
+    pairs = [(s, s + 1) for s in range(NSTATES - 1)]
+    n_d = torch.zeros((len(pairs), mol.natm, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step_dev():
+        ctx.build_aux(coords_d, mol.shells, mol.aux_j, mol.aux_k)
+        ctx.build_B(C_d, eps_d, mol.nocc)
+        ctx.excite(NSTATES, out=(om_d, X_d, None))
+        ctx.gradient(range(NSTATES), out=g_d)
+        ctx.nac(pairs, out=n_d)
+
+    for _ in range(args.warmup):
+        step_dev()
+    torch.cuda.synchronize()
+    ctx.stats()  # reset the per-class profile
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    l0 = ctx.stats()["launches"]
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step_dev()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    st = ctx.stats()
+    launches = int(st["launches"] - l0)
+    torch.cuda.synchronize()
+    tot = sum(times) / 1000.0
+    if dist:
+        t = torch.tensor([tot], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+        dist.barrier()
+    value = world * args.steps / tot
+
+    # end to end through host buffers
+    h2d = mol.coords.nbytes + mol.C.nbytes + mol.mo_energy.nbytes
+    d2h = 8 * (NSTATES + NSTATES * nov + NSTATES * mol.natm * 3 + len(pairs) * mol.natm * 3)
+    e2e_t = []
+    for it in range(max(2, args.steps // 2) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.build_aux(mol.coords, mol.shells, mol.aux_j, mol.aux_k)
+        ctx.build_B(mol.C, mol.mo_energy, mol.nocc)
+        om, X = ctx.excite(NSTATES)
+        g = ctx.gradient(range(NSTATES))
+        n = ctx.nac(pairs)
+        t1 = time.perf_counter()
+        if it > 0:
+            e2e_t.append(t1 - t0)
+    e2e = world / float(np.mean(e2e_t))
+
+    if rank != 0:
+        return 0
+    peaks, src = _peaks()
+    fp64_peak = peaks["bf16_tflops"] * 1.25 / 2250.0  # measured bf16 x nominal FP64/BF16 ratio
+    classes = {
+        "dgemm_fp64": (st["gemm_ms"], st["gemm_flops"] / 1e12, "tensor", "TFLOP/s", fp64_peak,
+                       f"of {src} bf16 x nominal FP64/BF16 (1.25/2250)"),
+        "int3c_deriv": (st["int3c_deriv_ms"], None, "alu", None, None, ""),
+        "int3c": (st["int3c_ms"], None, "alu", None, None, ""),
+        "contract": (st["contract_ms"], st["contract_bytes"] / 1e9, "hbm", "GB/s", peaks["hbm_gbs"],
+                     f"of {src} HBM copy"),
+        "subspace_eig": (st["eig_ms"], None, "alu", None, None, ""),
+    }
+    dom = max(classes, key=lambda k: classes[k][0])
+    ms, work, bound, unit, peak, note = classes[dom]
+    roof = {"kernel": dom, "bound": bound, "share_of_step": ms / (sum(times) or 1.0)}
+    if work is not None:
+        ach = work / (ms / 1000.0)
+        roof.update({"achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak, "peak_source": note,
+                     "traffic": None})
+    roof["class_ms"] = {k: round(v[0], 3) for k, v in classes.items()}
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32/tf32x3+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "l2": "flushed (512 MB write) between steps", "parallelism": "replicas"},
+            "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "clocks": clk.summary()}
+    if cpu is not None:
+        v, used, sample, w_ref, X_ref, d_ref = cpu
+        om_g = om_d.cpu().numpy()
+        line["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample, "seconds": round(used, 2)}
+        line["error_vs_oracle"] = {"omega_max_rel": float(np.max(np.abs(om_g - w_ref) / np.abs(w_ref)))}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

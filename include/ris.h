@@ -82,6 +82,7 @@ typedef struct {
   int occ_block;      /* occupied-orbital block for streamed B builds; 0 = all */
   void* cuda_stream;  /* cudaStream_t to run on; NULL = the context makes one */
   int device;         /* CUDA device ordinal */
+  int profile;        /* 1: time kernel classes with CUDA events (see ris_get_stats) */
 } ris_options;
 
 typedef struct {
@@ -164,10 +165,15 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
                         int* nauxK, int* npairs_screened);
 
 /*
- * Stage timings of the last calls in milliseconds, measured with CUDA events
- * on the context's stream: [0] aux, [1] B, [2] excite, [3] gradient/nac
- * derivative kernels, [4] number of A-products of the last excite,
- * [5] Davidson iterations of the last excite.  n: entries to copy (<= 16).
+ * Statistics, copied into out[0..n-1] (n <= 32):
+ *   [0] aux, [1] B, [2] excite, [3] gradient/nac: milliseconds of the last
+ *       call of each kind (CUDA events on the context's stream);
+ *   [4] A-products and [5] Davidson iterations of the last excite;
+ *   [15] kernels launched by the library since it was loaded (all contexts);
+ *   with the profile option, per kernel class since the previous call:
+ *   [16] GEMM ms, [17] GEMM flops, [18] 3c-integral ms, [19] shell triples,
+ *   [20] 3c-derivative ms, [21] shell triples, [22] derivative-contraction
+ *   ms, [23] its algorithmic bytes, [24] subspace-eigensolver ms, [25] calls.
  */
 ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n);
 

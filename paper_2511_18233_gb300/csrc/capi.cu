@@ -9,6 +9,64 @@ struct ris_ctx {
   ris::Engine eng;
 };
 
+namespace ris {
+long long g_launches = 0;
+
+namespace {
+struct Rec {
+  int cls;
+  cudaEvent_t a, b;
+  double work;
+};
+bool g_prof_on = false;
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+cudaEvent_t take_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  RIS_CUDA(cudaEventCreate(&e));
+  return e;
+}
+}  // namespace
+
+void prof_enable(bool on) { g_prof_on = on; }
+void prof_begin(int cls, cudaStream_t st) {
+  if (!g_prof_on) return;
+  Rec r{cls, take_event(), nullptr, 0.0};
+  RIS_CUDA(cudaEventRecord(r.a, st));
+  g_recs.push_back(r);
+}
+void prof_end(int cls, cudaStream_t st, double work) {
+  if (!g_prof_on) return;
+  for (auto it = g_recs.rbegin(); it != g_recs.rend(); ++it)
+    if (it->cls == cls && it->b == nullptr) {
+      it->b = take_event();
+      it->work = work;
+      RIS_CUDA(cudaEventRecord(it->b, st));
+      return;
+    }
+}
+void prof_collect(double* ms, double* work) {
+  for (int c = 0; c < kProfN; c++) ms[c] = work[c] = 0.0;
+  for (auto& r : g_recs) {
+    if (r.b) {
+      RIS_CUDA(cudaEventSynchronize(r.b));
+      float t = 0.f;
+      RIS_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+      ms[r.cls] += t;
+      work[r.cls] += r.work;
+      g_pool.push_back(r.b);
+    }
+    g_pool.push_back(r.a);
+  }
+  g_recs.clear();
+}
+}  // namespace ris
+
 namespace {
 
 template <class F>
@@ -59,6 +117,7 @@ ris_status ris_options_default(ris_options* opt) {
   opt->occ_block = 0;
   opt->cuda_stream = nullptr;
   opt->device = 0;
+  opt->profile = 0;
   return RIS_OK;
 }
 
@@ -74,6 +133,7 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
   if (!(o.conv_tol > 0) || o.max_iter <= 0 || !(o.screen_thr >= 0)) return RIS_ERR_ARG;
   c->eng.opt = o;
   c->eng.device = o.device;
+  if (o.profile) ris::prof_enable(true);
   ris_status s = guarded(c.get(), [&] {
     if (o.cuda_stream) {
       c->eng.st = (cudaStream_t)o.cuda_stream;
@@ -197,8 +257,22 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
 }
 
 ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n) {
-  if (!ctx || !out || n < 0 || n > 16) return RIS_ERR_ARG;
-  for (int i = 0; i < n; i++) out[i] = ctx->eng.stats[i];
+  if (!ctx || !out || n < 0 || n > 32) return RIS_ERR_ARG;
+  double all[32] = {0};
+  for (int i = 0; i < 16; i++) all[i] = ctx->eng.stats[i];
+  all[15] = (double)ris::g_launches;
+  try {
+    cudaSetDevice(ctx->eng.device);
+    double ms[ris::kProfN], work[ris::kProfN];
+    ris::prof_collect(ms, work);
+    for (int c = 0; c < ris::kProfN; c++) {
+      all[16 + 2 * c] = ms[c];
+      all[17 + 2 * c] = work[c];
+    }
+  } catch (const ris::Error&) {
+    return RIS_ERR_CUDA;
+  }
+  for (int i = 0; i < n; i++) out[i] = all[i];
   return RIS_OK;
 }
 

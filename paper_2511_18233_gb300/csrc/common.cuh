@@ -5,6 +5,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ris.h"
 
@@ -32,7 +33,21 @@ struct Error {
       throw ::ris::Error{RIS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
   } while (0)
 
-#define RIS_CHECK_LAUNCH() RIS_CUDA(cudaGetLastError())
+// Every kernel launch is followed by RIS_CHECK_LAUNCH, which also counts it.
+extern long long g_launches;
+#define RIS_CHECK_LAUNCH()        \
+  do {                            \
+    ++::ris::g_launches;          \
+    RIS_CUDA(cudaGetLastError()); \
+  } while (0)
+
+// Optional per-kernel-class timing with CUDA events on the launching stream
+// (enabled by the profile option; off by default).
+enum ProfClass { kProfGemm = 0, kProfInt3c, kProfInt3cDeriv, kProfContract, kProfEig, kProfN };
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st, double work);
+void prof_enable(bool on);
+void prof_collect(double* ms, double* work);  // sums per class since the last collect
 
 #define RIS_REQUIRE(cond, code, text)                    \
   do {                                                   \

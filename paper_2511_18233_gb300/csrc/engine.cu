@@ -1042,8 +1042,11 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
       dgemm(true, false, nK, nK, o * o, f, cKoo.p, nK, Goo.p, nK, 1.0, Om.p, nU, st);
     }
     if (rpa) throw Error{RIS_ERR_ARG, "RPA derivatives are not available in this build"};
+    prof_begin(kProfContract, st);
     k_contract<<<nn, 128, 0, st>>>(D.p, Gam.p, nn, nU, Wc.p);
     RIS_CHECK_LAUNCH();
+    // algorithmic bytes: D (3 planes) + Gamma read twice + W written
+    prof_end(kProfContract, st, 8.0 * ((double)gsz * 5.0 + 3.0 * nn * nU));
     k_grad_reduce<<<natm, 128, 0, st>>>(Wc.p, Om.p, dMU.p, ao.fun_atom, aux.fun_atom, nn, nU,
                                         out + (size_t)g * natm * 3);
     RIS_CHECK_LAUNCH();

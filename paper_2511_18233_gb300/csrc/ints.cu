@@ -658,7 +658,9 @@ void int3c(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const do
   int dev;
   RIS_CUDA(cudaGetDevice(&dev));
   const double* tab = boys_table_device(dev);
+  prof_begin(kProfInt3c, st);
   RIS_FOR_CLASSES(launch_int3c, ao, aux, pl, xyz, tab, nJ, nK, TJ, TK, st)
+  prof_end(kProfInt3c, st, (double)pl.npair * aux.n);
 }
 
 void int3c_deriv(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const double* xyz,
@@ -666,7 +668,9 @@ void int3c_deriv(const ShellSet& ao, const ShellSet& aux, const PairList& pl, co
   int dev;
   RIS_CUDA(cudaGetDevice(&dev));
   const double* tab = boys_table_device(dev);
+  prof_begin(kProfInt3cDeriv, st);
   RIS_FOR_CLASSES(launch_int3c_deriv, ao, aux, pl, xyz, tab, D, st)
+  prof_end(kProfInt3cDeriv, st, (double)pl.npair * aux.n);
 }
 
 void int2c(const ShellSet& aux, const double* xyz, double* M, double* dM, cudaStream_t st) {

@@ -12,6 +12,8 @@
 //   inside clusters of close eigenvalues, back-transformation.
 #include <math.h>
 
+#include <algorithm>
+
 #include "la.cuh"
 
 namespace ris {
@@ -110,6 +112,7 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
   if (k <= 0) {  // C = beta C
     RIS_REQUIRE(beta == 0.0, RIS_ERR_ARG, "dgemm: k = 0 with beta != 0");
   }
+  prof_begin(kProfGemm, st);
   if (!transA && !transB)
     k_dgemm<false, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
   else if (!transA && transB)
@@ -119,6 +122,7 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
   else
     k_dgemm<true, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
   RIS_CHECK_LAUNCH();
+  prof_end(kProfGemm, st, 2.0 * m * n * (double)std::max(k, 0) * nb);
 }
 
 // ------------------------------------------------------------------ reductions
@@ -432,8 +436,10 @@ __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* __restrict__ H,
 void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
                     cudaStream_t st) {
   RIS_REQUIRE(k >= 1 && k <= 64 && k <= m, RIS_ERR_ARG, "sym_eig_lowest: bad k");
+  prof_begin(kProfEig, st);
   k_sym_eig<<<1, kEigT, 0, st>>>(H, ldH, m, k, w, V, work);
   RIS_CHECK_LAUNCH();
+  prof_end(kProfEig, st, 1.0);
 }
 
 // ------------------------------------------------------------------ utilities

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
                 ("conv_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("max_subspace", ctypes.c_int), ("screen_thr", ctypes.c_double),
                 ("mem_budget", ctypes.c_size_t), ("occ_block", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 class Shell(ctypes.Structure):
@@ -198,11 +199,15 @@ class Context:
         keys = ["natm", "nao", "nocc", "nauxJ", "nauxK", "npairs"]
         return {k: x.value for k, x in zip(keys, v)}
 
+    STAT_KEYS = {0: "aux_ms", 1: "B_ms", 2: "excite_ms", 3: "deriv_ms", 4: "n_products",
+                 5: "n_iter", 15: "launches", 16: "gemm_ms", 17: "gemm_flops", 18: "int3c_ms",
+                 19: "int3c_triples", 20: "int3c_deriv_ms", 21: "int3c_deriv_triples",
+                 22: "contract_ms", 23: "contract_bytes", 24: "eig_ms", 25: "eig_calls"}
+
     def stats(self):
-        out = (ctypes.c_double * 16)()
-        self._check(self.L.ris_get_stats(self.h, out, 16))
-        keys = ["aux_ms", "B_ms", "excite_ms", "deriv_ms", "n_products", "n_iter"]
-        return {k: out[i] for i, k in enumerate(keys)}
+        out = (ctypes.c_double * 32)()
+        self._check(self.L.ris_get_stats(self.h, out, 32))
+        return {k: out[i] for i, k in self.STAT_KEYS.items()}
 
 
 def debug_boys(m, T):

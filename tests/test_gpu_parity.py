@@ -116,18 +116,30 @@ def test_random_amplitudes_and_device_pointers(ris_mod, small):
     mol, orc, w, X = small
     c = _ctx(ris_mod, mol)
     Xr = synth.random_amplitudes(3, mol.nocc, mol.nvir, seed=5)
-    pairs = [(0, 1), (2, 2), (1, 2)]
+    pairs = [(0, 1), (2, 0), (1, 2)]
+    om = np.array([0.1, 0.2, 0.35])
     ref = orc.pair_energy_derivs(pairs, Xr)
     num = np.zeros((3, mol.natm, 3))
-    c.nac(pairs, X=Xr, omega=np.array([0.1, 0.2, 0.3]), numerator=num)
+    nac = c.nac(pairs, X=Xr, omega=om, numerator=num)
     assert _rel(num, ref) <= 1e-9
-    # the same call with device buffers
+    den = np.array([om[J] - om[I] for I, J in pairs])
+    assert _rel(nac, ref / den[:, None, None]) <= 1e-9
+    g = c.gradient([2, 0], X=Xr)
+    assert _rel(g, orc.pair_energy_derivs([(2, 2), (0, 0)], Xr)) <= 1e-9
+    # a coupling of a state with itself is degenerate: error, numerator still written
+    num2 = np.zeros((1, mol.natm, 3))
+    with pytest.raises(ris_mod.RisError) as e:
+        c.nac([(2, 2)], X=Xr, omega=om, numerator=num2)
+    assert e.value.code == -8
+    np.testing.assert_array_equal(num2[0], g[0])
+    # the same calls with device buffers give identical bits
     Xd = torch.as_tensor(Xr, device="cuda")
-    od = torch.tensor([0.1, 0.2, 0.3], dtype=torch.float64, device="cuda")
+    od = torch.as_tensor(om, device="cuda")
     nd = torch.zeros((3, mol.natm, 3), dtype=torch.float64, device="cuda")
     numd = torch.zeros_like(nd)
     c.nac(pairs, X=Xd, omega=od, out=nd, numerator=numd)
     np.testing.assert_array_equal(numd.cpu().numpy(), num)
+    np.testing.assert_array_equal(nd.cpu().numpy(), nac)
 
 
 @gpu
