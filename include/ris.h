@@ -71,7 +71,10 @@ typedef enum {
 enum { RIS_FP64 = 0, RIS_MIXED = 1 };
 
 typedef struct {
-  int precision;      /* RIS_FP64 or RIS_MIXED */
+  int precision;      /* RIS_FP64, or RIS_MIXED: B^K tensors in FP32 and the exchange part
+                         of every Davidson product as 3xTF32 tensor-core GEMMs with FP32
+                         accumulation (Coulomb part, orthogonalisation and subspace
+                         eigenproblem stay FP64) */
   int rpa;            /* 0: TDA (Y = 0), 1: full RPA (X, Y) */
   double cx;          /* fraction of exact exchange c_x (Eq. g_integral); default 0.25 */
   double conv_tol;    /* Davidson residual 2-norm per state; default 1e-10 */
@@ -83,6 +86,8 @@ typedef struct {
   void* cuda_stream;  /* cudaStream_t to run on; NULL = the context makes one */
   int device;         /* CUDA device ordinal */
   int profile;        /* 1: time kernel classes with CUDA events (see ris_get_stats) */
+  double mixed_tol;   /* RIS_MIXED: residual tolerance of the 3xTF32 Davidson phase; default 1e-6 */
+  int refine;         /* RIS_MIXED: 1 = continue with FP64 products to conv_tol; default 0 */
 } ris_options;
 
 typedef struct {
@@ -184,6 +189,15 @@ ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n);
  * current device.  Synchronises the device; returns 0 or a ris_status.
  */
 int ris_debug_boys(int n, const int* m, const double* T, double* out);
+
+/*
+ * Test hook: C = A . B^T with the library's 3xTF32 tensor-core GEMM (the
+ * kernel behind RIS_MIXED).  A: [M][K], B: [N][K], C: [M][N], FP64 DEVICE
+ * pointers on the current device (inputs are rounded to FP32 and split).
+ * Synchronises the device; returns 0, RIS_ERR_TIMEOUT if a pipeline wait
+ * timed out, or another ris_status.
+ */
+int ris_debug_gemm_tf32x3(int M, int N, int K, const double* A, const double* B, double* C);
 
 /* Message of the last error on this context ("" if none). */
 const char* ris_last_error(const ris_ctx* ctx);

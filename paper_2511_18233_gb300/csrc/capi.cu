@@ -118,6 +118,8 @@ ris_status ris_options_default(ris_options* opt) {
   opt->cuda_stream = nullptr;
   opt->device = 0;
   opt->profile = 0;
+  opt->mixed_tol = 1e-6;
+  opt->refine = 0;
   return RIS_OK;
 }
 
@@ -131,6 +133,7 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
   if (opt) o = *opt;
   if (o.precision != RIS_FP64 && o.precision != RIS_MIXED) return RIS_ERR_ARG;
   if (!(o.conv_tol > 0) || o.max_iter <= 0 || !(o.screen_thr >= 0)) return RIS_ERR_ARG;
+  if (o.precision == RIS_MIXED && !(o.mixed_tol > 0)) return RIS_ERR_ARG;
   c->eng.opt = o;
   c->eng.device = o.device;
   if (o.profile) ris::prof_enable(true);

@@ -52,6 +52,26 @@ void DBuf::release() {
   n = 0;
 }
 
+void FBuf::ensure(size_t count, cudaStream_t st) {
+  if (p && count <= n) return;
+  release();
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    n = 0;
+    throw Error{RIS_ERR_OOM, "device allocation of " + std::to_string(count * 4) + " bytes failed"};
+  }
+  n = count;
+  RIS_CUDA(cudaMemsetAsync(p, 0, count * sizeof(float), st));
+}
+void FBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  n = 0;
+}
+
 static void free_shells(ShellSet& s) {
   int** ip[] = {&s.atom, &s.l, &s.off, &s.jmap, &s.kmap, &s.fun_atom, &s.d_by_l[0], &s.d_by_l[1]};
   for (auto q : ip)
@@ -74,6 +94,7 @@ Engine::~Engine() {
   if (d_jU) cudaFree(d_jU);
   if (d_kU) cudaFree(d_kU);
   if (d_info) cudaFree(d_info);
+  if (d_tcerr) cudaFree(d_tcerr);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   if (own_stream && st) cudaStreamDestroy(st);
@@ -714,7 +735,83 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
   dgemm(false, false, v * v, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKvv.p, nK, st);
   BKvvD.ensure((size_t)v * v * nK);
   transpose_last2(w4.p, v, v, nK, BKvvD.p, st);  // [b][R][a]
+  if (opt.precision == RIS_MIXED) prepare_mixed();
   stage = 2;
+}
+
+// FP32 hi/lo operands of the exchange products (Eq. A_matrix, (ij|ab) term)
+void Engine::prepare_mixed() {
+  const int o = nocc, v = nvir;
+  const int lo4 = ld4(o), lv4 = ld4(v);
+  if (!d_tcerr) {
+    RIS_CUDA(cudaMalloc(&d_tcerr, sizeof(int)));
+    RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
+  }
+  BooH.ensure((size_t)o * nK * lo4, st);
+  BooL.ensure((size_t)o * nK * lo4, st);
+  // per i: [j][R] -> [R][j]
+  split_f64_t(BKoo.p, o, nK, nK, BooH.p, BooL.p, lo4, st, o, (long long)o * nK, (long long)nK * lo4);
+  BvvH.ensure((size_t)v * nK * lv4, st);
+  BvvL.ensure((size_t)v * nK * lv4, st);
+  // BKvvD [b][R][a] = [a][R][b] by symmetry; rows (a,R), b padded
+  split_f64(BKvvD.p, v * nK, v, v, BvvH.p, BvvL.p, lv4, st);
+}
+
+void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
+  const int o = nocc, v = nvir;
+  const long long nov = (long long)o * v;
+  const int lo4 = ld4(o), lv4 = ld4(v);
+  // Coulomb in FP64: out = 2 (X B^J) B^J^T
+  w5.ensure((size_t)nvec * std::max(nJ, 1));
+  dgemm(false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
+  dgemm(false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
+  // X^T per vector, split
+  XtH.ensure((size_t)nvec * v * lo4, st);
+  XtL.ensure((size_t)nvec * v * lo4, st);
+  split_f64_t(Xin, o, v, v, XtH.p, XtL.p, lo4, st, nvec, nov, (long long)v * lo4);
+  // Y[vec][(i,R)][b] = sum_j Boo[(i,R)][j] Xt[vec][b][j]
+  const size_t ysz = (size_t)nvec * o * nK * lv4;
+  if (YH.n < ysz) {
+    YH.ensure(ysz, st);
+    YL.ensure(ysz, st);
+  }
+  TcOperand A, B;
+  A.hi = BooH.p;
+  A.lo = BooL.p;
+  A.rows = o * nK;
+  A.ld = lo4;
+  B.hi = XtH.p;
+  B.lo = XtL.p;
+  B.rows = v;
+  B.ld = lo4;
+  B.bstride = (long long)v * lo4;
+  B.nb = nvec;
+  TcEpilogue e1;
+  e1.mode = kOutSplit;
+  e1.chi = YH.p;
+  e1.clo = YL.p;
+  e1.ldc = lv4;
+  e1.bsc = (long long)o * nK * lv4;
+  tc_gemm(o * nK, v, o, A, B, nvec, e1, d_tcerr, st);
+  // out[(vec,i)][a] += -c_x sum_{(R,b)} Y[(vec,i)][(R,b)] Bvv[a][(R,b)]
+  TcOperand A2, B2;
+  A2.hi = YH.p;
+  A2.lo = YL.p;
+  A2.rows = nvec * o;
+  A2.ld = nK * lv4;
+  B2.hi = BvvH.p;
+  B2.lo = BvvL.p;
+  B2.rows = v;
+  B2.ld = nK * lv4;
+  TcEpilogue e2;
+  e2.mode = kOutF64;
+  e2.c64 = out;
+  e2.ldc = v;
+  e2.alpha = -opt.cx;
+  e2.beta = 1.0;
+  tc_gemm(nvec * o, v, nK * lv4, A2, B2, 1, e2, d_tcerr, st);
+  k_add_diag<<<cdiv(nov * nvec, 256), 256, 0, st>>>(de.p, Xin, nov, nvec, out);
+  RIS_CHECK_LAUNCH();
 }
 
 // ------------------------------------------------------------------ A products
@@ -757,6 +854,8 @@ void Engine::apply(int nvec, const double* Xh, double* out, double* out2) {
     z.ensure(n);
     apply_ApB_AmB(x.p, nvec, y.p, z.p);
     copy_out(out2, z.p, n, st);
+  } else if (opt.precision == RIS_MIXED) {
+    apply_A_mixed(x.p, nvec, y.p);
   } else {
     apply_A_tda(x.p, nvec, y.p);
   }
@@ -770,6 +869,31 @@ void Engine::apply_ApB_AmB(const double*, int, double*, double*) {
 
 // ------------------------------------------------------------------ Davidson (TDA)
 void Engine::davidson_tda(int ns) {
+  if (opt.precision != RIS_MIXED) {
+    dav_core(ns, nullptr, 0, false, opt.conv_tol);
+    return;
+  }
+  dav_core(ns, nullptr, 0, true, std::max(opt.conv_tol, opt.mixed_tol));
+  if (opt.refine) {
+    DBuf g;
+    g.ensure((size_t)ns * nocc * nvir);
+    RIS_CUDA(cudaMemcpyAsync(g.p, X.p, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, st));
+    const double s4 = stats[4], s5 = stats[5];
+    dav_core(ns, g.p, ns, false, opt.conv_tol);
+    stats[6] = stats[4];  // FP64 products of the refinement
+    stats[4] += s4;
+    stats[5] += s5;
+  }
+  int h_err = 0;
+  RIS_CUDA(cudaMemcpyAsync(&h_err, d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RIS_CUDA(cudaStreamSynchronize(st));
+  RIS_REQUIRE(h_err == 0, RIS_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait timed out");
+}
+
+// Block Davidson for the lowest ns eigenpairs of the TDA A.  Starts from
+// unit vectors on the lowest orbital-energy differences, or from nguess
+// given vectors; products in FP64 or (mixed) with 3xTF32 exchange GEMMs.
+void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, double tol) {
   const long long n = (long long)nocc * nvir;
   const int nb0 = (int)std::min<long long>(n, ns + std::min(ns, 8));
   int maxsp = opt.max_subspace > 0 ? opt.max_subspace : std::max(nb0 + 2 * ns, 8 * ns);
@@ -797,13 +921,39 @@ void Engine::davidson_tda(int ns) {
     int* p;
     ~Guard() { cudaFree(p); }
   } guard{d_idx};
-  k_lowest<<<1, 1024, 0, st>>>(de.p, (int)n, nb0, d_idx);
-  RIS_CHECK_LAUNCH();
-  k_unit_rows<<<nb0, 256, 0, st>>>(d_idx, nb0, n, V.p);
-  RIS_CHECK_LAUNCH();
-  apply_A_tda(V.p, nb0, AV.p);
-  int nprod = nb0;
+  auto product = [&](const double* x, int nv, double* y) {
+    if (mixed)
+      apply_A_mixed(x, nv, y);
+    else
+      apply_A_tda(x, nv, y);
+  };
   int m = nb0;
+  if (guess) {
+    // orthonormalise the given block (two CholQR passes)
+    m = nguess;
+    RIS_CUDA(cudaMemcpyAsync(V.p, guess, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, st));
+    for (int pass = 0; pass < 2; pass++) {
+      row_norms(V.p, m, n, G.p, st);
+      k_scale_rows<<<cdiv(n * m, 256), 256, 0, st>>>(V.p, n, m, G.p);
+      RIS_CHECK_LAUNCH();
+      dgemm(false, true, m, m, (int)n, 1.0, V.p, (int)n, V.p, (int)n, 0.0, G.p, m, st);
+      k_cholqr_small<<<1, 32, 0, st>>>(G.p, m, 1e-10, Pm.p, (int*)(Pm.p + m * m), Cc.p);
+      RIS_CHECK_LAUNCH();
+      int nk2 = 0;
+      RIS_CUDA(cudaMemcpyAsync(&nk2, Pm.p + m * m, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RIS_CUDA(cudaStreamSynchronize(st));
+      RIS_REQUIRE(nk2 == m, RIS_ERR_ARG, "initial Davidson block is linearly dependent");
+      dgemm(false, false, m, (int)n, m, 1.0, Pm.p, m, V.p, (int)n, 0.0, tmp.p, (int)n, st);
+      RIS_CUDA(cudaMemcpyAsync(V.p, tmp.p, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, st));
+    }
+  } else {
+    k_lowest<<<1, 1024, 0, st>>>(de.p, (int)n, nb0, d_idx);
+    RIS_CHECK_LAUNCH();
+    k_unit_rows<<<nb0, 256, 0, st>>>(d_idx, nb0, n, V.p);
+    RIS_CHECK_LAUNCH();
+  }
+  product(V.p, m, AV.p);
+  int nprod = m;
   dgemm(false, true, m, m, (int)n, 1.0, V.p, (int)n, AV.p, (int)n, 0.0, Hs.p, maxsp, st);
   std::vector<double> rn(ns);
   bool converged = false;
@@ -821,7 +971,7 @@ void Engine::davidson_tda(int ns) {
     RIS_CUDA(cudaStreamSynchronize(st));
     std::vector<int> u;
     for (int k = 0; k < ns; k++)
-      if (!(sqrt(rn[k]) <= opt.conv_tol)) u.push_back(k);
+      if (!(sqrt(rn[k]) <= tol)) u.push_back(k);
     if (u.empty()) {
       converged = true;
       break;
@@ -861,7 +1011,7 @@ void Engine::davidson_tda(int ns) {
     if (nkeep == 0) break;
     RIS_CUDA(cudaMemcpyAsync(V.p + (size_t)m * n, T.p, sizeof(double) * nt * n,
                              cudaMemcpyDeviceToDevice, st));
-    apply_A_tda(T.p, nt, AV.p + (size_t)m * n);
+    product(T.p, nt, AV.p + (size_t)m * n);
     nprod += nt;
     dgemm(false, true, nt, m + nt, (int)n, 1.0, V.p + (size_t)m * n, (int)n, AV.p, (int)n, 0.0,
           Hs.p + (size_t)m * maxsp, maxsp, st);

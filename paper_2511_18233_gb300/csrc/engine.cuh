@@ -3,6 +3,7 @@
 #include <string>
 #include <vector>
 
+#include "gemm_tc.cuh"
 #include "ints.cuh"
 #include "la.cuh"
 
@@ -15,6 +16,15 @@ struct DBuf {
   void ensure(size_t count);
   void release();
   ~DBuf() { release(); }
+};
+
+// FP32 device buffer (zero-filled when (re)allocated).
+struct FBuf {
+  float* p = nullptr;
+  size_t n = 0;
+  void ensure(size_t count, cudaStream_t st);
+  void release();
+  ~FBuf() { release(); }
 };
 
 struct Engine {
@@ -50,6 +60,13 @@ struct Engine {
   DBuf BKovR;     // [R][i][a] (RPA)
   DBuf cKoo, cKvv, cKov;  // fitting coefficients c = B L^-1, [p][q][P]
 
+  // mixed precision (3xTF32) operands: hi/lo FP32 splits
+  FBuf BooH, BooL;  // B^K_oo as [i][R][j] (ld ld4(nocc))
+  FBuf BvvH, BvvL;  // B^K_vv as [a][R][b] (b padded to ld4(nvir))
+  FBuf XtH, XtL;    // amplitudes transposed [vec][b][j]
+  FBuf YH, YL;      // [vec][i][R][b] = sum_j B^K_oo[R][i][j] X[vec][j][b]
+  int* d_tcerr = nullptr;
+
   // excitations
   int nstates = 0;
   DBuf omega, X, Y;
@@ -73,6 +90,9 @@ struct Engine {
 
   // helpers
   void apply_A_tda(const double* Xin, int nvec, double* out);
+  void apply_A_mixed(const double* Xin, int nvec, double* out);
+  void prepare_mixed();
+  void dav_core(int ns, const double* guess, int nguess, bool mixed, double tol);
   void apply_ApB_AmB(const double* Zin, int nvec, double* outP, double* outM);
   void davidson_tda(int ns);
   void davidson_rpa(int ns);

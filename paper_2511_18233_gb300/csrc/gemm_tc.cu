@@ -1,0 +1,433 @@
+// 3xTF32 GEMM on the 5th-generation tensor cores (tcgen05) of sm_103a.
+//
+// C = A . B^T with A [M][K] and B [N][K] in FP32 storage, each pre-split as
+// x = x_hi + x_lo (x_hi = tf32(x), x_lo = tf32(x - x_hi)).  Every K step
+// issues the three products hi.hi + hi.lo + lo.hi into one FP32 accumulator
+// in tensor memory (the lo.lo term is below FP32 resolution), which keeps
+// about FP32 accuracy at tensor-core rates.
+//
+// Kernel structure (one 128 x 128 output tile per CTA, 128 threads):
+//   warp 0 / lane 0 : TMA producer, 3-stage ring of (A_hi, A_lo, B_hi, B_lo)
+//                     tiles of 128 rows x 32 FP32 (128-byte swizzle)
+//   warp 1          : allocates 128 TMEM columns; lane 0 issues
+//                     tcgen05.mma.kind::tf32 (M=128, N=128, K=8) and commits
+//                     each stage back to the producer through an mbarrier
+//   warps 0-3       : epilogue, tcgen05.ld of TMEM lanes 32w..32w+31
+// All mbarrier waits are bounded (about one second of clock64 cycles); a
+// timeout sets the error flag, drains what this CTA has in flight and frees
+// its TMEM before returning.
+#include <cuda.h>
+
+#include <algorithm>
+
+#include "gemm_tc.cuh"
+
+namespace ris {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 4;                      // 16 KB
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;                  // hi/lo of A and B
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr long long kWaitCycles = 2000000000LL;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    RIS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    RIS_REQUIRE(p && q == cudaDriverEntryPointSuccess, RIS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 3-D map {K, rows, batch} of FP32, box {32, 128, 1}, 128-byte swizzle.
+CUtensorMap make_map(const float* base, int K, int rows, int ld, long long bstride, int nb) {
+  RIS_REQUIRE(((uintptr_t)base & 15) == 0, RIS_ERR_ARG, "tc_gemm: operand not 16-byte aligned");
+  RIS_REQUIRE(ld % 4 == 0 && (nb == 1 || bstride % 4 == 0), RIS_ERR_ARG,
+              "tc_gemm: leading dimension / batch stride not a multiple of 16 bytes");
+  CUtensorMap m;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nb};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)(nb > 1 ? bstride : (long long)ld * rows) * 4};
+  cuuint32_t box[3] = {BK, BM, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  RIS_REQUIRE(r == CUDA_SUCCESS, RIS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+__device__ __forceinline__ uint32_t sa(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(sa(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(b, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* m, uint64_t* bar, int x, int y,
+                                         int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sa(dst)),
+      "l"(m), "r"(sa(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// K-major operand tile of 128 rows x 128 bytes with 128-byte swizzle:
+// start address, leading offset unused (1), stride 1024 B between 8-row
+// groups, descriptor version 1, layout type 2 (SWIZZLE_128B).
+__device__ __forceinline__ uint64_t desc_sw128(const void* p) {
+  const uint64_t a = sa(p);
+  return ((a & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+
+// kind::tf32 instruction descriptor: D FP32 (bit 4), A and B TF32 (2 at bits
+// 7 and 10), both K-major, N>>3 at bit 17, M>>4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+struct TcArgs {
+  int M, N, K, nkb, ksplit, kb_per;
+  int nbA, nbB;
+  TcEpilogue ep;
+  float* partial;  // split-K workspace [ksplit][M][N] (FP32) or null
+  int* err;
+};
+
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mAh,
+                                                     const __grid_constant__ CUtensorMap mAl,
+                                                     const __grid_constant__ CUtensorMap mBh,
+                                                     const __grid_constant__ CUtensorMap mBl,
+                                                     TcArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  int z = blockIdx.z, ks = 0;
+  if (args.ksplit > 1) {
+    ks = z;
+    z = 0;
+  }
+  const int kb0 = ks * args.kb_per, kb1 = min(args.nkb, kb0 + args.kb_per);
+  const int zA = args.nbA > 1 ? z : 0, zB = args.nbB > 1 ? z : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tmem_slot)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int nk = kb1 - kb0;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    int issued = 0;
+    for (int i = 0; i < nk; i++) {
+      const int s = i % STAGES;
+      if (i >= STAGES && !mbar_wait(&empty[s], ((i / STAGES) - 1) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const int kx = (kb0 + i) * BK;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load(st, &mAh, &full[s], kx, m0, zA);
+      tma_load(st + TILE_BYTES, &mAl, &full[s], kx, m0, zA);
+      tma_load(st + 2 * TILE_BYTES, &mBh, &full[s], kx, n0, zB);
+      tma_load(st + 3 * TILE_BYTES, &mBl, &full[s], kx, n0, zB);
+      issued = i + 1;
+    }
+    // drain: make sure every TMA this CTA issued has landed before exit
+    for (int i = std::max(0, issued - STAGES); i < issued; i++)
+      mbar_wait(&full[i % STAGES], (i / STAGES) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int i = 0; i < nk; i++) {
+      const int s = i % STAGES;
+      if (!mbar_wait(&full[s], (i / STAGES) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const uint64_t ah = desc_sw128(st), al = desc_sw128(st + TILE_BYTES);
+      const uint64_t bh = desc_sw128(st + 2 * TILE_BYTES), bl = desc_sw128(st + 3 * TILE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 8; kk++) {
+        const uint64_t off = (uint64_t)((kk * 32) >> 4);  // 32 bytes per K=8 step
+        mma_tf32(tmem, ah + off, bl + off, (i > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, al + off, bh + off, 1u);
+        mma_tf32(tmem, ah + off, bh + off, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  // epilogue
+  const bool ok = mbar_wait(done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok) *abort_flag = 1;
+  __syncthreads();
+  const bool good = *abort_flag == 0 && nk > 0;
+  if (!good && threadIdx.x == 0 && nk > 0) atomicExch(args.err, 1);
+  const int row = m0 + warp * 32 + lane;
+  const TcEpilogue& ep = args.ep;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    float v[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (!good || row >= args.M) continue;
+    if (args.partial) {
+      float* dst = args.partial + ((size_t)ks * args.M + row) * args.N;
+#pragma unroll
+      for (int j = 0; j < 32; j++)
+        if (n0 + c0 + j < args.N) dst[n0 + c0 + j] = v[j];
+    } else if (ep.mode == kOutF64) {
+      double* dst = ep.c64 + (size_t)z * ep.bsc + (size_t)row * ep.ldc;
+#pragma unroll
+      for (int j = 0; j < 32; j++) {
+        const int col = n0 + c0 + j;
+        if (col < args.N)
+          dst[col] = ep.beta == 0.0 ? ep.alpha * v[j] : fma(ep.alpha, (double)v[j], ep.beta * dst[col]);
+      }
+    } else {
+      float* dh = ep.chi + (size_t)z * ep.bsc + (size_t)row * ep.ldc;
+      float* dl = ep.clo + (size_t)z * ep.bsc + (size_t)row * ep.ldc;
+#pragma unroll
+      for (int j = 0; j < 32; j++) {
+        const int col = n0 + c0 + j;
+        if (col < args.N) {
+          const float x = (float)ep.alpha * v[j];
+          const float h = to_tf32(x);
+          dh[col] = h;
+          dl[col] = to_tf32(x - h);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+  }
+}
+
+__global__ void k_tc_reduce(int M, int N, int ksplit, const float* __restrict__ part, double alpha,
+                            double beta, double* __restrict__ C, int ldc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)M * N) return;
+  const int i = (int)(t / N), j = (int)(t % N);
+  double s = 0.0;
+  for (int z = 0; z < ksplit; z++) s += (double)part[(size_t)z * M * N + t];
+  double* p = C + (size_t)i * ldc + j;
+  *p = beta == 0.0 ? alpha * s : fma(alpha, s, beta * *p);
+}
+
+__global__ void k_split(const double* __restrict__ src, int rows, int cols, long long lds, bool trans,
+                        float* __restrict__ hi, float* __restrict__ lo, int ldd, long long sbs,
+                        long long dbs) {
+  // destination [rows'][ldd] with rows' = trans ? cols : rows, batch blockIdx.y
+  const int drows = trans ? cols : rows, dcols = trans ? rows : cols;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)drows * ldd) return;
+  src += (size_t)blockIdx.y * sbs;
+  hi += (size_t)blockIdx.y * dbs;
+  lo += (size_t)blockIdx.y * dbs;
+  const int r = (int)(t / ldd), c = (int)(t % ldd);
+  float x = 0.f;
+  if (c < dcols) x = (float)(trans ? src[(size_t)c * lds + r] : src[(size_t)r * lds + c]);
+  const float h = to_tf32(x);
+  hi[t] = h;
+  lo[t] = to_tf32(x - h);
+}
+
+}  // namespace
+
+void split_f64(const double* src, int rows, int cols, long long lds, float* hi, float* lo, int ldd,
+               cudaStream_t st, int nbatch, long long sbs, long long dbs) {
+  dim3 g(cdiv((long long)rows * ldd, 256), nbatch);
+  k_split<<<g, 256, 0, st>>>(src, rows, cols, lds, false, hi, lo, ldd, sbs, dbs);
+  RIS_CHECK_LAUNCH();
+}
+void split_f64_t(const double* src, int rows, int cols, long long lds, float* hi, float* lo, int ldd,
+                 cudaStream_t st, int nbatch, long long sbs, long long dbs) {
+  dim3 g(cdiv((long long)cols * ldd, 256), nbatch);
+  k_split<<<g, 256, 0, st>>>(src, rows, cols, lds, true, hi, lo, ldd, sbs, dbs);
+  RIS_CHECK_LAUNCH();
+}
+
+void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb, const TcEpilogue& ep,
+             int* d_err, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || nb <= 0) return;
+  RIS_REQUIRE(K > 0, RIS_ERR_ARG, "tc_gemm: K must be positive");
+  RIS_REQUIRE(A.rows >= M && B.rows >= N, RIS_ERR_ARG, "tc_gemm: operand rows");
+  RIS_REQUIRE(nb <= 65535, RIS_ERR_ARG, "tc_gemm: batch too large");
+  static bool attr = false;
+  if (!attr) {
+    RIS_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  const CUtensorMap mAh = make_map(A.hi, K, M, A.ld, A.bstride, A.nb);
+  const CUtensorMap mAl = make_map(A.lo, K, M, A.ld, A.bstride, A.nb);
+  const CUtensorMap mBh = make_map(B.hi, K, N, B.ld, B.bstride, B.nb);
+  const CUtensorMap mBl = make_map(B.lo, K, N, B.ld, B.bstride, B.nb);
+  TcArgs a;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.nkb = cdiv(K, BK);
+  a.nbA = A.nb;
+  a.nbB = B.nb;
+  a.ep = ep;
+  a.err = d_err;
+  a.partial = nullptr;
+  a.ksplit = 1;
+  a.kb_per = 1;
+  const int tiles = cdiv(M, BM) * cdiv(N, BN);
+  a.kb_per = a.nkb;
+  if (nb == 1 && ep.mode == kOutF64 && tiles < 152 && a.nkb >= 8) {
+    int ks = std::max(1, std::min(std::max(1, 152 / tiles), a.nkb / 4));
+    a.kb_per = cdiv(a.nkb, ks);
+    a.ksplit = cdiv(a.nkb, a.kb_per);  // every slice non-empty
+  }
+  float* part = nullptr;
+  if (a.ksplit > 1) {
+    RIS_CUDA(cudaMallocAsync(&part, sizeof(float) * (size_t)a.ksplit * M * N, st));
+    a.partial = part;
+  }
+  dim3 grid(cdiv(N, BN), cdiv(M, BM), a.ksplit > 1 ? a.ksplit : nb);
+  prof_begin(kProfGemm, st);
+  k_tc_gemm<<<grid, 128, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a);
+  RIS_CHECK_LAUNCH();
+  if (a.ksplit > 1) {
+    k_tc_reduce<<<cdiv((long long)M * N, 256), 256, 0, st>>>(M, N, a.ksplit, part, ep.alpha, ep.beta,
+                                                             ep.c64, ep.ldc);
+    RIS_CHECK_LAUNCH();
+    RIS_CUDA(cudaFreeAsync(part, st));
+  }
+  prof_end(kProfGemm, st, 2.0 * M * N * (double)K * nb);
+}
+
+}  // namespace ris
+
+// Test hook (declared in include/ris.h): C = A B^T in 3xTF32 on the
+// tensor cores for FP64 inputs on the current device.
+extern "C" int ris_debug_gemm_tf32x3(int M, int N, int K, const double* A, const double* B, double* C) {
+  using namespace ris;
+  try {
+    cudaStream_t st = 0;
+    const int ld = ld4(K);
+    float *ah, *al, *bh, *bl;
+    int* err;
+    RIS_CUDA(cudaMalloc(&ah, sizeof(float) * (size_t)M * ld));
+    RIS_CUDA(cudaMalloc(&al, sizeof(float) * (size_t)M * ld));
+    RIS_CUDA(cudaMalloc(&bh, sizeof(float) * (size_t)N * ld));
+    RIS_CUDA(cudaMalloc(&bl, sizeof(float) * (size_t)N * ld));
+    RIS_CUDA(cudaMalloc(&err, sizeof(int)));
+    RIS_CUDA(cudaMemset(err, 0, sizeof(int)));
+    split_f64(A, M, K, K, ah, al, ld, st);
+    split_f64(B, N, K, K, bh, bl, ld, st);
+    TcOperand a, b;
+    a.hi = ah; a.lo = al; a.rows = M; a.ld = ld;
+    b.hi = bh; b.lo = bl; b.rows = N; b.ld = ld;
+    TcEpilogue ep;
+    ep.mode = kOutF64;
+    ep.c64 = C;
+    ep.ldc = N;
+    tc_gemm(M, N, K, a, b, 1, ep, err, st);
+    int h_err = 0;
+    RIS_CUDA(cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaFree(ah); cudaFree(al); cudaFree(bh); cudaFree(bl); cudaFree(err);
+    return h_err ? (int)RIS_ERR_TIMEOUT : 0;
+  } catch (const Error& e) {
+    fprintf(stderr, "ris_debug_gemm_tf32x3: %s\n", e.msg.c_str());
+    return (int)e.code;
+  }
+}

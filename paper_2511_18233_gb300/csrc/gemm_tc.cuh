@@ -1,0 +1,53 @@
+// 3xTF32 tensor-core GEMM for sm_103a (tcgen05 + TMA), used by the mixed
+// precision form of the ris contractions.
+#pragma once
+#include "common.cuh"
+
+namespace ris {
+
+// Operand in FP32 storage, split a = hi + lo with hi = tf32(a) and
+// lo = tf32(a - hi), both stored as FP32 bit patterns.  Row-major [rows][ld]
+// with the contraction index K contiguous (K-major); ld % 4 == 0 and the
+// pointers 16-byte aligned (TMA).  Optional batch: rows of batch z start at
+// z * bstride elements (bstride % 4 == 0); nb = 1 means shared.
+struct TcOperand {
+  const float* hi = nullptr;
+  const float* lo = nullptr;
+  int rows = 0, ld = 0;
+  long long bstride = 0;
+  int nb = 1;
+};
+
+// Epilogue: C[z][i][j] for i < M, j < N.
+//   kOutF64:   C64 = alpha * acc + beta * C64   (row stride ldc, batch stride bsc)
+//   kOutSplit: Chi/Clo = tf32 split of alpha * acc (FP32, row stride ldc)
+enum TcOut { kOutF64 = 0, kOutSplit = 1 };
+struct TcEpilogue {
+  int mode = kOutF64;
+  double* c64 = nullptr;
+  float* chi = nullptr;
+  float* clo = nullptr;
+  int ldc = 0;
+  long long bsc = 0;
+  double alpha = 1.0, beta = 0.0;
+};
+
+// C[z] (M x N) = A[z] (M x K) . B[z]^T (N x K), batches z < nb.  With
+// kOutF64 and nb == 1 the K range may be split across CTAs (deterministic
+// two-pass reduction).  *d_err (device int) is set non-zero if a pipeline
+// wait timed out.
+void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb,
+             const TcEpilogue& ep, int* d_err, cudaStream_t st);
+
+// Split FP64 -> (hi, lo) FP32 with a row-major source [rows][cols] (leading
+// dimension lds) into [rows][ldd] (padding columns zero-filled).
+// nbatch matrices at source / destination batch strides sbs / dbs.
+void split_f64(const double* src, int rows, int cols, long long lds, float* hi, float* lo, int ldd,
+               cudaStream_t st, int nbatch = 1, long long sbs = 0, long long dbs = 0);
+// Same with the source transposed: dst[c][r] = src[r][c].
+void split_f64_t(const double* src, int rows, int cols, long long lds, float* hi, float* lo,
+                 int ldd, cudaStream_t st, int nbatch = 1, long long sbs = 0, long long dbs = 0);
+
+inline int ld4(int k) { return (k + 3) & ~3; }
+
+}  // namespace ris

@@ -21,16 +21,27 @@ namespace ris {
 // ------------------------------------------------------------------ GEMM
 constexpr int kBM = 64, kBN = 64, kBK = 16;
 
+// With ksplit > 1 (single batch only) blockIdx.z selects a slice of k of
+// length kchunk and the raw partial product is written to C + z*m*n
+// (ldc = n); k_splitk_reduce then forms alpha*sum + beta*C in a fixed order.
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha,
                                                const double* __restrict__ A, int lda,
                                                const double* __restrict__ B, int ldb, double beta,
-                                               double* __restrict__ C, int ldc, GemmBatch bt) {
-  const int bz = blockIdx.z;
-  const int b1 = bz / bt.nb2, b2 = bz % bt.nb2;
-  A += b1 * bt.sA1 + b2 * bt.sA2;
-  B += b1 * bt.sB1 + b2 * bt.sB2;
-  C += b1 * bt.sC1 + b2 * bt.sC2;
+                                               double* __restrict__ C, int ldc, GemmBatch bt,
+                                               int ksplit, int kchunk) {
+  int kbeg = 0, kend = k;
+  if (ksplit > 1) {
+    kbeg = blockIdx.z * kchunk;
+    kend = min(k, kbeg + kchunk);
+    C += (size_t)blockIdx.z * m * n;
+  } else {
+    const int bz = blockIdx.z;
+    const int b1 = bz / bt.nb2, b2 = bz % bt.nb2;
+    A += b1 * bt.sA1 + b2 * bt.sA2;
+    B += b1 * bt.sB1 + b2 * bt.sB2;
+    C += b1 * bt.sC1 + b2 * bt.sC2;
+  }
   __shared__ double As[kBK][kBM + 1];
   __shared__ double Bs[kBK][kBN + 1];
   const int tid = threadIdx.x;
@@ -41,7 +52,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
   for (int r = 0; r < 4; r++)
 #pragma unroll
     for (int c = 0; c < 4; c++) acc[r][c] = 0.0;
-  for (int k0 = 0; k0 < k; k0 += kBK) {
+  for (int k0 = kbeg; k0 < kend; k0 += kBK) {
 #pragma unroll
     for (int e = tid; e < kBM * kBK; e += 256) {
       int i, kk;
@@ -54,7 +65,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
       }
       const int gi = row0 + i, gk = k0 + kk;
       double v = 0.0;
-      if (gi < m && gk < k) v = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
+      if (gi < m && gk < kend) v = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
       As[kk][i] = v;
     }
 #pragma unroll
@@ -69,7 +80,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
       }
       const int gj = col0 + j, gk = k0 + kk;
       double v = 0.0;
-      if (gj < n && gk < k) v = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
+      if (gj < n && gk < kend) v = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
       Bs[kk][j] = v;
     }
     __syncthreads();
@@ -95,10 +106,25 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
     for (int c = 0; c < 4; c++) {
       const int gj = col0 + tx + 16 * c;
       if (gj >= n) continue;
-      double* p = C + (size_t)gi * ldc + gj;
-      *p = beta == 0.0 ? alpha * acc[r][c] : fma(alpha, acc[r][c], beta * *p);
+      if (ksplit > 1) {
+        C[(size_t)gi * n + gj] = acc[r][c];
+      } else {
+        double* p = C + (size_t)gi * ldc + gj;
+        *p = beta == 0.0 ? alpha * acc[r][c] : fma(alpha, acc[r][c], beta * *p);
+      }
     }
   }
+}
+
+__global__ void k_splitk_reduce(int m, int n, int ksplit, const double* __restrict__ ws,
+                                double alpha, double beta, double* __restrict__ C, int ldc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)m * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  double s = 0.0;
+  for (int z = 0; z < ksplit; z++) s += ws[(size_t)z * m * n + t];
+  double* p = C + (size_t)i * ldc + j;
+  *p = beta == 0.0 ? alpha * s : fma(alpha, s, beta * *p);
 }
 
 void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const double* A, int lda,
@@ -108,20 +134,37 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
   const int nb = bt.nb1 * bt.nb2;
   if (nb <= 0) return;
   RIS_REQUIRE(nb <= 65535, RIS_ERR_ARG, "dgemm: batch too large");
-  dim3 grid(cdiv(n, kBN), cdiv(m, kBM), nb);
+  const int tiles = cdiv(n, kBN) * cdiv(m, kBM);
   if (k <= 0) {  // C = beta C
     RIS_REQUIRE(beta == 0.0, RIS_ERR_ARG, "dgemm: k = 0 with beta != 0");
   }
+  // split k when a single product has too few tiles to fill the GPU
+  int ksplit = 1, kchunk = k;
+  if (nb == 1 && tiles < 152 && k >= 2048) {
+    ksplit = std::min(std::max(1, 2 * 152 / tiles), k / 512);
+    ksplit = std::max(1, std::min(ksplit, 256));
+    kchunk = ((cdiv(k, ksplit) + kBK - 1) / kBK) * kBK;
+    ksplit = cdiv(k, kchunk);
+  }
+  double* ws = nullptr;
+  if (ksplit > 1) RIS_CUDA(cudaMallocAsync(&ws, sizeof(double) * (size_t)ksplit * m * n, st));
+  dim3 grid(cdiv(n, kBN), cdiv(m, kBM), ksplit > 1 ? ksplit : nb);
+  double* Cout = ksplit > 1 ? ws : C;
   prof_begin(kProfGemm, st);
   if (!transA && !transB)
-    k_dgemm<false, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+    k_dgemm<false, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
   else if (!transA && transB)
-    k_dgemm<false, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+    k_dgemm<false, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
   else if (transA && !transB)
-    k_dgemm<true, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+    k_dgemm<true, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
   else
-    k_dgemm<true, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+    k_dgemm<true, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
   RIS_CHECK_LAUNCH();
+  if (ksplit > 1) {
+    k_splitk_reduce<<<cdiv((long long)m * n, 256), 256, 0, st>>>(m, n, ksplit, ws, alpha, beta, C, ldc);
+    RIS_CHECK_LAUNCH();
+    RIS_CUDA(cudaFreeAsync(ws, st));
+  }
   prof_end(kProfGemm, st, 2.0 * m * n * (double)std::max(k, 0) * nb);
 }
 

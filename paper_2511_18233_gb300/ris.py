@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply",
+           "ris_apply", "ris_debug_gemm_tf32x3",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
 
@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
                 ("max_subspace", ctypes.c_int), ("screen_thr", ctypes.c_double),
                 ("mem_budget", ctypes.c_size_t), ("occ_block", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("mixed_tol", ctypes.c_double), ("refine", ctypes.c_int)]
 
 
 class Shell(ctypes.Structure):
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
     L.ris_get_dims.argtypes = [P] + [ctypes.POINTER(i)] * 6
     L.ris_get_stats.argtypes = [P, ctypes.POINTER(d), i]
     L.ris_debug_boys.argtypes = [i, P, P, P]
+    L.ris_debug_gemm_tf32x3.argtypes = [i, i, i, P, P, P]
     L.ris_last_error.argtypes = [P]
     L.ris_last_error.restype = ctypes.c_char_p
     L.ris_destroy.argtypes = [P]
@@ -220,3 +221,18 @@ def debug_boys(m, T):
     if st != 0:
         raise RisError(st, "ris_debug_boys failed")
     return out.cpu().numpy()
+
+
+def debug_gemm_tf32x3(A, B):
+    """C = A B^T through the library's 3xTF32 tcgen05 GEMM (numpy in/out)."""
+    import torch
+    A_t = torch.as_tensor(np.ascontiguousarray(A, dtype=np.float64), device="cuda")
+    B_t = torch.as_tensor(np.ascontiguousarray(B, dtype=np.float64), device="cuda")
+    M, K = A_t.shape
+    N = B_t.shape[0]
+    C_t = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    st = load().ris_debug_gemm_tf32x3(M, N, K, A_t.data_ptr(), B_t.data_ptr(), C_t.data_ptr())
+    torch.cuda.synchronize()
+    if st != 0:
+        raise RisError(st, "ris_debug_gemm_tf32x3 failed")
+    return C_t.cpu().numpy()

@@ -43,6 +43,7 @@ def test_options_defaults(lib):
     o = ris.options()
     assert o.cx == 0.25 and o.conv_tol == 1e-10 and o.max_iter == 100
     assert o.precision == ris.FP64 and o.rpa == 0 and o.screen_thr == 1e-14
+    assert o.mixed_tol == 1e-6 and o.refine == 0 and o.profile == 0
 
 
 def test_create_rejects_bad_options(lib):

@@ -1,0 +1,107 @@
+"""The 3xTF32 tensor-core path against FP64.
+
+Stated error of the mixed form (against the FP64 oracle): excitation
+energies <= 1e-6 Ha, gradients and couplings <= 1e-5 Ha/bohr and 1e-5 1/bohr
+(absolute, per component).  The GEMM itself: 3xTF32 with FP32 accumulation
+keeps |C - A B^T| <= 2e-6 * (|A| |B|^T) elementwise for the sizes here.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_18233_gb300 import synth
+
+gpu = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ris_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_18233_gb300 import build, ris
+    build.build()
+    return ris
+
+
+@gpu
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (200, 130, 71), (7, 300, 1000), (1278, 441, 18648),
+                                   (2982, 441, 71), (64, 64, 4)])
+def test_tc_gemm_against_fp64(ris_mod, M, N, K):
+    rng = np.random.default_rng(M + 7 * N + 13 * K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K))
+    C = ris_mod.debug_gemm_tf32x3(A, B)
+    ref = A @ B.T
+    bound = np.abs(A) @ np.abs(B).T
+    assert np.all(np.abs(C - ref) <= 2e-6 * bound + 1e-300)
+    # and clearly better than a single TF32 product would be
+    assert np.max(np.abs(C - ref) / bound) < 1e-5
+
+
+def _ctx(ris_mod, mol, **opt):
+    c = ris_mod.Context(**opt)
+    c.build_aux(mol.coords, mol.shells, mol.aux_j, mol.aux_k)
+    c.build_B(mol.C, mol.mo_energy, mol.nocc)
+    return c
+
+
+@pytest.fixture(scope="module")
+def small(oracle):
+    mol = synth.workload(0)
+    orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy,
+                           mol.nocc)
+    w, X = orc.tda_dense(6)
+    return mol, orc, w, X
+
+
+@gpu
+def test_mixed_apply(ris_mod, small):
+    mol, orc, w, X = small
+    c = _ctx(ris_mod, mol, precision=ris_mod.MIXED)
+    Xr = synth.random_amplitudes(5, mol.nocc, mol.nvir, seed=2)
+    got = c.apply(Xr)
+    ref = orc.apply_A(Xr)
+    assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref))
+
+
+@gpu
+def test_mixed_small_stated_error(ris_mod, small):
+    mol, orc, w, X = small
+    c = _ctx(ris_mod, mol, precision=ris_mod.MIXED)
+    om, Xg = c.excite(5)
+    assert np.max(np.abs(om - w[:5])) <= 1e-6
+    g = c.gradient(range(5))
+    gref = orc.gradients(range(5), X[:5])
+    assert np.max(np.abs(g - gref)) <= 1e-5
+    nac = c.nac([(0, 1), (2, 3)])
+    nref = orc.nacs([(0, 1), (2, 3)], w[:5], X[:5])
+    assert np.max(np.abs(nac - nref)) <= 1e-5
+
+
+@gpu
+def test_mixed_refined_to_fp64(ris_mod, small):
+    mol, orc, w, X = small
+    c = _ctx(ris_mod, mol, precision=ris_mod.MIXED, refine=1)
+    om, Xg = c.excite(5)
+    np.testing.assert_allclose(om, w[:5], rtol=1e-9)
+    st = c.stats()
+    assert st["n_products"] > 0
+
+
+@gpu
+@pytest.mark.slow
+def test_mixed_chain_stated_error(ris_mod, oracle):
+    mol = synth.workload(1)
+    orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy,
+                           mol.nocc)
+    w, X, _ = orc.tda_davidson(11, tol=1e-10)
+    c = _ctx(ris_mod, mol, precision=ris_mod.MIXED)
+    om, Xg = c.excite(10)
+    assert np.max(np.abs(om - w[:10])) <= 1e-6
+    g = c.gradient(range(10))
+    atoms = [3, 21]
+    gref = orc.gradients([0, 7], X[:10], atoms=atoms)
+    assert np.max(np.abs(g[[0, 7]][:, atoms] - gref[:, atoms])) <= 1e-5
+    nac = c.nac([(s, s + 1) for s in range(9)])
+    nref = orc.nacs([(2, 3)], w[:10], X[:10], atoms=atoms)
+    assert np.max(np.abs(nac[2, atoms] - nref[0, atoms])) <= 1e-5
