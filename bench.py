@@ -255,7 +255,10 @@ def main():
         return 0
     peaks, src = _peaks()
     fp64_peak = peaks["bf16_tflops"] * 1.25 / 2250.0  # measured bf16 x nominal FP64/BF16 ratio
+    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25     # measured bf16 x nominal TF32/BF16 ratio
     classes = {
+        "tc_gemm_3xtf32": (st["tc_gemm_ms"], 3 * st["tc_gemm_flops"] / 1e12, "tensor", "TFLOP/s", tf32_peak,
+                           f"of {src} bf16 x nominal TF32/BF16 (1.1/2.25); achieved counts the 3 TF32 passes"),
         "dgemm_fp64": (st["gemm_ms"], st["gemm_flops"] / 1e12, "tensor", "TFLOP/s", fp64_peak,
                        f"of {src} bf16 x nominal FP64/BF16 (1.25/2250)"),
         "int3c_deriv": (st["int3c_deriv_ms"], None, "alu", None, None, ""),

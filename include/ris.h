@@ -178,7 +178,9 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
  *   with the profile option, per kernel class since the previous call:
  *   [16] GEMM ms, [17] GEMM flops, [18] 3c-integral ms, [19] shell triples,
  *   [20] 3c-derivative ms, [21] shell triples, [22] derivative-contraction
- *   ms, [23] its algorithmic bytes, [24] subspace-eigensolver ms, [25] calls.
+ *   ms, [23] its algorithmic bytes, [24] subspace-eigensolver ms, [25] calls,
+ *   [26] 3xTF32 tensor-core GEMM ms, [27] its algorithmic flops (one per
+ *   multiply-add pair of the product, the three TF32 passes counted once).
  */
 ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n);
 

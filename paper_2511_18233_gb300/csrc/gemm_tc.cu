@@ -383,7 +383,7 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
     a.partial = part;
   }
   dim3 grid(cdiv(N, BN), cdiv(M, BM), a.ksplit > 1 ? a.ksplit : nb);
-  prof_begin(kProfGemm, st);
+  prof_begin(kProfTcGemm, st);
   k_tc_gemm<<<grid, 128, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a);
   RIS_CHECK_LAUNCH();
   if (a.ksplit > 1) {
@@ -392,7 +392,7 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
     RIS_CHECK_LAUNCH();
     RIS_CUDA(cudaFreeAsync(part, st));
   }
-  prof_end(kProfGemm, st, 2.0 * M * N * (double)K * nb);
+  prof_end(kProfTcGemm, st, 2.0 * M * N * (double)K * nb);
 }
 
 }  // namespace ris

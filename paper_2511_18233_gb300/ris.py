@@ -203,7 +203,8 @@ class Context:
     STAT_KEYS = {0: "aux_ms", 1: "B_ms", 2: "excite_ms", 3: "deriv_ms", 4: "n_products",
                  5: "n_iter", 15: "launches", 16: "gemm_ms", 17: "gemm_flops", 18: "int3c_ms",
                  19: "int3c_triples", 20: "int3c_deriv_ms", 21: "int3c_deriv_triples",
-                 22: "contract_ms", 23: "contract_bytes", 24: "eig_ms", 25: "eig_calls"}
+                 22: "contract_ms", 23: "contract_bytes", 24: "eig_ms", 25: "eig_calls",
+                 26: "tc_gemm_ms", 27: "tc_gemm_flops", 6: "refine_products"}
 
     def stats(self):
         out = (ctypes.c_double * 32)()
