@@ -145,6 +145,11 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
       RIS_CUDA(cudaStreamCreateWithFlags(&c->eng.st, cudaStreamNonBlocking));
       c->eng.own_stream = true;
     }
+    // keep freed stream-ordered allocations in the pool between calls
+    cudaMemPool_t pool;
+    RIS_CUDA(cudaDeviceGetDefaultMemPool(&pool, o.device));
+    uint64_t thr = UINT64_MAX;
+    RIS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
     RIS_CUDA(cudaEventCreate(&c->eng.ev0));
     RIS_CUDA(cudaEventCreate(&c->eng.ev1));
   });
@@ -192,8 +197,7 @@ ris_status ris_gradient(ris_ctx* ctx, int n, const int* states, int nx, const do
     StageTimer t(e, 3);
     std::vector<int> pairs(2 * n);
     for (int k = 0; k < n; k++) pairs[2 * k] = pairs[2 * k + 1] = states[k];
-    ris::DBuf out;
-    out.ensure((size_t)n * e.natm * 3);
+    ris::SBuf<double> out((size_t)n * e.natm * 3, e.st);
     e.pair_derivs(n, pairs.data(), nx, X_in, Y_in, out.p);
     RIS_CUDA(cudaMemcpyAsync(grad, out.p, sizeof(double) * n * e.natm * 3, cudaMemcpyDefault, e.st));
     t.stop();
@@ -225,10 +229,7 @@ ris_status ris_nac(ris_ctx* ctx, int npair, const int* pairs, int nx, const doub
     }
     StageTimer t(e, 3);
     const size_t per = (size_t)e.natm * 3;
-    ris::DBuf num, res, dd;
-    num.ensure(npair * per);
-    res.ensure(npair * per);
-    dd.ensure(npair);
+    ris::SBuf<double> num(npair * per, e.st), res(npair * per, e.st), dd(npair, e.st);
     e.pair_derivs(npair, pairs, nx, X_in, Y_in, num.p);
     if (numerator)
       RIS_CUDA(cudaMemcpyAsync(numerator, num.p, sizeof(double) * npair * per, cudaMemcpyDefault, e.st));

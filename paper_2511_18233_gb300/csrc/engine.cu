@@ -212,6 +212,17 @@ static void transpose_last2(const double* in, int nb, int na, int nr, double* ou
   RIS_CHECK_LAUNCH();
 }
 
+// out[b][a][c] = in[a][b][c]
+__global__ void k_permute021(const double* __restrict__ in, int na, int nb, int nc,
+                             double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)na * nb * nc) return;
+  const int c = (int)(t % nc);
+  const long long ab = t / nc;
+  const int b = (int)(ab % nb), a = (int)(ab / nb);
+  out[((size_t)b * na + a) * nc + c] = in[t];
+}
+
 __global__ void k_add_diag(const double* __restrict__ de, const double* __restrict__ X, long long nov,
                            int nvec, double* __restrict__ out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -755,6 +766,83 @@ void Engine::prepare_mixed() {
   BvvL.ensure((size_t)v * nK * lv4, st);
   // BKvvD [b][R][a] = [a][R][b] by symmetry; rows (a,R), b padded
   split_f64(BKvvD.p, v * nK, v, v, BvvH.p, BvvL.p, lv4, st);
+  // fitting coefficients for Gamma: c^vv[a][b][P] -> [P][b][a] (symmetric in a,b)
+  w3.ensure((size_t)v * v * nK);
+  transpose_last2(cKvv.p, 1, v * v, nK, w3.p, st);  // [P][(a,b)]
+  cvvH.ensure((size_t)nK * v * lv4, st);
+  cvvL.ensure((size_t)nK * v * lv4, st);
+  split_f64(w3.p, nK * v, v, v, cvvH.p, cvvL.p, lv4, st);
+  cKooP.ensure((size_t)o * o * nK);
+  transpose_last2(cKoo.p, 1, o * o, nK, cKooP.p, st);  // [P][i][k]
+}
+
+void Engine::gamma_K_mixed(const double* U, const double* V, const double* QU, const double* QV,
+                           double f, double* Gam, double* Om) {
+  const int o = nocc, v = nvir, nn = nao;
+  const int lv4 = ld4(v), kp = ld4(2 * o);
+  SBuf<float> US((size_t)o * lv4, st), UL((size_t)o * lv4, st), VS((size_t)o * lv4, st),
+      VL((size_t)o * lv4, st), ZH, ZL, MH, ML, WH, WL;
+  split_f64(U, o, v, v, US.p, UL.p, lv4, st);
+  split_f64(V, o, v, v, VS.p, VL.p, lv4, st);
+  // Z[j][P][b] = sum_a U[j][a] c^vv[P][b][a]
+  ZH.ensure((size_t)o * nK * lv4, st, true);
+  ZL.ensure((size_t)o * nK * lv4, st, true);
+  {
+    TcOperand A, B;
+    A.hi = US.p; A.lo = UL.p; A.rows = o; A.ld = lv4;
+    B.hi = cvvH.p; B.lo = cvvL.p; B.rows = nK * v; B.ld = lv4;
+    TcEpilogue e;
+    e.mode = kOutSplit; e.chi = ZH.p; e.clo = ZL.p; e.ldc = nK * lv4; e.cin = v; e.cld = lv4;
+    tc_gemm(o, nK * v, v, A, B, 1, e, d_tcerr, st);
+  }
+  // G[j][P][k] = sum_b V[k][b] Z[j][P][b]   (FP64, transposed store)
+  SBuf<double> Gt((size_t)o * nK * o, st), Gp, M1;
+  {
+    TcOperand A, B;
+    A.hi = VS.p; A.lo = VL.p; A.rows = o; A.ld = lv4;
+    B.hi = ZH.p; B.lo = ZL.p; B.rows = nK; B.ld = lv4; B.bstride = (long long)nK * lv4; B.nb = o;
+    TcEpilogue e;
+    e.mode = kOutF64; e.c64 = Gt.p; e.ldc = o; e.bsc = (long long)nK * o; e.trans = true;
+    tc_gemm(o, nK, lv4, A, B, o, e, d_tcerr, st);
+  }
+  // M1[mu][P][0:o] = sum_j C_o[mu][j] G[j][P][k];  M1[mu][P][o:2o] = sum_i QU[i][mu] c^oo[P][i][k]
+  M1.ensure((size_t)nn * nK * 2 * o, st);
+  {
+    GemmBatch bt;
+    bt.nb1 = nK;
+    bt.sB1 = o;
+    bt.sC1 = 2LL * o;
+    dgemm(false, false, nn, o, o, 1.0, C.p, nmo, Gt.p, nK * o, 0.0, M1.p, nK * 2 * o, st, bt);
+    GemmBatch b2;
+    b2.nb1 = nK;
+    b2.sB1 = (long long)o * o;
+    b2.sC1 = 2LL * o;
+    dgemm(true, false, nn, o, o, 1.0, QU, nn, cKooP.p, o, 0.0, M1.p + o, nK * 2 * o, st, b2);
+  }
+  MH.ensure((size_t)nn * nK * kp, st, true);
+  ML.ensure((size_t)nn * nK * kp, st, true);
+  split_f64(M1.p, nn * nK, 2 * o, 2 * o, MH.p, ML.p, kp, st);
+  // W_V[nu][k'] = [C_o | QV^T]
+  w7.ensure((size_t)nn * 2 * o);
+  k_build_W<<<cdiv(nn * 2 * o, 256), 256, 0, st>>>(C.p, nmo, QV, nn, o, w7.p);
+  RIS_CHECK_LAUNCH();
+  WH.ensure((size_t)nn * kp, st, true);
+  WL.ensure((size_t)nn * kp, st, true);
+  split_f64(w7.p, nn, 2 * o, 2 * o, WH.p, WL.p, kp, st);
+  // Gamma[mu][nu][P] += f sum_k' W_V[nu][k'] M1[mu][P][k']
+  {
+    TcOperand A, B;
+    A.hi = WH.p; A.lo = WL.p; A.rows = nn; A.ld = kp;
+    B.hi = MH.p; B.lo = ML.p; B.rows = nK; B.ld = kp; B.bstride = (long long)nK * kp; B.nb = nn;
+    TcEpilogue e;
+    e.mode = kOutF64; e.c64 = Gam; e.ldc = nU; e.bsc = (long long)nn * nU; e.alpha = f; e.beta = 1.0;
+    tc_gemm(nn, nK, 2 * o, A, B, nn, e, d_tcerr, st);
+  }
+  // Omega[A][B] += f sum_{jk} c^oo[A][j][k] G[j][B][k]
+  Gp.ensure((size_t)nK * o * o, st);
+  k_permute021<<<cdiv((long long)o * nK * o, 256), 256, 0, st>>>(Gt.p, o, nK, o, Gp.p);
+  RIS_CHECK_LAUNCH();
+  dgemm(false, true, nK, nK, o * o, f, cKooP.p, o * o, Gp.p, o * o, 1.0, Om, nU, st);
 }
 
 void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
@@ -846,12 +934,10 @@ void Engine::apply(int nvec, const double* Xh, double* out, double* out2) {
   RIS_REQUIRE(nvec >= 1 && Xh && out, RIS_ERR_ARG, "bad ris_apply arguments");
   RIS_REQUIRE((out2 != nullptr) == (opt.rpa != 0), RIS_ERR_ARG, "out2 must be given exactly for RPA");
   const size_t n = (size_t)nvec * nocc * nvir;
-  DBuf x, y, z;
-  x.ensure(n);
-  y.ensure(n);
+  SBuf<double> x(n, st), y(n, st), z;
   copy_in(x.p, Xh, n, st);
   if (opt.rpa) {
-    z.ensure(n);
+    z.ensure(n, st);
     apply_ApB_AmB(x.p, nvec, y.p, z.p);
     copy_out(out2, z.p, n, st);
   } else if (opt.precision == RIS_MIXED) {
@@ -875,8 +961,7 @@ void Engine::davidson_tda(int ns) {
   }
   dav_core(ns, nullptr, 0, true, std::max(opt.conv_tol, opt.mixed_tol));
   if (opt.refine) {
-    DBuf g;
-    g.ensure((size_t)ns * nocc * nvir);
+    SBuf<double> g((size_t)ns * nocc * nvir, st);
     RIS_CUDA(cudaMemcpyAsync(g.p, X.p, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, st));
     const double s4 = stats[4], s5 = stats[5];
     dav_core(ns, g.p, ns, false, opt.conv_tol);
@@ -900,27 +985,13 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
   maxsp = (int)std::min<long long>(std::min(maxsp, 256), n);
   RIS_REQUIRE(maxsp >= nb0, RIS_ERR_ARG, "max_subspace smaller than the initial block");
   const int kkeep = std::min(2 * ns, 64);
-  DBuf V, AV, Hs, S, w, Xr, AXr, Rr, T, Cc, G, Pm, ework, tmp;
-  V.ensure((size_t)maxsp * n);
-  AV.ensure((size_t)maxsp * n);
-  Hs.ensure((size_t)maxsp * maxsp);
-  S.ensure((size_t)64 * maxsp);
-  w.ensure(64);
-  Xr.ensure((size_t)ns * n);
-  AXr.ensure((size_t)ns * n);
-  Rr.ensure((size_t)ns * n);
-  T.ensure((size_t)ns * n);
-  tmp.ensure((size_t)std::max(ns, kkeep) * n);
-  Cc.ensure((size_t)ns * maxsp);
-  G.ensure((size_t)ns * ns);
-  Pm.ensure((size_t)ns * ns + 64);
-  ework.ensure(eig_work_size(maxsp));
-  int* d_idx = nullptr;
-  RIS_CUDA(cudaMalloc(&d_idx, sizeof(int) * (std::max(nb0, ns) + 8)));
-  struct Guard {
-    int* p;
-    ~Guard() { cudaFree(p); }
-  } guard{d_idx};
+  SBuf<double> V((size_t)maxsp * n, st), AV((size_t)maxsp * n, st), Hs((size_t)maxsp * maxsp, st),
+      S((size_t)64 * maxsp, st), w(64, st), Xr((size_t)ns * n, st), AXr((size_t)ns * n, st),
+      Rr((size_t)ns * n, st), T((size_t)ns * n, st), tmp((size_t)std::max(ns, kkeep) * n, st),
+      Cc((size_t)ns * maxsp, st), G((size_t)ns * ns, st), Pm((size_t)ns * ns + 64, st),
+      ework(eig_work_size(maxsp), st);
+  SBuf<int> idxbuf((size_t)std::max(nb0, ns) + 8, st);
+  int* d_idx = idxbuf.p;
   auto product = [&](const double* x, int nv, double* y) {
     if (mixed)
       apply_A_mixed(x, nv, y);
@@ -1073,14 +1144,14 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
   const long long nov = (long long)o * v;
   const double* Xa;
   const double* Ya = nullptr;
-  DBuf xin, yin;
+  SBuf<double> xin, yin;
   if (X_in) {
     RIS_REQUIRE(nx >= 1, RIS_ERR_ARG, "nx must be positive with X_in");
-    xin.ensure((size_t)nx * nov);
+    xin.ensure((size_t)nx * nov, st);
     copy_in(xin.p, X_in, (size_t)nx * nov, st);
     Xa = xin.p;
     if (Y_in) {
-      yin.ensure((size_t)nx * nov);
+      yin.ensure((size_t)nx * nov, st);
       copy_in(yin.p, Y_in, (size_t)nx * nov, st);
       Ya = yin.p;
     }
@@ -1106,21 +1177,19 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
     }
   const int nsu = (int)su.size();
   // per state: R, L, D^R = C_o R C_v^T, c^J, Q_R = R C_v^T, Q_L = L C_v^T
-  DBuf Rs, Ls, DR, cJ, QR, QL, t1;
-  Rs.ensure((size_t)nsu * nov);
-  Ls.ensure((size_t)nsu * nov);
+  SBuf<double> Rs((size_t)nsu * nov, st), Ls((size_t)nsu * nov, st), DR, cJ, QR, QL, t1;
   for (int s = 0; s < nsu; s++) {
     const double* xs = Xa + (size_t)su[s] * nov;
     const double* ys = rpa ? Ya + (size_t)su[s] * nov : nullptr;
     axpby(nov, 1.0, xs, 1.0, ys, Rs.p + s * nov, st);
     axpby(nov, 1.0, xs, -1.0, ys, Ls.p + s * nov, st);
   }
-  DR.ensure((size_t)nsu * nn * nn);
-  t1.ensure((size_t)nn * v);
-  cJ.ensure((size_t)nsu * nJ);
+  DR.ensure((size_t)nsu * nn * nn, st);
+  t1.ensure((size_t)nn * v, st);
+  cJ.ensure((size_t)nsu * nJ, st);
   w5.ensure((size_t)nsu * nJ);
-  QR.ensure((size_t)nsu * o * nn);
-  QL.ensure((size_t)nsu * o * nn);
+  QR.ensure((size_t)nsu * o * nn, st);
+  QL.ensure((size_t)nsu * o * nn, st);
   const double* Co = C.p;
   const double* Cv = C.p + o;
   for (int s = 0; s < nsu; s++) {
@@ -1134,14 +1203,13 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
   dgemm(false, false, nsu, nJ, nJ, 1.0, w5.p, nJ, LJinv.p, nJ, 0.0, cJ.p, nJ, st);
   // per pair
   const size_t gsz = (size_t)nn * nn * nU;
-  DBuf Gam, Om, Wc, Z, Goo, M1, WV, Wt, gtmp;
-  Gam.ensure(gsz);
-  Om.ensure((size_t)nU * nU);
-  Wc.ensure(3 * (size_t)nn * nU);
-  Z.ensure((size_t)o * v * nK);
-  Goo.ensure((size_t)o * o * nK);
-  M1.ensure((size_t)nn * 2 * o * nK);
-  WV.ensure((size_t)nn * 2 * o);
+  SBuf<double> Gam(gsz, st), Om((size_t)nU * nU, st), Wc(3 * (size_t)nn * nU, st), Z, Goo, M1, WV;
+  if (opt.precision != RIS_MIXED) {
+    Z.ensure((size_t)o * v * nK, st);
+    Goo.ensure((size_t)o * o * nK, st);
+    M1.ensure((size_t)nn * 2 * o * nK, st);
+    WV.ensure((size_t)nn * 2 * o, st);
+  }
   const double cx = opt.cx;
   for (int g = 0; g < npair; g++) {
     const int sI = slot[pairs[2 * g]], sJ = slot[pairs[2 * g + 1]];
@@ -1164,6 +1232,10 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
       const double* Vv = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sJ * nov;
       const double* QU = (cmb == 0 ? QR.p : QL.p) + (size_t)sI * o * nn;
       const double* QV = (cmb == 0 ? QR.p : QL.p) + (size_t)sJ * o * nn;
+      if (opt.precision == RIS_MIXED) {
+        gamma_K_mixed(U, Vv, QU, QV, f, Gam.p, Om.p);
+        continue;
+      }
       // Z[j][b][P] = sum_a U[j][a] c^vv[a][b][P]
       dgemm(false, false, o, v * nK, v, 1.0, U, v, cKvv.p, v * nK, 0.0, Z.p, v * nK, st);
       // G[j][k][P] = sum_b V[k][b] Z[j][b][P]
@@ -1200,6 +1272,12 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
     k_grad_reduce<<<natm, 128, 0, st>>>(Wc.p, Om.p, dMU.p, ao.fun_atom, aux.fun_atom, nn, nU,
                                         out + (size_t)g * natm * 3);
     RIS_CHECK_LAUNCH();
+  }
+  if (opt.precision == RIS_MIXED) {
+    int h_err = 0;
+    RIS_CUDA(cudaMemcpyAsync(&h_err, d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+    RIS_REQUIRE(h_err == 0, RIS_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait timed out");
   }
 }
 

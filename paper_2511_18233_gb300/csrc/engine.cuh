@@ -18,6 +18,40 @@ struct DBuf {
   ~DBuf() { release(); }
 };
 
+// Stream-ordered temporary (cudaMallocAsync / cudaFreeAsync from the
+// device's memory pool, which the context keeps from releasing), optionally
+// zero-filled.
+template <class T>
+struct SBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t st = nullptr;
+  SBuf() = default;
+  SBuf(size_t count, cudaStream_t s, bool zero = false) { ensure(count, s, zero); }
+  void ensure(size_t count, cudaStream_t s, bool zero = false) {
+    if (p && count <= n) return;
+    release();
+    st = s;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      throw Error{RIS_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+    }
+    n = count;
+    if (zero) RIS_CUDA(cudaMemsetAsync(p, 0, count * sizeof(T), st));
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+    n = 0;
+  }
+  ~SBuf() { release(); }
+  SBuf(const SBuf&) = delete;
+  SBuf& operator=(const SBuf&) = delete;
+};
+
 // FP32 device buffer (zero-filled when (re)allocated).
 struct FBuf {
   float* p = nullptr;
@@ -65,6 +99,8 @@ struct Engine {
   FBuf BvvH, BvvL;  // B^K_vv as [a][R][b] (b padded to ld4(nvir))
   FBuf XtH, XtL;    // amplitudes transposed [vec][b][j]
   FBuf YH, YL;      // [vec][i][R][b] = sum_j B^K_oo[R][i][j] X[vec][j][b]
+  FBuf cvvH, cvvL;  // c^K_vv as [(P,b)][a] (a padded)
+  DBuf cKooP;       // c^K_oo as [P][i][k] (FP64)
   int* d_tcerr = nullptr;
 
   // excitations
@@ -92,6 +128,9 @@ struct Engine {
   void apply_A_tda(const double* Xin, int nvec, double* out);
   void apply_A_mixed(const double* Xin, int nvec, double* out);
   void prepare_mixed();
+  // exchange part of Gamma / Omega for one (U,V) pair with weight f (3xTF32)
+  void gamma_K_mixed(const double* U, const double* V, const double* QU, const double* QV, double f,
+                     double* Gam, double* Om);
   void dav_core(int ns, const double* guess, int nguess, bool mixed, double tol);
   void apply_ApB_AmB(const double* Zin, int nvec, double* outP, double* outM);
   void davidson_tda(int ns);

@@ -269,25 +269,22 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
 #pragma unroll
       for (int j = 0; j < 32; j++)
         if (n0 + c0 + j < args.N) dst[n0 + c0 + j] = v[j];
-    } else if (ep.mode == kOutF64) {
-      double* dst = ep.c64 + (size_t)z * ep.bsc + (size_t)row * ep.ldc;
-#pragma unroll
-      for (int j = 0; j < 32; j++) {
-        const int col = n0 + c0 + j;
-        if (col < args.N)
-          dst[col] = ep.beta == 0.0 ? ep.alpha * v[j] : fma(ep.alpha, (double)v[j], ep.beta * dst[col]);
-      }
     } else {
-      float* dh = ep.chi + (size_t)z * ep.bsc + (size_t)row * ep.ldc;
-      float* dl = ep.clo + (size_t)z * ep.bsc + (size_t)row * ep.ldc;
 #pragma unroll
       for (int j = 0; j < 32; j++) {
         const int col = n0 + c0 + j;
-        if (col < args.N) {
+        if (col >= args.N) continue;
+        const long long cpos = ep.cin > 0 ? (long long)(col / ep.cin) * ep.cld + col % ep.cin : col;
+        const size_t off = (size_t)z * ep.bsc +
+                           (ep.trans ? (size_t)cpos * ep.ldc + row : (size_t)row * ep.ldc + cpos);
+        if (ep.mode == kOutF64) {
+          double* p = ep.c64 + off;
+          *p = ep.beta == 0.0 ? ep.alpha * v[j] : fma(ep.alpha, (double)v[j], ep.beta * *p);
+        } else {
           const float x = (float)ep.alpha * v[j];
           const float h = to_tf32(x);
-          dh[col] = h;
-          dl[col] = to_tf32(x - h);
+          ep.chi[off] = h;
+          ep.clo[off] = to_tf32(x - h);
         }
       }
     }
@@ -372,7 +369,7 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
   a.kb_per = 1;
   const int tiles = cdiv(M, BM) * cdiv(N, BN);
   a.kb_per = a.nkb;
-  if (nb == 1 && ep.mode == kOutF64 && tiles < 152 && a.nkb >= 8) {
+  if (nb == 1 && ep.mode == kOutF64 && !ep.trans && ep.cin == 0 && tiles < 152 && a.nkb >= 8) {
     int ks = std::max(1, std::min(std::max(1, 152 / tiles), a.nkb / 4));
     a.kb_per = cdiv(a.nkb, ks);
     a.ksplit = cdiv(a.nkb, a.kb_per);  // every slice non-empty

@@ -22,6 +22,9 @@ struct TcOperand {
 //   kOutF64:   C64 = alpha * acc + beta * C64   (row stride ldc, batch stride bsc)
 //   kOutSplit: Chi/Clo = tf32 split of alpha * acc (FP32, row stride ldc)
 enum TcOut { kOutF64 = 0, kOutSplit = 1 };
+// Column j is stored at (j / cin) * cld + j % cin when cin > 0 (blocks of
+// cin columns at stride cld, e.g. a padded inner index); with trans the
+// element (i, j) goes to j * ldc + i instead of i * ldc + j.
 struct TcEpilogue {
   int mode = kOutF64;
   double* c64 = nullptr;
@@ -30,6 +33,9 @@ struct TcEpilogue {
   int ldc = 0;
   long long bsc = 0;
   double alpha = 1.0, beta = 0.0;
+  int cin = 0;
+  long long cld = 0;
+  bool trans = false;
 };
 
 // C[z] (M x N) = A[z] (M x K) . B[z]^T (N x K), batches z < nb.  With
