@@ -201,6 +201,28 @@ int ris_debug_boys(int n, const int* m, const double* T, double* out);
  */
 int ris_debug_gemm_tf32x3(int M, int N, int K, const double* A, const double* B, double* C);
 
+/*
+ * Allocation-free 3xTF32 GEMM: C = A . B^T computed exactly like
+ * ris_debug_gemm_tf32x3, but without allocating device memory.  The paper
+ * has no counterpart; this exists for callers that cannot allocate at the
+ * point of the call, for example a serving process that hands all free
+ * device memory to its own pool up front, or a latency-critical loop where an
+ * allocation could block or fail.
+ * A: [M][K], B: [N][K], C: [M][N], FP64 DEVICE pointers on the current
+ * device; stream: a cudaStream_t or NULL.  Work space comes from one 32 MiB
+ * device array that the library reserves on every GPU it is loaded on and
+ * holds until the process exits; the call returns RIS_ERR_ARG (with a
+ * message on stderr) when 2*(M+N)*ceil4(K) + 64 exceeds its 8 Mi floats.
+ * The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress), so make that call before any stream capture.
+ * Every call uses the same array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The call synchronises the stream; returns 0, RIS_ERR_TIMEOUT if a
+ * pipeline wait timed out, or another ris_status.
+ */
+int ris_gemm_tf32x3_noalloc(int M, int N, int K, const double* A, const double* B, double* C,
+                            void* stream);
+
 /* Message of the last error on this context ("" if none). */
 const char* ris_last_error(const ris_ctx* ctx);
 

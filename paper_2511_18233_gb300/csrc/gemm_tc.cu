@@ -19,6 +19,8 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "gemm_tc.cuh"
 
@@ -341,7 +343,7 @@ void split_f64_t(const double* src, int rows, int cols, long long lds, float* hi
 }
 
 void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb, const TcEpilogue& ep,
-             int* d_err, cudaStream_t st) {
+             int* d_err, cudaStream_t st, float* ws, size_t ws_floats, bool allow_alloc) {
   if (M <= 0 || N <= 0 || nb <= 0) return;
   RIS_REQUIRE(K > 0, RIS_ERR_ARG, "tc_gemm: K must be positive");
   RIS_REQUIRE(A.rows >= M && B.rows >= N, RIS_ERR_ARG, "tc_gemm: operand rows");
@@ -375,8 +377,18 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
     a.ksplit = cdiv(a.nkb, a.kb_per);  // every slice non-empty
   }
   float* part = nullptr;
+  bool own_part = false;
   if (a.ksplit > 1) {
-    RIS_CUDA(cudaMallocAsync(&part, sizeof(float) * (size_t)a.ksplit * M * N, st));
+    const size_t need = (size_t)a.ksplit * M * N;
+    if (ws && ws_floats >= need) {
+      part = ws;
+    } else if (allow_alloc) {
+      RIS_CUDA(cudaMallocAsync(&part, sizeof(float) * need, st));
+      own_part = true;
+    } else {
+      a.ksplit = 1;
+      a.kb_per = a.nkb;
+    }
     a.partial = part;
   }
   dim3 grid(cdiv(N, BN), cdiv(M, BM), a.ksplit > 1 ? a.ksplit : nb);
@@ -387,7 +399,7 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
     k_tc_reduce<<<cdiv((long long)M * N, 256), 256, 0, st>>>(M, N, a.ksplit, part, ep.alpha, ep.beta,
                                                              ep.c64, ep.ldc);
     RIS_CHECK_LAUNCH();
-    RIS_CUDA(cudaFreeAsync(part, st));
+    if (own_part) RIS_CUDA(cudaFreeAsync(part, st));
   }
   prof_end(kProfTcGemm, st, 2.0 * M * N * (double)K * nb);
 }
@@ -425,6 +437,80 @@ extern "C" int ris_debug_gemm_tf32x3(int M, int N, int K, const double* A, const
     return h_err ? (int)RIS_ERR_TIMEOUT : 0;
   } catch (const Error& e) {
     fprintf(stderr, "ris_debug_gemm_tf32x3: %s\n", e.msg.c_str());
+    return (int)e.code;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the 3xTF32 GEMM (declared in include/ris.h).
+//
+// Its scratch lives in one file-scope device array, set aside when the
+// library is loaded on a device and held until the process exits:
+//   [0, 64)       the pipeline error flag (cleared at the start of each call)
+//   [64, ...)     hi/lo FP32 splits of A and B, then split-K partial sums.
+// Host code cannot use the array's name as a device address, so the first
+// call on each device looks its address up with cudaGetSymbolAddress (with
+// that device current) and caches it.
+namespace ris {
+namespace {
+constexpr size_t kNoAllocFloats = (size_t)8 << 20;  // 8 Mi floats = 32 MiB
+__device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+float* noalloc_scratch() {
+  static std::mutex mu;
+  static std::map<int, float*> addr;
+  int dev = 0;
+  RIS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(mu);
+  auto it = addr.find(dev);
+  if (it != addr.end()) return it->second;
+  float* p = nullptr;
+  RIS_CUDA(cudaGetSymbolAddress((void**)&p, g_noalloc_scratch));
+  addr[dev] = p;
+  return p;
+}
+}  // namespace
+}  // namespace ris
+
+extern "C" int ris_gemm_tf32x3_noalloc(int M, int N, int K, const double* A, const double* B,
+                                       double* C, void* stream) {
+  using namespace ris;
+  try {
+    if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return (int)RIS_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t ld = (size_t)ld4(K);
+    const size_t need = 64 + 2 * ((size_t)M + N) * ld;
+    if (need > kNoAllocFloats) {
+      fprintf(stderr,
+              "ris_gemm_tf32x3_noalloc: 2*(M+N)*ceil4(K) + 64 = %zu floats exceeds the "
+              "preallocated scratch of %zu floats\n",
+              need, kNoAllocFloats);
+      return (int)RIS_ERR_ARG;
+    }
+    float* base = noalloc_scratch();
+    int* err = (int*)base;
+    float* ah = base + 64;
+    float* al = ah + (size_t)M * ld;
+    float* bh = al + (size_t)M * ld;
+    float* bl = bh + (size_t)N * ld;
+    float* ws = bl + (size_t)N * ld;
+    RIS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    split_f64(A, M, K, K, ah, al, (int)ld, st);
+    split_f64(B, N, K, K, bh, bl, (int)ld, st);
+    TcOperand a, b;
+    a.hi = ah; a.lo = al; a.rows = M; a.ld = (int)ld;
+    b.hi = bh; b.lo = bl; b.rows = N; b.ld = (int)ld;
+    TcEpilogue ep;
+    ep.mode = kOutF64;
+    ep.c64 = C;
+    ep.ldc = N;
+    tc_gemm(M, N, K, a, b, 1, ep, err, st, ws, kNoAllocFloats - need, false);
+    int h_err = 0;
+    RIS_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+    return h_err ? (int)RIS_ERR_TIMEOUT : 0;
+  } catch (const Error& e) {
+    fprintf(stderr, "ris_gemm_tf32x3_noalloc: %s\n", e.msg.c_str());
     return (int)e.code;
   }
 }

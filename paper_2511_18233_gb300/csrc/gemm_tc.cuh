@@ -42,8 +42,12 @@ struct TcEpilogue {
 // kOutF64 and nb == 1 the K range may be split across CTAs (deterministic
 // two-pass reduction).  *d_err (device int) is set non-zero if a pipeline
 // wait timed out.
+// ws / ws_floats: optional caller-owned FP32 workspace for the split-K
+// partial sums; with allow_alloc false the GEMM never allocates (it splits K
+// only when ws is large enough).
 void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb,
-             const TcEpilogue& ep, int* d_err, cudaStream_t st);
+             const TcEpilogue& ep, int* d_err, cudaStream_t st, float* ws = nullptr,
+             size_t ws_floats = 0, bool allow_alloc = true);
 
 // Split FP64 -> (hi, lo) FP32 with a row-major source [rows][cols] (leading
 // dimension lds) into [rows][ldd] (padding columns zero-filled).

@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_debug_gemm_tf32x3",
+           "ris_apply", "ris_debug_gemm_tf32x3", "ris_gemm_tf32x3_noalloc",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
 
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
     L.ris_get_stats.argtypes = [P, ctypes.POINTER(d), i]
     L.ris_debug_boys.argtypes = [i, P, P, P]
     L.ris_debug_gemm_tf32x3.argtypes = [i, i, i, P, P, P]
+    L.ris_gemm_tf32x3_noalloc.argtypes = [i, i, i, P, P, P, P]
     L.ris_last_error.argtypes = [P]
     L.ris_last_error.restype = ctypes.c_char_p
     L.ris_destroy.argtypes = [P]
@@ -237,3 +238,12 @@ def debug_gemm_tf32x3(A, B):
     if st != 0:
         raise RisError(st, "ris_debug_gemm_tf32x3 failed")
     return C_t.cpu().numpy()
+
+
+def gemm_tf32x3_noalloc(A_t, B_t, C_t, stream=None) -> int:
+    """C_t = A_t B_t^T (CUDA float64 tensors) through the allocation-free
+    entry point; returns the status code."""
+    M, K = A_t.shape
+    N = B_t.shape[0]
+    return load().ris_gemm_tf32x3_noalloc(int(M), int(N), int(K), A_t.data_ptr(), B_t.data_ptr(),
+                                          C_t.data_ptr(), stream)
