@@ -225,6 +225,8 @@ def main():
             times.append(e0.elapsed_time(e1))
     st = ctx.stats()
     launches = int(st["launches"] - l0)
+    stages = {k: round(st[k], 3) for k in ("aux_ms", "B_ms", "excite_ms", "deriv_ms")}
+    stages.update({"davidson_products": int(st["n_products"]), "davidson_iterations": int(st["n_iter"])})
     torch.cuda.synchronize()
     tot = sum(times) / 1000.0
     if dist:
@@ -285,6 +287,7 @@ def main():
             "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches,
+            "stages_last_step": stages,
             "roofline": roof,
             "clocks": clk.summary()}
     if cpu is not None:

@@ -212,6 +212,15 @@ static void transpose_last2(const double* in, int nb, int na, int nr, double* ou
   RIS_CHECK_LAUNCH();
 }
 
+// dst[r][c0 + c] = src[r][c] for c < ncol (FP32, row strides lds / ldd)
+__global__ void k_copy_cols(const float* __restrict__ src, int lds, float* __restrict__ dst, int ldd,
+                            int c0, int nrow, int ncol) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nrow * ncol) return;
+  const int r = (int)(t / ncol), c = (int)(t % ncol);
+  dst[(size_t)r * ldd + c0 + c] = src[(size_t)r * lds + c];
+}
+
 // out[b][a][c] = in[a][b][c]
 __global__ void k_permute021(const double* __restrict__ in, int na, int nb, int nc,
                              double* __restrict__ out) {
@@ -689,12 +698,17 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
   copy_in(eps.p, eps_in, nmo, st);
   k_orb_diff<<<cdiv(nov, 256), 256, 0, st>>>(eps.p, o, v, de.p);
   RIS_CHECK_LAUNCH();
+  if (opt.precision == RIS_MIXED) {
+    build_B_mixed();
+    stage = 2;
+    return;
+  }
   const double* Co = C.p;
   const double* Cv = C.p + o;
   // Coulomb: H[i][nu][P] = sum_mu C_mu,i T[mu][nu][P]; B[i][a][P]; B L^-T
   w2.ensure((size_t)o * n * std::max(nJ, nK));
   dgemm(true, false, o, n * nJ, n, 1.0, Co, nmo, TJ.p, n * nJ, 0.0, w2.p, n * nJ, st);
-  w3.ensure((size_t)nov * std::max(nJ, nK));
+  w3.ensure((size_t)std::max(nov, (long long)o * o) * std::max(nJ, nK));
   {
     GemmBatch bt;
     bt.nb1 = o;
@@ -776,130 +790,140 @@ void Engine::prepare_mixed() {
   transpose_last2(cKoo.p, 1, o * o, nK, cKooP.p, st);  // [P][i][k]
 }
 
-void Engine::gamma_K_mixed(const double* U, const double* V, const double* QU, const double* QV,
-                           double f, double* Gam, double* Om) {
-  const int o = nocc, v = nvir, nn = nao;
-  const int lv4 = ld4(v), kp = ld4(2 * o);
-  SBuf<float> US((size_t)o * lv4, st), UL((size_t)o * lv4, st), VS((size_t)o * lv4, st),
-      VL((size_t)o * lv4, st), ZH, ZL, MH, ML, WH, WL;
-  split_f64(U, o, v, v, US.p, UL.p, lv4, st);
-  split_f64(V, o, v, v, VS.p, VL.p, lv4, st);
-  // Z[j][P][b] = sum_a U[j][a] c^vv[P][b][a]
-  ZH.ensure((size_t)o * nK * lv4, st, true);
-  ZL.ensure((size_t)o * nK * lv4, st, true);
-  {
-    TcOperand A, B;
-    A.hi = US.p; A.lo = UL.p; A.rows = o; A.ld = lv4;
-    B.hi = cvvH.p; B.lo = cvvL.p; B.rows = nK * v; B.ld = lv4;
-    TcEpilogue e;
-    e.mode = kOutSplit; e.chi = ZH.p; e.clo = ZL.p; e.ldc = nK * lv4; e.cin = v; e.cld = lv4;
-    tc_gemm(o, nK * v, v, A, B, 1, e, d_tcerr, st);
-  }
-  // G[j][P][k] = sum_b V[k][b] Z[j][P][b]   (FP64, transposed store)
-  SBuf<double> Gt((size_t)o * nK * o, st), Gp, M1;
-  {
-    TcOperand A, B;
-    A.hi = VS.p; A.lo = VL.p; A.rows = o; A.ld = lv4;
-    B.hi = ZH.p; B.lo = ZL.p; B.rows = nK; B.ld = lv4; B.bstride = (long long)nK * lv4; B.nb = o;
-    TcEpilogue e;
-    e.mode = kOutF64; e.c64 = Gt.p; e.ldc = o; e.bsc = (long long)nK * o; e.trans = true;
-    tc_gemm(o, nK, lv4, A, B, o, e, d_tcerr, st);
-  }
-  // M1[mu][P][0:o] = sum_j C_o[mu][j] G[j][P][k];  M1[mu][P][o:2o] = sum_i QU[i][mu] c^oo[P][i][k]
-  M1.ensure((size_t)nn * nK * 2 * o, st);
-  {
-    GemmBatch bt;
-    bt.nb1 = nK;
-    bt.sB1 = o;
-    bt.sC1 = 2LL * o;
-    dgemm(false, false, nn, o, o, 1.0, C.p, nmo, Gt.p, nK * o, 0.0, M1.p, nK * 2 * o, st, bt);
-    GemmBatch b2;
-    b2.nb1 = nK;
-    b2.sB1 = (long long)o * o;
-    b2.sC1 = 2LL * o;
-    dgemm(true, false, nn, o, o, 1.0, QU, nn, cKooP.p, o, 0.0, M1.p + o, nK * 2 * o, st, b2);
-  }
-  MH.ensure((size_t)nn * nK * kp, st, true);
-  ML.ensure((size_t)nn * nK * kp, st, true);
-  split_f64(M1.p, nn * nK, 2 * o, 2 * o, MH.p, ML.p, kp, st);
-  // W_V[nu][k'] = [C_o | QV^T]
-  w7.ensure((size_t)nn * 2 * o);
-  k_build_W<<<cdiv(nn * 2 * o, 256), 256, 0, st>>>(C.p, nmo, QV, nn, o, w7.p);
-  RIS_CHECK_LAUNCH();
-  WH.ensure((size_t)nn * kp, st, true);
-  WL.ensure((size_t)nn * kp, st, true);
-  split_f64(w7.p, nn, 2 * o, 2 * o, WH.p, WL.p, kp, st);
-  // Gamma[mu][nu][P] += f sum_k' W_V[nu][k'] M1[mu][P][k']
-  {
-    TcOperand A, B;
-    A.hi = WH.p; A.lo = WL.p; A.rows = nn; A.ld = kp;
-    B.hi = MH.p; B.lo = ML.p; B.rows = nK; B.ld = kp; B.bstride = (long long)nK * kp; B.nb = nn;
-    TcEpilogue e;
-    e.mode = kOutF64; e.c64 = Gam; e.ldc = nU; e.bsc = (long long)nn * nU; e.alpha = f; e.beta = 1.0;
-    tc_gemm(nn, nK, 2 * o, A, B, nn, e, d_tcerr, st);
-  }
-  // Omega[A][B] += f sum_{jk} c^oo[A][j][k] G[j][B][k]
-  Gp.ensure((size_t)nK * o * o, st);
-  k_permute021<<<cdiv((long long)o * nK * o, 256), 256, 0, st>>>(Gt.p, o, nK, o, Gp.p);
-  RIS_CHECK_LAUNCH();
-  dgemm(false, true, nK, nK, o * o, f, cKooP.p, o * o, Gp.p, o * o, 1.0, Om, nU, st);
+// One tensor-core GEMM with split operands; helper for the mixed path.
+static void tcg(int M, int N, int K, const float* ah, const float* al, int lda, const float* bh,
+                const float* bl, int ldb, long long bsb, int nb, const TcEpilogue& e, int* err,
+                cudaStream_t st, long long bsa = 0, int nba = 1) {
+  TcOperand A, B;
+  A.hi = ah; A.lo = al; A.rows = M; A.ld = lda; A.bstride = bsa; A.nb = nba;
+  B.hi = bh; B.lo = bl; B.rows = N; B.ld = ldb; B.bstride = bsb; B.nb = nb > 1 ? nb : 1;
+  tc_gemm(M, N, K, A, B, nb, e, err, st);
+}
+static TcEpilogue ep_split(float* h, float* l, long long rs, long long cs = 1, long long bsc = 0) {
+  TcEpilogue e;
+  e.mode = kOutSplit; e.chi = h; e.clo = l; e.rs = rs; e.cs = cs; e.bsc = bsc;
+  return e;
+}
+static TcEpilogue ep_f64(double* c, long long rs, long long bsc = 0, double alpha = 1.0,
+                         double beta = 0.0, long long cs = 1) {
+  TcEpilogue e;
+  e.mode = kOutF64; e.c64 = c; e.rs = rs; e.cs = cs; e.bsc = bsc; e.alpha = alpha; e.beta = beta;
+  return e;
 }
 
-void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
-  const int o = nocc, v = nvir;
-  const long long nov = (long long)o * v;
-  const int lo4 = ld4(o), lv4 = ld4(v);
-  // Coulomb in FP64: out = 2 (X B^J) B^J^T
-  w5.ensure((size_t)nvec * std::max(nJ, 1));
-  dgemm(false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
-  dgemm(false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
-  // X^T per vector, split
-  XtH.ensure((size_t)nvec * v * lo4, st);
-  XtL.ensure((size_t)nvec * v * lo4, st);
-  split_f64_t(Xin, o, v, v, XtH.p, XtL.p, lo4, st, nvec, nov, (long long)v * lo4);
-  // Y[vec][(i,R)][b] = sum_j Boo[(i,R)][j] Xt[vec][b][j]
-  const size_t ysz = (size_t)nvec * o * nK * lv4;
-  if (YH.n < ysz) {
-    YH.ensure(ysz, st);
-    YL.ensure(ysz, st);
+void Engine::gamma_K_mixed(const float* USh, const float* USl, const float* VSh, const float* VSl,
+                           const float* WUh, const float* WUl, const float* WVh, const float* WVl,
+                           double f, double* Gam, double* Om) {
+  const int o = nocc, v = nvir, nn = nao;
+  const int lv4 = ld4(v), lo4 = ld4(o), kp = ld4(2 * o);
+  // Z[j][P][b] = sum_a U[j][a] c^vv[P][b][a]
+  SBuf<float> ZH((size_t)o * nK * lv4, st, true), ZL((size_t)o * nK * lv4, st, true);
+  {
+    TcEpilogue e = ep_split(ZH.p, ZL.p, (long long)nK * lv4);
+    e.cin = v;
+    e.cld = lv4;
+    tcg(o, nK * v, v, USh, USl, lv4, cvvH.p, cvvL.p, lv4, 0, 1, e, d_tcerr, st);
   }
-  TcOperand A, B;
-  A.hi = BooH.p;
-  A.lo = BooL.p;
-  A.rows = o * nK;
-  A.ld = lo4;
-  B.hi = XtH.p;
-  B.lo = XtL.p;
-  B.rows = v;
-  B.ld = lo4;
-  B.bstride = (long long)v * lo4;
-  B.nb = nvec;
-  TcEpilogue e1;
-  e1.mode = kOutSplit;
-  e1.chi = YH.p;
-  e1.clo = YL.p;
-  e1.ldc = lv4;
-  e1.bsc = (long long)o * nK * lv4;
-  tc_gemm(o * nK, v, o, A, B, nvec, e1, d_tcerr, st);
-  // out[(vec,i)][a] += -c_x sum_{(R,b)} Y[(vec,i)][(R,b)] Bvv[a][(R,b)]
-  TcOperand A2, B2;
-  A2.hi = YH.p;
-  A2.lo = YL.p;
-  A2.rows = nvec * o;
-  A2.ld = nK * lv4;
-  B2.hi = BvvH.p;
-  B2.lo = BvvL.p;
-  B2.rows = v;
-  B2.ld = nK * lv4;
-  TcEpilogue e2;
-  e2.mode = kOutF64;
-  e2.c64 = out;
-  e2.ldc = v;
-  e2.alpha = -opt.cx;
-  e2.beta = 1.0;
-  tc_gemm(nvec * o, v, nK * lv4, A2, B2, 1, e2, d_tcerr, st);
-  k_add_diag<<<cdiv(nov * nvec, 256), 256, 0, st>>>(de.p, Xin, nov, nvec, out);
-  RIS_CHECK_LAUNCH();
+  // G[P][k][j] = sum_b V[k][b] Z[j][P][b]   (batch j)
+  SBuf<float> GH((size_t)nK * o * lo4, st, true), GL((size_t)nK * o * lo4, st, true);
+  tcg(o, nK, lv4, VSh, VSl, lv4, ZH.p, ZL.p, lv4, (long long)nK * lv4, o,
+      ep_split(GH.p, GL.p, lo4, (long long)o * lo4, 1), d_tcerr, st);
+  // M1[mu][P][k'] : k' < o  sum_i Q_U[i][mu] c^oo[P][i][k]
+  //                 k' >= o sum_j C_o[mu][j] G[P][k][j]          (batch P)
+  SBuf<float> MH((size_t)nn * nK * kp, st, true), ML((size_t)nn * nK * kp, st, true);
+  tcg(nn, o, o, WUh, WUl, kp, cooH.p, cooL.p, lo4, (long long)o * lo4, nK,
+      ep_split(MH.p, ML.p, (long long)nK * kp, 1, kp), d_tcerr, st);
+  tcg(nn, o, o, CoH.p, CoL.p, lo4, GH.p, GL.p, lo4, (long long)o * lo4, nK,
+      ep_split(MH.p + o, ML.p + o, (long long)nK * kp, 1, kp), d_tcerr, st);
+  // Gamma[mu][nu][P] += f sum_k' W_V[nu][k'] M1[mu][P][k']   (batch mu)
+  tcg(nn, nK, 2 * o, WVh, WVl, kp, MH.p, ML.p, kp, (long long)nK * kp, nn,
+      ep_f64(Gam, nU, (long long)nn * nU, f, 1.0), d_tcerr, st);
+  // Omega[A][B] += f sum_{k,j} c^oo[A][k][j] G[B][k][j]
+  tcg(nK, nK, o * lo4, cooH.p, cooL.p, o * lo4, GH.p, GL.p, o * lo4, 0, 1, ep_f64(Om, nU, 0, f, 1.0),
+      d_tcerr, st);
+}
+
+// B tensors with 3xTF32 GEMMs: T^X laid out per auxiliary function as
+// [P][nu][mu], H[p][P][nu] = sum_mu C_mu,p T[P][nu][mu], then
+// B[p][q][P] = sum_nu C_nu,q H[p][P][nu]; the metric factors and the
+// layouts the products need follow in FP64 as in the FP64 path.
+void Engine::build_B_mixed() {
+  const int o = nocc, v = nvir, n = nao;
+  const long long nov = (long long)o * v;
+  const int ln = ld4(n), lo4 = ld4(o), lv4 = ld4(v);
+  if (!d_tcerr) {
+    RIS_CUDA(cudaMalloc(&d_tcerr, sizeof(int)));
+    RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
+  }
+  // C_o^T, C_v^T as [p][mu]; C_o, C_v as [mu][p]
+  SBuf<float> CoTh((size_t)o * ln, st), CoTl((size_t)o * ln, st), CvTh((size_t)v * ln, st),
+      CvTl((size_t)v * ln, st);
+  split_f64_t(C.p, n, o, nmo, CoTh.p, CoTl.p, ln, st);
+  split_f64_t(C.p + o, n, v, nmo, CvTh.p, CvTl.p, ln, st);
+  CoH.ensure((size_t)n * lo4, st);
+  CoL.ensure((size_t)n * lo4, st);
+  split_f64(C.p, n, o, nmo, CoH.p, CoL.p, lo4, st);
+  CvH.ensure((size_t)n * lv4, st);
+  CvL.ensure((size_t)n * lv4, st);
+  split_f64(C.p + o, n, v, nmo, CvH.p, CvL.p, lv4, st);
+  const int nX = std::max(nJ, nK);
+  SBuf<double> Tp((size_t)nX * n * n, st);
+  SBuf<float> TH((size_t)nX * n * ln, st), TL((size_t)nX * n * ln, st);
+  SBuf<float> HH((size_t)v * nX * ln, st), HL((size_t)v * nX * ln, st);
+  auto prep_T = [&](const double* T, int nP) {
+    transpose_last2(T, 1, n * n, nP, Tp.p, st);  // [P][(mu,nu)]
+    split_f64(Tp.p, nP * n, n, n, TH.p, TL.p, ln, st);
+  };
+  auto half = [&](const float* ah, const float* al, int np, int nP) {
+    // H[p][(P,nu)] = sum_mu CT[p][mu] T[(P,nu)][mu]
+    TcEpilogue e = ep_split(HH.p, HL.p, (long long)nP * ln);
+    e.cin = n;
+    e.cld = ln;
+    tcg(np, nP * n, n, ah, al, ln, TH.p, TL.p, ln, 0, 1, e, d_tcerr, st);
+  };
+  auto second = [&](const float* ah, const float* al, int nq, int np, int nP, double* out) {
+    // out[p][q][P] = sum_nu CT[q][nu] H[p][P][nu]   (batch p)
+    tcg(nq, nP, n, ah, al, ln, HH.p, HL.p, ln, (long long)nP * ln, np,
+        ep_f64(out, nP, (long long)nq * nP), d_tcerr, st);
+  };
+  // Coulomb: B^J_ov
+  prep_T(TJ.p, nJ);
+  half(CoTh.p, CoTl.p, o, nJ);
+  w3.ensure((size_t)std::max(nov, (long long)o * o) * nX);
+  second(CvTh.p, CvTl.p, v, o, nJ, w3.p);
+  BJ.ensure((size_t)nov * nJ);
+  dgemm(false, true, (int)nov, nJ, nJ, 1.0, w3.p, nJ, LJinv.p, nJ, 0.0, BJ.p, nJ, st);
+  // exchange: oo (and ov for RPA), then vv
+  prep_T(TK.p, nK);
+  half(CoTh.p, CoTl.p, o, nK);
+  second(CoTh.p, CoTl.p, o, o, nK, w3.p);
+  BKoo.ensure((size_t)o * o * nK);
+  dgemm(false, true, o * o, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, BKoo.p, nK, st);
+  cKoo.ensure((size_t)o * o * nK);
+  dgemm(false, false, o * o, nK, nK, 1.0, BKoo.p, nK, LKinv.p, nK, 0.0, cKoo.p, nK, st);
+  if (opt.rpa) {
+    second(CvTh.p, CvTl.p, v, o, nK, w3.p);
+    w4.ensure((size_t)nov * nK);
+    dgemm(false, true, (int)nov, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);
+    cKov.ensure((size_t)nov * nK);
+    dgemm(false, false, (int)nov, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKov.p, nK, st);
+    BKovR.ensure((size_t)nov * nK);
+    transpose_last2(w4.p, 1, (int)nov, nK, BKovR.p, st);
+  }
+  half(CvTh.p, CvTl.p, v, nK);
+  w3.ensure((size_t)v * v * nK);
+  second(CvTh.p, CvTl.p, v, v, nK, w3.p);
+  w4.ensure((size_t)v * v * nK);
+  dgemm(false, true, v * v, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // B[a][b][R]
+  cKvv.ensure((size_t)v * v * nK);
+  dgemm(false, false, v * v, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKvv.p, nK, st);
+  BKvvD.ensure((size_t)v * v * nK);
+  transpose_last2(w4.p, v, v, nK, BKvvD.p, st);  // [b][R][a]
+  prepare_mixed();
+  // c^oo as [(P,k)][i]
+  cooH.ensure((size_t)nK * o * lo4, st);
+  cooL.ensure((size_t)nK * o * lo4, st);
+  split_f64(cKooP.p, nK * o, o, o, cooH.p, cooL.p, lo4, st);
 }
 
 // ------------------------------------------------------------------ A products
@@ -1188,15 +1212,54 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
   t1.ensure((size_t)nn * v, st);
   cJ.ensure((size_t)nsu * nJ, st);
   w5.ensure((size_t)nsu * nJ);
-  QR.ensure((size_t)nsu * o * nn, st);
-  QL.ensure((size_t)nsu * o * nn, st);
   const double* Co = C.p;
   const double* Cv = C.p + o;
-  for (int s = 0; s < nsu; s++) {
-    dgemm(false, false, nn, v, o, 1.0, Co, nmo, Rs.p + s * nov, v, 0.0, t1.p, v, st);
-    dgemm(false, true, nn, nn, v, 1.0, t1.p, v, Cv, nmo, 0.0, DR.p + (size_t)s * nn * nn, nn, st);
-    dgemm(false, true, o, nn, v, 1.0, Rs.p + s * nov, v, Cv, nmo, 0.0, QR.p + (size_t)s * o * nn, nn, st);
-    dgemm(false, true, o, nn, v, 1.0, Ls.p + s * nov, v, Cv, nmo, 0.0, QL.p + (size_t)s * o * nn, nn, st);
+  const bool mixed = opt.precision == RIS_MIXED;
+  const int lv4 = ld4(v), lo4 = ld4(o), kp = ld4(2 * o);
+  // mixed: splits of R and L [s][i][a]; W_R / W_L = [Q^T | C_o] as [s][nu][k']
+  SBuf<float> RSh, RSl, LSh, LSl, WRh, WRl, WLh, WLl;
+  if (mixed) {
+    RSh.ensure((size_t)nsu * o * lv4, st);
+    RSl.ensure((size_t)nsu * o * lv4, st);
+    LSh.ensure((size_t)nsu * o * lv4, st);
+    LSl.ensure((size_t)nsu * o * lv4, st);
+    WRh.ensure((size_t)nsu * nn * kp, st, true);
+    WRl.ensure((size_t)nsu * nn * kp, st, true);
+    WLh.ensure((size_t)nsu * nn * kp, st, true);
+    WLl.ensure((size_t)nsu * nn * kp, st, true);
+    split_f64(Rs.p, nsu * o, v, v, RSh.p, RSl.p, lv4, st);
+    split_f64(Ls.p, nsu * o, v, v, LSh.p, LSl.p, lv4, st);
+    SBuf<float> RtH((size_t)v * lo4, st), RtL((size_t)v * lo4, st), t1H((size_t)nn * lv4, st),
+        t1L((size_t)nn * lv4, st);
+    for (int s = 0; s < nsu; s++) {
+      // D^R_s = C_o R_s C_v^T: t1 = C_o R_s (split), D = t1 C_v^T
+      split_f64_t(Rs.p + s * nov, o, v, v, RtH.p, RtL.p, lo4, st);
+      tcg(nn, v, o, CoH.p, CoL.p, lo4, RtH.p, RtL.p, lo4, 0, 1, ep_split(t1H.p, t1L.p, lv4), d_tcerr,
+          st);
+      tcg(nn, nn, v, t1H.p, t1L.p, lv4, CvH.p, CvL.p, lv4, 0, 1,
+          ep_f64(DR.p + (size_t)s * nn * nn, nn), d_tcerr, st);
+      // Q^T[nu][i] = sum_a C_v[nu][a] U[i][a] into W[:, 0:o]; C_o into W[:, o:2o]
+      for (int w = 0; w < (rpa ? 2 : 1); w++) {
+        float* Wh = (w == 0 ? WRh.p : WLh.p) + (size_t)s * nn * kp;
+        float* Wl = (w == 0 ? WRl.p : WLl.p) + (size_t)s * nn * kp;
+        const float* Uh = (w == 0 ? RSh.p : LSh.p) + (size_t)s * o * lv4;
+        const float* Ul = (w == 0 ? RSl.p : LSl.p) + (size_t)s * o * lv4;
+        tcg(nn, o, v, CvH.p, CvL.p, lv4, Uh, Ul, lv4, 0, 1, ep_split(Wh, Wl, kp), d_tcerr, st);
+        k_copy_cols<<<cdiv((long long)nn * o, 256), 256, 0, st>>>(CoH.p, lo4, Wh, kp, o, nn, o);
+        RIS_CHECK_LAUNCH();
+        k_copy_cols<<<cdiv((long long)nn * o, 256), 256, 0, st>>>(CoL.p, lo4, Wl, kp, o, nn, o);
+        RIS_CHECK_LAUNCH();
+      }
+    }
+  } else {
+    QR.ensure((size_t)nsu * o * nn, st);
+    QL.ensure((size_t)nsu * o * nn, st);
+    for (int s = 0; s < nsu; s++) {
+      dgemm(false, false, nn, v, o, 1.0, Co, nmo, Rs.p + s * nov, v, 0.0, t1.p, v, st);
+      dgemm(false, true, nn, nn, v, 1.0, t1.p, v, Cv, nmo, 0.0, DR.p + (size_t)s * nn * nn, nn, st);
+      dgemm(false, true, o, nn, v, 1.0, Rs.p + s * nov, v, Cv, nmo, 0.0, QR.p + (size_t)s * o * nn, nn, st);
+      dgemm(false, true, o, nn, v, 1.0, Ls.p + s * nov, v, Cv, nmo, 0.0, QL.p + (size_t)s * o * nn, nn, st);
+    }
   }
   // u_s = R_s . B^J (nJ), c_s = u_s L^-1 (row vector)
   dgemm(false, false, nsu, nJ, (int)nov, 1.0, Rs.p, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
@@ -1228,14 +1291,23 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
     const int ncomb = rpa ? 2 : 1;
     for (int cmb = 0; cmb < ncomb; cmb++) {
       const double f = rpa ? -0.5 * cx : -cx;
+      if (mixed) {
+        const size_t so = (size_t)o * lv4, sw = (size_t)nn * kp;
+        const float* USh = (cmb == 0 ? RSh.p : LSh.p) + sI * so;
+        const float* USl = (cmb == 0 ? RSl.p : LSl.p) + sI * so;
+        const float* VSh = (cmb == 0 ? RSh.p : LSh.p) + sJ * so;
+        const float* VSl = (cmb == 0 ? RSl.p : LSl.p) + sJ * so;
+        const float* WUh = (cmb == 0 ? WRh.p : WLh.p) + sI * sw;
+        const float* WUl = (cmb == 0 ? WRl.p : WLl.p) + sI * sw;
+        const float* WVh = (cmb == 0 ? WRh.p : WLh.p) + sJ * sw;
+        const float* WVl = (cmb == 0 ? WRl.p : WLl.p) + sJ * sw;
+        gamma_K_mixed(USh, USl, VSh, VSl, WUh, WUl, WVh, WVl, f, Gam.p, Om.p);
+        continue;
+      }
       const double* U = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sI * nov;
       const double* Vv = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sJ * nov;
       const double* QU = (cmb == 0 ? QR.p : QL.p) + (size_t)sI * o * nn;
       const double* QV = (cmb == 0 ? QR.p : QL.p) + (size_t)sJ * o * nn;
-      if (opt.precision == RIS_MIXED) {
-        gamma_K_mixed(U, Vv, QU, QV, f, Gam.p, Om.p);
-        continue;
-      }
       // Z[j][b][P] = sum_a U[j][a] c^vv[a][b][P]
       dgemm(false, false, o, v * nK, v, 1.0, U, v, cKvv.p, v * nK, 0.0, Z.p, v * nK, st);
       // G[j][k][P] = sum_b V[k][b] Z[j][b][P]

@@ -101,6 +101,9 @@ struct Engine {
   FBuf YH, YL;      // [vec][i][R][b] = sum_j B^K_oo[R][i][j] X[vec][j][b]
   FBuf cvvH, cvvL;  // c^K_vv as [(P,b)][a] (a padded)
   DBuf cKooP;       // c^K_oo as [P][i][k] (FP64)
+  FBuf cooH, cooL;  // c^K_oo as [(P,k)][i] (i padded)
+  FBuf CoH, CoL;    // C_o as [mu][j] (j padded)
+  FBuf CvH, CvL;    // C_v as [mu][a] (a padded)
   int* d_tcerr = nullptr;
 
   // excitations
@@ -128,9 +131,12 @@ struct Engine {
   void apply_A_tda(const double* Xin, int nvec, double* out);
   void apply_A_mixed(const double* Xin, int nvec, double* out);
   void prepare_mixed();
-  // exchange part of Gamma / Omega for one (U,V) pair with weight f (3xTF32)
-  void gamma_K_mixed(const double* U, const double* V, const double* QU, const double* QV, double f,
-                     double* Gam, double* Om);
+  void build_B_mixed();
+  // exchange part of Gamma / Omega for one (U,V) pair with weight f (3xTF32);
+  // US/VS: splits of U, V [i][a]; WU/WV: [Q^T | C_o] splits of U and V
+  void gamma_K_mixed(const float* USh, const float* USl, const float* VSh, const float* VSl,
+                     const float* WUh, const float* WUl, const float* WVh, const float* WVl,
+                     double f, double* Gam, double* Om);
   void dav_core(int ns, const double* guess, int nguess, bool mixed, double tol);
   void apply_ApB_AmB(const double* Zin, int nvec, double* outP, double* outM);
   void davidson_tda(int ns);

@@ -277,8 +277,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
         const int col = n0 + c0 + j;
         if (col >= args.N) continue;
         const long long cpos = ep.cin > 0 ? (long long)(col / ep.cin) * ep.cld + col % ep.cin : col;
-        const size_t off = (size_t)z * ep.bsc +
-                           (ep.trans ? (size_t)cpos * ep.ldc + row : (size_t)row * ep.ldc + cpos);
+        const size_t off = (size_t)z * ep.bsc + (size_t)row * ep.rs + (size_t)cpos * ep.cs;
         if (ep.mode == kOutF64) {
           double* p = ep.c64 + off;
           *p = ep.beta == 0.0 ? ep.alpha * v[j] : fma(ep.alpha, (double)v[j], ep.beta * *p);
@@ -371,7 +370,7 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
   a.kb_per = 1;
   const int tiles = cdiv(M, BM) * cdiv(N, BN);
   a.kb_per = a.nkb;
-  if (nb == 1 && ep.mode == kOutF64 && !ep.trans && ep.cin == 0 && tiles < 152 && a.nkb >= 8) {
+  if (nb == 1 && ep.mode == kOutF64 && ep.cs == 1 && ep.cin == 0 && tiles < 152 && a.nkb >= 8) {
     int ks = std::max(1, std::min(std::max(1, 152 / tiles), a.nkb / 4));
     a.kb_per = cdiv(a.nkb, ks);
     a.ksplit = cdiv(a.nkb, a.kb_per);  // every slice non-empty
@@ -397,7 +396,7 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
   RIS_CHECK_LAUNCH();
   if (a.ksplit > 1) {
     k_tc_reduce<<<cdiv((long long)M * N, 256), 256, 0, st>>>(M, N, a.ksplit, part, ep.alpha, ep.beta,
-                                                             ep.c64, ep.ldc);
+                                                             ep.c64, (int)ep.rs);
     RIS_CHECK_LAUNCH();
     if (own_part) RIS_CUDA(cudaFreeAsync(part, st));
   }
@@ -429,7 +428,7 @@ extern "C" int ris_debug_gemm_tf32x3(int M, int N, int K, const double* A, const
     TcEpilogue ep;
     ep.mode = kOutF64;
     ep.c64 = C;
-    ep.ldc = N;
+    ep.rs = N;
     tc_gemm(M, N, K, a, b, 1, ep, err, st);
     int h_err = 0;
     RIS_CUDA(cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -503,7 +502,7 @@ extern "C" int ris_gemm_tf32x3_noalloc(int M, int N, int K, const double* A, con
     TcEpilogue ep;
     ep.mode = kOutF64;
     ep.c64 = C;
-    ep.ldc = N;
+    ep.rs = N;
     tc_gemm(M, N, K, a, b, 1, ep, err, st, ws, kNoAllocFloats - need, false);
     int h_err = 0;
     RIS_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -18,24 +18,23 @@ struct TcOperand {
   int nb = 1;
 };
 
-// Epilogue: C[z][i][j] for i < M, j < N.
-//   kOutF64:   C64 = alpha * acc + beta * C64   (row stride ldc, batch stride bsc)
-//   kOutSplit: Chi/Clo = tf32 split of alpha * acc (FP32, row stride ldc)
+// Epilogue: element (i, j) of batch z, i < M, j < N, is stored at
+//   z * bsc + i * rs + cpos(j) * cs,
+// cpos(j) = (j / cin) * cld + j % cin when cin > 0 (column blocks of cin at
+// stride cld, e.g. a padded inner index), else j.
+//   kOutF64:   C64 = alpha * acc + beta * C64
+//   kOutSplit: Chi/Clo = tf32 split of alpha * acc (FP32)
 enum TcOut { kOutF64 = 0, kOutSplit = 1 };
-// Column j is stored at (j / cin) * cld + j % cin when cin > 0 (blocks of
-// cin columns at stride cld, e.g. a padded inner index); with trans the
-// element (i, j) goes to j * ldc + i instead of i * ldc + j.
 struct TcEpilogue {
   int mode = kOutF64;
   double* c64 = nullptr;
   float* chi = nullptr;
   float* clo = nullptr;
-  int ldc = 0;
+  long long rs = 0, cs = 1;
   long long bsc = 0;
   double alpha = 1.0, beta = 0.0;
   int cin = 0;
   long long cld = 0;
-  bool trans = false;
 };
 
 // C[z] (M x N) = A[z] (M x K) . B[z]^T (N x K), batches z < nb.  With

@@ -270,11 +270,12 @@ __device__ int sturm_count(const double* d, const double* e, int m, double x) {
 
 __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* __restrict__ H, int ldH, int m, int k,
                                                    double* __restrict__ w, double* __restrict__ V,
-                                                   double* __restrict__ work) {
+                                                   double* __restrict__ work, int use_smem) {
+  extern __shared__ double sm_A[];
   __shared__ double red[33];
   __shared__ double sh_alpha, sh_tau;
-  double* A = work;
-  double* d = A + (size_t)m * m;
+  double* A = use_smem ? sm_A : work;
+  double* d = work + (size_t)m * m;
   double* e = d + m;
   double* p = e + m;
   double* tau = p + m;
@@ -286,16 +287,10 @@ __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* __restrict__ H,
   double* DU2 = DU + (size_t)64 * m;
   double* PIV = DU2 + (size_t)64 * m;
   const int tid = threadIdx.x;
-  for (size_t i = tid; i < (size_t)m * m; i += kEigT) A[i] = H[(i / m) * ldH + i % m];
-  __syncthreads();
-  // symmetrise
+  // load and symmetrise
   for (size_t ij = tid; ij < (size_t)m * m; ij += kEigT) {
     const int i = (int)(ij / m), j = (int)(ij % m);
-    if (j < i) {
-      const double s = 0.5 * (A[(size_t)i * m + j] + A[(size_t)j * m + i]);
-      A[(size_t)i * m + j] = s;
-      A[(size_t)j * m + i] = s;
-    }
+    A[ij] = 0.5 * (H[(size_t)i * ldH + j] + H[(size_t)j * ldH + i]);
   }
   __syncthreads();
   // --- Householder tridiagonalisation
@@ -354,7 +349,8 @@ __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* __restrict__ H,
     tau[m - 1] = 0.0;
   }
   __syncthreads();
-  // --- bisection (thread j -> eigenvalue j)
+  // --- eigenvalues by multisection: one warp per eigenvalue, 32 Sturm
+  //     counts per step shrink the bracket 33-fold
   double glo = 0.0, ghi = 0.0;
   for (int i = 0; i < m; i++) {
     const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
@@ -363,17 +359,25 @@ __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* __restrict__ H,
     if (i == 0 || hi > ghi) ghi = hi;
   }
   const double tnorm = fmax(fmax(fabs(glo), fabs(ghi)), 1e-300);
-  if (tid < k) {
-    double lo = glo - 1e-12 * tnorm, hi = ghi + 1e-12 * tnorm;
-    for (int it = 0; it < 200; it++) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (sturm_count(d, e, m, mid) > tid)
-        hi = mid;
-      else
-        lo = mid;
+  {
+    const int wid = tid >> 5, lane = tid & 31;
+    for (int j = wid; j < k; j += kEigT / 32) {
+      double lo = glo - 1e-12 * tnorm, hi = ghi + 1e-12 * tnorm;
+      for (int it = 0; it < 40; it++) {
+        const double h = (hi - lo) / 33.0;
+        if (!(h > 0.0) || lo + h <= lo) break;
+        const double x = lo + h * (lane + 1);
+        const bool above = sturm_count(d, e, m, x) > j;  // lambda_j < x
+        const unsigned mask = __ballot_sync(0xffffffffu, above);
+        // first lane whose point lies above lambda_j
+        const int f = mask ? __ffs(mask) - 1 : 32;
+        const double nlo = f == 0 ? lo : lo + h * f;
+        const double nhi = f == 32 ? hi : lo + h * (f + 1);
+        lo = nlo;
+        hi = nhi;
+      }
+      if (lane == 0) lam[j] = 0.5 * (lo + hi);
     }
-    lam[tid] = 0.5 * (lo + hi);
   }
   __syncthreads();
   // --- inverse iteration: thread j factors T - lam_j I by Gaussian
@@ -479,8 +483,16 @@ __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* __restrict__ H,
 void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
                     cudaStream_t st) {
   RIS_REQUIRE(k >= 1 && k <= 64 && k <= m, RIS_ERR_ARG, "sym_eig_lowest: bad k");
+  static bool attr = false;
+  const size_t smem_max = 200 * 1024;
+  if (!attr) {
+    RIS_CUDA(cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    attr = true;
+  }
+  const size_t need = (size_t)m * m * sizeof(double);
+  const int use_smem = need <= smem_max;
   prof_begin(kProfEig, st);
-  k_sym_eig<<<1, kEigT, 0, st>>>(H, ldH, m, k, w, V, work);
+  k_sym_eig<<<1, kEigT, use_smem ? need : 0, st>>>(H, ldH, m, k, w, V, work, use_smem);
   RIS_CHECK_LAUNCH();
   prof_end(kProfEig, st, 1.0);
 }
