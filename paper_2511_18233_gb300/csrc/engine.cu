@@ -926,6 +926,63 @@ void Engine::build_B_mixed() {
   split_f64(cKooP.p, nK * o, o, o, cooH.p, cooL.p, lo4, st);
 }
 
+void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
+  const int o = nocc, v = nvir;
+  const long long nov = (long long)o * v;
+  const int lo4 = ld4(o), lv4 = ld4(v);
+  // Coulomb in FP64: out = 2 (X B^J) B^J^T
+  w5.ensure((size_t)nvec * std::max(nJ, 1));
+  dgemm(false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
+  dgemm(false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
+  // X^T per vector, split
+  XtH.ensure((size_t)nvec * v * lo4, st);
+  XtL.ensure((size_t)nvec * v * lo4, st);
+  split_f64_t(Xin, o, v, v, XtH.p, XtL.p, lo4, st, nvec, nov, (long long)v * lo4);
+  // Y[vec][(i,R)][b] = sum_j Boo[(i,R)][j] Xt[vec][b][j]
+  const size_t ysz = (size_t)nvec * o * nK * lv4;
+  if (YH.n < ysz) {
+    YH.ensure(ysz, st);
+    YL.ensure(ysz, st);
+  }
+  TcOperand A, B;
+  A.hi = BooH.p;
+  A.lo = BooL.p;
+  A.rows = o * nK;
+  A.ld = lo4;
+  B.hi = XtH.p;
+  B.lo = XtL.p;
+  B.rows = v;
+  B.ld = lo4;
+  B.bstride = (long long)v * lo4;
+  B.nb = nvec;
+  TcEpilogue e1;
+  e1.mode = kOutSplit;
+  e1.chi = YH.p;
+  e1.clo = YL.p;
+  e1.rs = lv4;
+  e1.bsc = (long long)o * nK * lv4;
+  tc_gemm(o * nK, v, o, A, B, nvec, e1, d_tcerr, st);
+  // out[(vec,i)][a] += -c_x sum_{(R,b)} Y[(vec,i)][(R,b)] Bvv[a][(R,b)]
+  TcOperand A2, B2;
+  A2.hi = YH.p;
+  A2.lo = YL.p;
+  A2.rows = nvec * o;
+  A2.ld = nK * lv4;
+  B2.hi = BvvH.p;
+  B2.lo = BvvL.p;
+  B2.rows = v;
+  B2.ld = nK * lv4;
+  TcEpilogue e2;
+  e2.mode = kOutF64;
+  e2.c64 = out;
+  e2.rs = v;
+  e2.alpha = -opt.cx;
+  e2.beta = 1.0;
+  tc_gemm(nvec * o, v, nK * lv4, A2, B2, 1, e2, d_tcerr, st);
+  k_add_diag<<<cdiv(nov * nvec, 256), 256, 0, st>>>(de.p, Xin, nov, nvec, out);
+  RIS_CHECK_LAUNCH();
+}
+
 // ------------------------------------------------------------------ A products
 // out[n] = A X[n] for TDA (Eq. A_matrix with the ris kernel)
 void Engine::apply_A_tda(const double* Xin, int nvec, double* out) {
