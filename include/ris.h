@@ -193,6 +193,14 @@ ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n);
 int ris_debug_boys(int n, const int* m, const double* T, double* out);
 
 /*
+ * Test hook: lowest k (<= 64) eigenpairs of a symmetric m x m row-major
+ * matrix with the device eigensolver of the Davidson subspace problem.
+ * H: [m][m], w: [k] ascending, V: [k][m] (row j = eigenvector j); DEVICE
+ * pointers on the current device.  Synchronises the device.
+ */
+int ris_debug_sym_eig(int m, int k, const double* H, double* w, double* V);
+
+/*
  * Test hook: C = A . B^T with the library's 3xTF32 tensor-core GEMM (the
  * kernel behind RIS_MIXED).  A: [M][K], B: [N][K], C: [M][N], FP64 DEVICE
  * pointers on the current device (inputs are rounded to FP32 and split).

@@ -698,11 +698,6 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
   copy_in(eps.p, eps_in, nmo, st);
   k_orb_diff<<<cdiv(nov, 256), 256, 0, st>>>(eps.p, o, v, de.p);
   RIS_CHECK_LAUNCH();
-  if (opt.precision == RIS_MIXED) {
-    build_B_mixed();
-    stage = 2;
-    return;
-  }
   const double* Co = C.p;
   const double* Cv = C.p + o;
   // Coulomb: H[i][nu][P] = sum_mu C_mu,i T[mu][nu][P]; B[i][a][P]; B L^-T
@@ -766,7 +761,7 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
 
 // FP32 hi/lo operands of the exchange products (Eq. A_matrix, (ij|ab) term)
 void Engine::prepare_mixed() {
-  const int o = nocc, v = nvir;
+  const int o = nocc, v = nvir, n = nao;
   const int lo4 = ld4(o), lv4 = ld4(v);
   if (!d_tcerr) {
     RIS_CUDA(cudaMalloc(&d_tcerr, sizeof(int)));
@@ -788,6 +783,16 @@ void Engine::prepare_mixed() {
   split_f64(w3.p, nK * v, v, v, cvvH.p, cvvL.p, lv4, st);
   cKooP.ensure((size_t)o * o * nK);
   transpose_last2(cKoo.p, 1, o * o, nK, cKooP.p, st);  // [P][i][k]
+  cooH.ensure((size_t)nK * o * lo4, st);
+  cooL.ensure((size_t)nK * o * lo4, st);
+  split_f64(cKooP.p, nK * o, o, o, cooH.p, cooL.p, lo4, st);
+  // C_o and C_v as [mu][p]
+  CoH.ensure((size_t)n * lo4, st);
+  CoL.ensure((size_t)n * lo4, st);
+  split_f64(C.p, n, o, nmo, CoH.p, CoL.p, lo4, st);
+  CvH.ensure((size_t)n * lv4, st);
+  CvL.ensure((size_t)n * lv4, st);
+  split_f64(C.p + o, n, v, nmo, CvH.p, CvL.p, lv4, st);
 }
 
 // One tensor-core GEMM with split operands; helper for the mixed path.
@@ -841,89 +846,6 @@ void Engine::gamma_K_mixed(const float* USh, const float* USl, const float* VSh,
   // Omega[A][B] += f sum_{k,j} c^oo[A][k][j] G[B][k][j]
   tcg(nK, nK, o * lo4, cooH.p, cooL.p, o * lo4, GH.p, GL.p, o * lo4, 0, 1, ep_f64(Om, nU, 0, f, 1.0),
       d_tcerr, st);
-}
-
-// B tensors with 3xTF32 GEMMs: T^X laid out per auxiliary function as
-// [P][nu][mu], H[p][P][nu] = sum_mu C_mu,p T[P][nu][mu], then
-// B[p][q][P] = sum_nu C_nu,q H[p][P][nu]; the metric factors and the
-// layouts the products need follow in FP64 as in the FP64 path.
-void Engine::build_B_mixed() {
-  const int o = nocc, v = nvir, n = nao;
-  const long long nov = (long long)o * v;
-  const int ln = ld4(n), lo4 = ld4(o), lv4 = ld4(v);
-  if (!d_tcerr) {
-    RIS_CUDA(cudaMalloc(&d_tcerr, sizeof(int)));
-    RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
-  }
-  // C_o^T, C_v^T as [p][mu]; C_o, C_v as [mu][p]
-  SBuf<float> CoTh((size_t)o * ln, st), CoTl((size_t)o * ln, st), CvTh((size_t)v * ln, st),
-      CvTl((size_t)v * ln, st);
-  split_f64_t(C.p, n, o, nmo, CoTh.p, CoTl.p, ln, st);
-  split_f64_t(C.p + o, n, v, nmo, CvTh.p, CvTl.p, ln, st);
-  CoH.ensure((size_t)n * lo4, st);
-  CoL.ensure((size_t)n * lo4, st);
-  split_f64(C.p, n, o, nmo, CoH.p, CoL.p, lo4, st);
-  CvH.ensure((size_t)n * lv4, st);
-  CvL.ensure((size_t)n * lv4, st);
-  split_f64(C.p + o, n, v, nmo, CvH.p, CvL.p, lv4, st);
-  const int nX = std::max(nJ, nK);
-  SBuf<double> Tp((size_t)nX * n * n, st);
-  SBuf<float> TH((size_t)nX * n * ln, st), TL((size_t)nX * n * ln, st);
-  SBuf<float> HH((size_t)v * nX * ln, st), HL((size_t)v * nX * ln, st);
-  auto prep_T = [&](const double* T, int nP) {
-    transpose_last2(T, 1, n * n, nP, Tp.p, st);  // [P][(mu,nu)]
-    split_f64(Tp.p, nP * n, n, n, TH.p, TL.p, ln, st);
-  };
-  auto half = [&](const float* ah, const float* al, int np, int nP) {
-    // H[p][(P,nu)] = sum_mu CT[p][mu] T[(P,nu)][mu]
-    TcEpilogue e = ep_split(HH.p, HL.p, (long long)nP * ln);
-    e.cin = n;
-    e.cld = ln;
-    tcg(np, nP * n, n, ah, al, ln, TH.p, TL.p, ln, 0, 1, e, d_tcerr, st);
-  };
-  auto second = [&](const float* ah, const float* al, int nq, int np, int nP, double* out) {
-    // out[p][q][P] = sum_nu CT[q][nu] H[p][P][nu]   (batch p)
-    tcg(nq, nP, n, ah, al, ln, HH.p, HL.p, ln, (long long)nP * ln, np,
-        ep_f64(out, nP, (long long)nq * nP), d_tcerr, st);
-  };
-  // Coulomb: B^J_ov
-  prep_T(TJ.p, nJ);
-  half(CoTh.p, CoTl.p, o, nJ);
-  w3.ensure((size_t)std::max(nov, (long long)o * o) * nX);
-  second(CvTh.p, CvTl.p, v, o, nJ, w3.p);
-  BJ.ensure((size_t)nov * nJ);
-  dgemm(false, true, (int)nov, nJ, nJ, 1.0, w3.p, nJ, LJinv.p, nJ, 0.0, BJ.p, nJ, st);
-  // exchange: oo (and ov for RPA), then vv
-  prep_T(TK.p, nK);
-  half(CoTh.p, CoTl.p, o, nK);
-  second(CoTh.p, CoTl.p, o, o, nK, w3.p);
-  BKoo.ensure((size_t)o * o * nK);
-  dgemm(false, true, o * o, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, BKoo.p, nK, st);
-  cKoo.ensure((size_t)o * o * nK);
-  dgemm(false, false, o * o, nK, nK, 1.0, BKoo.p, nK, LKinv.p, nK, 0.0, cKoo.p, nK, st);
-  if (opt.rpa) {
-    second(CvTh.p, CvTl.p, v, o, nK, w3.p);
-    w4.ensure((size_t)nov * nK);
-    dgemm(false, true, (int)nov, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);
-    cKov.ensure((size_t)nov * nK);
-    dgemm(false, false, (int)nov, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKov.p, nK, st);
-    BKovR.ensure((size_t)nov * nK);
-    transpose_last2(w4.p, 1, (int)nov, nK, BKovR.p, st);
-  }
-  half(CvTh.p, CvTl.p, v, nK);
-  w3.ensure((size_t)v * v * nK);
-  second(CvTh.p, CvTl.p, v, v, nK, w3.p);
-  w4.ensure((size_t)v * v * nK);
-  dgemm(false, true, v * v, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // B[a][b][R]
-  cKvv.ensure((size_t)v * v * nK);
-  dgemm(false, false, v * v, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKvv.p, nK, st);
-  BKvvD.ensure((size_t)v * v * nK);
-  transpose_last2(w4.p, v, v, nK, BKvvD.p, st);  // [b][R][a]
-  prepare_mixed();
-  // c^oo as [(P,k)][i]
-  cooH.ensure((size_t)nK * o * lo4, st);
-  cooL.ensure((size_t)nK * o * lo4, st);
-  split_f64(cKooP.p, nK * o, o, o, cooH.p, cooL.p, lo4, st);
 }
 
 void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {

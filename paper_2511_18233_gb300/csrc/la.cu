@@ -533,3 +533,20 @@ void gemv_rows(const double* V, int nrow, long long ncol, const double* x, doubl
 }
 
 }  // namespace ris
+
+// Test hook (declared in include/ris.h): lowest k eigenpairs of a symmetric
+// m x m matrix with the device subspace eigensolver; device pointers.
+extern "C" int ris_debug_sym_eig(int m, int k, const double* H, double* w, double* V) {
+  using namespace ris;
+  try {
+    double* work = nullptr;
+    RIS_CUDA(cudaMalloc(&work, sizeof(double) * eig_work_size(m)));
+    sym_eig_lowest(H, m, m, k, w, V, work, 0);
+    RIS_CUDA(cudaDeviceSynchronize());
+    cudaFree(work);
+    return 0;
+  } catch (const Error& e) {
+    fprintf(stderr, "ris_debug_sym_eig: %s\n", e.msg.c_str());
+    return (int)e.code;
+  }
+}

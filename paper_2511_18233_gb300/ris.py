@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_debug_gemm_tf32x3", "ris_gemm_tf32x3_noalloc",
+           "ris_apply", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_gemm_tf32x3_noalloc",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
 
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH):
     L.ris_get_stats.argtypes = [P, ctypes.POINTER(d), i]
     L.ris_debug_boys.argtypes = [i, P, P, P]
     L.ris_debug_gemm_tf32x3.argtypes = [i, i, i, P, P, P]
+    L.ris_debug_sym_eig.argtypes = [i, i, P, P, P]
     L.ris_gemm_tf32x3_noalloc.argtypes = [i, i, i, P, P, P, P]
     L.ris_last_error.argtypes = [P]
     L.ris_last_error.restype = ctypes.c_char_p
@@ -247,3 +248,16 @@ def gemm_tf32x3_noalloc(A_t, B_t, C_t, stream=None) -> int:
     N = B_t.shape[0]
     return load().ris_gemm_tf32x3_noalloc(int(M), int(N), int(K), A_t.data_ptr(), B_t.data_ptr(),
                                           C_t.data_ptr(), stream)
+
+
+def debug_sym_eig(H, k):
+    """Lowest k eigenpairs of symmetric H via the device subspace eigensolver."""
+    import torch
+    H_t = torch.as_tensor(np.ascontiguousarray(H, dtype=np.float64), device="cuda")
+    m = H_t.shape[0]
+    w = torch.zeros(k, dtype=torch.float64, device="cuda")
+    V = torch.zeros((k, m), dtype=torch.float64, device="cuda")
+    st = load().ris_debug_sym_eig(int(m), int(k), H_t.data_ptr(), w.data_ptr(), V.data_ptr())
+    if st != 0:
+        raise RisError(st, "ris_debug_sym_eig failed")
+    return w.cpu().numpy(), V.cpu().numpy()
