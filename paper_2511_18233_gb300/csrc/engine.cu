@@ -336,8 +336,8 @@ __global__ void k_scale_rows(double* __restrict__ X, long long n, int nrow, cons
 // Cholesky of the Gram matrix G (nt x nt, unit diagonal expected) with
 // dropping of (near-)dependent rows; P[i][c] such that the kept rows
 // Tnew_i = sum_c P[i][c] T_c are orthonormal.  *nkeep = number kept.
-__global__ void k_cholqr_small(const double* __restrict__ G, int nt, double drop, double* __restrict__ P,
-                               int* __restrict__ nkeep, double* __restrict__ work) {
+__global__ void k_cholqr_small(const double* G, int nt, double drop, double* P, int* nkeep,
+                               double* work) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* R = work;        // nt x nt upper factor over kept columns
   int* keep = (int*)(work + nt * nt);

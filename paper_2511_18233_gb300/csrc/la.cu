@@ -11,8 +11,10 @@
 //   iteration for the eigenvectors of the tridiagonal matrix, Gram-Schmidt
 //   inside clusters of close eigenvalues, back-transformation.
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "la.cuh"
 
@@ -268,9 +270,12 @@ __device__ int sturm_count(const double* d, const double* e, int m, double x) {
   return c;
 }
 
-__global__ void __launch_bounds__(kEigT) k_sym_eig(const double* __restrict__ H, int ldH, int m, int k,
-                                                   double* __restrict__ w, double* __restrict__ V,
-                                                   double* __restrict__ work, int use_smem) {
+// No __restrict__ here: every work array below is carved out of `work`, and
+// with restrict-qualified parameters the compiler reordered the in-place
+// updates of the inverse iteration (wrong eigenvectors at m >~ 40).
+__global__ void __launch_bounds__(kEigT) k_sym_eig(const double* H, int ldH, int m, int k,
+                                                   double* w, double* V, double* work,
+                                                   int use_smem) {
   extern __shared__ double sm_A[];
   __shared__ double red[33];
   __shared__ double sh_alpha, sh_tau;
