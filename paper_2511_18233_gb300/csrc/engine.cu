@@ -221,6 +221,17 @@ __global__ void k_copy_cols(const float* __restrict__ src, int lds, float* __res
   dst[(size_t)r * ldd + c0 + c] = src[(size_t)r * lds + c];
 }
 
+// out[c][a][b] = in[a][b][c]
+__global__ void k_permute120(const double* __restrict__ in, int na, int nb, int nc,
+                             double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)na * nb * nc) return;
+  const int c = (int)(t % nc);
+  const long long ab = t / nc;
+  const int b = (int)(ab % nb), a = (int)(ab / nb);
+  out[((size_t)c * na + a) * nb + b] = in[t];
+}
+
 // out[b][a][c] = in[a][b][c]
 __global__ void k_permute021(const double* __restrict__ in, int na, int nb, int nc,
                              double* __restrict__ out) {
@@ -543,6 +554,19 @@ void divide_pairs(double* out, const double* num, const double* den, int npair, 
   RIS_CHECK_LAUNCH();
 }
 
+// RPA operators from their parts: P = de Z + 4 J - cx (K1 + K2), M = de Z - cx (K1 - K2);
+// on entry outP holds J.
+__global__ void k_rpa_combine(const double* __restrict__ de, const double* __restrict__ Z,
+                              const double* __restrict__ K1, const double* __restrict__ K2,
+                              long long nov, int nvec, double cx, double* __restrict__ outP,
+                              double* __restrict__ outM) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nov * nvec) return;
+  const double dz = de[t % nov] * Z[t];
+  outP[t] = dz + 4.0 * outP[t] - cx * (K1[t] + K2[t]);
+  outM[t] = dz - cx * (K1[t] - K2[t]);
+}
+
 // ------------------------------------------------------------------ setup
 void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_shell* aos, int nJs,
                        const ris_shell* auxJ, int nKs, const ris_shell* auxK) {
@@ -738,6 +762,8 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
     dgemm(false, false, (int)nov, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKov.p, nK, st);
     BKovR.ensure((size_t)nov * nK);
     transpose_last2(w4.p, 1, (int)nov, nK, BKovR.p, st);  // [R][ia]
+    cKovP.ensure((size_t)nov * nK);
+    transpose_last2(cKov.p, 1, (int)nov, nK, cKovP.p, st);  // [P][ia]
   }
   w2.ensure((size_t)v * n * nK);
   dgemm(true, false, v, n * nK, n, 1.0, Cv, nmo, TK.p, n * nK, 0.0, w2.p, n * nK, st);
@@ -848,19 +874,18 @@ void Engine::gamma_K_mixed(const float* USh, const float* USl, const float* VSh,
       d_tcerr, st);
 }
 
-void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
+// out = alpha * K1 + beta * out with K1 the (ij|ab) exchange contraction of
+// the nvec vectors Z, as two 3xTF32 GEMMs:
+//   Y[vec][(i,R)][b] = sum_j B^K_oo[(i,R)][j] Z[vec][j][b]
+//   K1[(vec,i)][a]   = sum_{(R,b)} Y[(vec,i)][(R,b)] B^K_vv[a][(R,b)]
+void Engine::apply_exchange_mixed(const double* Z, int nvec, double* out, double alpha,
+                                  double beta) {
   const int o = nocc, v = nvir;
   const long long nov = (long long)o * v;
   const int lo4 = ld4(o), lv4 = ld4(v);
-  // Coulomb in FP64: out = 2 (X B^J) B^J^T
-  w5.ensure((size_t)nvec * std::max(nJ, 1));
-  dgemm(false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
-  dgemm(false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
-  // X^T per vector, split
   XtH.ensure((size_t)nvec * v * lo4, st);
   XtL.ensure((size_t)nvec * v * lo4, st);
-  split_f64_t(Xin, o, v, v, XtH.p, XtL.p, lo4, st, nvec, nov, (long long)v * lo4);
-  // Y[vec][(i,R)][b] = sum_j Boo[(i,R)][j] Xt[vec][b][j]
+  split_f64_t(Z, o, v, v, XtH.p, XtL.p, lo4, st, nvec, nov, (long long)v * lo4);
   const size_t ysz = (size_t)nvec * o * nK * lv4;
   if (YH.n < ysz) {
     YH.ensure(ysz, st);
@@ -884,7 +909,6 @@ void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
   e1.rs = lv4;
   e1.bsc = (long long)o * nK * lv4;
   tc_gemm(o * nK, v, o, A, B, nvec, e1, d_tcerr, st);
-  // out[(vec,i)][a] += -c_x sum_{(R,b)} Y[(vec,i)][(R,b)] Bvv[a][(R,b)]
   TcOperand A2, B2;
   A2.hi = YH.p;
   A2.lo = YL.p;
@@ -898,9 +922,18 @@ void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
   e2.mode = kOutF64;
   e2.c64 = out;
   e2.rs = v;
-  e2.alpha = -opt.cx;
-  e2.beta = 1.0;
+  e2.alpha = alpha;
+  e2.beta = beta;
   tc_gemm(nvec * o, v, nK * lv4, A2, B2, 1, e2, d_tcerr, st);
+}
+
+void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
+  const long long nov = (long long)nocc * nvir;
+  // Coulomb in FP64: out = 2 (X B^J) B^J^T
+  w5.ensure((size_t)nvec * std::max(nJ, 1));
+  dgemm(false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
+  dgemm(false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
+  apply_exchange_mixed(Xin, nvec, out, -opt.cx, 1.0);
   k_add_diag<<<cdiv(nov * nvec, 256), 256, 0, st>>>(de.p, Xin, nov, nvec, out);
   RIS_CHECK_LAUNCH();
 }
@@ -952,8 +985,56 @@ void Engine::apply(int nvec, const double* Xh, double* out, double* out2) {
   RIS_CUDA(cudaStreamSynchronize(st));
 }
 
-void Engine::apply_ApB_AmB(const double*, int, double*, double*) {
-  throw Error{RIS_ERR_ARG, "RPA products are not available in this build"};
+// (ij|ab) and (ib|ja) exchange contractions (Eqs. A_matrix, B_matrix):
+//   K1[n][i][a] = sum_{R,j,b} B^K_ij,R Z_n[j][b] B^K_ab,R
+//   K2[n][i][a] = sum_{R,j,b} B^K_ib,R Z_n[j][b] B^K_ja,R
+void Engine::exchange_terms(const double* Z, int nvec, double* K1, double* K2, bool mixed) {
+  const int o = nocc, v = nvir;
+  const long long nov = (long long)o * v;
+  if (mixed) {
+    apply_exchange_mixed(Z, nvec, K1, 1.0, 0.0);
+  } else {
+    w6.ensure((size_t)nvec * o * nK * v);
+    GemmBatch bt;
+    bt.nb1 = nvec;
+    bt.sA1 = nov;
+    bt.sC1 = (long long)o * nK * v;
+    dgemm(false, false, o, nK * v, v, 1.0, Z, v, BKvvD.p, nK * v, 0.0, w6.p, nK * v, st, bt);
+    GemmBatch b2;
+    b2.nb1 = nvec;
+    b2.sB1 = (long long)o * nK * v;
+    b2.sC1 = nov;
+    dgemm(false, false, o, v, o * nK, 1.0, BKoo.p, o * nK, w6.p, v, 0.0, K1, v, st, b2);
+  }
+  // Y1[n][i][R][j] = sum_b B^K_ib,R Z_n[j][b];  K2_n = Y1_n . B^K as [(R,j)][a]
+  SBuf<double> Y1((size_t)nvec * o * nK * o, st);
+  GemmBatch bt;
+  bt.nb1 = nvec;
+  bt.nb2 = nK;
+  bt.sA1 = 0;
+  bt.sA2 = nov;
+  bt.sB1 = nov;
+  bt.sB2 = 0;
+  bt.sC1 = (long long)o * nK * o;
+  bt.sC2 = o;
+  dgemm(false, true, o, o, v, 1.0, BKovR.p, v, Z, v, 0.0, Y1.p, nK * o, st, bt);
+  GemmBatch b2;
+  b2.nb1 = nvec;
+  b2.sA1 = (long long)o * nK * o;
+  b2.sC1 = nov;
+  dgemm(false, false, o, v, nK * o, 1.0, Y1.p, nK * o, BKovR.p, v, 0.0, K2, v, st, b2);
+}
+
+void Engine::apply_ApB_AmB(const double* Z, int nvec, double* outP, double* outM) {
+  const long long nov = (long long)nocc * nvir;
+  const bool mixed = opt.precision == RIS_MIXED;
+  w5.ensure((size_t)nvec * std::max(nJ, 1));
+  dgemm(false, false, nvec, nJ, (int)nov, 1.0, Z, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
+  dgemm(false, true, nvec, (int)nov, nJ, 1.0, w5.p, nJ, BJ.p, nJ, 0.0, outP, (int)nov, st);
+  SBuf<double> K1((size_t)nvec * nov, st), K2((size_t)nvec * nov, st);
+  exchange_terms(Z, nvec, K1.p, K2.p, mixed);
+  k_rpa_combine<<<cdiv(nov * nvec, 256), 256, 0, st>>>(de.p, Z, K1.p, K2.p, nov, nvec, opt.cx, outP, outM);
+  RIS_CHECK_LAUNCH();
 }
 
 // ------------------------------------------------------------------ Davidson (TDA)
@@ -1125,8 +1206,203 @@ void Engine::excite(int ns, double* om, double* Xo, double* Yo) {
   stage = 3;
 }
 
-void Engine::davidson_rpa(int) {
-  throw Error{RIS_ERR_ARG, "RPA excitations are not available in this build"};
+// copy the leading m x m block of a matrix with leading dimension ld
+__global__ void k_copy_sub(const double* __restrict__ src, int ld, int m, double* __restrict__ dst) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  dst[t] = src[(size_t)(t / m) * ld + t % m];
+}
+// w2[k] -> omega[k] = sqrt(w2[k]); rows of Y scaled by omega^-1/2
+__global__ void k_rpa_omega(const double* __restrict__ w2, int ns, double* __restrict__ om,
+                            double* __restrict__ Y, int m) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns * m) return;
+  const int k = t / m;
+  const double o = sqrt(fmax(w2[k], 0.0));
+  if (t % m == 0) om[k] = o;
+  Y[t] *= 1.0 / sqrt(o);
+}
+// out[k][i] = a * X[k][i] * s[k]^p + b * Y[k][i]   (row scales)
+__global__ void k_rowcomb(const double* __restrict__ X, const double* __restrict__ Y,
+                          const double* __restrict__ s, double a, double b, int pw, long long n,
+                          int nrow, double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nrow) return;
+  const int k = (int)(t / n);
+  double f = a;
+  if (pw == 1) f *= s[k];
+  if (pw == -1) f /= s[k];
+  out[t] = f * X[t] + (Y ? b * Y[t] : 0.0);
+}
+
+// Davidson for the Casida problem, Eq. (casida), in the symmetric form: with
+// a basis V, a+ = V (A+B) V^T and a- = V (A-B) V^T = L L^T, the reduced
+// problem (L^T a+ L) y = omega^2 y gives R = X+Y = V^T L y / sqrt(omega) and
+// X-Y = a+ R / omega, normalised so that sum X^2 - Y^2 = 1.
+void Engine::davidson_rpa(int ns) {
+  const bool mixed = opt.precision == RIS_MIXED;
+  const double tol = mixed ? std::max(opt.conv_tol, opt.mixed_tol) : opt.conv_tol;
+  const long long n = (long long)nocc * nvir;
+  const int nb0 = (int)std::min<long long>(n, ns + std::min(ns, 8));
+  int maxsp = opt.max_subspace > 0 ? opt.max_subspace : std::max(nb0 + 4 * ns, 10 * ns);
+  maxsp = (int)std::min<long long>(std::min(maxsp, 256), n);
+  RIS_REQUIRE(maxsp >= std::max(nb0, 2 * ns) + 2, RIS_ERR_ARG, "max_subspace too small for RPA");
+  const int ntmax = 2 * ns;
+  SBuf<double> V((size_t)maxsp * n, st), PV((size_t)maxsp * n, st), MV((size_t)maxsp * n, st),
+      Ap((size_t)maxsp * maxsp, st), Am((size_t)maxsp * maxsp, st), Lc((size_t)maxsp * maxsp, st),
+      Ht((size_t)maxsp * maxsp, st), Hm((size_t)maxsp * maxsp, st), S((size_t)64 * maxsp, st),
+      w2(64, st), om(64, st), Rs((size_t)ns * maxsp, st), Ls((size_t)ns * maxsp, st),
+      Rf((size_t)ns * n, st), Lf((size_t)ns * n, st), rR((size_t)ns * n, st), rL((size_t)ns * n, st),
+      T((size_t)ntmax * n, st), tmp((size_t)std::max(ntmax, nb0) * n, st),
+      Cc((size_t)ntmax * maxsp + ntmax * ntmax + 64, st), G((size_t)ntmax * ntmax + ntmax, st),
+      Pm((size_t)ntmax * ntmax + 64, st), nrm((size_t)2 * ns, st), ework(eig_work_size(maxsp), st);
+  SBuf<int> idxbuf((size_t)std::max(nb0, ns) + 8, st);
+  int* d_idx = idxbuf.p;
+  int nprod = 0;
+  auto products = [&](const double* x, int nv, double* p, double* mm) {
+    apply_ApB_AmB(x, nv, p, mm);
+    nprod += nv;
+  };
+  // orthonormalise rows [0, nt) of T against V[0, m) and among themselves
+  auto orthonormalise = [&](int nt, int m) -> int {
+    int nkeep = nt;
+    for (int pass = 0; pass < 2 && nkeep > 0; pass++) {
+      if (m > 0) {
+        dgemm(false, true, nt, m, (int)n, 1.0, T.p, (int)n, V.p, (int)n, 0.0, Cc.p, m, st);
+        dgemm(false, false, nt, (int)n, m, -1.0, Cc.p, m, V.p, (int)n, 1.0, T.p, (int)n, st);
+      }
+      row_norms(T.p, nt, n, G.p, st);
+      k_scale_rows<<<cdiv(n * nt, 256), 256, 0, st>>>(T.p, n, nt, G.p);
+      RIS_CHECK_LAUNCH();
+      dgemm(false, true, nt, nt, (int)n, 1.0, T.p, (int)n, T.p, (int)n, 0.0, G.p, nt, st);
+      k_cholqr_small<<<1, 32, 0, st>>>(G.p, nt, 1e-10, Pm.p, (int*)(Pm.p + nt * nt), Cc.p);
+      RIS_CHECK_LAUNCH();
+      RIS_CUDA(cudaMemcpyAsync(&nkeep, Pm.p + nt * nt, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RIS_CUDA(cudaStreamSynchronize(st));
+      if (nkeep == 0) break;
+      dgemm(false, false, nkeep, (int)n, nt, 1.0, Pm.p, nt, T.p, (int)n, 0.0, tmp.p, (int)n, st);
+      RIS_CUDA(cudaMemcpyAsync(T.p, tmp.p, sizeof(double) * nkeep * n, cudaMemcpyDeviceToDevice, st));
+      nt = nkeep;
+    }
+    return nkeep;
+  };
+  auto subspace_rows = [&](int m0, int m1) {
+    // rows m0..m1 of a+ and a-, mirrored
+    dgemm(false, true, m1 - m0, m1, (int)n, 1.0, V.p + (size_t)m0 * n, (int)n, PV.p, (int)n, 0.0,
+          Ap.p + (size_t)m0 * maxsp, maxsp, st);
+    dgemm(false, true, m1 - m0, m1, (int)n, 1.0, V.p + (size_t)m0 * n, (int)n, MV.p, (int)n, 0.0,
+          Am.p + (size_t)m0 * maxsp, maxsp, st);
+    if (m0 > 0) {
+      k_mirror<<<cdiv((long long)(m1 - m0) * m0 + 1, 256), 256, 0, st>>>(Ap.p, maxsp, m0, m1);
+      RIS_CHECK_LAUNCH();
+      k_mirror<<<cdiv((long long)(m1 - m0) * m0 + 1, 256), 256, 0, st>>>(Am.p, maxsp, m0, m1);
+      RIS_CHECK_LAUNCH();
+    }
+  };
+  k_lowest<<<1, 1024, 0, st>>>(de.p, (int)n, nb0, d_idx);
+  RIS_CHECK_LAUNCH();
+  k_unit_rows<<<nb0, 256, 0, st>>>(d_idx, nb0, n, V.p);
+  RIS_CHECK_LAUNCH();
+  int m = nb0;
+  products(V.p, m, PV.p, MV.p);
+  subspace_rows(0, m);
+  std::vector<double> rn(2 * ns);
+  bool converged = false;
+  int it = 0;
+  int* d_info = idxbuf.p + std::max(nb0, ns);
+  for (it = 0; it < opt.max_iter; it++) {
+    // reduced problem
+    k_copy_sub<<<cdiv(m * m, 256), 256, 0, st>>>(Am.p, maxsp, m, Lc.p);
+    RIS_CHECK_LAUNCH();
+    cholesky(Lc.p, m, d_info, st);
+    int info = 0;
+    RIS_CUDA(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    dgemm(false, false, m, m, m, 1.0, Ap.p, maxsp, Lc.p, m, 0.0, Ht.p, m, st);
+    dgemm(true, false, m, m, m, 1.0, Lc.p, m, Ht.p, m, 0.0, Hm.p, m, st);
+    const int nk = std::min(m, ns);
+    sym_eig_lowest(Hm.p, m, m, nk, w2.p, S.p, ework.p, st);
+    RIS_CUDA(cudaStreamSynchronize(st));
+    RIS_REQUIRE(info == 0, RIS_ERR_ARG, "A-B is not positive definite in the Davidson subspace");
+    k_rpa_omega<<<cdiv(ns * m, 256), 256, 0, st>>>(w2.p, ns, om.p, S.p, m);
+    RIS_CHECK_LAUNCH();
+    // R_sub = y L^T, L_sub = R_sub a+ / omega
+    dgemm(false, true, ns, m, m, 1.0, S.p, m, Lc.p, m, 0.0, Rs.p, m, st);
+    dgemm(false, false, ns, m, m, 1.0, Rs.p, m, Ap.p, maxsp, 0.0, Ls.p, m, st);
+    k_rowcomb<<<cdiv((long long)ns * m, 256), 256, 0, st>>>(Ls.p, nullptr, om.p, 1.0, 0.0, -1, m, ns, Ls.p);
+    RIS_CHECK_LAUNCH();
+    dgemm(false, false, ns, (int)n, m, 1.0, Rs.p, m, V.p, (int)n, 0.0, Rf.p, (int)n, st);
+    dgemm(false, false, ns, (int)n, m, 1.0, Ls.p, m, V.p, (int)n, 0.0, Lf.p, (int)n, st);
+    // residuals: (A+B)R - omega L and (A-B)L - omega R
+    dgemm(false, false, ns, (int)n, m, 1.0, Rs.p, m, PV.p, (int)n, 0.0, rR.p, (int)n, st);
+    dgemm(false, false, ns, (int)n, m, 1.0, Ls.p, m, MV.p, (int)n, 0.0, rL.p, (int)n, st);
+    k_rowcomb<<<cdiv(n * ns, 256), 256, 0, st>>>(Lf.p, rR.p, om.p, -1.0, 1.0, 1, n, ns, rR.p);
+    RIS_CHECK_LAUNCH();
+    k_rowcomb<<<cdiv(n * ns, 256), 256, 0, st>>>(Rf.p, rL.p, om.p, -1.0, 1.0, 1, n, ns, rL.p);
+    RIS_CHECK_LAUNCH();
+    row_norms(rR.p, ns, n, nrm.p, st);
+    row_norms(rL.p, ns, n, nrm.p + ns, st);
+    RIS_CUDA(cudaMemcpyAsync(rn.data(), nrm.p, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> u;
+    for (int k = 0; k < ns; k++)
+      if (!(sqrt(rn[k] + rn[ns + k]) <= tol)) u.push_back(k);
+    if (u.empty()) {
+      converged = true;
+      break;
+    }
+    const int nu = (int)u.size();
+    RIS_CUDA(cudaMemcpyAsync(d_idx, u.data(), sizeof(int) * nu, cudaMemcpyHostToDevice, st));
+    k_precond<<<cdiv(n * nu, 256), 256, 0, st>>>(rR.p, de.p, om.p, d_idx, n, nu, T.p);
+    RIS_CHECK_LAUNCH();
+    k_precond<<<cdiv(n * nu, 256), 256, 0, st>>>(rL.p, de.p, om.p, d_idx, n, nu, T.p + (size_t)nu * n);
+    RIS_CHECK_LAUNCH();
+    int nt = 2 * nu;
+    if (m + nt > maxsp) {
+      // restart from the current R and L vectors
+      RIS_CUDA(cudaMemcpyAsync(tmp.p, T.p, sizeof(double) * nt * n, cudaMemcpyDeviceToDevice, st));
+      RIS_CUDA(cudaMemcpyAsync(T.p, Rf.p, sizeof(double) * ns * n, cudaMemcpyDeviceToDevice, st));
+      RIS_CUDA(cudaMemcpyAsync(T.p + (size_t)ns * n, Lf.p, sizeof(double) * ns * n,
+                               cudaMemcpyDeviceToDevice, st));
+      SBuf<double> keepT((size_t)nt * n, st);
+      RIS_CUDA(cudaMemcpyAsync(keepT.p, tmp.p, sizeof(double) * nt * n, cudaMemcpyDeviceToDevice, st));
+      const int nr = orthonormalise(2 * ns, 0);
+      RIS_REQUIRE(nr > 0, RIS_ERR_NOT_CONVERGED, "RPA Davidson restart lost its basis");
+      RIS_CUDA(cudaMemcpyAsync(V.p, T.p, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, st));
+      m = nr;
+      products(V.p, m, PV.p, MV.p);
+      subspace_rows(0, m);
+      RIS_CUDA(cudaMemcpyAsync(T.p, keepT.p, sizeof(double) * nt * n, cudaMemcpyDeviceToDevice, st));
+      nt = std::min(nt, maxsp - m);
+    }
+    const int nk2 = orthonormalise(nt, m);
+    if (nk2 == 0) break;
+    RIS_CUDA(cudaMemcpyAsync(V.p + (size_t)m * n, T.p, sizeof(double) * nk2 * n, cudaMemcpyDeviceToDevice, st));
+    products(V.p + (size_t)m * n, nk2, PV.p + (size_t)m * n, MV.p + (size_t)m * n);
+    subspace_rows(m, m + nk2);
+    m += nk2;
+  }
+  stats[4] = nprod;
+  stats[5] = it;
+  RIS_REQUIRE(converged, RIS_ERR_NOT_CONVERGED,
+              "RPA Davidson did not converge in " + std::to_string(it) + " iterations");
+  nstates = ns;
+  omega.ensure(ns);
+  X.ensure((size_t)ns * n);
+  Y.ensure((size_t)ns * n);
+  RIS_CUDA(cudaMemcpyAsync(omega.p, om.p, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
+  // X = (R + L)/2, Y = (R - L)/2
+  k_rowcomb<<<cdiv(n * ns, 256), 256, 0, st>>>(Rf.p, Lf.p, nullptr, 0.5, 0.5, 0, n, ns, X.p);
+  RIS_CHECK_LAUNCH();
+  k_rowcomb<<<cdiv(n * ns, 256), 256, 0, st>>>(Rf.p, Lf.p, nullptr, 0.5, -0.5, 0, n, ns, Y.p);
+  RIS_CHECK_LAUNCH();
+  k_phase<<<ns, 256, 0, st>>>(X.p, Y.p, n);
+  RIS_CHECK_LAUNCH();
+  if (mixed) {
+    int h_err = 0;
+    RIS_CUDA(cudaMemcpyAsync(&h_err, d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+    RIS_REQUIRE(h_err == 0, RIS_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait timed out");
+  }
 }
 
 // ------------------------------------------------------------------ derivatives
@@ -1230,12 +1506,15 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
         RIS_CHECK_LAUNCH();
       }
     }
-  } else {
+  }
+  if (!mixed || rpa) {
     QR.ensure((size_t)nsu * o * nn, st);
     QL.ensure((size_t)nsu * o * nn, st);
     for (int s = 0; s < nsu; s++) {
-      dgemm(false, false, nn, v, o, 1.0, Co, nmo, Rs.p + s * nov, v, 0.0, t1.p, v, st);
-      dgemm(false, true, nn, nn, v, 1.0, t1.p, v, Cv, nmo, 0.0, DR.p + (size_t)s * nn * nn, nn, st);
+      if (!mixed) {
+        dgemm(false, false, nn, v, o, 1.0, Co, nmo, Rs.p + s * nov, v, 0.0, t1.p, v, st);
+        dgemm(false, true, nn, nn, v, 1.0, t1.p, v, Cv, nmo, 0.0, DR.p + (size_t)s * nn * nn, nn, st);
+      }
       dgemm(false, true, o, nn, v, 1.0, Rs.p + s * nov, v, Cv, nmo, 0.0, QR.p + (size_t)s * o * nn, nn, st);
       dgemm(false, true, o, nn, v, 1.0, Ls.p + s * nov, v, Cv, nmo, 0.0, QL.p + (size_t)s * o * nn, nn, st);
     }
@@ -1314,7 +1593,43 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
       // Omega[P][Q] += f sum_ij c^oo_ij,P G_ij,Q   (K functions are union 0..nK-1)
       dgemm(true, false, nK, nK, o * o, f, cKoo.p, nK, Goo.p, nK, 1.0, Om.p, nU, st);
     }
-    if (rpa) throw Error{RIS_ERR_ARG, "RPA derivatives are not available in this build"};
+    if (rpa) {
+      // (ib|ja) terms, weights -c_x/2 for (R_I,R_J) and +c_x/2 for (L_I,L_J):
+      //   E1_P = U c_P^T, E2_P = V c_P^T (nocc x nocc), c_P = c^ov[P] as [k][a]
+      //   Gamma_ov^T[nu][mu] += w sum_k C_o[nu][k] (E1_P Q_V + E2_P Q_U)[k][mu]
+      //   Omega[A][B] += w sum_{k,i} E2_A[k][i] E1_B[i][k]
+      SBuf<double> E1((size_t)nK * o * o, st), E2((size_t)nK * o * o, st), E1t((size_t)nK * o * o, st),
+          M2((size_t)nK * o * nn, st), M2p((size_t)nK * o * nn, st);
+      for (int cmb = 0; cmb < 2; cmb++) {
+        const double wgt = cmb == 0 ? -0.5 * cx : 0.5 * cx;
+        const double* U = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sI * nov;
+        const double* Vv = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sJ * nov;
+        const double* QU = (cmb == 0 ? QR.p : QL.p) + (size_t)sI * o * nn;
+        const double* QV = (cmb == 0 ? QR.p : QL.p) + (size_t)sJ * o * nn;
+        GemmBatch bP;
+        bP.nb1 = nK;
+        bP.sB1 = nov;
+        bP.sC1 = (long long)o * o;
+        dgemm(false, true, o, o, v, 1.0, U, v, cKovP.p, v, 0.0, E1.p, o, st, bP);
+        dgemm(false, true, o, o, v, 1.0, Vv, v, cKovP.p, v, 0.0, E2.p, o, st, bP);
+        GemmBatch bM;
+        bM.nb1 = nK;
+        bM.sA1 = (long long)o * o;
+        bM.sC1 = (long long)o * nn;
+        dgemm(false, false, o, nn, o, 1.0, E1.p, o, QV, nn, 0.0, M2.p, nn, st, bM);
+        dgemm(false, false, o, nn, o, 1.0, E2.p, o, QU, nn, 1.0, M2.p, nn, st, bM);
+        k_permute120<<<cdiv((long long)nK * o * nn, 256), 256, 0, st>>>(M2.p, nK, o, nn, M2p.p);
+        RIS_CHECK_LAUNCH();
+        GemmBatch bG;
+        bG.nb1 = nn;
+        bG.sB1 = (long long)nK * o;
+        bG.sC1 = (long long)nn * nU;
+        dgemm(false, true, nn, nK, o, wgt, C.p, nmo, M2p.p, o, 1.0, Gam.p, nU, st, bG);
+        // E1t[P][k][i] = E1[P][i][k]
+        transpose_last2(E1.p, nK, o, o, E1t.p, st);
+        dgemm(false, true, nK, nK, o * o, wgt, E2.p, o * o, E1t.p, o * o, 1.0, Om.p, nU, st);
+      }
+    }
     prof_begin(kProfContract, st);
     k_contract<<<nn, 128, 0, st>>>(D.p, Gam.p, nn, nU, Wc.p);
     RIS_CHECK_LAUNCH();

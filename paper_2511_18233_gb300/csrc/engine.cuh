@@ -92,6 +92,7 @@ struct Engine {
   DBuf BKoo;      // [i][j][R]
   DBuf BKvvD;     // [b][R][a] (Davidson layout)
   DBuf BKovR;     // [R][i][a] (RPA)
+  DBuf cKovP;     // c^K_ov as [P][i][a] (RPA)
   DBuf cKoo, cKvv, cKov;  // fitting coefficients c = B L^-1, [p][q][P]
 
   // mixed precision (3xTF32) operands: hi/lo FP32 splits
@@ -130,6 +131,7 @@ struct Engine {
   // helpers
   void apply_A_tda(const double* Xin, int nvec, double* out);
   void apply_A_mixed(const double* Xin, int nvec, double* out);
+  void apply_exchange_mixed(const double* Z, int nvec, double* out, double alpha, double beta);
   void prepare_mixed();
   // exchange part of Gamma / Omega for one (U,V) pair with weight f (3xTF32);
   // US/VS: splits of U, V [i][a]; WU/WV: [Q^T | C_o] splits of U and V
@@ -140,6 +142,8 @@ struct Engine {
   void apply_ApB_AmB(const double* Zin, int nvec, double* outP, double* outM);
   void davidson_tda(int ns);
   void davidson_rpa(int ns);
+  // exchange (ij|ab) and (ib|ja) contractions of nvec vectors: K1, K2 [nvec][nov]
+  void exchange_terms(const double* Z, int nvec, double* K1, double* K2, bool mixed);
 };
 
 // out[g][k] = num[g][k] / den[g]
