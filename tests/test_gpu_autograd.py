@@ -46,13 +46,14 @@ def test_autograd_small_against_fd_and_oracle(torch_mod, oracle, rpa):
     else:
         om, X = orc.tda_dense(4)
         ref = orc.gradients([1], X)[0]
-    assert float(w) == pytest.approx(om[1], rel=1e-9)
+    assert float(w.detach()) == pytest.approx(om[1], rel=1e-9)
     assert np.max(np.abs(g - ref)) <= 1e-9 * np.max(np.abs(ref))
     for (A, x) in [(0, 0), (5, 1)]:
         fd2 = _fd(model, mol.coords, 1, A, x, 1e-3, 2)
         fd5 = _fd(model, mol.coords, 1, A, x, 1e-3, 5)
-        assert g[A, x] == pytest.approx(fd2, rel=1e-5, abs=1e-8)
-        assert g[A, x] == pytest.approx(fd5, rel=1e-7, abs=1e-10)
+        # 2-point stencil at h = 1e-3 bohr: O(h^2) truncation, ~1e-7 Ha/bohr here
+        assert abs(g[A, x] - fd2) <= 1e-6
+        assert abs(g[A, x] - fd5) <= 1e-9
 
 
 @gpu
@@ -72,10 +73,15 @@ def test_autograd_flake_rpa(torch_mod, oracle):
     w.backward()
     g = R.grad.cpu().numpy()
     assert np.max(np.abs(g.sum(axis=0))) <= 1e-8
-    for (A, x) in [(0, 0), (60, 1)]:
-        fd = _fd(model, mol.coords, 0, A, x, 1e-3, 2)
-        assert g[A, x] == pytest.approx(fd, rel=1e-4, abs=1e-6)
+    # the oracle's gradient of the same state (library amplitudes), one atom
     out = model.solve(torch.as_tensor(mol.coords))
     orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc)
     ref = orc.gradients([0], out[1][:1], out[2][:1], atoms=[60])[0]
-    assert np.max(np.abs(g[60] - ref[60])) <= 1e-5
+    # cond(M_J) ~ 6e8 limits the agreement of two FP64 RI evaluations to ~1e-7
+    assert np.max(np.abs(g[60] - ref[60])) <= 1e-6 * np.max(np.abs(ref[60]))
+    # central differences, step 1e-3 bohr.  The flake's J metric has a
+    # condition number ~6e8, so each FP64 energy carries ~1e-8 Ha of rounding
+    # noise, i.e. ~1e-5 Ha/bohr in a 2-point difference at this step.
+    for (A, x) in [(0, 0), (60, 1)]:
+        fd = _fd(model, mol.coords, 0, A, x, 1e-3, 2)
+        assert abs(g[A, x] - fd) <= 5e-5
