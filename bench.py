@@ -153,6 +153,49 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
+def run_serving(args):
+    """Serving stream of surface-hopping requests (energies + active-state
+    gradient + NACs to the neighbouring states) from a closed pool of
+    trajectories with Poisson arrivals; mixed precision with continuous
+    batching over several slots, then the same stream replayed on the plain
+    FP64 path one request at a time (cold Davidson, one slot)."""
+    import torch
+    from paper_2511_18233_gb300 import build, serve
+    build.build()
+    torch.cuda.set_device(0)
+    specs = serve.make_trajectories(args.serve_trajectories, seed=2025)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    out = {}
+    for mode in ("mixed", "fp64_plain"):
+        mixed = mode == "mixed"
+        nreq = args.serve_requests if mixed else args.serve_fp64_requests
+        nwarm = args.serve_warmup if mixed else max(2, args.serve_warmup // 20)
+        with Clocks(0) as clk:
+            res = serve.serve(specs, n_requests=nreq, n_warmup=nwarm, rate=args.serve_rate,
+                              nslots=args.serve_slots if mixed else 1, budget_bytes=budget,
+                              precision="mixed" if mixed else "fp64", use_guess=args.serve_guess and mixed, seed=7)
+        done = res.pop("done")
+        res.pop("trajectories")
+        iters = [r.result["n_iter"] for r in done if r.result]
+        res["mean_davidson_iterations"] = float(np.mean(iters)) if iters else None
+        res["clocks"] = clk.summary()
+        out[mode] = res
+    m, f = out["mixed"], out["fp64_plain"]
+    line = {"metric": "serving grad+NAC evals/s; p50/p99 latency", "value": m["throughput_per_s"],
+            "unit": "evals/s", "higher_is_better": True, "n_gpus": 1,
+            "p50_ms": m["p50_ms"], "p99_ms": m["p99_ms"],
+            "vs_fp64_plain": m["throughput_per_s"] / f["throughput_per_s"],
+            "dtype": "f32/tf32x3+f64", "data": "synthetic",
+            "config": {"workload": f"{args.serve_trajectories} trajectories, chains C4..C40 and flakes "
+                                   f"4-7 A, 5-10 states, Poisson {args.serve_rate}/s, closed pool",
+                       "slots": args.serve_slots, "budget_bytes": budget,
+                       "davidson_seed": "previous step" if args.serve_guess else "cold"},
+            "mixed": m, "fp64_plain": f}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -161,9 +204,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the serving stream instead")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-fp64-requests", type=int, default=100)
+    ap.add_argument("--serve-trajectories", type=int, default=64)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-guess", action="store_true",
+                    help="seed each step's Davidson with the trajectory's resident amplitudes")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serving(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

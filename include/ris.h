@@ -88,6 +88,9 @@ typedef struct {
   int profile;        /* 1: time kernel classes with CUDA events (see ris_get_stats) */
   double mixed_tol;   /* RIS_MIXED: residual tolerance of the 3xTF32 Davidson phase; default 1e-6 */
   int refine;         /* RIS_MIXED: 1 = continue with FP64 products to conv_tol; default 0 */
+  int precond;        /* TDA Davidson preconditioner: 0 (default) = (D - s + 2 B^J B^J^T)^-1
+                         applied exactly (Woodbury) with one shift s just below the smallest
+                         orbital-energy difference; 1 = diagonal (D - omega_k)^-1 per state */
 } ris_options;
 
 typedef struct {
@@ -120,7 +123,8 @@ ris_status ris_build_aux(ris_ctx* ctx, int natm, const double* coords, int nshel
  * MO data and the B tensors B^X_{pq,R} = sum_P (pq|P) (L_X^-T)_PR (RI of
  * Eq. (g_modified)): B^J over the ov block and B^K over the oo and vv blocks
  * (plus ov for RPA).  C: [nao][nmo] row-major, occupied columns first;
- * mo_energy: [nmo].  nmo must equal nao; 0 < nocc < nmo.
+ * mo_energy: [nmo].  nmo <= nao (fewer MOs than AOs when near-dependent AO
+ * combinations were dropped); 0 < nocc < nmo.
  */
 ris_status ris_build_B(ris_ctx* ctx, int nao, int nmo, int nocc, const double* C,
                        const double* mo_energy);
@@ -134,6 +138,17 @@ ris_status ris_build_B(ris_ctx* ctx, int nao, int nmo, int nocc, const double* C
  * Errors: RIS_ERR_NOT_CONVERGED after max_iter (outputs untouched).
  */
 ris_status ris_excite(ris_ctx* ctx, int nstates, double* omega, double* X, double* Y);
+
+/*
+ * As ris_excite (TDA), but the Davidson search starts from the nstates given
+ * vectors X_guess [nstates][nocc][nvir] (host or device) instead of unit
+ * vectors — for instance the amplitudes of the previous step of a
+ * trajectory.  The guesses need not be normalised but must be linearly
+ * independent (RIS_ERR_ARG otherwise).  With the rpa option the guess is
+ * ignored and the search starts cold.
+ */
+ris_status ris_excite_guess(ris_ctx* ctx, int nstates, const double* X_guess, double* omega,
+                            double* X, double* Y);
 
 /*
  * The response operator applied to nvec vectors (the Davidson product of
@@ -173,16 +188,32 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
  * Statistics, copied into out[0..n-1] (n <= 32):
  *   [0] aux, [1] B, [2] excite, [3] gradient/nac: milliseconds of the last
  *       call of each kind (CUDA events on the context's stream);
- *   [4] A-products and [5] Davidson iterations of the last excite;
+ *   [4] A-products and [5] Davidson iterations of the last excite,
+ *   [6] FP64 products of its refinement phase (mixed with refine), [7] the
+ *   largest residual norm |A x - omega x| at its last iteration (TDA);
  *   [15] kernels launched by the library since it was loaded (all contexts);
  *   with the profile option, per kernel class since the previous call:
  *   [16] GEMM ms, [17] GEMM flops, [18] 3c-integral ms, [19] shell triples,
  *   [20] 3c-derivative ms, [21] shell triples, [22] derivative-contraction
  *   ms, [23] its algorithmic bytes, [24] subspace-eigensolver ms, [25] calls,
  *   [26] 3xTF32 tensor-core GEMM ms, [27] its algorithmic flops (one per
- *   multiply-add pair of the product, the three TF32 passes counted once).
+ *   multiply-add pair of the product, the three TF32 passes counted once);
+ *   [28] device bytes the context holds now, [29] the most it has held
+ *   since it was created or last trimmed (its HBM footprint).
  */
 ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n);
+
+/*
+ * Release every device buffer the context holds (integrals, B tensors,
+ * amplitudes, work space) back to the device's stream-ordered pool and
+ * return it to its just-created state; the next call must be
+ * ris_build_aux.  Resets the footprint high-water mark (stats [29]).
+ * The library allocates from the device's default memory pool in stream
+ * order on the context's stream, so several contexts driven from
+ * different host threads run concurrently without device-wide
+ * synchronisation.  A context must not be used by two threads at once.
+ */
+ris_status ris_trim(ris_ctx* ctx);
 
 /*
  * Test hook: Boys function F_m(T) = int_0^1 t^{2m} e^{-T t^2} dt as used by

@@ -1,6 +1,8 @@
 // extern "C" boundary of the TDDFT-ris engine (declared in include/ris.h).
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
 #include <memory>
 
 #include "engine.cuh"
@@ -10,7 +12,7 @@ struct ris_ctx {
 };
 
 namespace ris {
-long long g_launches = 0;
+std::atomic<long long> g_launches{0};
 
 namespace {
 struct Rec {
@@ -18,6 +20,9 @@ struct Rec {
   cudaEvent_t a, b;
   double work;
 };
+// Profiling is process-wide (one context at a time); the mutex only keeps
+// concurrent contexts from corrupting the record list.
+std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
@@ -36,12 +41,14 @@ cudaEvent_t take_event() {
 void prof_enable(bool on) { g_prof_on = on; }
 void prof_begin(int cls, cudaStream_t st) {
   if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   Rec r{cls, take_event(), nullptr, 0.0};
   RIS_CUDA(cudaEventRecord(r.a, st));
   g_recs.push_back(r);
 }
 void prof_end(int cls, cudaStream_t st, double work) {
   if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   for (auto it = g_recs.rbegin(); it != g_recs.rend(); ++it)
     if (it->cls == cls && it->b == nullptr) {
       it->b = take_event();
@@ -51,6 +58,7 @@ void prof_end(int cls, cudaStream_t st, double work) {
     }
 }
 void prof_collect(double* ms, double* work) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   for (int c = 0; c < kProfN; c++) ms[c] = work[c] = 0.0;
   for (auto& r : g_recs) {
     if (r.b) {
@@ -72,6 +80,11 @@ namespace {
 template <class F>
 ris_status guarded(ris_ctx* ctx, F&& f) {
   if (!ctx) return RIS_ERR_ARG;
+  struct TrackScope {  // route this thread's allocations to the context
+    ris::MemTrack* prev;
+    explicit TrackScope(ris::MemTrack* t) : prev(ris::t_track) { ris::t_track = t; }
+    ~TrackScope() { ris::t_track = prev; }
+  } scope(&ctx->eng.mem);
   try {
     RIS_CUDA(cudaSetDevice(ctx->eng.device));
     f();
@@ -120,6 +133,7 @@ ris_status ris_options_default(ris_options* opt) {
   opt->profile = 0;
   opt->mixed_tol = 1e-6;
   opt->refine = 0;
+  opt->precond = 0;
   return RIS_OK;
 }
 
@@ -134,6 +148,7 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
   if (o.precision != RIS_FP64 && o.precision != RIS_MIXED) return RIS_ERR_ARG;
   if (!(o.conv_tol > 0) || o.max_iter <= 0 || !(o.screen_thr >= 0)) return RIS_ERR_ARG;
   if (o.precision == RIS_MIXED && !(o.mixed_tol > 0)) return RIS_ERR_ARG;
+  if (o.precond != 0 && o.precond != 1) return RIS_ERR_ARG;
   c->eng.opt = o;
   c->eng.device = o.device;
   if (o.profile) ris::prof_enable(true);
@@ -189,6 +204,16 @@ ris_status ris_apply(ris_ctx* ctx, int nvec, const double* X, double* out, doubl
   return guarded(ctx, [&] { ctx->eng.apply(nvec, X, out, out2); });
 }
 
+ris_status ris_excite_guess(ris_ctx* ctx, int nstates, const double* X_guess, double* omega,
+                            double* X, double* Y) {
+  return guarded(ctx, [&] {
+    RIS_REQUIRE(X_guess, RIS_ERR_ARG, "X_guess is NULL");
+    StageTimer t(ctx->eng, 2);
+    ctx->eng.excite(nstates, omega, X, Y, X_guess);
+    t.stop();
+  });
+}
+
 ris_status ris_gradient(ris_ctx* ctx, int n, const int* states, int nx, const double* X_in,
                         const double* Y_in, double* grad) {
   return guarded(ctx, [&] {
@@ -214,7 +239,7 @@ ris_status ris_nac(ris_ctx* ctx, int npair, const int* pairs, int nx, const doub
     if (X_in) {
       RIS_REQUIRE(omega_in, RIS_ERR_ARG, "omega_in is required with X_in");
       om.resize(nx);
-      RIS_CUDA(cudaMemcpy(om.data(), omega_in, sizeof(double) * nx, cudaMemcpyDefault));
+      ris::copy_to_host(om.data(), omega_in, nx, e.st);
     } else {
       RIS_REQUIRE(e.stage >= 3, RIS_ERR_STATE, "no amplitudes: call ris_excite or pass X_in");
       om = e.h_omega;
@@ -264,7 +289,7 @@ ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n) {
   if (!ctx || !out || n < 0 || n > 32) return RIS_ERR_ARG;
   double all[32] = {0};
   for (int i = 0; i < 16; i++) all[i] = ctx->eng.stats[i];
-  all[15] = (double)ris::g_launches;
+  all[15] = (double)ris::g_launches.load();
   try {
     cudaSetDevice(ctx->eng.device);
     double ms[ris::kProfN], work[ris::kProfN];
@@ -276,8 +301,17 @@ ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n) {
   } catch (const ris::Error&) {
     return RIS_ERR_CUDA;
   }
+  all[28] = (double)ctx->eng.mem.cur;
+  all[29] = (double)ctx->eng.mem.peak;
   for (int i = 0; i < n; i++) out[i] = all[i];
   return RIS_OK;
+}
+
+ris_status ris_trim(ris_ctx* ctx) {
+  return guarded(ctx, [&] {
+    ctx->eng.trim();
+    RIS_CUDA(cudaStreamSynchronize(ctx->eng.st));
+  });
 }
 
 const char* ris_last_error(const ris_ctx* ctx) { return ctx ? ctx->eng.err.c_str() : "null context"; }

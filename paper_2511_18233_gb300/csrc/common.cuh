@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -34,7 +35,7 @@ struct Error {
   } while (0)
 
 // Every kernel launch is followed by RIS_CHECK_LAUNCH, which also counts it.
-extern long long g_launches;
+extern std::atomic<long long> g_launches;
 #define RIS_CHECK_LAUNCH()        \
   do {                            \
     ++::ris::g_launches;          \
@@ -57,5 +58,28 @@ void prof_collect(double* ms, double* work);  // sums per class since the last c
 __host__ __device__ inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Device bytes a context holds: now and the high-water mark since it was
+// created or last trimmed.  A context is driven by one host thread at a time,
+// so the counters need no atomics.
+struct MemTrack {
+  long long cur = 0, peak = 0;
+  void add(long long b) {
+    cur += b;
+    if (cur > peak) peak = cur;
+  }
+};
+// Tracker of the context the calling thread is serving (set per API call).
+extern thread_local MemTrack* t_track;
+
+// Stream-ordered allocation from the device's default pool (no device-wide
+// synchronisation, unlike cudaMalloc / cudaFree), counted against t_track.
+// Throws RIS_ERR_OOM.
+void* dev_alloc(size_t bytes, cudaStream_t st, MemTrack** owner);
+void dev_free(void* p, size_t bytes, cudaStream_t st, MemTrack* owner);
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device),
+// safe to call from several threads.
+void ensure_smem_attr(const void* func, int bytes);
 
 }  // namespace ris

@@ -27,83 +27,119 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <set>
 
 #include "engine.cuh"
 
 namespace ris {
 
-void DBuf::ensure(size_t count) {
+thread_local MemTrack* t_track = nullptr;
+
+void* dev_alloc(size_t bytes, cudaStream_t st, MemTrack** owner) {
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{RIS_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+  }
+  *owner = t_track;
+  if (t_track) t_track->add((long long)bytes);
+  return p;
+}
+void dev_free(void* p, size_t bytes, cudaStream_t st, MemTrack* owner) {
+  cudaFreeAsync(p, st);
+  if (owner) owner->cur -= (long long)bytes;
+}
+
+void ensure_smem_attr(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  RIS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({func, dev})) return;
+  RIS_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert({func, dev});
+}
+
+void DBuf::ensure(size_t count, cudaStream_t s) {
   if (p && count <= n) return;
   release();
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(&p, count * sizeof(double));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    p = nullptr;
-    n = 0;
-    throw Error{RIS_ERR_OOM, "device allocation of " + std::to_string(count * 8) + " bytes failed"};
-  }
+  st = s;
+  p = (double*)dev_alloc(count * sizeof(double), st, &tr);
   n = count;
 }
 void DBuf::release() {
-  if (p) cudaFree(p);
+  if (p) dev_free(p, n * sizeof(double), st, tr);
   p = nullptr;
   n = 0;
 }
 
-void FBuf::ensure(size_t count, cudaStream_t st) {
+void FBuf::ensure(size_t count, cudaStream_t s) {
   if (p && count <= n) return;
   release();
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(&p, count * sizeof(float));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    p = nullptr;
-    n = 0;
-    throw Error{RIS_ERR_OOM, "device allocation of " + std::to_string(count * 4) + " bytes failed"};
-  }
+  st = s;
+  p = (float*)dev_alloc(count * sizeof(float), st, &tr);
   n = count;
   RIS_CUDA(cudaMemsetAsync(p, 0, count * sizeof(float), st));
 }
 void FBuf::release() {
-  if (p) cudaFree(p);
+  if (p) dev_free(p, n * sizeof(float), st, tr);
   p = nullptr;
   n = 0;
 }
 
-static void free_shells(ShellSet& s) {
+static void free_shells(ShellSet& s, cudaStream_t st) {
   int** ip[] = {&s.atom, &s.l, &s.off, &s.jmap, &s.kmap, &s.fun_atom, &s.d_by_l[0], &s.d_by_l[1]};
   for (auto q : ip)
     if (*q) {
-      cudaFree(*q);
+      cudaFreeAsync(*q, st);
       *q = nullptr;
     }
   double** dp[] = {&s.ex, &s.nbase};
   for (auto q : dp)
     if (*q) {
-      cudaFree(*q);
+      cudaFreeAsync(*q, st);
       *q = nullptr;
     }
 }
 
+void Engine::trim() {
+  free_shells(ao, st);
+  free_shells(aux, st);
+  free_pairs(pl, st);
+  if (d_jU) cudaFreeAsync(d_jU, st);
+  if (d_kU) cudaFreeAsync(d_kU, st);
+  d_jU = d_kU = nullptr;
+  DBuf* dbs[] = {&xyz, &TJ, &TK, &MU, &dMU, &LJinv, &LKinv, &D, &C, &eps, &de, &BJ, &BKoo,
+                 &BKvvD, &BKovR, &cKovP, &cKoo, &cKvv, &cKov, &cKooP, &omega, &X, &Y,
+                 &w1, &w2, &w3, &w4, &w5, &w6, &w7, &w8};
+  for (DBuf* b : dbs) b->release();
+  FBuf* fbs[] = {&BooH, &BooL, &BvvH, &BvvL, &XtH, &XtL, &YH, &YL, &cvvH, &cvvL,
+                 &cooH, &cooL, &CoH, &CoL, &CvH, &CvL};
+  for (FBuf* b : fbs) b->release();
+  have_D = false;
+  stage = 0;
+  nstates = 0;
+  mem.peak = mem.cur;
+}
+
 Engine::~Engine() {
-  free_shells(ao);
-  free_shells(aux);
-  free_pairs(pl);
-  if (d_jU) cudaFree(d_jU);
-  if (d_kU) cudaFree(d_kU);
-  if (d_info) cudaFree(d_info);
-  if (d_tcerr) cudaFree(d_tcerr);
+  trim();
+  if (d_info) cudaFreeAsync(d_info, st);
+  if (d_tcerr) cudaFreeAsync(d_tcerr, st);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
-  if (own_stream && st) cudaStreamDestroy(st);
+  if (st) cudaStreamSynchronize(st);
 }
 
 template <class T>
 static T* upload(const std::vector<T>& v, cudaStream_t st) {
   T* d = nullptr;
-  RIS_CUDA(cudaMalloc(&d, sizeof(T) * std::max<size_t>(v.size(), 1)));
+  RIS_CUDA(cudaMallocAsync((void**)&d, sizeof(T) * std::max<size_t>(v.size(), 1), st));
   if (!v.empty())
     RIS_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
   return d;
@@ -126,6 +162,16 @@ static void copy_in(double* dst, const double* src, size_t n, cudaStream_t st) {
                            is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                            st));
 }
+// Copy n doubles from a user pointer (host or device) into host memory;
+// a device source is read on the context's stream (no device-wide sync).
+void copy_to_host(double* dst, const double* src, size_t n, cudaStream_t st) {
+  if (is_device_ptr(src)) {
+    RIS_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+  } else {
+    memcpy(dst, src, n * sizeof(double));
+  }
+}
 static void copy_out(double* dst, const double* src, size_t n, cudaStream_t st) {
   RIS_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double),
                            is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -135,7 +181,7 @@ static void copy_out(double* dst, const double* src, size_t n, cudaStream_t st) 
 static void make_shells(ShellSet& s, const std::vector<int>& atom, const std::vector<int>& l,
                         const std::vector<double>& ex, const std::vector<int>* jmap,
                         const std::vector<int>* kmap, cudaStream_t st) {
-  free_shells(s);
+  free_shells(s, st);
   s.n = (int)atom.size();
   s.h_atom = atom;
   s.h_l = l;
@@ -335,6 +381,60 @@ __global__ void k_precond(const double* __restrict__ R, const double* __restrict
   double den = de[i] - w[s];
   if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
   T[t] = R[(size_t)s * n + i] / den;
+}
+
+// Shift of the Coulomb-exact preconditioner: this far below the smallest
+// orbital-energy difference (Hartree), so that D - s stays positive.
+constexpr double kPrecondGap = 2e-3;
+
+// out[0] = min(x[0..n)); one block
+__global__ void __launch_bounds__(1024) k_min(const double* __restrict__ x, long long n,
+                                              double* __restrict__ out) {
+  __shared__ double red[32];
+  double m = 1e308;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, x[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 1e308;
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) out[0] = m;
+  }
+}
+
+// dinv = 1 / (de - s), s = min(de) - gap;  W[i][R] = dinv[i] BJ[i][R]
+__global__ void k_precond_setup(const double* __restrict__ de, const double* __restrict__ dmin,
+                                long long n, double gap, const double* __restrict__ BJ, int nJ,
+                                double* __restrict__ dinv, double* __restrict__ W) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nJ) return;
+  const long long i = t / nJ;
+  const double d = 1.0 / (de[i] - (dmin[0] - gap));
+  W[t] = d * BJ[t];
+  if (t % nJ == 0) dinv[i] = d;
+}
+
+__global__ void k_add_identity(double* __restrict__ A, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[(size_t)i * n + i] += 1.0;
+}
+
+// T[j] = R[u_j] * dinv
+__global__ void k_precond_scale(const double* __restrict__ R, const double* __restrict__ dinv,
+                                const int* __restrict__ u, long long n, int nt, double* __restrict__ T) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nt) return;
+  const long long i = t % n;
+  T[t] = R[(size_t)u[t / n] * n + i] * dinv[i];
+}
+
+// T -= 2 dinv * P (rows of length n)
+__global__ void k_precond_update(double* __restrict__ T, const double* __restrict__ P,
+                                 const double* __restrict__ dinv, long long n, int nt) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nt) return;
+  T[t] -= 2.0 * dinv[t % n] * P[t];
 }
 
 __global__ void k_scale_rows(double* __restrict__ X, long long n, int nrow, const double* __restrict__ nrm2) {
@@ -573,7 +673,7 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
   RIS_REQUIRE(natm_ > 0 && nshell > 0 && nJs > 0 && nKs > 0, RIS_ERR_ARG, "empty input");
   RIS_REQUIRE(coords && aos && auxJ && auxK, RIS_ERR_ARG, "null pointer");
   std::vector<double> hxyz(3 * (size_t)natm_);
-  RIS_CUDA(cudaMemcpy(hxyz.data(), coords, sizeof(double) * 3 * natm_, cudaMemcpyDefault));
+  copy_to_host(hxyz.data(), coords, 3 * (size_t)natm_, st);
   for (double v : hxyz) RIS_REQUIRE(std::isfinite(v), RIS_ERR_ARG, "non-finite coordinate");
   auto check = [&](const ris_shell* s, int n, int lmax, const char* what) {
     for (int i = 0; i < n; i++) {
@@ -591,7 +691,7 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
   stage = 0;
   have_D = false;
   natm = natm_;
-  xyz.ensure(3 * (size_t)natm);
+  xyz.ensure(3 * (size_t)natm, st);
   RIS_CUDA(cudaMemcpyAsync(xyz.p, hxyz.data(), sizeof(double) * 3 * natm, cudaMemcpyHostToDevice, st));
   // AO shells
   {
@@ -656,8 +756,8 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
         if (jm[s] >= 0) h_jU[jm[s] + c] = aux.h_off[s] + c;
         if (km[s] >= 0) h_kU[km[s] + c] = aux.h_off[s] + c;
       }
-    if (d_jU) cudaFree(d_jU);
-    if (d_kU) cudaFree(d_kU);
+    if (d_jU) cudaFreeAsync(d_jU, st);
+    if (d_kU) cudaFreeAsync(d_kU, st);
     d_jU = upload(h_jU, st);
     d_kU = upload(h_kU, st);
   }
@@ -672,19 +772,19 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
   build_pairs(ao, xyz.p, opt.screen_thr / std::max(vmax, 1e-300), pl, nullptr, st);
   // integrals
   const int nao_ = ao.nfun;
-  TJ.ensure((size_t)nao_ * nao_ * nJ);
-  TK.ensure((size_t)nao_ * nao_ * nK);
+  TJ.ensure((size_t)nao_ * nao_ * nJ, st);
+  TK.ensure((size_t)nao_ * nao_ * nK, st);
   RIS_CUDA(cudaMemsetAsync(TJ.p, 0, sizeof(double) * (size_t)nao_ * nao_ * nJ, st));
   RIS_CUDA(cudaMemsetAsync(TK.p, 0, sizeof(double) * (size_t)nao_ * nao_ * nK, st));
   int3c(ao, aux, pl, xyz.p, nJ, nK, TJ.p, TK.p, st);
-  MU.ensure((size_t)nU * nU);
-  dMU.ensure(3 * (size_t)nU * nU);
+  MU.ensure((size_t)nU * nU, st);
+  dMU.ensure(3 * (size_t)nU * nU, st);
   int2c(aux, xyz.p, MU.p, dMU.p, st);
   // metric factors
-  if (!d_info) RIS_CUDA(cudaMalloc(&d_info, sizeof(int) * 2));
-  LJinv.ensure((size_t)nJ * nJ);
-  LKinv.ensure((size_t)nK * nK);
-  w1.ensure((size_t)std::max(nJ, nK) * std::max(nJ, nK));
+  if (!d_info) RIS_CUDA(cudaMallocAsync((void**)&d_info, sizeof(int) * 2, st));
+  LJinv.ensure((size_t)nJ * nJ, st);
+  LKinv.ensure((size_t)nK * nK, st);
+  w1.ensure((size_t)std::max(nJ, nK) * std::max(nJ, nK), st);
   for (int set = 0; set < 2; set++) {
     const int n = set == 0 ? nJ : nK;
     const int* map = set == 0 ? d_jU : d_kU;
@@ -706,7 +806,7 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
 void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const double* eps_in) {
   RIS_REQUIRE(stage >= 1, RIS_ERR_STATE, "ris_build_B before ris_build_aux");
   RIS_REQUIRE(nao_ == ao.nfun, RIS_ERR_ARG, "nao does not match the AO basis");
-  RIS_REQUIRE(nmo_ == nao_, RIS_ERR_ARG, "nmo must equal nao");
+  RIS_REQUIRE(nmo_ <= nao_, RIS_ERR_ARG, "nmo must not exceed nao");
   RIS_REQUIRE(nocc_ > 0 && nocc_ < nmo_, RIS_ERR_ARG, "need 0 < nocc < nmo");
   RIS_REQUIRE(Cin && eps_in, RIS_ERR_ARG, "null pointer");
   stage = 1;
@@ -715,9 +815,9 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
   nvir = nmo - nocc;
   const int o = nocc, v = nvir, n = nao;
   const long long nov = (long long)o * v;
-  C.ensure((size_t)n * nmo);
-  eps.ensure(nmo);
-  de.ensure(nov);
+  C.ensure((size_t)n * nmo, st);
+  eps.ensure(nmo, st);
+  de.ensure(nov, st);
   copy_in(C.p, Cin, (size_t)n * nmo, st);
   copy_in(eps.p, eps_in, nmo, st);
   k_orb_diff<<<cdiv(nov, 256), 256, 0, st>>>(eps.p, o, v, de.p);
@@ -725,9 +825,9 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
   const double* Co = C.p;
   const double* Cv = C.p + o;
   // Coulomb: H[i][nu][P] = sum_mu C_mu,i T[mu][nu][P]; B[i][a][P]; B L^-T
-  w2.ensure((size_t)o * n * std::max(nJ, nK));
+  w2.ensure((size_t)o * n * std::max(nJ, nK), st);
   dgemm(true, false, o, n * nJ, n, 1.0, Co, nmo, TJ.p, n * nJ, 0.0, w2.p, n * nJ, st);
-  w3.ensure((size_t)std::max(nov, (long long)o * o) * std::max(nJ, nK));
+  w3.ensure((size_t)std::max(nov, (long long)o * o) * std::max(nJ, nK), st);
   {
     GemmBatch bt;
     bt.nb1 = o;
@@ -735,7 +835,7 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
     bt.sC1 = (long long)v * nJ;
     dgemm(true, false, v, nJ, n, 1.0, Cv, nmo, w2.p, nJ, 0.0, w3.p, nJ, st, bt);
   }
-  BJ.ensure((size_t)nov * nJ);
+  BJ.ensure((size_t)nov * nJ, st);
   dgemm(false, true, (int)nov, nJ, nJ, 1.0, w3.p, nJ, LJinv.p, nJ, 0.0, BJ.p, nJ, st);
   // exchange: oo and ov from C_o^T T^K, vv from C_v^T T^K
   dgemm(true, false, o, n * nK, n, 1.0, Co, nmo, TK.p, n * nK, 0.0, w2.p, n * nK, st);
@@ -746,9 +846,9 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
     bt.sC1 = (long long)o * nK;
     dgemm(true, false, o, nK, n, 1.0, Co, nmo, w2.p, nK, 0.0, w3.p, nK, st, bt);
   }
-  BKoo.ensure((size_t)o * o * nK);
+  BKoo.ensure((size_t)o * o * nK, st);
   dgemm(false, true, o * o, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, BKoo.p, nK, st);
-  cKoo.ensure((size_t)o * o * nK);
+  cKoo.ensure((size_t)o * o * nK, st);
   dgemm(false, false, o * o, nK, nK, 1.0, BKoo.p, nK, LKinv.p, nK, 0.0, cKoo.p, nK, st);
   if (opt.rpa) {
     GemmBatch bt;
@@ -756,18 +856,18 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
     bt.sB1 = (long long)n * nK;
     bt.sC1 = (long long)v * nK;
     dgemm(true, false, v, nK, n, 1.0, Cv, nmo, w2.p, nK, 0.0, w3.p, nK, st, bt);
-    w4.ensure((size_t)nov * nK);
+    w4.ensure((size_t)nov * nK, st);
     dgemm(false, true, (int)nov, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // [i][a][R]
-    cKov.ensure((size_t)nov * nK);
+    cKov.ensure((size_t)nov * nK, st);
     dgemm(false, false, (int)nov, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKov.p, nK, st);
-    BKovR.ensure((size_t)nov * nK);
+    BKovR.ensure((size_t)nov * nK, st);
     transpose_last2(w4.p, 1, (int)nov, nK, BKovR.p, st);  // [R][ia]
-    cKovP.ensure((size_t)nov * nK);
+    cKovP.ensure((size_t)nov * nK, st);
     transpose_last2(cKov.p, 1, (int)nov, nK, cKovP.p, st);  // [P][ia]
   }
-  w2.ensure((size_t)v * n * nK);
+  w2.ensure((size_t)v * n * nK, st);
   dgemm(true, false, v, n * nK, n, 1.0, Cv, nmo, TK.p, n * nK, 0.0, w2.p, n * nK, st);
-  w3.ensure((size_t)v * v * nK);
+  w3.ensure((size_t)v * v * nK, st);
   {
     GemmBatch bt;
     bt.nb1 = v;
@@ -775,11 +875,11 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
     bt.sC1 = (long long)v * nK;
     dgemm(true, false, v, nK, n, 1.0, Cv, nmo, w2.p, nK, 0.0, w3.p, nK, st, bt);
   }
-  w4.ensure((size_t)v * v * nK);
+  w4.ensure((size_t)v * v * nK, st);
   dgemm(false, true, v * v, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // B[a][b][R]
-  cKvv.ensure((size_t)v * v * nK);
+  cKvv.ensure((size_t)v * v * nK, st);
   dgemm(false, false, v * v, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKvv.p, nK, st);
-  BKvvD.ensure((size_t)v * v * nK);
+  BKvvD.ensure((size_t)v * v * nK, st);
   transpose_last2(w4.p, v, v, nK, BKvvD.p, st);  // [b][R][a]
   if (opt.precision == RIS_MIXED) prepare_mixed();
   stage = 2;
@@ -790,7 +890,7 @@ void Engine::prepare_mixed() {
   const int o = nocc, v = nvir, n = nao;
   const int lo4 = ld4(o), lv4 = ld4(v);
   if (!d_tcerr) {
-    RIS_CUDA(cudaMalloc(&d_tcerr, sizeof(int)));
+    RIS_CUDA(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
     RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
   }
   BooH.ensure((size_t)o * nK * lo4, st);
@@ -802,12 +902,12 @@ void Engine::prepare_mixed() {
   // BKvvD [b][R][a] = [a][R][b] by symmetry; rows (a,R), b padded
   split_f64(BKvvD.p, v * nK, v, v, BvvH.p, BvvL.p, lv4, st);
   // fitting coefficients for Gamma: c^vv[a][b][P] -> [P][b][a] (symmetric in a,b)
-  w3.ensure((size_t)v * v * nK);
+  w3.ensure((size_t)v * v * nK, st);
   transpose_last2(cKvv.p, 1, v * v, nK, w3.p, st);  // [P][(a,b)]
   cvvH.ensure((size_t)nK * v * lv4, st);
   cvvL.ensure((size_t)nK * v * lv4, st);
   split_f64(w3.p, nK * v, v, v, cvvH.p, cvvL.p, lv4, st);
-  cKooP.ensure((size_t)o * o * nK);
+  cKooP.ensure((size_t)o * o * nK, st);
   transpose_last2(cKoo.p, 1, o * o, nK, cKooP.p, st);  // [P][i][k]
   cooH.ensure((size_t)nK * o * lo4, st);
   cooL.ensure((size_t)nK * o * lo4, st);
@@ -930,7 +1030,7 @@ void Engine::apply_exchange_mixed(const double* Z, int nvec, double* out, double
 void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
   const long long nov = (long long)nocc * nvir;
   // Coulomb in FP64: out = 2 (X B^J) B^J^T
-  w5.ensure((size_t)nvec * std::max(nJ, 1));
+  w5.ensure((size_t)nvec * std::max(nJ, 1), st);
   dgemm(false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
   dgemm(false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
   apply_exchange_mixed(Xin, nvec, out, -opt.cx, 1.0);
@@ -943,10 +1043,10 @@ void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
 void Engine::apply_A_tda(const double* Xin, int nvec, double* out) {
   const int o = nocc, v = nvir;
   const long long nov = (long long)o * v;
-  w5.ensure((size_t)nvec * std::max(nJ, 1));
+  w5.ensure((size_t)nvec * std::max(nJ, 1), st);
   dgemm(false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
   dgemm(false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
-  w6.ensure((size_t)nvec * o * nK * v);
+  w6.ensure((size_t)nvec * o * nK * v, st);
   {
     GemmBatch bt;
     bt.nb1 = nvec;
@@ -994,7 +1094,7 @@ void Engine::exchange_terms(const double* Z, int nvec, double* K1, double* K2, b
   if (mixed) {
     apply_exchange_mixed(Z, nvec, K1, 1.0, 0.0);
   } else {
-    w6.ensure((size_t)nvec * o * nK * v);
+    w6.ensure((size_t)nvec * o * nK * v, st);
     GemmBatch bt;
     bt.nb1 = nvec;
     bt.sA1 = nov;
@@ -1028,7 +1128,7 @@ void Engine::exchange_terms(const double* Z, int nvec, double* K1, double* K2, b
 void Engine::apply_ApB_AmB(const double* Z, int nvec, double* outP, double* outM) {
   const long long nov = (long long)nocc * nvir;
   const bool mixed = opt.precision == RIS_MIXED;
-  w5.ensure((size_t)nvec * std::max(nJ, 1));
+  w5.ensure((size_t)nvec * std::max(nJ, 1), st);
   dgemm(false, false, nvec, nJ, (int)nov, 1.0, Z, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
   dgemm(false, true, nvec, (int)nov, nJ, 1.0, w5.p, nJ, BJ.p, nJ, 0.0, outP, (int)nov, st);
   SBuf<double> K1((size_t)nvec * nov, st), K2((size_t)nvec * nov, st);
@@ -1038,12 +1138,12 @@ void Engine::apply_ApB_AmB(const double* Z, int nvec, double* outP, double* outM
 }
 
 // ------------------------------------------------------------------ Davidson (TDA)
-void Engine::davidson_tda(int ns) {
+void Engine::davidson_tda(int ns, const double* guess) {
   if (opt.precision != RIS_MIXED) {
-    dav_core(ns, nullptr, 0, false, opt.conv_tol);
+    dav_core(ns, guess, guess ? ns : 0, false, opt.conv_tol, true);
     return;
   }
-  dav_core(ns, nullptr, 0, true, std::max(opt.conv_tol, opt.mixed_tol));
+  dav_core(ns, guess, guess ? ns : 0, true, std::max(opt.conv_tol, opt.mixed_tol), true);
   if (opt.refine) {
     SBuf<double> g((size_t)ns * nocc * nvir, st);
     RIS_CUDA(cudaMemcpyAsync(g.p, X.p, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, st));
@@ -1061,8 +1161,10 @@ void Engine::davidson_tda(int ns) {
 
 // Block Davidson for the lowest ns eigenpairs of the TDA A.  Starts from
 // unit vectors on the lowest orbital-energy differences, or from nguess
-// given vectors; products in FP64 or (mixed) with 3xTF32 exchange GEMMs.
-void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, double tol) {
+// given vectors (augment: plus unit vectors up to the usual block size);
+// products in FP64 or (mixed) with 3xTF32 exchange GEMMs.
+void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, double tol,
+                      bool augment) {
   const long long n = (long long)nocc * nvir;
   const int nb0 = (int)std::min<long long>(n, ns + std::min(ns, 8));
   int maxsp = opt.max_subspace > 0 ? opt.max_subspace : std::max(nb0 + 2 * ns, 8 * ns);
@@ -1082,24 +1184,80 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
     else
       apply_A_tda(x, nv, y);
   };
+  // Preconditioner M = D - s + 2 B^J B^J^T (the orbital-energy differences and
+  // the Coulomb part of A, Eq. A_matrix), inverted exactly by the Woodbury
+  // identity: M^-1 r = D'^-1 r - 2 D'^-1 B (I + 2 B^T D'^-1 B)^-1 B^T D'^-1 r,
+  // D' = D - s, with one shift s below the smallest difference for all states.
+  const bool cprec = opt.precond == 0 && nJ > 0;
+  SBuf<double> dinv, capinv, pY, pZ, pP;
+  if (cprec) {
+    dinv.ensure(n, st);
+    capinv.ensure((size_t)nJ * nJ, st);
+    pY.ensure((size_t)ns * nJ, st);
+    pZ.ensure((size_t)ns * nJ, st);
+    pP.ensure((size_t)ns * n, st);
+    SBuf<double> W((size_t)n * nJ, st), cap((size_t)nJ * nJ, st), Li((size_t)nJ * nJ, st), dm(1, st);
+    SBuf<int> info(1, st);
+    k_min<<<1, 1024, 0, st>>>(de.p, n, dm.p);
+    RIS_CHECK_LAUNCH();
+    k_precond_setup<<<cdiv(n * nJ, 256), 256, 0, st>>>(de.p, dm.p, n, kPrecondGap, BJ.p, nJ, dinv.p, W.p);
+    RIS_CHECK_LAUNCH();
+    dgemm(true, false, nJ, nJ, (int)n, 2.0, BJ.p, nJ, W.p, nJ, 0.0, cap.p, nJ, st);
+    k_add_identity<<<cdiv(nJ, 128), 128, 0, st>>>(cap.p, nJ);
+    RIS_CHECK_LAUNCH();
+    cholesky(cap.p, nJ, info.p, st);
+    tri_inverse(cap.p, Li.p, nJ, st);
+    dgemm(true, false, nJ, nJ, nJ, 1.0, Li.p, nJ, Li.p, nJ, 0.0, capinv.p, nJ, st);
+    int h_info = 0;
+    RIS_CUDA(cudaMemcpyAsync(&h_info, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+    RIS_REQUIRE(h_info == 0, RIS_ERR_ARG, "preconditioner capacitance matrix not positive definite");
+  }
+  auto precondition = [&](int nt) {  // T[j] = M^-1 R[d_idx[j]]
+    if (!cprec) {
+      k_precond<<<cdiv(n * nt, 256), 256, 0, st>>>(Rr.p, de.p, w.p, d_idx, n, nt, T.p);
+      RIS_CHECK_LAUNCH();
+      return;
+    }
+    k_precond_scale<<<cdiv(n * nt, 256), 256, 0, st>>>(Rr.p, dinv.p, d_idx, n, nt, T.p);
+    RIS_CHECK_LAUNCH();
+    dgemm(false, false, nt, nJ, (int)n, 1.0, T.p, (int)n, BJ.p, nJ, 0.0, pY.p, nJ, st);
+    dgemm(false, false, nt, nJ, nJ, 1.0, pY.p, nJ, capinv.p, nJ, 0.0, pZ.p, nJ, st);
+    dgemm(false, true, nt, (int)n, nJ, 1.0, pZ.p, nJ, BJ.p, nJ, 0.0, pP.p, (int)n, st);
+    k_precond_update<<<cdiv(n * nt, 256), 256, 0, st>>>(T.p, pP.p, dinv.p, n, nt);
+    RIS_CHECK_LAUNCH();
+  };
   int m = nb0;
   if (guess) {
-    // orthonormalise the given block (two CholQR passes)
-    m = nguess;
-    RIS_CUDA(cudaMemcpyAsync(V.p, guess, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, st));
-    for (int pass = 0; pass < 2; pass++) {
-      row_norms(V.p, m, n, G.p, st);
-      k_scale_rows<<<cdiv(n * m, 256), 256, 0, st>>>(V.p, n, m, G.p);
+    // the given rows, optionally followed by unit vectors on the lowest
+    // orbital-energy differences, orthonormalised by two CholQR passes that
+    // drop rows dependent on earlier ones (the given rows come first)
+    const int nunit = augment ? std::max(0, nb0 - nguess) : 0;
+    m = nguess + nunit;
+    RIS_REQUIRE(m <= 64 && m <= maxsp, RIS_ERR_ARG, "initial Davidson block too large");
+    RIS_CUDA(cudaMemcpyAsync(V.p, guess, sizeof(double) * nguess * n, cudaMemcpyDeviceToDevice, st));
+    if (nunit > 0) {
+      k_lowest<<<1, 1024, 0, st>>>(de.p, (int)n, nunit, d_idx);
       RIS_CHECK_LAUNCH();
-      dgemm(false, true, m, m, (int)n, 1.0, V.p, (int)n, V.p, (int)n, 0.0, G.p, m, st);
-      k_cholqr_small<<<1, 32, 0, st>>>(G.p, m, 1e-10, Pm.p, (int*)(Pm.p + m * m), Cc.p);
+      k_unit_rows<<<nunit, 256, 0, st>>>(d_idx, nunit, n, V.p + (size_t)nguess * n);
+      RIS_CHECK_LAUNCH();
+    }
+    SBuf<double> G0((size_t)m * m, st), P0((size_t)m * m + 64, st), W0((size_t)m * m + m, st);
+    for (int pass = 0; pass < 2; pass++) {
+      row_norms(V.p, m, n, G0.p, st);
+      k_scale_rows<<<cdiv(n * m, 256), 256, 0, st>>>(V.p, n, m, G0.p);
+      RIS_CHECK_LAUNCH();
+      dgemm(false, true, m, m, (int)n, 1.0, V.p, (int)n, V.p, (int)n, 0.0, G0.p, m, st);
+      k_cholqr_small<<<1, 32, 0, st>>>(G0.p, m, 1e-10, P0.p, (int*)(P0.p + m * m), W0.p);
       RIS_CHECK_LAUNCH();
       int nk2 = 0;
-      RIS_CUDA(cudaMemcpyAsync(&nk2, Pm.p + m * m, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RIS_CUDA(cudaMemcpyAsync(&nk2, P0.p + m * m, sizeof(int), cudaMemcpyDeviceToHost, st));
       RIS_CUDA(cudaStreamSynchronize(st));
-      RIS_REQUIRE(nk2 == m, RIS_ERR_ARG, "initial Davidson block is linearly dependent");
-      dgemm(false, false, m, (int)n, m, 1.0, Pm.p, m, V.p, (int)n, 0.0, tmp.p, (int)n, st);
-      RIS_CUDA(cudaMemcpyAsync(V.p, tmp.p, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, st));
+      RIS_REQUIRE(nk2 >= ns && (augment || nk2 == m), RIS_ERR_ARG,
+                  "initial Davidson block is linearly dependent");
+      dgemm(false, false, nk2, (int)n, m, 1.0, P0.p, m, V.p, (int)n, 0.0, tmp.p, (int)n, st);
+      RIS_CUDA(cudaMemcpyAsync(V.p, tmp.p, sizeof(double) * nk2 * n, cudaMemcpyDeviceToDevice, st));
+      m = nk2;
     }
   } else {
     k_lowest<<<1, 1024, 0, st>>>(de.p, (int)n, nb0, d_idx);
@@ -1113,6 +1271,7 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
   std::vector<double> rn(ns);
   bool converged = false;
   int it = 0;
+  double rmax = 0.0;
   const double drop = 1e-10;
   for (it = 0; it < opt.max_iter; it++) {
     const int nk = std::min(m, std::max(ns, kkeep));
@@ -1125,16 +1284,18 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
     RIS_CUDA(cudaMemcpyAsync(rn.data(), G.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
     RIS_CUDA(cudaStreamSynchronize(st));
     std::vector<int> u;
-    for (int k = 0; k < ns; k++)
+    rmax = 0.0;
+    for (int k = 0; k < ns; k++) {
       if (!(sqrt(rn[k]) <= tol)) u.push_back(k);
+      rmax = std::max(rmax, sqrt(rn[k]));
+    }
     if (u.empty()) {
       converged = true;
       break;
     }
     int nt = (int)u.size();
     RIS_CUDA(cudaMemcpyAsync(d_idx, u.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
-    k_precond<<<cdiv(n * nt, 256), 256, 0, st>>>(Rr.p, de.p, w.p, d_idx, n, nt, T.p);
-    RIS_CHECK_LAUNCH();
+    precondition(nt);
     if (m + nt > maxsp) {  // restart with the lowest Ritz vectors
       const int keep = std::min(nk, maxsp - nt);
       dgemm(false, false, keep, (int)n, m, 1.0, S.p, m, V.p, (int)n, 0.0, tmp.p, (int)n, st);
@@ -1176,27 +1337,34 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
   }
   stats[4] = nprod;
   stats[5] = it;
+  stats[7] = rmax;
   RIS_REQUIRE(converged, RIS_ERR_NOT_CONVERGED,
-              "Davidson did not converge in " + std::to_string(it) + " iterations");
+              "Davidson did not converge in " + std::to_string(it) + " iterations (largest residual " +
+                  std::to_string(rmax) + ")");
   k_phase<<<ns, 256, 0, st>>>(Xr.p, nullptr, n);
   RIS_CHECK_LAUNCH();
   nstates = ns;
-  omega.ensure(ns);
-  X.ensure((size_t)ns * n);
+  omega.ensure(ns, st);
+  X.ensure((size_t)ns * n, st);
   RIS_CUDA(cudaMemcpyAsync(omega.p, w.p, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
   RIS_CUDA(cudaMemcpyAsync(X.p, Xr.p, sizeof(double) * ns * n, cudaMemcpyDeviceToDevice, st));
 }
 
-void Engine::excite(int ns, double* om, double* Xo, double* Yo) {
+void Engine::excite(int ns, double* om, double* Xo, double* Yo, const double* guess) {
   RIS_REQUIRE(stage >= 2, RIS_ERR_STATE, "ris_excite before ris_build_B");
   const long long n = (long long)nocc * nvir;
   RIS_REQUIRE(ns >= 1 && ns <= 32 && ns <= n, RIS_ERR_ARG, "nstates out of range (1..32)");
   RIS_REQUIRE(om, RIS_ERR_ARG, "omega is NULL");
   stage = 2;
-  if (opt.rpa)
+  if (opt.rpa) {
     davidson_rpa(ns);
-  else
+  } else if (guess) {
+    SBuf<double> g((size_t)ns * n, st);
+    copy_in(g.p, guess, (size_t)ns * n, st);
+    davidson_tda(ns, g.p);
+  } else {
     davidson_tda(ns);
+  }
   h_omega.resize(ns);
   RIS_CUDA(cudaMemcpyAsync(h_omega.data(), omega.p, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
   copy_out(om, omega.p, ns, st);
@@ -1386,9 +1554,9 @@ void Engine::davidson_rpa(int ns) {
   RIS_REQUIRE(converged, RIS_ERR_NOT_CONVERGED,
               "RPA Davidson did not converge in " + std::to_string(it) + " iterations");
   nstates = ns;
-  omega.ensure(ns);
-  X.ensure((size_t)ns * n);
-  Y.ensure((size_t)ns * n);
+  omega.ensure(ns, st);
+  X.ensure((size_t)ns * n, st);
+  Y.ensure((size_t)ns * n, st);
   RIS_CUDA(cudaMemcpyAsync(omega.p, om.p, sizeof(double) * ns, cudaMemcpyDeviceToDevice, st));
   // X = (R + L)/2, Y = (R - L)/2
   k_rowcomb<<<cdiv(n * ns, 256), 256, 0, st>>>(Rf.p, Lf.p, nullptr, 0.5, 0.5, 0, n, ns, X.p);
@@ -1409,7 +1577,7 @@ void Engine::davidson_rpa(int ns) {
 void Engine::ensure_D() {
   if (have_D) return;
   const size_t plane = (size_t)nao * nao * nU;
-  D.ensure(3 * plane);
+  D.ensure(3 * plane, st);
   RIS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * 3 * plane, st));
   int3c_deriv(ao, aux, pl, xyz.p, D.p, st);
   have_D = true;
@@ -1466,7 +1634,7 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
   DR.ensure((size_t)nsu * nn * nn, st);
   t1.ensure((size_t)nn * v, st);
   cJ.ensure((size_t)nsu * nJ, st);
-  w5.ensure((size_t)nsu * nJ);
+  w5.ensure((size_t)nsu * nJ, st);
   const double* Co = C.p;
   const double* Cv = C.p + o;
   const bool mixed = opt.precision == RIS_MIXED;

@@ -9,11 +9,13 @@
 
 namespace ris {
 
-// Device buffer owned by the context.
+// Device buffer owned by the context (stream-ordered, tracked).
 struct DBuf {
   double* p = nullptr;
   size_t n = 0;
-  void ensure(size_t count);
+  cudaStream_t st = nullptr;
+  MemTrack* tr = nullptr;
+  void ensure(size_t count, cudaStream_t s);
   void release();
   ~DBuf() { release(); }
 };
@@ -26,6 +28,7 @@ struct SBuf {
   T* p = nullptr;
   size_t n = 0;
   cudaStream_t st = nullptr;
+  MemTrack* tr = nullptr;
   SBuf() = default;
   SBuf(size_t count, cudaStream_t s, bool zero = false) { ensure(count, s, zero); }
   void ensure(size_t count, cudaStream_t s, bool zero = false) {
@@ -33,17 +36,12 @@ struct SBuf {
     release();
     st = s;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), st);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-      throw Error{RIS_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed"};
-    }
+    p = (T*)dev_alloc(count * sizeof(T), st, &tr);
     n = count;
     if (zero) RIS_CUDA(cudaMemsetAsync(p, 0, count * sizeof(T), st));
   }
   void release() {
-    if (p) cudaFreeAsync(p, st);
+    if (p) dev_free(p, n * sizeof(T), st, tr);
     p = nullptr;
     n = 0;
   }
@@ -56,16 +54,27 @@ struct SBuf {
 struct FBuf {
   float* p = nullptr;
   size_t n = 0;
-  void ensure(size_t count, cudaStream_t st);
+  cudaStream_t st = nullptr;
+  MemTrack* tr = nullptr;
+  void ensure(size_t count, cudaStream_t s);
   void release();
   ~FBuf() { release(); }
 };
 
-struct Engine {
-  ris_options opt{};
-  int device = 0;
+// The context's stream; a base class so that it outlives every buffer
+// member, whose stream-ordered frees are queued on it.
+struct StreamOwner {
   cudaStream_t st = nullptr;
   bool own_stream = false;
+  ~StreamOwner() {
+    if (own_stream && st) cudaStreamDestroy(st);
+  }
+};
+
+struct Engine : StreamOwner {
+  ris_options opt{};
+  int device = 0;
+  MemTrack mem;
   std::string err;
   int stage = 0;  // 0 created, 1 aux built, 2 B built, 3 excited
 
@@ -118,10 +127,12 @@ struct Engine {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   ~Engine();
+  // release every device buffer (the context returns to its created state)
+  void trim();
   void build_aux(int natm, const double* coords, int nshell, const ris_shell* ao,
                  int nJs, const ris_shell* auxJ, int nKs, const ris_shell* auxK);
   void build_B(int nao, int nmo, int nocc, const double* C, const double* mo_energy);
-  void excite(int nstates, double* omega, double* X, double* Y);
+  void excite(int nstates, double* omega, double* X, double* Y, const double* guess = nullptr);
   // numerators dE_IJ/dR for pairs, [npair][natm][3] into out (host or device)
   void pair_derivs(int npair, const int* pairs, int nx, const double* X_in, const double* Y_in,
                    double* out_dev);
@@ -138,13 +149,17 @@ struct Engine {
   void gamma_K_mixed(const float* USh, const float* USl, const float* VSh, const float* VSl,
                      const float* WUh, const float* WUl, const float* WVh, const float* WVl,
                      double f, double* Gam, double* Om);
-  void dav_core(int ns, const double* guess, int nguess, bool mixed, double tol);
+  void dav_core(int ns, const double* guess, int nguess, bool mixed, double tol,
+                bool augment = false);
   void apply_ApB_AmB(const double* Zin, int nvec, double* outP, double* outM);
-  void davidson_tda(int ns);
+  void davidson_tda(int ns, const double* guess = nullptr);
   void davidson_rpa(int ns);
   // exchange (ij|ab) and (ib|ja) contractions of nvec vectors: K1, K2 [nvec][nov]
   void exchange_terms(const double* Z, int nvec, double* K1, double* K2, bool mixed);
 };
+
+// n doubles from a host or device pointer into host memory
+void copy_to_host(double* dst, const double* src, size_t n, cudaStream_t st);
 
 // out[g][k] = num[g][k] / den[g]
 void divide_pairs(double* out, const double* num, const double* den, int npair, int per,

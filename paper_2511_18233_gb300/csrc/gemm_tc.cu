@@ -40,7 +40,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
+  static std::mutex mu;
   static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lk(mu);
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -347,11 +349,7 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
   RIS_REQUIRE(K > 0, RIS_ERR_ARG, "tc_gemm: K must be positive");
   RIS_REQUIRE(A.rows >= M && B.rows >= N, RIS_ERR_ARG, "tc_gemm: operand rows");
   RIS_REQUIRE(nb <= 65535, RIS_ERR_ARG, "tc_gemm: batch too large");
-  static bool attr = false;
-  if (!attr) {
-    RIS_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
-  }
+  ensure_smem_attr((const void*)k_tc_gemm, SMEM_BYTES);
   const CUtensorMap mAh = make_map(A.hi, K, M, A.ld, A.bstride, A.nb);
   const CUtensorMap mAl = make_map(A.lo, K, M, A.ld, A.bstride, A.nb);
   const CUtensorMap mBh = make_map(B.hi, K, N, B.ld, B.bstride, B.nb);
@@ -377,12 +375,13 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
   }
   float* part = nullptr;
   bool own_part = false;
+  MemTrack* part_tr = nullptr;
   if (a.ksplit > 1) {
     const size_t need = (size_t)a.ksplit * M * N;
     if (ws && ws_floats >= need) {
       part = ws;
     } else if (allow_alloc) {
-      RIS_CUDA(cudaMallocAsync(&part, sizeof(float) * need, st));
+      part = (float*)dev_alloc(sizeof(float) * need, st, &part_tr);
       own_part = true;
     } else {
       a.ksplit = 1;
@@ -398,7 +397,7 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
     k_tc_reduce<<<cdiv((long long)M * N, 256), 256, 0, st>>>(M, N, a.ksplit, part, ep.alpha, ep.beta,
                                                              ep.c64, (int)ep.rs);
     RIS_CHECK_LAUNCH();
-    if (own_part) RIS_CUDA(cudaFreeAsync(part, st));
+    if (own_part) dev_free(part, sizeof(float) * (size_t)a.ksplit * M * N, st, part_tr);
   }
   prof_end(kProfTcGemm, st, 2.0 * M * N * (double)K * nb);
 }

@@ -569,7 +569,7 @@ __global__ void k_pair_scatter(int nsh, const int* l, const int* atom, const dou
 
 void build_pairs(const ShellSet& ao, const double* d_coords, double thr, PairList& pl,
                  void* /*scratch*/, cudaStream_t st) {
-  free_pairs(pl);
+  free_pairs(pl, st);
   const int nsh = ao.n;
   const int nitem = nsh * nsh;
   const int nblk = cdiv(nitem, kPairBlock);
@@ -592,8 +592,8 @@ void build_pairs(const ShellSet& ao, const double* d_coords, double thr, PairLis
     pl.class_off[k + 1] = n;
   }
   pl.npair = n;
-  RIS_CUDA(cudaMalloc(&pl.a, sizeof(int) * std::max(n, 1)));
-  RIS_CUDA(cudaMalloc(&pl.b, sizeof(int) * std::max(n, 1)));
+  RIS_CUDA(cudaMallocAsync((void**)&pl.a, sizeof(int) * std::max(n, 1), st));
+  RIS_CUDA(cudaMallocAsync((void**)&pl.b, sizeof(int) * std::max(n, 1), st));
   k_pair_scatter<<<nblk, kPairBlock, 0, st>>>(nsh, ao.l, ao.atom, ao.ex, ao.nbase, d_coords,
                                              thr, offs, pl.a, pl.b);
   RIS_CHECK_LAUNCH();
@@ -602,9 +602,9 @@ void build_pairs(const ShellSet& ao, const double* d_coords, double thr, PairLis
   RIS_CUDA(cudaFreeAsync(totals, st));
 }
 
-void free_pairs(PairList& pl) {
-  if (pl.a) cudaFree(pl.a);
-  if (pl.b) cudaFree(pl.b);
+void free_pairs(PairList& pl, cudaStream_t st) {
+  if (pl.a) cudaFreeAsync(pl.a, st);
+  if (pl.b) cudaFreeAsync(pl.b, st);
   pl.a = pl.b = nullptr;
   pl.npair = 0;
 }

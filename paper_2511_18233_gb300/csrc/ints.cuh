@@ -39,7 +39,7 @@ const double* boys_table_device(int device);
 
 void build_pairs(const ShellSet& ao, const double* d_coords, double thr, PairList& pl,
                  void* scratch_pool, cudaStream_t st);
-void free_pairs(PairList& pl);
+void free_pairs(PairList& pl, cudaStream_t st);
 
 // (mu nu|P) for the auxiliary union set, written to TJ[mu][nu][PJ] and
 // TK[mu][nu][PK] (both orderings of mu, nu).  The buffers must be zeroed.

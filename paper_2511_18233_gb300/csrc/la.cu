@@ -149,7 +149,8 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
     ksplit = cdiv(k, kchunk);
   }
   double* ws = nullptr;
-  if (ksplit > 1) RIS_CUDA(cudaMallocAsync(&ws, sizeof(double) * (size_t)ksplit * m * n, st));
+  MemTrack* ws_tr = nullptr;
+  if (ksplit > 1) ws = (double*)dev_alloc(sizeof(double) * (size_t)ksplit * m * n, st, &ws_tr);
   dim3 grid(cdiv(n, kBN), cdiv(m, kBM), ksplit > 1 ? ksplit : nb);
   double* Cout = ksplit > 1 ? ws : C;
   prof_begin(kProfGemm, st);
@@ -165,7 +166,7 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
   if (ksplit > 1) {
     k_splitk_reduce<<<cdiv((long long)m * n, 256), 256, 0, st>>>(m, n, ksplit, ws, alpha, beta, C, ldc);
     RIS_CHECK_LAUNCH();
-    RIS_CUDA(cudaFreeAsync(ws, st));
+    dev_free(ws, sizeof(double) * (size_t)ksplit * m * n, st, ws_tr);
   }
   prof_end(kProfGemm, st, 2.0 * m * n * (double)std::max(k, 0) * nb);
 }
@@ -488,12 +489,8 @@ __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* H, int ldH, int
 void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
                     cudaStream_t st) {
   RIS_REQUIRE(k >= 1 && k <= 64 && k <= m, RIS_ERR_ARG, "sym_eig_lowest: bad k");
-  static bool attr = false;
   const size_t smem_max = 200 * 1024;
-  if (!attr) {
-    RIS_CUDA(cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-    attr = true;
-  }
+  ensure_smem_attr((const void*)k_sym_eig, (int)smem_max);
   const size_t need = (size_t)m * m * sizeof(double);
   const int use_smem = need <= smem_max;
   prof_begin(kProfEig, st);

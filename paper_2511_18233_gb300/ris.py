@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_gemm_tf32x3_noalloc",
+           "ris_apply", "ris_excite_guess", "ris_trim", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_gemm_tf32x3_noalloc",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
 
@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("max_subspace", ctypes.c_int), ("screen_thr", ctypes.c_double),
                 ("mem_budget", ctypes.c_size_t), ("occ_block", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("profile", ctypes.c_int), ("mixed_tol", ctypes.c_double), ("refine", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("mixed_tol", ctypes.c_double), ("refine", ctypes.c_int),
+                ("precond", ctypes.c_int)]
 
 
 class Shell(ctypes.Structure):
@@ -65,6 +66,8 @@ def load(path: str = LIB_PATH):
     L.ris_build_aux.argtypes = [P, i, P, i, P, i, P, i, P]
     L.ris_build_B.argtypes = [P, i, i, i, P, P]
     L.ris_excite.argtypes = [P, i, P, P, P]
+    L.ris_excite_guess.argtypes = [P, i, P, P, P, P]
+    L.ris_trim.argtypes = [P]
     L.ris_apply.argtypes = [P, i, P, P, P]
     L.ris_gradient.argtypes = [P, i, P, i, P, P, P]
     L.ris_nac.argtypes = [P, i, P, i, P, P, P, P, P]
@@ -99,6 +102,8 @@ def _ptr(a) -> Optional[int]:
 
 
 def _shells(arr) -> ctypes.Array:
+    if isinstance(arr, ctypes.Array):
+        return arr
     n = len(arr)
     out = (Shell * n)()
     for k in range(n):
@@ -172,6 +177,19 @@ class Context:
         self._check(self.L.ris_excite(self.h, int(nstates), _ptr(om), _ptr(X), _ptr(Y)))
         return (om, X, Y) if rpa else (om, X)
 
+    def excite_guess(self, nstates: int, guess, out=None):
+        """ris_excite seeded with guess vectors [nstates][nocc][nvir]."""
+        rpa = bool(self.opt.rpa)
+        if out is None:
+            om = np.zeros(nstates)
+            X = np.zeros((nstates, self.nocc, self.nvir))
+            Y = np.zeros_like(X) if rpa else None
+        else:
+            om, X, Y = out
+        self._check(self.L.ris_excite_guess(self.h, int(nstates), _ptr(guess), _ptr(om), _ptr(X),
+                                            _ptr(Y)))
+        return (om, X, Y) if rpa else (om, X)
+
     def apply(self, X, out=None, out2=None):
         """TDA: A X.  RPA: ((A+B) X, (A-B) X)."""
         rpa = bool(self.opt.rpa)
@@ -196,6 +214,10 @@ class Context:
                                    _ptr(n), _ptr(numerator)))
         return n
 
+    def trim(self):
+        """Release every device buffer of the context (ris_trim)."""
+        self._check(self.L.ris_trim(self.h))
+
     def dims(self):
         v = [ctypes.c_int() for _ in range(6)]
         self._check(self.L.ris_get_dims(self.h, *[ctypes.byref(x) for x in v]))
@@ -206,7 +228,8 @@ class Context:
                  5: "n_iter", 15: "launches", 16: "gemm_ms", 17: "gemm_flops", 18: "int3c_ms",
                  19: "int3c_triples", 20: "int3c_deriv_ms", 21: "int3c_deriv_triples",
                  22: "contract_ms", 23: "contract_bytes", 24: "eig_ms", 25: "eig_calls",
-                 26: "tc_gemm_ms", 27: "tc_gemm_flops", 6: "refine_products"}
+                 26: "tc_gemm_ms", 27: "tc_gemm_flops", 6: "refine_products",
+                 28: "bytes_held", 29: "bytes_peak", 7: "residual_max"}
 
     def stats(self):
         out = (ctypes.c_double * 32)()

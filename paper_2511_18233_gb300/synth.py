@@ -85,8 +85,12 @@ class Molecule:
         return int(sum(ncart(int(l)) for l in self.shells["l"]))
 
     @property
+    def nmo(self) -> int:
+        return self.nao if self.C is None else int(self.C.shape[1])
+
+    @property
     def nvir(self) -> int:
-        return self.nao - self.nocc
+        return self.nmo - self.nocc
 
     def naux(self, which: str = "J") -> int:
         s = self.aux_j if which == "J" else self.aux_k
@@ -295,8 +299,20 @@ def n_electrons(elements: Sequence[str]) -> int:
     return sum(Z_OF[e] for e in elements)
 
 
+def canonical_mo(S: np.ndarray, rng: np.random.Generator, cutoff: float) -> np.ndarray:
+    """C = U_k diag(lambda_k^-1/2) Q over the overlap eigenpairs with
+    lambda_k > cutoff (canonical orthogonalisation), Q Haar-orthogonal of the
+    kept dimension: orthonormal MOs, nmo <= nao, with |C| <= cutoff^-1/2."""
+    w, U = np.linalg.eigh(S)
+    keep = w > cutoff
+    Q = haar_orthogonal(int(keep.sum()), rng)
+    return (U[:, keep] * (w[keep] ** -0.5)[None, :]) @ Q
+
+
 def make_molecule(name: str, elements: List[str], coords: np.ndarray, seed: int,
-                  p_aux: bool, with_mo: bool = True) -> Molecule:
+                  p_aux: bool, with_mo: bool = True, lindep: float = 0.0) -> Molecule:
+    """lindep = 0: Loewdin MOs S^-1/2 Q over all nao AOs; lindep > 0: canonical
+    MOs dropping overlap eigenvalues <= lindep (fewer virtual orbitals)."""
     shells = build_shells(elements)
     aux_j = build_aux(elements, p_aux)
     aux_k = build_aux(elements, False)
@@ -306,10 +322,13 @@ def make_molecule(name: str, elements: List[str], coords: np.ndarray, seed: int,
     if with_mo:
         rng = np.random.default_rng(seed)
         nao = mol.nao
-        Q = haar_orthogonal(nao, rng)
-        eps = orbital_energies(nocc, nao - nocc, rng)
         S = overlap_matrix(mol.coords, shells)
-        mol.C = np.ascontiguousarray(lowdin_mo(S, Q))
+        if lindep > 0:
+            C = canonical_mo(S, rng, lindep)
+        else:
+            C = lowdin_mo(S, haar_orthogonal(nao, rng))
+        eps = orbital_energies(nocc, C.shape[1] - nocc, rng)
+        mol.C = np.ascontiguousarray(C)
         mol.mo_energy = eps
     return mol
 
@@ -348,10 +367,23 @@ def workload(idx: int, with_mo: bool = True) -> Molecule:
     raise ValueError(idx)
 
 
+# Overlap-eigenvalue cutoff of the serving molecules' MOs.  Their C stays fixed
+# along a trajectory while the geometry moves by 0.05 A per component; with
+# Loewdin MOs over the near-dependent combinations of this basis C^T S C then
+# ranges over [0.01, 550] for the flakes, and the response matrix acquires
+# spurious large negative eigenvalues.  Dropping eigenvalues <= 1e-2 keeps
+# C^T S C within about [0.17, 3.3].
+SERVING_LINDEP = 1e-2
+
+
 def serving_molecule(kind: str, size: float, seed: int) -> Molecule:
     if kind == "chain":
-        return chain_molecule(int(size), seed, p_aux=True)
-    return flake_molecule(float(size), seed)
+        el, xyz = chain_geometry(int(size))
+        return make_molecule(f"C{int(size)}H{int(size) + 2}", el, xyz, seed, True,
+                             lindep=SERVING_LINDEP)
+    el, xyz = flake_geometry(float(size))
+    nc = el.count("C")
+    return make_molecule(f"C{nc}H{len(el) - nc}", el, xyz, seed, True, lindep=SERVING_LINDEP)
 
 
 def perturb(coords: np.ndarray, sigma_ang: float, rng: np.random.Generator) -> np.ndarray:
