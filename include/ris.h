@@ -224,6 +224,17 @@ ris_status ris_trim(ris_ctx* ctx);
 int ris_debug_boys(int n, const int* m, const double* T, double* out);
 
 /*
+ * Test hook: C = alpha op(A) op(B) + beta C with the library's FP64 GEMM
+ * (the dense contractions of the B-tensor transforms and the Davidson
+ * subspace).  Row-major; op(A) is m x k, op(B) is k x n; transA/transB
+ * nonzero = transposed operand; lda/ldb/ldc are row strides of the stored
+ * arrays.  DEVICE pointers on the current device.  Synchronises the device;
+ * returns 0 or a ris_status.
+ */
+int ris_debug_dgemm(int transA, int transB, int m, int n, int k, double alpha, const double* A,
+                    int lda, const double* B, int ldb, double beta, double* C, int ldc);
+
+/*
  * Test hook: lowest k (<= 64) eigenpairs of a symmetric m x m row-major
  * matrix with the device eigensolver of the Davidson subspace problem.
  * H: [m][m], w: [k] ascending, V: [k][m] (row j = eigenvector j); DEVICE

@@ -1,7 +1,8 @@
 // Dense FP64 linear algebra on the device.
 //
-// * dgemm: tiled FP64 GEMM (64x64 block tile, 4x4 per thread), batched over
-//   two strided levels, transposes folded into the tile loads.
+// * dgemm: tiled FP64 GEMM (block tile from 8x32 to 64x64 fitted to the
+//   problem, up to 4x4 per thread), batched over two strided levels,
+//   transposes folded into the tile loads, split along k for few tiles.
 // * cholesky / tri_inverse: the metric factor M = L L^T of Eq. (g_modified)
 //   and L^{-1}; left-looking, one CTA (the metric is at most a few thousand
 //   functions for one molecule of the ris basis).
@@ -21,17 +22,27 @@
 namespace ris {
 
 // ------------------------------------------------------------------ GEMM
-constexpr int kBM = 64, kBN = 64, kBK = 16;
+// FP64 runs at about two fused multiply-adds per clock per SM on this part,
+// so the GEMM is bound by the FMA pipe alone and every padded (wasted) FMA
+// costs time: the block tile is chosen per call from a family of shapes to
+// fit the problem (the Davidson products have 5-40 rows), and a product with
+// too few tiles is split along k to occupy all SMs.
+//
+// Block tile BM x BN = (THY*TM) x ((256/THY)*TN); thread (ty, tx) owns the
+// TM x TN outputs (ty + THY*r, tx + THX*c).
+constexpr int kBK = 16;
 
 // With ksplit > 1 (single batch only) blockIdx.z selects a slice of k of
 // length kchunk and the raw partial product is written to C + z*m*n
 // (ldc = n); k_splitk_reduce then forms alpha*sum + beta*C in a fixed order.
-template <bool TA, bool TB>
+template <bool TA, bool TB, int THY, int TM, int TN>
 __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha,
                                                const double* __restrict__ A, int lda,
                                                const double* __restrict__ B, int ldb, double beta,
                                                double* __restrict__ C, int ldc, GemmBatch bt,
                                                int ksplit, int kchunk) {
+  constexpr int THX = 256 / THY;
+  constexpr int BM = THY * TM, BN = THX * TN;
   int kbeg = 0, kend = k;
   if (ksplit > 1) {
     kbeg = blockIdx.z * kchunk;
@@ -44,26 +55,26 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
     B += b1 * bt.sB1 + b2 * bt.sB2;
     C += b1 * bt.sC1 + b2 * bt.sC2;
   }
-  __shared__ double As[kBK][kBM + 1];
-  __shared__ double Bs[kBK][kBN + 1];
+  __shared__ double As[kBK][BM + 1];
+  __shared__ double Bs[kBK][BN + 1];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
-  const int row0 = blockIdx.y * kBM, col0 = blockIdx.x * kBN;
-  double acc[4][4];
+  const int tx = tid % THX, ty = tid / THX;
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  double acc[TM][TN];
 #pragma unroll
-  for (int r = 0; r < 4; r++)
+  for (int r = 0; r < TM; r++)
 #pragma unroll
-    for (int c = 0; c < 4; c++) acc[r][c] = 0.0;
+    for (int c = 0; c < TN; c++) acc[r][c] = 0.0;
   for (int k0 = kbeg; k0 < kend; k0 += kBK) {
 #pragma unroll
-    for (int e = tid; e < kBM * kBK; e += 256) {
+    for (int e = tid; e < BM * kBK; e += 256) {
       int i, kk;
       if (!TA) {
         i = e / kBK;
         kk = e % kBK;
       } else {
-        kk = e / kBM;
-        i = e % kBM;
+        kk = e / BM;
+        i = e % BM;
       }
       const int gi = row0 + i, gk = k0 + kk;
       double v = 0.0;
@@ -71,11 +82,11 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
       As[kk][i] = v;
     }
 #pragma unroll
-    for (int e = tid; e < kBN * kBK; e += 256) {
+    for (int e = tid; e < BN * kBK; e += 256) {
       int j, kk;
       if (!TB) {
-        kk = e / kBN;
-        j = e % kBN;
+        kk = e / BN;
+        j = e % BN;
       } else {
         j = e / kBK;
         kk = e % kBK;
@@ -88,25 +99,25 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kBK; kk++) {
-      double a[4], b[4];
+      double a[TM], b[TN];
 #pragma unroll
-      for (int r = 0; r < 4; r++) a[r] = As[kk][ty + 16 * r];
+      for (int r = 0; r < TM; r++) a[r] = As[kk][ty + THY * r];
 #pragma unroll
-      for (int c = 0; c < 4; c++) b[c] = Bs[kk][tx + 16 * c];
+      for (int c = 0; c < TN; c++) b[c] = Bs[kk][tx + THX * c];
 #pragma unroll
-      for (int r = 0; r < 4; r++)
+      for (int r = 0; r < TM; r++)
 #pragma unroll
-        for (int c = 0; c < 4; c++) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < TN; c++) acc[r][c] = fma(a[r], b[c], acc[r][c]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < 4; r++) {
-    const int gi = row0 + ty + 16 * r;
+  for (int r = 0; r < TM; r++) {
+    const int gi = row0 + ty + THY * r;
     if (gi >= m) continue;
 #pragma unroll
-    for (int c = 0; c < 4; c++) {
-      const int gj = col0 + tx + 16 * c;
+    for (int c = 0; c < TN; c++) {
+      const int gj = col0 + tx + THX * c;
       if (gj >= n) continue;
       if (ksplit > 1) {
         C[(size_t)gi * n + gj] = acc[r][c];
@@ -129,6 +140,58 @@ __global__ void k_splitk_reduce(int m, int n, int ksplit, const double* __restri
   *p = beta == 0.0 ? alpha * s : fma(alpha, s, beta * *p);
 }
 
+namespace {
+
+struct TileShape {
+  int thy, tm, tn;
+  int bm() const { return thy * tm; }
+  int bn() const { return (256 / thy) * tn; }
+};
+constexpr TileShape kShapes[] = {{16, 4, 4}, {16, 4, 2}, {16, 2, 4}, {16, 2, 2}, {16, 4, 1},
+                                 {16, 1, 4}, {16, 2, 1}, {16, 1, 2}, {16, 1, 1}, {8, 1, 4},
+                                 {8, 1, 2}, {8, 1, 1}};
+
+// The shape with the fewest padded multiply-adds; among equals the one with
+// the largest tile (more reuse of each loaded element).
+TileShape pick_shape(int m, int n) {
+  TileShape best = kShapes[0];
+  long long best_cost = -1;
+  for (const TileShape& t : kShapes) {
+    const long long cost = (long long)cdiv(m, t.bm()) * t.bm() * cdiv(n, t.bn()) * t.bn();
+    const long long area = (long long)t.bm() * t.bn();
+    const long long barea = (long long)best.bm() * best.bn();
+    if (best_cost < 0 || cost < best_cost || (cost == best_cost && area > barea)) {
+      best = t;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
+template <bool TA, bool TB, int THY, int TM, int TN>
+void launch_shape(dim3 grid, cudaStream_t st, int m, int n, int k, double alpha, const double* A,
+                  int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                  const GemmBatch& bt, int ksplit, int kchunk) {
+  k_dgemm<TA, TB, THY, TM, TN><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                     bt, ksplit, kchunk);
+}
+
+template <bool TA, bool TB>
+void launch_t(const TileShape& s, dim3 grid, cudaStream_t st, int m, int n, int k, double alpha,
+              const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+              const GemmBatch& bt, int ksplit, int kchunk) {
+#define RIS_SHAPE(Y, M_, N_)                                                                     \
+  if (s.thy == Y && s.tm == M_ && s.tn == N_)                                                    \
+    return launch_shape<TA, TB, Y, M_, N_>(grid, st, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, \
+                                           bt, ksplit, kchunk);
+  RIS_SHAPE(16, 4, 4) RIS_SHAPE(16, 4, 2) RIS_SHAPE(16, 2, 4) RIS_SHAPE(16, 2, 2)
+  RIS_SHAPE(16, 4, 1) RIS_SHAPE(16, 1, 4) RIS_SHAPE(16, 2, 1) RIS_SHAPE(16, 1, 2)
+  RIS_SHAPE(16, 1, 1) RIS_SHAPE(8, 1, 4) RIS_SHAPE(8, 1, 2) RIS_SHAPE(8, 1, 1)
+#undef RIS_SHAPE
+}
+
+}  // namespace
+
 void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const double* A, int lda,
            const double* B, int ldb, double beta, double* C, int ldc, cudaStream_t st,
            const GemmBatch& bt) {
@@ -136,32 +199,33 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
   const int nb = bt.nb1 * bt.nb2;
   if (nb <= 0) return;
   RIS_REQUIRE(nb <= 65535, RIS_ERR_ARG, "dgemm: batch too large");
-  const int tiles = cdiv(n, kBN) * cdiv(m, kBM);
   if (k <= 0) {  // C = beta C
     RIS_REQUIRE(beta == 0.0, RIS_ERR_ARG, "dgemm: k = 0 with beta != 0");
   }
-  // split k when a single product has too few tiles to fill the GPU
+  const TileShape sh = pick_shape(m, n);
+  const int tiles = cdiv(n, sh.bn()) * cdiv(m, sh.bm());
+  // split k when a single product has too few tiles to occupy every SM twice
   int ksplit = 1, kchunk = k;
-  if (nb == 1 && tiles < 152 && k >= 2048) {
-    ksplit = std::min(std::max(1, 2 * 152 / tiles), k / 512);
-    ksplit = std::max(1, std::min(ksplit, 256));
+  if (nb == 1 && tiles < 2 * 152 && k >= 512) {
+    ksplit = std::min(cdiv(2 * 152, tiles), k / 256);
+    ksplit = std::max(1, std::min(ksplit, 512));
     kchunk = ((cdiv(k, ksplit) + kBK - 1) / kBK) * kBK;
     ksplit = cdiv(k, kchunk);
   }
   double* ws = nullptr;
   MemTrack* ws_tr = nullptr;
   if (ksplit > 1) ws = (double*)dev_alloc(sizeof(double) * (size_t)ksplit * m * n, st, &ws_tr);
-  dim3 grid(cdiv(n, kBN), cdiv(m, kBM), ksplit > 1 ? ksplit : nb);
+  dim3 grid(cdiv(n, sh.bn()), cdiv(m, sh.bm()), ksplit > 1 ? ksplit : nb);
   double* Cout = ksplit > 1 ? ws : C;
   prof_begin(kProfGemm, st);
   if (!transA && !transB)
-    k_dgemm<false, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
+    launch_t<false, false>(sh, grid, st, m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
   else if (!transA && transB)
-    k_dgemm<false, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
+    launch_t<false, true>(sh, grid, st, m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
   else if (transA && !transB)
-    k_dgemm<true, false><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
+    launch_t<true, false>(sh, grid, st, m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
   else
-    k_dgemm<true, true><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
+    launch_t<true, true>(sh, grid, st, m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
   RIS_CHECK_LAUNCH();
   if (ksplit > 1) {
     k_splitk_reduce<<<cdiv((long long)m * n, 256), 256, 0, st>>>(m, n, ksplit, ws, alpha, beta, C, ldc);
@@ -538,6 +602,21 @@ void gemv_rows(const double* V, int nrow, long long ncol, const double* x, doubl
 
 // Test hook (declared in include/ris.h): lowest k eigenpairs of a symmetric
 // m x m matrix with the device subspace eigensolver; device pointers.
+extern "C" int ris_debug_dgemm(int transA, int transB, int m, int n, int k, double alpha,
+                               const double* A, int lda, const double* B, int ldb, double beta,
+                               double* C, int ldc) {
+  using namespace ris;
+  try {
+    RIS_REQUIRE(m >= 0 && n >= 0 && k >= 0 && A && B && C, RIS_ERR_ARG, "bad dgemm arguments");
+    dgemm(transA != 0, transB != 0, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 0);
+    RIS_CUDA(cudaDeviceSynchronize());
+    return 0;
+  } catch (const Error& e) {
+    fprintf(stderr, "ris_debug_dgemm: %s\n", e.msg.c_str());
+    return (int)e.code;
+  }
+}
+
 extern "C" int ris_debug_sym_eig(int m, int k, const double* H, double* w, double* V) {
   using namespace ris;
   try {

@@ -23,7 +23,8 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_excite_guess", "ris_trim", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_gemm_tf32x3_noalloc",
+           "ris_apply", "ris_excite_guess", "ris_trim", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_debug_dgemm",
+           "ris_gemm_tf32x3_noalloc",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
 
@@ -76,6 +77,8 @@ def load(path: str = LIB_PATH):
     L.ris_debug_boys.argtypes = [i, P, P, P]
     L.ris_debug_gemm_tf32x3.argtypes = [i, i, i, P, P, P]
     L.ris_debug_sym_eig.argtypes = [i, i, P, P, P]
+    d = ctypes.c_double
+    L.ris_debug_dgemm.argtypes = [i, i, i, i, i, d, P, i, P, i, d, P, i]
     L.ris_gemm_tf32x3_noalloc.argtypes = [i, i, i, P, P, P, P]
     L.ris_last_error.argtypes = [P]
     L.ris_last_error.restype = ctypes.c_char_p
@@ -271,6 +274,23 @@ def gemm_tf32x3_noalloc(A_t, B_t, C_t, stream=None) -> int:
     N = B_t.shape[0]
     return load().ris_gemm_tf32x3_noalloc(int(M), int(N), int(K), A_t.data_ptr(), B_t.data_ptr(),
                                           C_t.data_ptr(), stream)
+
+
+def debug_dgemm(A, B, C, transA=False, transB=False, alpha=1.0, beta=0.0):
+    """C = alpha op(A) op(B) + beta C with the library's FP64 GEMM (numpy in, numpy out)."""
+    import torch
+    A_t = torch.as_tensor(np.ascontiguousarray(A, dtype=np.float64), device="cuda")
+    B_t = torch.as_tensor(np.ascontiguousarray(B, dtype=np.float64), device="cuda")
+    C_t = torch.as_tensor(np.ascontiguousarray(C, dtype=np.float64), device="cuda")
+    m = A_t.shape[1] if transA else A_t.shape[0]
+    k = A_t.shape[0] if transA else A_t.shape[1]
+    n = B_t.shape[0] if transB else B_t.shape[1]
+    st = load().ris_debug_dgemm(int(transA), int(transB), m, n, k, float(alpha), A_t.data_ptr(),
+                                A_t.shape[1], B_t.data_ptr(), B_t.shape[1], float(beta),
+                                C_t.data_ptr(), C_t.shape[1])
+    if st != 0:
+        raise RisError(st, "ris_debug_dgemm failed")
+    return C_t.cpu().numpy()
 
 
 def debug_sym_eig(H, k):

@@ -30,3 +30,35 @@ def test_sym_eig_lowest(ris_mod, m, k):
     np.testing.assert_allclose(V @ V.T, np.eye(k), atol=1e-10)
     res = H @ V.T - V.T * w[None, :]
     assert np.max(np.abs(res)) < 1e-10
+
+
+# Shapes cover every tile family (8..64 rows, 16..128 columns), ragged edges,
+# split k (few tiles, long k) and all four transposes.
+_GEMM_SHAPES = [(1, 1, 1), (3, 5, 7), (10, 80, 31000), (10, 31000, 80), (71, 5000, 512),
+                (80, 10, 4000), (16, 16, 16), (17, 33, 65), (64, 64, 1), (130, 257, 300),
+                (8, 128, 2000), (5, 2, 100000)]
+
+
+@gpu
+@pytest.mark.parametrize("m,n,k", _GEMM_SHAPES)
+@pytest.mark.parametrize("ta,tb", [(False, False), (False, True), (True, False), (True, True)])
+def test_dgemm_shapes(ris_mod, m, n, k, ta, tb):
+    rng = np.random.default_rng(m * 7 + n * 3 + k)
+    A = rng.standard_normal((k, m) if ta else (m, k))
+    B = rng.standard_normal((n, k) if tb else (k, n))
+    C0 = rng.standard_normal((m, n))
+    alpha, beta = 0.75, -1.25
+    got = ris_mod.debug_dgemm(A, B, C0, ta, tb, alpha, beta)
+    ref = alpha * ((A.T if ta else A) @ (B.T if tb else B)) + beta * C0
+    # FP64 sums of k products of unit normals: error ~ sqrt(k) eps per entry
+    scale = np.sqrt(k) * (np.abs(alpha) + 1) + abs(beta) * np.abs(C0)
+    assert np.max(np.abs(got - ref) / scale) <= 1e-13
+
+
+@gpu
+def test_dgemm_beta_zero_ignores_nan(ris_mod):
+    A = np.ones((9, 40))
+    B = np.ones((40, 11))
+    C0 = np.full((9, 11), np.nan)
+    got = ris_mod.debug_dgemm(A, B, C0, False, False, 1.0, 0.0)
+    np.testing.assert_array_equal(got, np.full((9, 11), 40.0))
