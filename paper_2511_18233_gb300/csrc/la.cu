@@ -7,10 +7,11 @@
 //   and L^{-1}; left-looking, one CTA (the metric is at most a few thousand
 //   functions for one molecule of the ris basis).
 // * sym_eig_lowest: lowest k eigenpairs of a small symmetric matrix (the
-//   Davidson subspace problem), one CTA: Householder reduction to
-//   tridiagonal form, Sturm-sequence bisection for the eigenvalues, inverse
-//   iteration for the eigenvectors of the tridiagonal matrix, Gram-Schmidt
-//   inside clusters of close eigenvalues, back-transformation.
+//   Davidson subspace problem): Householder reduction to tridiagonal form
+//   (one CTA), then one CTA per eigenvalue for Sturm-sequence multisection,
+//   inverse iteration and back-transformation (FP64 runs at about two FMAs
+//   per clock per SM, so the per-eigenvalue work is spread over SMs), and
+//   Gram-Schmidt inside clusters of close eigenvalues.
 #include <math.h>
 #include <stdlib.h>
 
@@ -321,7 +322,7 @@ void tri_inverse(const double* L, double* Linv, int n, cudaStream_t st) {
 // ------------------------------------------------------------------ eigensolver
 constexpr int kEigT = 512;
 
-size_t eig_work_size(int m) { return (size_t)m * m + 5 * (size_t)m + 64 + 64 * (size_t)m * 6; }
+size_t eig_work_size(int m) { return (size_t)m * m + 3 * (size_t)m + 64 + 64 * (size_t)m; }
 
 __device__ int sturm_count(const double* d, const double* e, int m, double x) {
   int c = 0;
@@ -335,35 +336,51 @@ __device__ int sturm_count(const double* d, const double* e, int m, double x) {
   return c;
 }
 
-// No __restrict__ here: every work array below is carved out of `work`, and
-// with restrict-qualified parameters the compiler reordered the in-place
-// updates of the inverse iteration (wrong eigenvectors at m >~ 40).
-__global__ void __launch_bounds__(kEigT) k_sym_eig(const double* H, int ldH, int m, int k,
-                                                   double* w, double* V, double* work,
-                                                   int use_smem) {
+// The work array holds A (m x m: Householder vectors below the diagonal),
+// d, e, tau (m each), the eigenvalues (64) and the eigenvectors (k x m).
+struct EigWork {
+  double *A, *d, *e, *tau, *lam, *Z;
+  __host__ __device__ EigWork(double* work, int m) {
+    A = work;
+    d = A + (size_t)m * m;
+    e = d + m;
+    tau = e + m;
+    lam = tau + m;
+    Z = lam + 64;
+  }
+};
+
+// Gershgorin bounds of the tridiagonal matrix (d, e).
+__device__ void tri_bounds(const double* d, const double* e, int m, double& glo, double& ghi) {
+  for (int i = 0; i < m; i++) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    const double lo = d[i] - r, hi = d[i] + r;
+    if (i == 0 || lo < glo) glo = lo;
+    if (i == 0 || hi > ghi) ghi = hi;
+  }
+}
+
+// Stage 1 (one CTA): symmetrise H and reduce it to tridiagonal form
+// T = Q^T H Q by Householder reflections (d, e; reflectors kept in A).
+// No __restrict__: every array is carved out of `work`, and with
+// restrict-qualified parameters the compiler reordered in-place updates.
+__global__ void __launch_bounds__(kEigT) k_eig_tridiag(const double* H, int ldH, int m,
+                                                       double* work, int use_smem) {
   extern __shared__ double sm_A[];
   __shared__ double red[33];
   __shared__ double sh_alpha, sh_tau;
-  double* A = use_smem ? sm_A : work;
-  double* d = work + (size_t)m * m;
-  double* e = d + m;
-  double* p = e + m;
-  double* tau = p + m;
-  double* lam = tau + 2 * (size_t)m;  // 64
-  double* Z = lam + 64;               // k x m
-  double* DL = Z + (size_t)64 * m;
-  double* DD = DL + (size_t)64 * m;
-  double* DU = DD + (size_t)64 * m;
-  double* DU2 = DU + (size_t)64 * m;
-  double* PIV = DU2 + (size_t)64 * m;
+  EigWork W(work, m);
+  double* A = use_smem ? sm_A : W.A;
+  double* d = W.d;
+  double* e = W.e;
+  double* tau = W.tau;
+  double* p = W.Z;  // scratch (m) before the eigenvectors exist
   const int tid = threadIdx.x;
-  // load and symmetrise
   for (size_t ij = tid; ij < (size_t)m * m; ij += kEigT) {
     const int i = (int)(ij / m), j = (int)(ij % m);
     A[ij] = 0.5 * (H[(size_t)i * ldH + j] + H[(size_t)j * ldH + i]);
   }
   __syncthreads();
-  // --- Householder tridiagonalisation
   for (int c = 0; c + 2 < m; c++) {
     double part = 0.0;
     for (int i = c + 1 + tid; i < m; i += kEigT) part += A[(size_t)i * m + c] * A[(size_t)i * m + c];
@@ -418,50 +435,69 @@ __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* H, int ldH, int
     e[m - 1] = 0.0;
     tau[m - 1] = 0.0;
   }
-  __syncthreads();
-  // --- eigenvalues by multisection: one warp per eigenvalue, 32 Sturm
-  //     counts per step shrink the bracket 33-fold
-  double glo = 0.0, ghi = 0.0;
-  for (int i = 0; i < m; i++) {
-    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
-    const double lo = d[i] - r, hi = d[i] + r;
-    if (i == 0 || lo < glo) glo = lo;
-    if (i == 0 || hi > ghi) ghi = hi;
+  if (use_smem) {  // the reflectors are read back by the next stage
+    for (size_t ij = tid; ij < (size_t)m * m; ij += kEigT) W.A[ij] = A[ij];
   }
+}
+
+constexpr int kEigVecT = 128;
+constexpr int kSectLanes = 8;  // Sturm counts per multisection step
+
+// Stage 2 (one CTA per wanted eigenvalue j, so that the FP64 work of the
+// eigenvalues runs on as many SMs): lambda_j by multisection on Sturm
+// counts (kSectLanes points per step shrink the bracket 9-fold), the
+// eigenvector of T by inverse iteration (Gaussian elimination with partial
+// pivoting of T - lambda_j I, three solves), and its back-transformation
+// x = H_0 ... H_{m-3} z.
+__global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work) {
+  extern __shared__ double sm[];
+  __shared__ double red[33];
+  __shared__ double sh_lo, sh_hi;
+  EigWork W(work, m);
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x;
+  double* d = sm;
+  double* e = d + m;
+  double* z = e + m;
+  double* dl = z + m;
+  double* dd = dl + m;
+  double* du = dd + m;
+  double* du2 = du + m;
+  double* piv = du2 + m;
+  for (int i = tid; i < m; i += kEigVecT) {
+    d[i] = W.d[i];
+    e[i] = W.e[i];
+  }
+  __syncthreads();
+  double glo = 0.0, ghi = 0.0;
+  tri_bounds(d, e, m, glo, ghi);
   const double tnorm = fmax(fmax(fabs(glo), fabs(ghi)), 1e-300);
-  {
-    const int wid = tid >> 5, lane = tid & 31;
-    for (int j = wid; j < k; j += kEigT / 32) {
-      double lo = glo - 1e-12 * tnorm, hi = ghi + 1e-12 * tnorm;
-      for (int it = 0; it < 40; it++) {
-        const double h = (hi - lo) / 33.0;
-        if (!(h > 0.0) || lo + h <= lo) break;
+  if (tid < 32) {
+    const int lane = tid;
+    double lo = glo - 1e-12 * tnorm, hi = ghi + 1e-12 * tnorm;
+    for (int it = 0; it < 80; it++) {
+      const double h = (hi - lo) / (kSectLanes + 1);
+      if (!(h > 0.0) || lo + h <= lo) break;
+      bool above = false;
+      if (lane < kSectLanes) {
         const double x = lo + h * (lane + 1);
-        const bool above = sturm_count(d, e, m, x) > j;  // lambda_j < x
-        const unsigned mask = __ballot_sync(0xffffffffu, above);
-        // first lane whose point lies above lambda_j
-        const int f = mask ? __ffs(mask) - 1 : 32;
-        const double nlo = f == 0 ? lo : lo + h * f;
-        const double nhi = f == 32 ? hi : lo + h * (f + 1);
-        lo = nlo;
-        hi = nhi;
+        above = sturm_count(d, e, m, x) > j;  // lambda_j < x
       }
-      if (lane == 0) lam[j] = 0.5 * (lo + hi);
+      const unsigned mask = __ballot_sync(0xffffffffu, above) & ((1u << kSectLanes) - 1u);
+      const int f = mask ? __ffs(mask) - 1 : kSectLanes;  // first point above lambda_j
+      const double nlo = f == 0 ? lo : lo + h * f;
+      const double nhi = f == kSectLanes ? hi : lo + h * (f + 1);
+      lo = nlo;
+      hi = nhi;
+    }
+    if (lane == 0) {
+      sh_lo = lo;
+      sh_hi = hi;
     }
   }
   __syncthreads();
-  // --- inverse iteration: thread j factors T - lam_j I by Gaussian
-  //     elimination with partial pivoting (unit lower L, upper U with two
-  //     super-diagonals) and applies three solves to a fixed start vector.
-  if (tid < k) {
-    const int j = tid;
-    double* z = Z + (size_t)j * m;
-    double* dl = DL + (size_t)j * m;
-    double* dd = DD + (size_t)j * m;
-    double* du = DU + (size_t)j * m;
-    double* du2 = DU2 + (size_t)j * m;
-    double* piv = PIV + (size_t)j * m;
-    const double lj = lam[j];
+  const double lj = 0.5 * (sh_lo + sh_hi);
+  if (tid == 0) {
     const double tiny = 1e-15 * tnorm;
     for (int i = 0; i < m; i++) {
       dd[i] = d[i] - lj;
@@ -510,13 +546,37 @@ __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* H, int ldH, int
       nrm = 1.0 / sqrt(nrm);
       for (int i = 0; i < m; i++) z[i] *= nrm;
     }
+    W.lam[j] = lj;
   }
   __syncthreads();
-  // --- Gram-Schmidt within clusters of close eigenvalues
+  // back-transformation, H_{m-3} applied first
+  for (int c = m - 3; c >= 0; c--) {
+    const double t = W.tau[c];
+    if (t == 0.0) continue;
+    double part = 0.0;
+    for (int i = c + 1 + tid; i < m; i += kEigVecT) part += W.A[(size_t)i * m + c] * z[i];
+    const double f = t * block_sum<kEigVecT>(part, red);
+    for (int i = c + 1 + tid; i < m; i += kEigVecT) z[i] -= f * W.A[(size_t)i * m + c];
+    __syncthreads();
+  }
+  for (int i = tid; i < m; i += kEigVecT) W.Z[(size_t)j * m + i] = z[i];
+}
+
+// Stage 3 (one CTA): Gram-Schmidt within clusters of close eigenvalues
+// (inverse iteration alone does not separate them), then the output.
+__global__ void __launch_bounds__(kEigT) k_eig_finish(int m, int k, double* w, double* V,
+                                                      double* work) {
+  __shared__ double red[33];
+  EigWork W(work, m);
+  const int tid = threadIdx.x;
+  double glo = 0.0, ghi = 0.0;
+  tri_bounds(W.d, W.e, m, glo, ghi);
+  const double tnorm = fmax(fmax(fabs(glo), fabs(ghi)), 1e-300);
   const double gap_tol = 1e-7 * tnorm;
+  double* Z = W.Z;
   for (int j = 1; j < k; j++) {
     for (int i = 0; i < j; i++) {
-      if (fabs(lam[j] - lam[i]) > gap_tol) continue;
+      if (fabs(W.lam[j] - W.lam[i]) > gap_tol) continue;
       double part = 0.0;
       for (int q = tid; q < m; q += kEigT) part += Z[(size_t)i * m + q] * Z[(size_t)j * m + q];
       const double s = block_sum<kEigT>(part, red);
@@ -529,24 +589,7 @@ __global__ void __launch_bounds__(kEigT) k_sym_eig(const double* H, int ldH, int
       __syncthreads();
     }
   }
-  // --- back-transformation x = H_0 ... H_{m-3} z  (apply H_{m-3} first)
-  for (int c = m - 3; c >= 0; c--) {
-    const double t = tau[c];
-    if (t == 0.0) continue;
-    // one warp per eigenvector
-    const int wid = tid >> 5, lane = tid & 31;
-    for (int j = wid; j < k; j += kEigT / 32) {
-      double* z = Z + (size_t)j * m;
-      double part = 0.0;
-      for (int i = c + 1 + lane; i < m; i += 32) part += A[(size_t)i * m + c] * z[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      const double f = t * part;
-      for (int i = c + 1 + lane; i < m; i += 32) z[i] -= f * A[(size_t)i * m + c];
-    }
-    __syncthreads();
-  }
-  for (int j = tid; j < k; j += kEigT) w[j] = lam[j];
+  for (int j = tid; j < k; j += kEigT) w[j] = W.lam[j];
   for (size_t i = tid; i < (size_t)k * m; i += kEigT) V[i] = Z[i];
 }
 
@@ -554,11 +597,18 @@ void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V
                     cudaStream_t st) {
   RIS_REQUIRE(k >= 1 && k <= 64 && k <= m, RIS_ERR_ARG, "sym_eig_lowest: bad k");
   const size_t smem_max = 200 * 1024;
-  ensure_smem_attr((const void*)k_sym_eig, (int)smem_max);
+  ensure_smem_attr((const void*)k_eig_tridiag, (int)smem_max);
   const size_t need = (size_t)m * m * sizeof(double);
   const int use_smem = need <= smem_max;
+  const size_t vec_smem = 8 * (size_t)m * sizeof(double);
+  RIS_REQUIRE(vec_smem <= 200 * 1024, RIS_ERR_ARG, "sym_eig_lowest: subspace too large");
+  if (vec_smem > 48 * 1024) ensure_smem_attr((const void*)k_eig_vec, (int)(200 * 1024));
   prof_begin(kProfEig, st);
-  k_sym_eig<<<1, kEigT, use_smem ? need : 0, st>>>(H, ldH, m, k, w, V, work, use_smem);
+  k_eig_tridiag<<<1, kEigT, use_smem ? need : 0, st>>>(H, ldH, m, work, use_smem);
+  RIS_CHECK_LAUNCH();
+  k_eig_vec<<<k, kEigVecT, vec_smem, st>>>(m, work);
+  RIS_CHECK_LAUNCH();
+  k_eig_finish<<<1, kEigT, 0, st>>>(m, k, w, V, work);
   RIS_CHECK_LAUNCH();
   prof_end(kProfEig, st, 1.0);
 }

@@ -26,7 +26,7 @@ void tri_inverse(const double* L, double* Linv, int n, cudaStream_t st);
 // Lowest k eigenpairs of the symmetric m x m row-major matrix H (leading
 // dimension ldH; only read).
 // w[k] ascending; V[k][m] (row j = eigenvector j).  work: eig_work_size(m)
-// doubles.  Single CTA.
+// doubles.  Three launches on st.
 size_t eig_work_size(int m);
 void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
                     cudaStream_t st);
