@@ -71,10 +71,12 @@ typedef enum {
 enum { RIS_FP64 = 0, RIS_MIXED = 1 };
 
 typedef struct {
-  int precision;      /* RIS_FP64, or RIS_MIXED: B^K tensors in FP32 and the exchange part
-                         of every Davidson product as 3xTF32 tensor-core GEMMs with FP32
-                         accumulation (Coulomb part, orthogonalisation and subspace
-                         eigenproblem stay FP64) */
+  int precision;      /* RIS_FP64, or RIS_MIXED: the (ab|P)_K half transforms of the
+                         B-tensor build, the exchange part of every Davidson product and
+                         the exchange part of Gamma as 3xTF32 tensor-core GEMMs with FP32
+                         accumulation (integrals, metric Cholesky, the Coulomb part,
+                         orthogonalisation, subspace eigenproblem and the gradient
+                         accumulation stay FP64) */
   int rpa;            /* 0: TDA (Y = 0), 1: full RPA (X, Y) */
   double cx;          /* fraction of exact exchange c_x (Eq. g_integral); default 0.25 */
   double conv_tol;    /* Davidson residual 2-norm per state; default 1e-10 */
@@ -87,7 +89,8 @@ typedef struct {
   int device;         /* CUDA device ordinal */
   int profile;        /* 1: time kernel classes with CUDA events (see ris_get_stats) */
   double mixed_tol;   /* RIS_MIXED: residual tolerance of the 3xTF32 Davidson phase; default 1e-6 */
-  int refine;         /* RIS_MIXED: 1 = continue with FP64 products to conv_tol; default 0 */
+  int refine;         /* RIS_MIXED: 1 = continue with FP64 products to conv_tol (the B
+                         tensors are then built in FP64 throughout); default 0 */
   int precond;        /* TDA Davidson preconditioner: 0 (default) = (D - s + 2 B^J B^J^T)^-1
                          applied exactly (Woodbury) with one shift s just below the smallest
                          orbital-energy difference; 1 = diagonal (D - omega_k)^-1 per state */

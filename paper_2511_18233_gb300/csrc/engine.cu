@@ -383,6 +383,21 @@ __global__ void k_precond(const double* __restrict__ R, const double* __restrict
   T[t] = R[(size_t)s * n + i] / den;
 }
 
+// X[a][b][R] and X[b][a][R] both set to their mean (a < b)
+__global__ void k_sym_pairs(double* __restrict__ X, int v, int nR) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)v * v * nR) return;
+  const int R = (int)(t % nR);
+  const long long ab = t / nR;
+  const int a = (int)(ab / v), b = (int)(ab % v);
+  if (a >= b) return;
+  double* p = X + ((size_t)a * v + b) * nR + R;
+  double* q = X + ((size_t)b * v + a) * nR + R;
+  const double m = 0.5 * (*p + *q);
+  *p = m;
+  *q = m;
+}
+
 // Shift of the Coulomb-exact preconditioner: this far below the smallest
 // orbital-energy difference (Hartree), so that D - s stays positive.
 constexpr double kPrecondGap = 2e-3;
@@ -865,18 +880,20 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
     cKovP.ensure((size_t)nov * nK, st);
     transpose_last2(cKov.p, 1, (int)nov, nK, cKovP.p, st);  // [P][ia]
   }
-  w2.ensure((size_t)v * n * nK, st);
-  dgemm(true, false, v, n * nK, n, 1.0, Cv, nmo, TK.p, n * nK, 0.0, w2.p, n * nK, st);
-  w3.ensure((size_t)v * v * nK, st);
-  {
+  w4.ensure((size_t)v * v * nK, st);
+  if (opt.precision == RIS_MIXED && !opt.refine) {
+    build_Kvv_tc(w4.p);  // B[a][b][R]
+  } else {
+    w2.ensure((size_t)v * n * nK, st);
+    dgemm(true, false, v, n * nK, n, 1.0, Cv, nmo, TK.p, n * nK, 0.0, w2.p, n * nK, st);
+    w3.ensure((size_t)v * v * nK, st);
     GemmBatch bt;
     bt.nb1 = v;
     bt.sB1 = (long long)n * nK;
     bt.sC1 = (long long)v * nK;
     dgemm(true, false, v, nK, n, 1.0, Cv, nmo, w2.p, nK, 0.0, w3.p, nK, st, bt);
+    dgemm(false, true, v * v, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // B[a][b][R]
   }
-  w4.ensure((size_t)v * v * nK, st);
-  dgemm(false, true, v * v, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // B[a][b][R]
   cKvv.ensure((size_t)v * v * nK, st);
   dgemm(false, false, v * v, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKvv.p, nK, st);
   BKvvD.ensure((size_t)v * v * nK, st);
@@ -940,6 +957,43 @@ static TcEpilogue ep_f64(double* c, long long rs, long long bsc = 0, double alph
   TcEpilogue e;
   e.mode = kOutF64; e.c64 = c; e.rs = rs; e.cs = cs; e.bsc = bsc; e.alpha = alpha; e.beta = beta;
   return e;
+}
+
+// Mixed precision: (ab|P)_K = sum_mu,nu C_mu,a C_nu,b (mu nu|P) by two
+// 3xTF32 tensor-core transforms, then B = (ab|P) L_K^-T in FP64 (out
+// [a][b][R]).  Half transform 1: H[a][P][nu] = sum_mu C_v^T[a][mu] T[(P,nu)][mu]
+// with T[(P,nu)][mu] = (nu mu|P) (symmetric in mu, nu); transform 2:
+// G[(a,P)][b] = sum_nu H[(a,P)][nu] C_v^T[b][nu].
+void Engine::build_Kvv_tc(double* out) {
+  const int o = nocc, v = nvir, n = nao;
+  const int ldn = ld4(n);
+  if (!d_tcerr) {
+    RIS_CUDA(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
+    RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
+  }
+  SBuf<float> Th((size_t)nK * n * ldn, st), Tl((size_t)nK * n * ldn, st);
+  SBuf<float> CvTh((size_t)v * ldn, st), CvTl((size_t)v * ldn, st);
+  SBuf<float> Hh((size_t)v * nK * ldn, st), Hl((size_t)v * nK * ldn, st);
+  split_f64_tpad(TK.p, (long long)n * n, nK, n, ldn, Th.p, Tl.p, st);  // [P][nu][mu]
+  split_f64_t(C.p + o, n, v, nmo, CvTh.p, CvTl.p, ldn, st);            // [a][mu]
+  {
+    TcEpilogue e = ep_split(Hh.p, Hl.p, (long long)nK * ldn);
+    e.cin = n;
+    e.cld = ldn;
+    tcg(v, nK * n, n, CvTh.p, CvTl.p, ldn, Th.p, Tl.p, ldn, 0, 1, e, d_tcerr, st);
+  }
+  SBuf<double> G((size_t)v * nK * v, st);
+  tcg(v * nK, v, n, Hh.p, Hl.p, ldn, CvTh.p, CvTl.p, ldn, 0, 1, ep_f64(G.p, v), d_tcerr, st);
+  // out[a][b][R] = sum_P G[a][P][b] L^-1[R][P]
+  GemmBatch bt;
+  bt.nb1 = v;
+  bt.sA1 = (long long)nK * v;
+  bt.sC1 = (long long)v * nK;
+  dgemm(true, true, v, nK, nK, 1.0, G.p, v, LKinv.p, nK, 0.0, out, nK, st, bt);
+  // restore the exact a <-> b symmetry that rounding broke (A must stay symmetric)
+  k_sym_pairs<<<cdiv((long long)v * v * nK, 256), 256, 0, st>>>(out, v, nK);
+  RIS_CHECK_LAUNCH();
+  (void)o;
 }
 
 void Engine::gamma_K_mixed(const float* USh, const float* USl, const float* VSh, const float* VSl,

@@ -144,6 +144,7 @@ struct Engine : StreamOwner {
   void apply_A_mixed(const double* Xin, int nvec, double* out);
   void apply_exchange_mixed(const double* Z, int nvec, double* out, double alpha, double beta);
   void prepare_mixed();
+  void build_Kvv_tc(double* out);
   // exchange part of Gamma / Omega for one (U,V) pair with weight f (3xTF32);
   // US/VS: splits of U, V [i][a]; WU/WV: [Q^T | C_o] splits of U and V
   void gamma_K_mixed(const float* USh, const float* USl, const float* VSh, const float* VSl,

@@ -328,7 +328,41 @@ __global__ void k_split(const double* __restrict__ src, int rows, int cols, long
   lo[t] = to_tf32(x - h);
 }
 
+// Tiled transpose + split: src X[r][c] (r < nr, c < nc, row length nc) to
+// dst[c][r / nin][r % nin] with the inner index padded to ldin.
+__global__ void k_split_tpad(const double* __restrict__ X, long long nr, int nc, int nin, int ldin,
+                             float* __restrict__ hi, float* __restrict__ lo) {
+  __shared__ float tile[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const long long r = r0 + y;
+    const int c = c0 + threadIdx.x;
+    tile[y][threadIdx.x] = (r < nr && c < nc) ? (float)X[(size_t)r * nc + c] : 0.f;
+  }
+  __syncthreads();
+  const long long nouter = nr / nin;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int c = c0 + y;
+    const long long r = r0 + threadIdx.x;
+    if (c >= nc || r >= nr) continue;
+    const float x = tile[threadIdx.x][y];
+    const size_t d = ((size_t)c * nouter + (size_t)(r / nin)) * ldin + (size_t)(r % nin);
+    const float h = to_tf32(x);
+    hi[d] = h;
+    lo[d] = to_tf32(x - h);
+  }
+}
+
 }  // namespace
+
+void split_f64_tpad(const double* src, long long nr, int nc, int nin, int ldin, float* hi,
+                    float* lo, cudaStream_t st) {
+  RIS_REQUIRE(nin > 0 && nr % nin == 0 && ldin >= nin, RIS_ERR_ARG, "split_f64_tpad: bad shape");
+  dim3 g((unsigned)cdiv(nr, 32), (unsigned)cdiv(nc, 32));
+  k_split_tpad<<<g, dim3(32, 8), 0, st>>>(src, nr, nc, nin, ldin, hi, lo);
+  RIS_CHECK_LAUNCH();
+}
 
 void split_f64(const double* src, int rows, int cols, long long lds, float* hi, float* lo, int ldd,
                cudaStream_t st, int nbatch, long long sbs, long long dbs) {

@@ -57,6 +57,11 @@ void split_f64(const double* src, int rows, int cols, long long lds, float* hi, 
 void split_f64_t(const double* src, int rows, int cols, long long lds, float* hi, float* lo,
                  int ldd, cudaStream_t st, int nbatch = 1, long long sbs = 0, long long dbs = 0);
 
+// Transpose + split: src X[r][c] (nr x nc, row-major) into dst[c][r / nin]
+// [r % nin] with the innermost index padded to ldin (padding not written).
+void split_f64_tpad(const double* src, long long nr, int nc, int nin, int ldin, float* hi,
+                    float* lo, cudaStream_t st);
+
 inline int ld4(int k) { return (k + 3) & ~3; }
 
 }  // namespace ris
