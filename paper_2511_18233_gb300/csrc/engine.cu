@@ -119,8 +119,12 @@ void Engine::trim() {
                  &w1, &w2, &w3, &w4, &w5, &w6, &w7, &w8};
   for (DBuf* b : dbs) b->release();
   FBuf* fbs[] = {&BooH, &BooL, &BvvH, &BvvL, &XtH, &XtL, &YH, &YL, &cvvH, &cvvL,
-                 &cooH, &cooL, &CoH, &CoL, &CvH, &CvL};
+                 &cooH, &cooL, &CoH, &CoL, &CvH, &CvL, &Df};
   for (FBuf* b : fbs) b->release();
+  aoPtr.release();
+  aoList.release();
+  axPtr.release();
+  axList.release();
   have_D = false;
   stage = 0;
   nstates = 0;
@@ -572,15 +576,32 @@ static void axpby(long long n, double a, const double* x, double b, const double
 }
 
 // Gamma[mu][nu][jU[P]] += f (DI[mu][nu] cJ[P] + DJ[mu][nu] cI[P])
-__global__ void k_gamma_J(const double* __restrict__ DI, const double* __restrict__ DJ,
-                          const double* __restrict__ cI, const double* __restrict__ cJ,
-                          const int* __restrict__ jU, int nao, int nJ, int nU, double f,
-                          double* __restrict__ G) {
+// Symmetrise n x n matrices in place: X = (X + X^T) / 2, nb of them.
+__global__ void k_symmetrize_sq(double* __restrict__ X, int n, int nb) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)nao * nao * nJ) return;
-  const int P = (int)(t % nJ);
-  const long long mn = t / nJ;
-  G[mn * nU + jU[P]] += f * (DI[mn] * cJ[P] + DJ[mn] * cI[P]);
+  if (t >= (long long)nb * n * n) return;
+  const int b = (int)(t / ((long long)n * n));
+  const long long ij = t % ((long long)n * n);
+  const int i = (int)(ij / n), j = (int)(ij % n);
+  if (i >= j) return;
+  double* M = X + (size_t)b * n * n;
+  const double m = 0.5 * (M[(size_t)i * n + j] + M[(size_t)j * n + i]);
+  M[(size_t)i * n + j] = m;
+  M[(size_t)j * n + i] = m;
+}
+
+__global__ void k_to_f32(const double* __restrict__ x, long long n, float* __restrict__ y) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = (float)x[t];
+}
+
+// cU[s][jU[Q]] = cJ[s][Q] (union index), zero elsewhere (cU zeroed by the caller)
+__global__ void k_expand_cJ(const double* __restrict__ cJ, const int* __restrict__ jU, int ns,
+                            int nJ, int nU, double* __restrict__ cU) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns * nJ) return;
+  const int s = t / nJ, Q = t % nJ;
+  cU[(size_t)s * nU + jU[Q]] = cJ[t];
 }
 
 // Omega[jU[P]][jU[Q]] = f cI[P] cJ[Q]   (whole matrix zeroed first by caller)
@@ -601,50 +622,184 @@ __global__ void k_build_W(const double* __restrict__ C, int nmo, const double* _
   W[t] = k < nocc ? C[(size_t)nu * nmo + k] : Q[(size_t)(k - nocc) * nao + nu];
 }
 
-// W[x][mu][P] = sum_nu D[x][mu][nu][P] * (G[mu][nu][P] + G[nu][mu][P]) / 2
-__global__ void __launch_bounds__(128) k_contract(const double* __restrict__ D,
-                                                  const double* __restrict__ G, int nao, int nU,
-                                                  double* __restrict__ W) {
-  const int mu = blockIdx.x;
-  const size_t plane = (size_t)nao * nao * nU;
-  for (int P = threadIdx.x; P < nU; P += blockDim.x) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int nu = 0; nu < nao; nu++) {
-      const size_t a = ((size_t)mu * nao + nu) * nU + P;
-      const size_t b = ((size_t)nu * nao + mu) * nU + P;
-      const double g = 0.5 * (G[a] + G[b]);
-      s0 += D[a] * g;
-      s1 += D[plane + a] * g;
-      s2 += D[2 * plane + a] * g;
+constexpr int kCBatch = 8;  // states (or pairs) sharing one pass over the derivative integrals
+
+// The contractions below run one thread per (mu, P, slice of nu): the sum
+// over nu is cut into nslice slices so that enough warps are in flight, each
+// slice writes its partial sums and k_sum_slices adds them in a fixed order.
+// With T = float (mixed precision: derivative integrals stored in FP32) the
+// products and runs of kChunk terms are summed in FP32 and the runs in FP64;
+// with T = double everything is FP64.
+constexpr int kChunk = 32;
+
+__host__ __device__ inline void slice_range(int nao, int nslice, int s, int& lo, int& hi) {
+  lo = (int)((long long)nao * s / nslice);
+  hi = (int)((long long)nao * (s + 1) / nslice);
+}
+
+// Coulomb part, per state (the pair densities are linear in the per-state
+// transition densities): part[slice][b][x][mu][P] = sum_{nu in slice}
+// D[x][mu][nu][P] DRs_{s0+b}[mu][nu], b < ns <= kCBatch, DRs symmetrised.
+template <class T>
+__global__ void __launch_bounds__(128) k_contract_states(const T* __restrict__ D,
+                                                         const T* __restrict__ DRs, int s0,
+                                                         int ns, int nao, int nU, int nslice,
+                                                         double* __restrict__ part) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nao * nU) return;
+  const int mu = (int)(idx / nU), P = (int)(idx % nU);
+  int nu0, nu1;
+  slice_range(nao, nslice, blockIdx.y, nu0, nu1);
+  const size_t nn2 = (size_t)nao * nao;
+  const size_t plane = nn2 * nU;
+  double y[kCBatch][3];
+  T c[kCBatch][3];
+#pragma unroll
+  for (int b = 0; b < kCBatch; b++)
+#pragma unroll
+    for (int x = 0; x < 3; x++) y[b][x] = 0.0, c[b][x] = (T)0;
+  const T* dr = DRs + (size_t)s0 * nn2 + (size_t)mu * nao;
+  for (int nu = nu0; nu < nu1; nu++) {
+    const size_t a = ((size_t)mu * nao + nu) * nU + P;
+    const T d0 = D[a], d1 = D[plane + a], d2 = D[2 * plane + a];
+#pragma unroll
+    for (int b = 0; b < kCBatch; b++) {
+      if (b >= ns) break;
+      const T w = dr[(size_t)b * nn2 + nu];
+      c[b][0] += d0 * w;
+      c[b][1] += d1 * w;
+      c[b][2] += d2 * w;
     }
-    W[((size_t)0 * nao + mu) * nU + P] = s0;
-    W[((size_t)1 * nao + mu) * nU + P] = s1;
-    W[((size_t)2 * nao + mu) * nU + P] = s2;
+    if (((nu - nu0) % kChunk) == kChunk - 1 || nu == nu1 - 1) {
+#pragma unroll
+      for (int b = 0; b < kCBatch; b++)
+#pragma unroll
+        for (int x = 0; x < 3; x++) y[b][x] += (double)c[b][x], c[b][x] = (T)0;
+    }
+  }
+  double* ps = part + (size_t)blockIdx.y * ns * 3 * nao * nU;
+#pragma unroll
+  for (int b = 0; b < kCBatch; b++) {
+    if (b >= ns) break;
+#pragma unroll
+    for (int x = 0; x < 3; x++) ps[(((size_t)b * 3 + x) * nao + mu) * nU + P] = y[b][x];
   }
 }
 
-// grad[A][x] = 2 sum_{mu in A, P} W - 2 sum_{P in A, mu} W
-//              - sum_{P in A, Q} (O[P][Q] + O[Q][P]) dM[x][P][Q]
-__global__ void __launch_bounds__(128) k_grad_reduce(const double* __restrict__ W,
-                                                     const double* __restrict__ O,
-                                                     const double* __restrict__ dM,
-                                                     const int* __restrict__ ao_atom,
-                                                     const int* __restrict__ ax_atom, int nao,
-                                                     int nU, double* __restrict__ grad) {
-  __shared__ double red[3][128];
-  const int A = blockIdx.x;
-  double s[3] = {0.0, 0.0, 0.0};
-  for (long long t = threadIdx.x; t < (long long)nao * nU; t += 128) {
-    const int mu = (int)(t / nU), P = (int)(t % nU);
-    const double f = (ao_atom[mu] == A ? 2.0 : 0.0) - (ax_atom[P] == A ? 2.0 : 0.0);
-    if (f != 0.0)
-      for (int x = 0; x < 3; x++) s[x] += f * W[((size_t)x * nao + mu) * nU + P];
+// Exchange part, per pair of a batch (nb <= kCBatch), P < nK:
+//   part[slice][g][x][mu][P] = sum_{nu in slice} D[x][mu][nu][P]
+//                              (GK_g[mu][nu][P] + GK_g[nu][mu][P]) / 2
+template <class T, class G>
+__global__ void __launch_bounds__(128) k_contract_exchange(const T* __restrict__ D,
+                                                           const G* __restrict__ GK, int nb,
+                                                           int nao, int nU, int nK, int nslice,
+                                                           double* __restrict__ part) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nao * nK) return;
+  const int mu = (int)(idx / nK), P = (int)(idx % nK);
+  int nu0, nu1;
+  slice_range(nao, nslice, blockIdx.y, nu0, nu1);
+  const size_t nn2 = (size_t)nao * nao;
+  const size_t plane = nn2 * nU;
+  const size_t gk = nn2 * nK;
+  double s[kCBatch][3];
+  T c[kCBatch][3];
+#pragma unroll
+  for (int b = 0; b < kCBatch; b++)
+#pragma unroll
+    for (int x = 0; x < 3; x++) s[b][x] = 0.0, c[b][x] = (T)0;
+  for (int nu = nu0; nu < nu1; nu++) {
+    const size_t mn = (size_t)mu * nao + nu;
+    const size_t a = mn * nU + P;
+    const T d0 = D[a], d1 = D[plane + a], d2 = D[2 * plane + a];
+    const size_t k1 = mn * nK + P, k2 = ((size_t)nu * nao + mu) * nK + P;
+#pragma unroll
+    for (int b = 0; b < kCBatch; b++) {
+      if (b >= nb) break;
+      const T g = (T)0.5 * ((T)GK[b * gk + k1] + (T)GK[b * gk + k2]);
+      c[b][0] += d0 * g;
+      c[b][1] += d1 * g;
+      c[b][2] += d2 * g;
+    }
+    if (((nu - nu0) % kChunk) == kChunk - 1 || nu == nu1 - 1) {
+#pragma unroll
+      for (int b = 0; b < kCBatch; b++)
+#pragma unroll
+        for (int x = 0; x < 3; x++) s[b][x] += (double)c[b][x], c[b][x] = (T)0;
+    }
   }
-  for (long long t = threadIdx.x; t < (long long)nU * nU; t += 128) {
-    const int P = (int)(t / nU), Q = (int)(t % nU);
-    if (ax_atom[P] != A) continue;
-    const double o = O[(size_t)P * nU + Q] + O[(size_t)Q * nU + P];
-    for (int x = 0; x < 3; x++) s[x] -= o * dM[(size_t)x * nU * nU + t];
+  double* ps = part + (size_t)blockIdx.y * nb * 3 * nao * nK;
+#pragma unroll
+  for (int b = 0; b < kCBatch; b++) {
+    if (b >= nb) break;
+#pragma unroll
+    for (int x = 0; x < 3; x++) ps[(((size_t)b * 3 + x) * nao + mu) * nK + P] = s[b][x];
+  }
+}
+
+// out[i] = sum_s part[s][i], i < n (fixed order)
+__global__ void k_sum_slices(const double* __restrict__ part, int nslice, long long n,
+                             double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int sl = 0; sl < nslice; sl++) acc += part[(size_t)sl * n + i];
+  out[i] = acc;
+}
+
+// slices of the nu sum so that about eight blocks per SM are in flight
+static int pick_slices(long long threads, int nao) {
+  const int base = cdiv(threads, 128);
+  return std::max(1, std::min({cdiv(8 * 152, base), nao / 16, 64}));
+}
+
+// W_g[x][mu][P] of pair g = (I, J): exchange part plus the Coulomb part
+// 2 (cU_J[P] Y_I[x][mu][P] + cU_I[P] Y_J[x][mu][P]).
+__device__ __forceinline__ double pair_w(const double* WKg, const double* YI, const double* YJ,
+                                         const double* cI, const double* cJ, int x, int mu, int P,
+                                         int nao, int nU, int nK) {
+  const size_t y = ((size_t)x * nao + mu) * nU + P;
+  double w = 2.0 * (cJ[P] * YI[y] + cI[P] * YJ[y]);
+  if (P < nK) w += WKg[((size_t)x * nao + mu) * nK + P];
+  return w;
+}
+
+// grad[g][A][x] = 2 sum_{mu in A, P} W_g - 2 sum_{P in A, mu} W_g
+//                 - sum_{P in A, Q} (O[P][Q] + O[Q][P]) dM[x][P][Q]
+// (block (A, g); the functions of atom A from the CSR lists)
+__global__ void __launch_bounds__(128) k_grad_reduce_pairs(
+    const double* __restrict__ WK, const double* __restrict__ Y, const double* __restrict__ cU,
+    const int* __restrict__ pst, const double* __restrict__ O, const double* __restrict__ dM,
+    const int* __restrict__ aoPtr, const int* __restrict__ aoList, const int* __restrict__ axPtr,
+    const int* __restrict__ axList, int nao, int nU, int nK, int natm,
+    double* __restrict__ grad) {
+  __shared__ double red[3][128];
+  const int A = blockIdx.x, g = blockIdx.y;
+  const int sI = pst[2 * g], sJ = pst[2 * g + 1];
+  const double* WKg = WK + (size_t)g * 3 * nao * nK;
+  const double* YI = Y + (size_t)sI * 3 * nao * nU;
+  const double* YJ = Y + (size_t)sJ * 3 * nao * nU;
+  const double* cI = cU + (size_t)sI * nU;
+  const double* cJ = cU + (size_t)sJ * nU;
+  const double* Og = O + (size_t)g * nU * nU;
+  double s[3] = {0.0, 0.0, 0.0};
+  const int a0 = aoPtr[A], na = aoPtr[A + 1] - a0;
+  for (long long t = threadIdx.x; t < (long long)na * nU; t += 128) {
+    const int mu = aoList[a0 + (int)(t / nU)], P = (int)(t % nU);
+#pragma unroll
+    for (int x = 0; x < 3; x++) s[x] += 2.0 * pair_w(WKg, YI, YJ, cI, cJ, x, mu, P, nao, nU, nK);
+  }
+  const int p0 = axPtr[A], np = axPtr[A + 1] - p0;
+  for (long long t = threadIdx.x; t < (long long)np * nao; t += 128) {
+    const int P = axList[p0 + (int)(t / nao)], mu = (int)(t % nao);
+#pragma unroll
+    for (int x = 0; x < 3; x++) s[x] -= 2.0 * pair_w(WKg, YI, YJ, cI, cJ, x, mu, P, nao, nU, nK);
+  }
+  for (long long t = threadIdx.x; t < (long long)np * nU; t += 128) {
+    const int P = axList[p0 + (int)(t / nU)], Q = (int)(t % nU);
+    const double o = Og[(size_t)P * nU + Q] + Og[(size_t)Q * nU + P];
+#pragma unroll
+    for (int x = 0; x < 3; x++) s[x] -= o * dM[((size_t)x * nU + P) * nU + Q];
   }
   for (int x = 0; x < 3; x++) red[x][threadIdx.x] = s[x];
   __syncthreads();
@@ -653,7 +808,7 @@ __global__ void __launch_bounds__(128) k_grad_reduce(const double* __restrict__ 
       for (int x = 0; x < 3; x++) red[x][threadIdx.x] += red[x][threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x < 3) grad[A * 3 + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x < 3) grad[((size_t)g * natm + A) * 3 + threadIdx.x] = red[threadIdx.x][0];
 }
 
 __global__ void k_divide_pairs(double* __restrict__ out, const double* __restrict__ num,
@@ -764,6 +919,24 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
       }
     make_shells(aux, a, l, e, &jm, &km, st);
     nU = aux.nfun;
+    // functions of each atom (CSR) for the per-atom gradient sums
+    auto csr = [&](const ShellSet& sh, SBuf<int>& ptr, SBuf<int>& list) {
+      std::vector<int> cnt(natm + 1, 0), lst;
+      std::vector<std::vector<int>> per(natm);
+      for (int i = 0; i < sh.n; i++)
+        for (int c = 0; c < ncart(sh.h_l[i]); c++) per[sh.h_atom[i]].push_back(sh.h_off[i] + c);
+      for (int A = 0; A < natm; A++) {
+        cnt[A + 1] = cnt[A] + (int)per[A].size();
+        lst.insert(lst.end(), per[A].begin(), per[A].end());
+      }
+      ptr.ensure(natm + 1, st);
+      list.ensure(std::max<size_t>(lst.size(), 1), st);
+      RIS_CUDA(cudaMemcpyAsync(ptr.p, cnt.data(), sizeof(int) * (natm + 1), cudaMemcpyHostToDevice, st));
+      RIS_CUDA(cudaMemcpyAsync(list.p, lst.data(), sizeof(int) * lst.size(), cudaMemcpyHostToDevice, st));
+      RIS_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
+    };
+    csr(ao, aoPtr, aoList);
+    csr(aux, axPtr, axList);
     h_jU.assign(nJ, -1);
     h_kU.assign(nK, -1);
     for (int s = 0; s < aux.n; s++)
@@ -998,7 +1171,7 @@ void Engine::build_Kvv_tc(double* out) {
 
 void Engine::gamma_K_mixed(const float* USh, const float* USl, const float* VSh, const float* VSl,
                            const float* WUh, const float* WUl, const float* WVh, const float* WVl,
-                           double f, double* Gam, double* Om) {
+                           double f, double* Gam, float* Gam32, double* Om) {
   const int o = nocc, v = nvir, nn = nao;
   const int lv4 = ld4(v), lo4 = ld4(o), kp = ld4(2 * o);
   // Z[j][P][b] = sum_a U[j][a] c^vv[P][b][a]
@@ -1021,8 +1194,14 @@ void Engine::gamma_K_mixed(const float* USh, const float* USl, const float* VSh,
   tcg(nn, o, o, CoH.p, CoL.p, lo4, GH.p, GL.p, lo4, (long long)o * lo4, nK,
       ep_split(MH.p + o, ML.p + o, (long long)nK * kp, 1, kp), d_tcerr, st);
   // Gamma[mu][nu][P] += f sum_k' W_V[nu][k'] M1[mu][P][k']   (batch mu)
-  tcg(nn, nK, 2 * o, WVh, WVl, kp, MH.p, ML.p, kp, (long long)nK * kp, nn,
-      ep_f64(Gam, nU, (long long)nn * nU, f, 1.0), d_tcerr, st);
+  if (Gam32) {
+    TcEpilogue e;
+    e.mode = kOutF32; e.c32 = Gam32; e.rs = nK; e.bsc = (long long)nn * nK; e.alpha = f; e.beta = 1.0;
+    tcg(nn, nK, 2 * o, WVh, WVl, kp, MH.p, ML.p, kp, (long long)nK * kp, nn, e, d_tcerr, st);
+  } else {
+    tcg(nn, nK, 2 * o, WVh, WVl, kp, MH.p, ML.p, kp, (long long)nK * kp, nn,
+        ep_f64(Gam, nK, (long long)nn * nK, f, 1.0), d_tcerr, st);
+  }
   // Omega[A][B] += f sum_{k,j} c^oo[A][k][j] G[B][k][j]
   tcg(nK, nK, o * lo4, cooH.p, cooL.p, o * lo4, GH.p, GL.p, o * lo4, 0, 1, ep_f64(Om, nU, 0, f, 1.0),
       d_tcerr, st);
@@ -1628,12 +1807,21 @@ void Engine::davidson_rpa(int ns) {
 }
 
 // ------------------------------------------------------------------ derivatives
+// Derivative integrals for the current geometry: FP64 storage, or FP32 in
+// mixed precision (the integral recursion itself is FP64 either way).
 void Engine::ensure_D() {
   if (have_D) return;
   const size_t plane = (size_t)nao * nao * nU;
-  D.ensure(3 * plane, st);
-  RIS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * 3 * plane, st));
-  int3c_deriv(ao, aux, pl, xyz.p, D.p, st);
+  if (opt.precision == RIS_MIXED) {
+    D.release();
+    Df.ensure(3 * plane, st);
+    RIS_CUDA(cudaMemsetAsync(Df.p, 0, sizeof(float) * 3 * plane, st));
+    int3c_deriv<float>(ao, aux, pl, xyz.p, Df.p, st);
+  } else {
+    D.ensure(3 * plane, st);
+    RIS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * 3 * plane, st));
+    int3c_deriv<double>(ao, aux, pl, xyz.p, D.p, st);
+  }
   have_D = true;
 }
 
@@ -1744,9 +1932,53 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
   // u_s = R_s . B^J (nJ), c_s = u_s L^-1 (row vector)
   dgemm(false, false, nsu, nJ, (int)nov, 1.0, Rs.p, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
   dgemm(false, false, nsu, nJ, nJ, 1.0, w5.p, nJ, LJinv.p, nJ, 0.0, cJ.p, nJ, st);
-  // per pair
-  const size_t gsz = (size_t)nn * nn * nU;
-  SBuf<double> Gam(gsz, st), Om((size_t)nU * nU, st), Wc(3 * (size_t)nn * nU, st), Z, Goo, M1, WV;
+  // Coulomb part of every pair density from per-state data: symmetrised
+  // D^R and c^J on the union index (the contraction forms G^J on the fly)
+  k_symmetrize_sq<<<cdiv((long long)nsu * nn * nn, 256), 256, 0, st>>>(DR.p, nn, nsu);
+  RIS_CHECK_LAUNCH();
+  SBuf<double> cU((size_t)nsu * nU, st, true);
+  k_expand_cJ<<<cdiv(nsu * nJ, 256), 256, 0, st>>>(cJ.p, d_jU, nsu, nJ, nU, cU.p);
+  RIS_CHECK_LAUNCH();
+  // Coulomb part: Y_s = D . DRs_s for every state, kCBatch states per pass
+  SBuf<double> Yst((size_t)nsu * 3 * nn * nU, st);
+  prof_begin(kProfContract, st);
+  const double dbytes = mixed ? 4.0 : 8.0;  // derivative integrals in FP32 / FP64
+  SBuf<float> DRf;
+  if (mixed) {
+    DRf.ensure((size_t)nsu * nn * nn, st);
+    k_to_f32<<<cdiv((long long)nsu * nn * nn, 256), 256, 0, st>>>(DR.p, (long long)nsu * nn * nn,
+                                                                  DRf.p);
+    RIS_CHECK_LAUNCH();
+  }
+  const int slJ = pick_slices((long long)nn * nU, nn);
+  SBuf<double> partJ((size_t)slJ * std::min(nsu, kCBatch) * 3 * nn * nU, st);
+  for (int s0 = 0; s0 < nsu; s0 += kCBatch) {
+    const int ns = std::min(kCBatch, nsu - s0);
+    const dim3 grid(cdiv((long long)nn * nU, 128), slJ);
+    if (mixed)
+      k_contract_states<float><<<grid, 128, 0, st>>>(Df.p, DRf.p, s0, ns, nn, nU, slJ, partJ.p);
+    else
+      k_contract_states<double><<<grid, 128, 0, st>>>(D.p, DR.p, s0, ns, nn, nU, slJ, partJ.p);
+    RIS_CHECK_LAUNCH();
+    const long long cnt = (long long)ns * 3 * nn * nU;
+    k_sum_slices<<<cdiv(cnt, 256), 256, 0, st>>>(partJ.p, slJ, cnt,
+                                                Yst.p + (size_t)s0 * 3 * nn * nU);
+    RIS_CHECK_LAUNCH();
+  }
+  prof_end(kProfContract, st, dbytes * cdiv(nsu, kCBatch) * (3.0 * nn * nn * nU) +
+                                  8.0 * (nsu * (double)nn * nn + 3.0 * nsu * nn * nU));
+  // exchange part: pairs in batches sharing one pass over the derivative
+  // integrals; G^K[mu][nu][P < nK] and Omega are formed per pair
+  const int NB = std::min(npair, kCBatch);
+  const size_t gk = (size_t)nn * nn * nK;
+  // G^K in FP32 when every term of it comes from the tensor cores (mixed TDA)
+  const bool gk32 = mixed && !rpa;
+  SBuf<double> GK(gk32 ? 1 : (size_t)NB * gk, st), OmB((size_t)NB * nU * nU, st),
+      WK((size_t)NB * 3 * nn * nK, st), Z, Goo, M1, WV;
+  SBuf<float> GK32(gk32 ? (size_t)NB * gk : 1, st);
+  const int slK = pick_slices((long long)nn * nK, nn);
+  SBuf<double> partK((size_t)slK * NB * 3 * nn * nK, st);
+  SBuf<int> pst(2 * NB, st);
   if (opt.precision != RIS_MIXED) {
     Z.ensure((size_t)o * v * nK, st);
     Goo.ensure((size_t)o * o * nK, st);
@@ -1754,112 +1986,136 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
     WV.ensure((size_t)nn * 2 * o, st);
   }
   const double cx = opt.cx;
-  for (int g = 0; g < npair; g++) {
-    const int sI = slot[pairs[2 * g]], sJ = slot[pairs[2 * g + 1]];
-    RIS_CUDA(cudaMemsetAsync(Gam.p, 0, sizeof(double) * gsz, st));
-    RIS_CUDA(cudaMemsetAsync(Om.p, 0, sizeof(double) * nU * nU, st));
-    // Coulomb
-    k_gamma_J<<<cdiv((long long)nn * nn * nJ, 256), 256, 0, st>>>(
-        DR.p + (size_t)sI * nn * nn, DR.p + (size_t)sJ * nn * nn, cJ.p + (size_t)sI * nJ,
-        cJ.p + (size_t)sJ * nJ, d_jU, nn, nJ, nU, 2.0, Gam.p);
-    RIS_CHECK_LAUNCH();
-    k_omega_J<<<cdiv(nJ * nJ, 256), 256, 0, st>>>(cJ.p + (size_t)sI * nJ, cJ.p + (size_t)sJ * nJ,
-                                                   d_jU, nJ, nU, 2.0, Om.p);
-    RIS_CHECK_LAUNCH();
-    // exchange (ij|ab) for (R_I,R_J) and (L_I,L_J), each with weight -c_x/2;
-    // with Y = 0 both combinations coincide, so one pass with -c_x.
-    const int ncomb = rpa ? 2 : 1;
-    for (int cmb = 0; cmb < ncomb; cmb++) {
-      const double f = rpa ? -0.5 * cx : -cx;
-      if (mixed) {
-        const size_t so = (size_t)o * lv4, sw = (size_t)nn * kp;
-        const float* USh = (cmb == 0 ? RSh.p : LSh.p) + sI * so;
-        const float* USl = (cmb == 0 ? RSl.p : LSl.p) + sI * so;
-        const float* VSh = (cmb == 0 ? RSh.p : LSh.p) + sJ * so;
-        const float* VSl = (cmb == 0 ? RSl.p : LSl.p) + sJ * so;
-        const float* WUh = (cmb == 0 ? WRh.p : WLh.p) + sI * sw;
-        const float* WUl = (cmb == 0 ? WRl.p : WLl.p) + sI * sw;
-        const float* WVh = (cmb == 0 ? WRh.p : WLh.p) + sJ * sw;
-        const float* WVl = (cmb == 0 ? WRl.p : WLl.p) + sJ * sw;
-        gamma_K_mixed(USh, USl, VSh, VSl, WUh, WUl, WVh, WVl, f, Gam.p, Om.p);
-        continue;
-      }
-      const double* U = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sI * nov;
-      const double* Vv = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sJ * nov;
-      const double* QU = (cmb == 0 ? QR.p : QL.p) + (size_t)sI * o * nn;
-      const double* QV = (cmb == 0 ? QR.p : QL.p) + (size_t)sJ * o * nn;
-      // Z[j][b][P] = sum_a U[j][a] c^vv[a][b][P]
-      dgemm(false, false, o, v * nK, v, 1.0, U, v, cKvv.p, v * nK, 0.0, Z.p, v * nK, st);
-      // G[j][k][P] = sum_b V[k][b] Z[j][b][P]
-      {
-        GemmBatch bt;
-        bt.nb1 = o;
-        bt.sB1 = (long long)v * nK;
-        bt.sC1 = (long long)o * nK;
-        dgemm(false, false, o, nK, v, 1.0, Vv, v, Z.p, nK, 0.0, Goo.p, nK, st, bt);
-      }
-      // M1[mu][0:o][P] = C_o G ; M1[mu][o:2o][P] = Q_U^T c^oo
-      dgemm(false, false, nn, o * nK, o, 1.0, Co, nmo, Goo.p, o * nK, 0.0, M1.p, 2 * o * nK, st);
-      dgemm(true, false, nn, o * nK, o, 1.0, QU, nn, cKoo.p, o * nK, 0.0, M1.p + (size_t)o * nK,
-            2 * o * nK, st);
-      k_build_W<<<cdiv(nn * 2 * o, 256), 256, 0, st>>>(C.p, nmo, QV, nn, o, WV.p);
+  for (int g0 = 0; g0 < npair; g0 += NB) {
+    const int nb = std::min(NB, npair - g0);
+    if (gk32)
+      RIS_CUDA(cudaMemsetAsync(GK32.p, 0, sizeof(float) * nb * gk, st));
+    else
+      RIS_CUDA(cudaMemsetAsync(GK.p, 0, sizeof(double) * nb * gk, st));
+    RIS_CUDA(cudaMemsetAsync(OmB.p, 0, sizeof(double) * nb * nU * nU, st));
+    std::vector<int> h_pst(2 * nb);
+    for (int b = 0; b < nb; b++) {
+      const int g = g0 + b;
+      const int sI = slot[pairs[2 * g]], sJ = slot[pairs[2 * g + 1]];
+      h_pst[2 * b] = sI;
+      h_pst[2 * b + 1] = sJ;
+      double* Gam = gk32 ? nullptr : GK.p + (size_t)b * gk;
+      float* Gam32 = gk32 ? GK32.p + (size_t)b * gk : nullptr;
+      double* Om = OmB.p + (size_t)b * nU * nU;
+      k_omega_J<<<cdiv(nJ * nJ, 256), 256, 0, st>>>(cJ.p + (size_t)sI * nJ, cJ.p + (size_t)sJ * nJ,
+                                                     d_jU, nJ, nU, 2.0, Om);
       RIS_CHECK_LAUNCH();
-      // Gamma[mu][nu][P<nK] += f sum_k W_V[nu][k] M1[mu][k][P]
-      {
-        GemmBatch bt;
-        bt.nb1 = nn;
-        bt.sB1 = 2LL * o * nK;
-        bt.sC1 = (long long)nn * nU;
-        dgemm(false, false, nn, nK, 2 * o, f, WV.p, 2 * o, M1.p, nK, 1.0, Gam.p, nU, st, bt);
-      }
-      // Omega[P][Q] += f sum_ij c^oo_ij,P G_ij,Q   (K functions are union 0..nK-1)
-      dgemm(true, false, nK, nK, o * o, f, cKoo.p, nK, Goo.p, nK, 1.0, Om.p, nU, st);
-    }
-    if (rpa) {
-      // (ib|ja) terms, weights -c_x/2 for (R_I,R_J) and +c_x/2 for (L_I,L_J):
-      //   E1_P = U c_P^T, E2_P = V c_P^T (nocc x nocc), c_P = c^ov[P] as [k][a]
-      //   Gamma_ov^T[nu][mu] += w sum_k C_o[nu][k] (E1_P Q_V + E2_P Q_U)[k][mu]
-      //   Omega[A][B] += w sum_{k,i} E2_A[k][i] E1_B[i][k]
-      SBuf<double> E1((size_t)nK * o * o, st), E2((size_t)nK * o * o, st), E1t((size_t)nK * o * o, st),
-          M2((size_t)nK * o * nn, st), M2p((size_t)nK * o * nn, st);
-      for (int cmb = 0; cmb < 2; cmb++) {
-        const double wgt = cmb == 0 ? -0.5 * cx : 0.5 * cx;
+      // exchange (ij|ab) for (R_I,R_J) and (L_I,L_J), each with weight -c_x/2;
+      // with Y = 0 both combinations coincide, so one pass with -c_x.
+      const int ncomb = rpa ? 2 : 1;
+      for (int cmb = 0; cmb < ncomb; cmb++) {
+        const double f = rpa ? -0.5 * cx : -cx;
+        if (mixed) {
+          const size_t so = (size_t)o * lv4, sw = (size_t)nn * kp;
+          const float* USh = (cmb == 0 ? RSh.p : LSh.p) + sI * so;
+          const float* USl = (cmb == 0 ? RSl.p : LSl.p) + sI * so;
+          const float* VSh = (cmb == 0 ? RSh.p : LSh.p) + sJ * so;
+          const float* VSl = (cmb == 0 ? RSl.p : LSl.p) + sJ * so;
+          const float* WUh = (cmb == 0 ? WRh.p : WLh.p) + sI * sw;
+          const float* WUl = (cmb == 0 ? WRl.p : WLl.p) + sI * sw;
+          const float* WVh = (cmb == 0 ? WRh.p : WLh.p) + sJ * sw;
+          const float* WVl = (cmb == 0 ? WRl.p : WLl.p) + sJ * sw;
+          gamma_K_mixed(USh, USl, VSh, VSl, WUh, WUl, WVh, WVl, f, Gam, Gam32, Om);
+          continue;
+        }
         const double* U = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sI * nov;
         const double* Vv = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sJ * nov;
         const double* QU = (cmb == 0 ? QR.p : QL.p) + (size_t)sI * o * nn;
         const double* QV = (cmb == 0 ? QR.p : QL.p) + (size_t)sJ * o * nn;
-        GemmBatch bP;
-        bP.nb1 = nK;
-        bP.sB1 = nov;
-        bP.sC1 = (long long)o * o;
-        dgemm(false, true, o, o, v, 1.0, U, v, cKovP.p, v, 0.0, E1.p, o, st, bP);
-        dgemm(false, true, o, o, v, 1.0, Vv, v, cKovP.p, v, 0.0, E2.p, o, st, bP);
-        GemmBatch bM;
-        bM.nb1 = nK;
-        bM.sA1 = (long long)o * o;
-        bM.sC1 = (long long)o * nn;
-        dgemm(false, false, o, nn, o, 1.0, E1.p, o, QV, nn, 0.0, M2.p, nn, st, bM);
-        dgemm(false, false, o, nn, o, 1.0, E2.p, o, QU, nn, 1.0, M2.p, nn, st, bM);
-        k_permute120<<<cdiv((long long)nK * o * nn, 256), 256, 0, st>>>(M2.p, nK, o, nn, M2p.p);
+        // Z[j][b][P] = sum_a U[j][a] c^vv[a][b][P]
+        dgemm(false, false, o, v * nK, v, 1.0, U, v, cKvv.p, v * nK, 0.0, Z.p, v * nK, st);
+        // G[j][k][P] = sum_b V[k][b] Z[j][b][P]
+        {
+          GemmBatch bt;
+          bt.nb1 = o;
+          bt.sB1 = (long long)v * nK;
+          bt.sC1 = (long long)o * nK;
+          dgemm(false, false, o, nK, v, 1.0, Vv, v, Z.p, nK, 0.0, Goo.p, nK, st, bt);
+        }
+        // M1[mu][0:o][P] = C_o G ; M1[mu][o:2o][P] = Q_U^T c^oo
+        dgemm(false, false, nn, o * nK, o, 1.0, Co, nmo, Goo.p, o * nK, 0.0, M1.p, 2 * o * nK, st);
+        dgemm(true, false, nn, o * nK, o, 1.0, QU, nn, cKoo.p, o * nK, 0.0, M1.p + (size_t)o * nK,
+              2 * o * nK, st);
+        k_build_W<<<cdiv(nn * 2 * o, 256), 256, 0, st>>>(C.p, nmo, QV, nn, o, WV.p);
         RIS_CHECK_LAUNCH();
-        GemmBatch bG;
-        bG.nb1 = nn;
-        bG.sB1 = (long long)nK * o;
-        bG.sC1 = (long long)nn * nU;
-        dgemm(false, true, nn, nK, o, wgt, C.p, nmo, M2p.p, o, 1.0, Gam.p, nU, st, bG);
-        // E1t[P][k][i] = E1[P][i][k]
-        transpose_last2(E1.p, nK, o, o, E1t.p, st);
-        dgemm(false, true, nK, nK, o * o, wgt, E2.p, o * o, E1t.p, o * o, 1.0, Om.p, nU, st);
+        // Gamma[mu][nu][P<nK] += f sum_k W_V[nu][k] M1[mu][k][P]
+        {
+          GemmBatch bt;
+          bt.nb1 = nn;
+          bt.sB1 = 2LL * o * nK;
+          bt.sC1 = (long long)nn * nK;
+          dgemm(false, false, nn, nK, 2 * o, f, WV.p, 2 * o, M1.p, nK, 1.0, Gam, nK, st, bt);
+        }
+        // Omega[P][Q] += f sum_ij c^oo_ij,P G_ij,Q   (K functions are union 0..nK-1)
+        dgemm(true, false, nK, nK, o * o, f, cKoo.p, nK, Goo.p, nK, 1.0, Om, nU, st);
+      }
+      if (rpa) {
+        // (ib|ja) terms, weights -c_x/2 for (R_I,R_J) and +c_x/2 for (L_I,L_J):
+        //   E1_P = U c_P^T, E2_P = V c_P^T (nocc x nocc), c_P = c^ov[P] as [k][a]
+        //   Gamma_ov^T[nu][mu] += w sum_k C_o[nu][k] (E1_P Q_V + E2_P Q_U)[k][mu]
+        //   Omega[A][B] += w sum_{k,i} E2_A[k][i] E1_B[i][k]
+        SBuf<double> E1((size_t)nK * o * o, st), E2((size_t)nK * o * o, st), E1t((size_t)nK * o * o, st),
+            M2((size_t)nK * o * nn, st), M2p((size_t)nK * o * nn, st);
+        for (int cmb = 0; cmb < 2; cmb++) {
+          const double wgt = cmb == 0 ? -0.5 * cx : 0.5 * cx;
+          const double* U = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sI * nov;
+          const double* Vv = (cmb == 0 ? Rs.p : Ls.p) + (size_t)sJ * nov;
+          const double* QU = (cmb == 0 ? QR.p : QL.p) + (size_t)sI * o * nn;
+          const double* QV = (cmb == 0 ? QR.p : QL.p) + (size_t)sJ * o * nn;
+          GemmBatch bP;
+          bP.nb1 = nK;
+          bP.sB1 = nov;
+          bP.sC1 = (long long)o * o;
+          dgemm(false, true, o, o, v, 1.0, U, v, cKovP.p, v, 0.0, E1.p, o, st, bP);
+          dgemm(false, true, o, o, v, 1.0, Vv, v, cKovP.p, v, 0.0, E2.p, o, st, bP);
+          GemmBatch bM;
+          bM.nb1 = nK;
+          bM.sA1 = (long long)o * o;
+          bM.sC1 = (long long)o * nn;
+          dgemm(false, false, o, nn, o, 1.0, E1.p, o, QV, nn, 0.0, M2.p, nn, st, bM);
+          dgemm(false, false, o, nn, o, 1.0, E2.p, o, QU, nn, 1.0, M2.p, nn, st, bM);
+          k_permute120<<<cdiv((long long)nK * o * nn, 256), 256, 0, st>>>(M2.p, nK, o, nn, M2p.p);
+          RIS_CHECK_LAUNCH();
+          GemmBatch bG;
+          bG.nb1 = nn;
+          bG.sB1 = (long long)nK * o;
+          bG.sC1 = (long long)nn * nK;
+          dgemm(false, true, nn, nK, o, wgt, C.p, nmo, M2p.p, o, 1.0, Gam, nK, st, bG);
+          // E1t[P][k][i] = E1[P][i][k]
+          transpose_last2(E1.p, nK, o, o, E1t.p, st);
+          dgemm(false, true, nK, nK, o * o, wgt, E2.p, o * o, E1t.p, o * o, 1.0, Om, nU, st);
+        }
       }
     }
+    RIS_CUDA(cudaMemcpyAsync(pst.p, h_pst.data(), sizeof(int) * 2 * nb, cudaMemcpyHostToDevice, st));
     prof_begin(kProfContract, st);
-    k_contract<<<nn, 128, 0, st>>>(D.p, Gam.p, nn, nU, Wc.p);
+    const dim3 gridK(cdiv((long long)nn * nK, 128), slK);
+    if (gk32)
+      k_contract_exchange<float, float><<<gridK, 128, 0, st>>>(Df.p, GK32.p, nb, nn, nU, nK, slK,
+                                                              partK.p);
+    else if (mixed)
+      k_contract_exchange<float, double><<<gridK, 128, 0, st>>>(Df.p, GK.p, nb, nn, nU, nK, slK,
+                                                               partK.p);
+    else
+      k_contract_exchange<double, double><<<gridK, 128, 0, st>>>(D.p, GK.p, nb, nn, nU, nK, slK,
+                                                                partK.p);
     RIS_CHECK_LAUNCH();
-    // algorithmic bytes: D (3 planes) + Gamma read twice + W written
-    prof_end(kProfContract, st, 8.0 * ((double)gsz * 5.0 + 3.0 * nn * nU));
-    k_grad_reduce<<<natm, 128, 0, st>>>(Wc.p, Om.p, dMU.p, ao.fun_atom, aux.fun_atom, nn, nU,
-                                        out + (size_t)g * natm * 3);
+    const long long cntK = (long long)nb * 3 * nn * nK;
+    k_sum_slices<<<cdiv(cntK, 256), 256, 0, st>>>(partK.p, slK, cntK, WK.p);
     RIS_CHECK_LAUNCH();
+    // algorithmic bytes: the P < nK part of D once, G^K twice per pair, W written
+    prof_end(kProfContract, st,
+             dbytes * 3.0 * nn * nn * nK + (gk32 ? 4.0 : 8.0) * 2.0 * nb * gk + 24.0 * nb * nn * nK);
+    k_grad_reduce_pairs<<<dim3(natm, nb), 128, 0, st>>>(WK.p, Yst.p, cU.p, pst.p, OmB.p, dMU.p,
+                                                        aoPtr.p, aoList.p, axPtr.p, axList.p, nn,
+                                                        nU, nK, natm, out + (size_t)g0 * natm * 3);
+    RIS_CHECK_LAUNCH();
+    RIS_CUDA(cudaStreamSynchronize(st));  // h_pst goes out of scope
   }
   if (opt.precision == RIS_MIXED) {
     int h_err = 0;

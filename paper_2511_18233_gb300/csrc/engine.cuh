@@ -86,11 +86,14 @@ struct Engine : StreamOwner {
   std::vector<int> h_jU, h_kU;  // J / K function -> union function
   int* d_jU = nullptr;
   int* d_kU = nullptr;
+  // functions of each atom (CSR): AO functions and union auxiliary functions
+  SBuf<int> aoPtr, aoList, axPtr, axList;
   PairList pl;
   DBuf TJ, TK;              // (mu nu|P) [mu][nu][P] per set
   DBuf MU, dMU;             // union metric and d/dP_x
   DBuf LJinv, LKinv;        // inverse Cholesky factors
-  DBuf D;                   // derivative integrals [3][mu][nu][P_U]
+  DBuf D;                   // derivative integrals [3][mu][nu][P_U] (FP64 path)
+  FBuf Df;                  // the same in FP32 storage (mixed precision)
   bool have_D = false;
   int* d_info = nullptr;
 
@@ -146,10 +149,11 @@ struct Engine : StreamOwner {
   void prepare_mixed();
   void build_Kvv_tc(double* out);
   // exchange part of Gamma / Omega for one (U,V) pair with weight f (3xTF32);
-  // US/VS: splits of U, V [i][a]; WU/WV: [Q^T | C_o] splits of U and V
+  // US/VS: splits of U, V [i][a]; WU/WV: [Q^T | C_o] splits of U and V;
+  // Gamma accumulated in FP64 (Gam) or, when Gam32 is given, in FP32
   void gamma_K_mixed(const float* USh, const float* USl, const float* VSh, const float* VSl,
                      const float* WUh, const float* WUl, const float* WVh, const float* WVl,
-                     double f, double* Gam, double* Om);
+                     double f, double* Gam, float* Gam32, double* Om);
   void dav_core(int ns, const double* guess, int nguess, bool mixed, double tol,
                 bool augment = false);
   void apply_ApB_AmB(const double* Zin, int nvec, double* outP, double* outM);

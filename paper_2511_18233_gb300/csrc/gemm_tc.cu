@@ -283,6 +283,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
         if (ep.mode == kOutF64) {
           double* p = ep.c64 + off;
           *p = ep.beta == 0.0 ? ep.alpha * v[j] : fma(ep.alpha, (double)v[j], ep.beta * *p);
+        } else if (ep.mode == kOutF32) {
+          float* p = ep.c32 + off;
+          const float a = (float)ep.alpha, b = (float)ep.beta;
+          *p = b == 0.f ? a * v[j] : fmaf(a, v[j], b * *p);
         } else {
           const float x = (float)ep.alpha * v[j];
           const float h = to_tf32(x);

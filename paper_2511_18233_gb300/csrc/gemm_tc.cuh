@@ -24,10 +24,12 @@ struct TcOperand {
 // stride cld, e.g. a padded inner index), else j.
 //   kOutF64:   C64 = alpha * acc + beta * C64
 //   kOutSplit: Chi/Clo = tf32 split of alpha * acc (FP32)
-enum TcOut { kOutF64 = 0, kOutSplit = 1 };
+//   kOutF32:   C32 = alpha * acc + beta * C32 (FP32 arithmetic)
+enum TcOut { kOutF64 = 0, kOutSplit = 1, kOutF32 = 2 };
 struct TcEpilogue {
   int mode = kOutF64;
   double* c64 = nullptr;
+  float* c32 = nullptr;
   float* chi = nullptr;
   float* clo = nullptr;
   long long rs = 0, cs = 1;

@@ -337,8 +337,8 @@ __global__ void __launch_bounds__(128) k_int3c(const int* __restrict__ pa, const
 }
 
 // d(mu nu|P)/dA_x (A = centre of mu) and d(mu nu|P)/dB_x, written as
-// D[x][mu][nu][P] and D[x][nu][mu][P].
-template <int LA, int LB, int LC>
+// D[x][mu][nu][P] and D[x][nu][mu][P] (computed in FP64, stored as T).
+template <int LA, int LB, int LC, class T>
 __global__ void __launch_bounds__(128) k_int3c_deriv(
     const int* __restrict__ pa, const int* __restrict__ pb, int p0, int np,
     const int* __restrict__ auxl, int nax, const int* __restrict__ sh_atom,
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(128) k_int3c_deriv(
     const double* __restrict__ sh_nb, const int* __restrict__ ax_atom,
     const int* __restrict__ ax_off, const double* __restrict__ ax_ex,
     const double* __restrict__ ax_nb, const double* __restrict__ xyz,
-    const double* __restrict__ boys_tab, int nao, int naux, double* __restrict__ D) {
+    const double* __restrict__ boys_tab, int nao, int naux, T* __restrict__ D) {
   constexpr int L = LA + LB + LC + 1;
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (long long)np * nax) return;
@@ -415,8 +415,8 @@ __global__ void __launch_bounds__(128) k_int3c_deriv(
             sA += eA * r;
             sB += eB * r;
           }
-          D[x * plane + ((size_t)mu * nao + nu) * naux + P] = sA * sc_;
-          D[x * plane + ((size_t)nu * nao + mu) * naux + P] = sB * sc_;
+          D[x * plane + ((size_t)mu * nao + nu) * naux + P] = (T)(sA * sc_);
+          D[x * plane + ((size_t)nu * nao + mu) * naux + P] = (T)(sB * sc_);
         }
       }
     }
@@ -625,15 +625,15 @@ static void launch_int3c(const ShellSet& ao, const ShellSet& aux, const PairList
   RIS_CHECK_LAUNCH();
 }
 
-template <int LA, int LB, int LC>
+template <int LA, int LB, int LC, class T>
 static void launch_int3c_deriv(const ShellSet& ao, const ShellSet& aux, const PairList& pl,
-                               const double* xyz, const double* tab, double* D, cudaStream_t st) {
+                               const double* xyz, const double* tab, T* D, cudaStream_t st) {
   const int cls = LA * (LA + 1) / 2 + LB;
   const int p0 = pl.class_off[cls], np = pl.class_off[cls + 1] - p0;
   const int nax = (int)aux.by_l[LC].size();
   if (np == 0 || nax == 0) return;
   const long long nt = (long long)np * nax;
-  k_int3c_deriv<LA, LB, LC><<<(unsigned)cdiv(nt, 128), 128, 0, st>>>(
+  k_int3c_deriv<LA, LB, LC, T><<<(unsigned)cdiv(nt, 128), 128, 0, st>>>(
       pl.a, pl.b, p0, np, aux.d_by_l[LC], nax, ao.atom, ao.off, ao.ex, ao.nbase, aux.atom,
       aux.off, aux.ex, aux.nbase, xyz, tab, ao.nfun, aux.nfun, D);
   RIS_CHECK_LAUNCH();
@@ -663,8 +663,9 @@ void int3c(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const do
   prof_end(kProfInt3c, st, (double)pl.npair * aux.n);
 }
 
+template <class T>
 void int3c_deriv(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const double* xyz,
-                 double* D, cudaStream_t st) {
+                 T* D, cudaStream_t st) {
   int dev;
   RIS_CUDA(cudaGetDevice(&dev));
   const double* tab = boys_table_device(dev);
@@ -672,6 +673,10 @@ void int3c_deriv(const ShellSet& ao, const ShellSet& aux, const PairList& pl, co
   RIS_FOR_CLASSES(launch_int3c_deriv, ao, aux, pl, xyz, tab, D, st)
   prof_end(kProfInt3cDeriv, st, (double)pl.npair * aux.n);
 }
+template void int3c_deriv<double>(const ShellSet&, const ShellSet&, const PairList&, const double*,
+                                  double*, cudaStream_t);
+template void int3c_deriv<float>(const ShellSet&, const ShellSet&, const PairList&, const double*,
+                                 float*, cudaStream_t);
 
 void int2c(const ShellSet& aux, const double* xyz, double* M, double* dM, cudaStream_t st) {
   int dev;

@@ -47,9 +47,11 @@ void int3c(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const do
            int nJ, int nK, double* TJ, double* TK, cudaStream_t st);
 
 // D[x][mu][nu][P] = d(mu nu|P)/dA_x with A the centre of mu (union auxiliary
-// set, P fastest).  Zeroed by the caller.
+// set, P fastest), computed in FP64 and stored as T (double or float).
+// Zeroed by the caller.
+template <class T>
 void int3c_deriv(const ShellSet& ao, const ShellSet& aux, const PairList& pl,
-                 const double* d_coords, double* D, cudaStream_t st);
+                 const double* d_coords, T* D, cudaStream_t st);
 
 // M[P][Q] = (P|Q) over the union set, and dM[x][P][Q] = d(P|Q)/dP_x.
 void int2c(const ShellSet& aux, const double* d_coords, double* M, double* dM, cudaStream_t st);

@@ -52,9 +52,10 @@ def footprint_bytes(nao: int, nocc: int, nJ: int, nK: int, nU: int, nstates: int
 
     Persistent per-request buffers (3c integrals of both fitting sets, the
     metric and its inverse factors, the transformed B tensors and, in mixed
-    precision, their FP32 hi/lo splits) plus the larger of the Davidson
-    work space and the derivative stage (the derivative integrals
-    d(mu nu|P)/dR, the pair density Gamma and per-state densities).
+    precision, their FP32 hi/lo splits and the tensor-core operands of the
+    (ab|P)_K transform) plus the larger of the Davidson work space and the
+    derivative stage (the derivative integrals d(mu nu|P)/dR, the exchange
+    parts of a batch of pair densities and per-state densities).
     """
     n, o = nao, nocc
     v = n - o
@@ -68,6 +69,8 @@ def footprint_bytes(nao: int, nocc: int, nJ: int, nK: int, nU: int, nstates: int
     if mixed:
         B += f * (2 * o * nK * _ld4(o) + 4 * nK * v * _ld4(v) + 2 * nK * o * _ld4(o)
                   + 2 * n * (_ld4(o) + _ld4(v))) + d * o * o * nK
+        # (ab|P)_K on tensor cores: T^K and H splits, C_v^T split, FP64 G
+        B += f * 2 * _ld4(n) * (nK * n + v * nK + v) + d * v * nK * v
     ns = nstates
     nb0 = min(nov, ns + min(ns, 8))
     maxsp = min(max(nb0 + 2 * ns, 8 * ns), 256, nov)
@@ -75,8 +78,9 @@ def footprint_bytes(nao: int, nocc: int, nJ: int, nK: int, nU: int, nstates: int
     if mixed:
         dav += f * 2 * nb0 * v * _ld4(o)
     s = nstate_deriv
-    deriv = d * (4 * n * n * nU + s * n * n + 4 * s * o * n + 3 * n * nU + n * v + 2 * o * v * nK
-                 + 2 * n * o * nK + nU * nU)
+    nbp = min(s, 8)  # pairs sharing one pass over the derivative integrals
+    deriv = d * (3 * n * n * nU + nbp * (n * n * nK + 3 * n * nK + nU * nU) + s * n * n
+                 + 3 * s * n * nU + 4 * s * o * n + n * v + 2 * o * v * nK + 2 * n * o * nK)
     if mixed:
         deriv += f * 4 * s * (o * _ld4(v) + n * _ld4(2 * o))
     total = aux + B + d * 2 * ns * nov + max(dav, deriv)
