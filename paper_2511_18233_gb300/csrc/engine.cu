@@ -301,24 +301,32 @@ __global__ void k_add_diag(const double* __restrict__ de, const double* __restri
 }
 
 // indices of the k smallest de (ties: smaller index first), one CTA
+// Order-preserving integer key of a double (sign-magnitude to offset binary),
+// so that the selection below compares integers, not FP64 values.
+__device__ __forceinline__ unsigned long long dkey(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// idx[0..k) = indices of the k smallest de (ties by index), one block.
 __global__ void __launch_bounds__(1024) k_lowest(const double* __restrict__ de, int n, int k,
                                                  int* __restrict__ idx) {
-  __shared__ double bv[32];
+  __shared__ unsigned long long bv[32];
   __shared__ int bi[32];
-  __shared__ double lastv;
+  __shared__ unsigned long long lastv;
   __shared__ int lasti;
   if (threadIdx.x == 0) {
-    lastv = -1e308;
+    lastv = 0ull;
     lasti = -1;
   }
   __syncthreads();
   for (int r = 0; r < k; r++) {
-    double best = 1e308;
+    unsigned long long best = ~0ull;
     int besti = 0x7fffffff;
-    const double lv = lastv;
+    const unsigned long long lv = lastv;
     const int li = lasti;
     for (int i = threadIdx.x; i < n; i += 1024) {
-      const double v = de[i];
+      const unsigned long long v = dkey(de[i]);
       const bool after = (v > lv) || (v == lv && i > li);
       if (after && (v < best || (v == best && i < besti))) {
         best = v;
@@ -326,7 +334,7 @@ __global__ void __launch_bounds__(1024) k_lowest(const double* __restrict__ de, 
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, besti, o);
       if (ov < best || (ov == best && oi < besti)) {
         best = ov;
@@ -342,7 +350,7 @@ __global__ void __launch_bounds__(1024) k_lowest(const double* __restrict__ de, 
       best = bv[threadIdx.x];
       besti = bi[threadIdx.x];
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, besti, o);
         if (ov < best || (ov == best && oi < besti)) {
           best = ov;
@@ -468,38 +476,59 @@ __global__ void k_scale_rows(double* __restrict__ X, long long n, int nrow, cons
 // Tnew_i = sum_c P[i][c] T_c are orthonormal.  *nkeep = number kept.
 __global__ void k_cholqr_small(const double* G, int nt, double drop, double* P, int* nkeep,
                                double* work) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* R = work;        // nt x nt upper factor over kept columns
-  int* keep = (int*)(work + nt * nt);
-  int r = 0;
-  for (int j = 0; j < nt; j++) {
-    // R[i][j] for kept i
-    double d = G[j * nt + j];
+  // G, R and P live in shared memory (nt <= 64); one thread runs the
+  // factorisation, the block loads and stores.
+  extern __shared__ double sh[];
+  double* Gs = sh;
+  double* R = Gs + nt * nt;
+  double* Ps = R + nt * nt;
+  int* keep = (int*)(Ps + nt * nt);
+  (void)work;
+  for (int i = threadIdx.x; i < nt * nt; i += blockDim.x) {
+    Gs[i] = G[i];
+    Ps[i] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int r = 0;
+    for (int j = 0; j < nt; j++) {
+      double d = Gs[j * nt + j];
+      for (int q = 0; q < r; q++) {
+        const int i = keep[q];
+        double s = Gs[i * nt + j];
+        for (int q2 = 0; q2 < q; q2++) s -= R[keep[q2] * nt + i] * R[keep[q2] * nt + j];
+        R[i * nt + j] = s / R[i * nt + i];
+        d -= R[i * nt + j] * R[i * nt + j];
+      }
+      if (d > drop * Gs[j * nt + j] && d > 0) {
+        R[j * nt + j] = sqrt(d);
+        keep[r++] = j;
+      }
+    }
+    // P = R^{-T} over the kept indices: Tnew_s = sum_q (R^{-T})_sq T_keep[q];
+    // column q of R^{-T} solves R^T y = e_q (forward substitution).
     for (int q = 0; q < r; q++) {
-      const int i = keep[q];
-      double s = G[i * nt + j];
-      for (int q2 = 0; q2 < q; q2++) s -= R[keep[q2] * nt + i] * R[keep[q2] * nt + j];
-      R[i * nt + j] = s / R[i * nt + i];
-      d -= R[i * nt + j] * R[i * nt + j];
+      double y[64];
+      for (int s = 0; s < r; s++) {
+        double acc = (s == q) ? 1.0 : 0.0;
+        for (int s2 = 0; s2 < s; s2++) acc -= R[keep[s2] * nt + keep[s]] * y[s2];
+        y[s] = acc / R[keep[s] * nt + keep[s]];
+      }
+      for (int s = 0; s < r; s++) Ps[s * nt + keep[q]] = y[s];
     }
-    if (d > drop * G[j * nt + j] && d > 0) {
-      R[j * nt + j] = sqrt(d);
-      keep[r++] = j;
-    }
+    *nkeep = r;
   }
-  // P = R^{-T} over the kept indices: Tnew_s = sum_q (R^{-T})_sq T_keep[q].
-  // Column q of R^{-T} solves R^T y = e_q (forward substitution).
-  for (int i = 0; i < nt * nt; i++) P[i] = 0.0;
-  for (int q = 0; q < r; q++) {
-    double y[64];
-    for (int s = 0; s < r; s++) {
-      double acc = (s == q) ? 1.0 : 0.0;
-      for (int s2 = 0; s2 < s; s2++) acc -= R[keep[s2] * nt + keep[s]] * y[s2];
-      y[s] = acc / R[keep[s] * nt + keep[s]];
-    }
-    for (int s = 0; s < r; s++) P[s * nt + keep[q]] = y[s];
-  }
-  *nkeep = r;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nt * nt; i += blockDim.x) P[i] = Ps[i];
+}
+
+static void cholqr_small(const double* G, int nt, double drop, double* P, int* nkeep,
+                         cudaStream_t st) {
+  RIS_REQUIRE(nt >= 1 && nt <= 64, RIS_ERR_ARG, "cholqr_small: block of 1..64 vectors");
+  const size_t smem = 3 * (size_t)nt * nt * sizeof(double) + nt * sizeof(int) + 16;
+  ensure_smem_attr((const void*)k_cholqr_small, (int)(3 * 64 * 64 * sizeof(double) + 64 * sizeof(int) + 16));
+  k_cholqr_small<<<1, 32, smem, st>>>(G, nt, drop, P, nkeep, nullptr);
+  RIS_CHECK_LAUNCH();
 }
 
 __global__ void k_diag_set(double* __restrict__ H, int ld, int m, const double* __restrict__ w) {
@@ -1481,8 +1510,7 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
       k_scale_rows<<<cdiv(n * m, 256), 256, 0, st>>>(V.p, n, m, G0.p);
       RIS_CHECK_LAUNCH();
       dgemm(false, true, m, m, (int)n, 1.0, V.p, (int)n, V.p, (int)n, 0.0, G0.p, m, st);
-      k_cholqr_small<<<1, 32, 0, st>>>(G0.p, m, 1e-10, P0.p, (int*)(P0.p + m * m), W0.p);
-      RIS_CHECK_LAUNCH();
+      cholqr_small(G0.p, m, 1e-10, P0.p, (int*)(P0.p + m * m), st);
       int nk2 = 0;
       RIS_CUDA(cudaMemcpyAsync(&nk2, P0.p + m * m, sizeof(int), cudaMemcpyDeviceToHost, st));
       RIS_CUDA(cudaStreamSynchronize(st));
@@ -1548,8 +1576,7 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
       k_scale_rows<<<cdiv(n * nt, 256), 256, 0, st>>>(T.p, n, nt, G.p);
       RIS_CHECK_LAUNCH();
       dgemm(false, true, nt, nt, (int)n, 1.0, T.p, (int)n, T.p, (int)n, 0.0, G.p, nt, st);
-      k_cholqr_small<<<1, 32, 0, st>>>(G.p, nt, drop, Pm.p, (int*)(Pm.p + nt * nt), Cc.p);
-      RIS_CHECK_LAUNCH();
+      cholqr_small(G.p, nt, drop, Pm.p, (int*)(Pm.p + nt * nt), st);
       RIS_CUDA(cudaMemcpyAsync(&nkeep, Pm.p + nt * nt, sizeof(int), cudaMemcpyDeviceToHost, st));
       RIS_CUDA(cudaStreamSynchronize(st));
       if (nkeep == 0) break;
@@ -1676,8 +1703,7 @@ void Engine::davidson_rpa(int ns) {
       k_scale_rows<<<cdiv(n * nt, 256), 256, 0, st>>>(T.p, n, nt, G.p);
       RIS_CHECK_LAUNCH();
       dgemm(false, true, nt, nt, (int)n, 1.0, T.p, (int)n, T.p, (int)n, 0.0, G.p, nt, st);
-      k_cholqr_small<<<1, 32, 0, st>>>(G.p, nt, 1e-10, Pm.p, (int*)(Pm.p + nt * nt), Cc.p);
-      RIS_CHECK_LAUNCH();
+      cholqr_small(G.p, nt, 1e-10, Pm.p, (int*)(Pm.p + nt * nt), st);
       RIS_CUDA(cudaMemcpyAsync(&nkeep, Pm.p + nt * nt, sizeof(int), cudaMemcpyDeviceToHost, st));
       RIS_CUDA(cudaStreamSynchronize(st));
       if (nkeep == 0) break;

@@ -261,40 +261,48 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   __syncthreads();
   const bool good = *abort_flag == 0 && nk > 0;
   if (!good && threadIdx.x == 0 && nk > 0) atomicExch(args.err, 1);
-  const int row = m0 + warp * 32 + lane;
+  // Each warp owns 32 accumulator rows; a 32 x 32 block is read from TMEM
+  // (one row per lane), transposed through shared memory (the pipeline
+  // stages are idle now) and stored row by row with the lanes on consecutive
+  // columns, so that every store instruction is coalesced.
   const TcEpilogue& ep = args.ep;
+  float* tile = (float*)smem + warp * (32 * 33);
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
     float v[32];
     tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    if (!good || row >= args.M) continue;
-    if (args.partial) {
-      float* dst = args.partial + ((size_t)ks * args.M + row) * args.N;
 #pragma unroll
-      for (int j = 0; j < 32; j++)
-        if (n0 + c0 + j < args.N) dst[n0 + c0 + j] = v[j];
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; j++) {
-        const int col = n0 + c0 + j;
-        if (col >= args.N) continue;
-        const long long cpos = ep.cin > 0 ? (long long)(col / ep.cin) * ep.cld + col % ep.cin : col;
+    for (int j = 0; j < 32; j++) tile[lane * 33 + j] = v[j];
+    __syncwarp();
+    const int col = n0 + c0 + lane;
+    if (good && col < args.N) {
+      const long long cpos = ep.cin > 0 ? (long long)(col / ep.cin) * ep.cld + col % ep.cin : col;
+#pragma unroll 4
+      for (int r = 0; r < 32; r++) {
+        const int row = m0 + warp * 32 + r;
+        if (row >= args.M) break;
+        const float x = tile[r * 33 + lane];
+        if (args.partial) {
+          args.partial[((size_t)ks * args.M + row) * args.N + col] = x;
+          continue;
+        }
         const size_t off = (size_t)z * ep.bsc + (size_t)row * ep.rs + (size_t)cpos * ep.cs;
         if (ep.mode == kOutF64) {
           double* p = ep.c64 + off;
-          *p = ep.beta == 0.0 ? ep.alpha * v[j] : fma(ep.alpha, (double)v[j], ep.beta * *p);
+          *p = ep.beta == 0.0 ? ep.alpha * x : fma(ep.alpha, (double)x, ep.beta * *p);
         } else if (ep.mode == kOutF32) {
           float* p = ep.c32 + off;
           const float a = (float)ep.alpha, b = (float)ep.beta;
-          *p = b == 0.f ? a * v[j] : fmaf(a, v[j], b * *p);
+          *p = b == 0.f ? a * x : fmaf(a, x, b * *p);
         } else {
-          const float x = (float)ep.alpha * v[j];
-          const float h = to_tf32(x);
+          const float y = (float)ep.alpha * x;
+          const float h = to_tf32(y);
           ep.chi[off] = h;
-          ep.clo[off] = to_tf32(x - h);
+          ep.clo[off] = to_tf32(y - h);
         }
       }
     }
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

@@ -297,8 +297,59 @@ __global__ void __launch_bounds__(1024) k_cholesky(double* A, int n, int* info) 
   if (tid == 0) *info = bad;
 }
 
+// Shared-memory form for n <= kSmemChol: right-looking, the trailing update
+// spread over the block; the same relative pivot test as k_cholesky.
+constexpr int kSmemChol = 160;
+__global__ void __launch_bounds__(1024) k_cholesky_smem(double* A, int n, int* info) {
+  extern __shared__ double S[];
+  double* diag0 = S + (size_t)n * n;
+  __shared__ double piv;
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  for (size_t e = tid; e < (size_t)n * n; e += 1024) S[e] = A[e];
+  for (int j = tid; j < n; j += 1024) diag0[j] = A[(size_t)j * n + j];
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; j++) {
+    if (tid == 0) {
+      const double d = S[(size_t)j * n + j];
+      if (!(d > 1e-13 * diag0[j])) {
+        bad = j + 1;
+      } else {
+        piv = sqrt(d);
+        S[(size_t)j * n + j] = piv;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double pj = piv;
+    for (int i = j + 1 + tid; i < n; i += 1024) S[(size_t)i * n + j] /= pj;
+    __syncthreads();
+    // trailing lower triangle: S[i][k] -= S[i][j] S[k][j], j < k <= i
+    const int m = n - j - 1;
+    for (long long t = tid; t < (long long)m * m; t += 1024) {
+      const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
+      if (k <= i) S[(size_t)i * n + k] -= S[(size_t)i * n + j] * S[(size_t)k * n + j];
+    }
+    __syncthreads();
+  }
+  if (!bad) {
+    for (size_t e = tid; e < (size_t)n * n; e += 1024) {
+      const int i = (int)(e / n), k = (int)(e % n);
+      A[e] = k > i ? 0.0 : S[e];
+    }
+  }
+  if (tid == 0) *info = bad;
+}
+
 void cholesky(double* A, int n, int* d_info, cudaStream_t st) {
-  k_cholesky<<<1, 1024, 0, st>>>(A, n, d_info);
+  if (n <= kSmemChol) {
+    const size_t smem = ((size_t)n * n + n) * sizeof(double);
+    ensure_smem_attr((const void*)k_cholesky_smem, (int)(((size_t)kSmemChol * kSmemChol + kSmemChol) * sizeof(double)));
+    k_cholesky_smem<<<1, 1024, smem, st>>>(A, n, d_info);
+  } else {
+    k_cholesky<<<1, 1024, 0, st>>>(A, n, d_info);
+  }
   RIS_CHECK_LAUNCH();
 }
 
@@ -314,8 +365,42 @@ __global__ void k_tri_inverse(const double* __restrict__ L, double* __restrict__
   }
 }
 
+// Shared-memory form for n <= kSmemChol: L staged once, one thread per
+// column j of X = L^-1.  Thread j keeps X[k][j] (k > j) in the upper
+// triangle of its own row of the staged copy (Ls[j][k], zero in L), which no
+// other thread reads; two partial sums shorten the dependent chain.
+__global__ void __launch_bounds__(kSmemChol) k_tri_inverse_smem(const double* __restrict__ L,
+                                                                double* __restrict__ X, int n) {
+  extern __shared__ double Ls[];
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) Ls[e] = L[e];
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j >= n) return;
+  for (int i = 0; i < j; i++) X[(size_t)i * n + j] = 0.0;
+  const double xj = 1.0 / Ls[(size_t)j * n + j];
+  X[(size_t)j * n + j] = xj;
+  for (int i = j + 1; i < n; i++) {
+    double a0 = Ls[(size_t)i * n + j] * xj, a1 = 0.0;
+    int k = j + 1;
+    for (; k + 1 < i; k += 2) {
+      a0 += Ls[(size_t)i * n + k] * Ls[(size_t)j * n + k];
+      a1 += Ls[(size_t)i * n + k + 1] * Ls[(size_t)j * n + k + 1];
+    }
+    if (k < i) a0 += Ls[(size_t)i * n + k] * Ls[(size_t)j * n + k];
+    const double v = -(a0 + a1) / Ls[(size_t)i * n + i];
+    Ls[(size_t)j * n + i] = v;
+    X[(size_t)i * n + j] = v;
+  }
+}
+
 void tri_inverse(const double* L, double* Linv, int n, cudaStream_t st) {
-  k_tri_inverse<<<cdiv(n, 32), 32, 0, st>>>(L, Linv, n);
+  if (n <= kSmemChol) {
+    const size_t smem = (size_t)n * n * sizeof(double);
+    ensure_smem_attr((const void*)k_tri_inverse_smem, (int)((size_t)kSmemChol * kSmemChol * sizeof(double)));
+    k_tri_inverse_smem<<<1, kSmemChol, smem, st>>>(L, Linv, n);
+  } else {
+    k_tri_inverse<<<cdiv(n, 32), 32, 0, st>>>(L, Linv, n);
+  }
   RIS_CHECK_LAUNCH();
 }
 
