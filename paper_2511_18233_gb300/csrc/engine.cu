@@ -1203,33 +1203,45 @@ void Engine::gamma_K_mixed(const float* USh, const float* USl, const float* VSh,
                            double f, double* Gam, float* Gam32, double* Om) {
   const int o = nocc, v = nvir, nn = nao;
   const int lv4 = ld4(v), lo4 = ld4(o), kp = ld4(2 * o);
-  // Z[j][P][b] = sum_a U[j][a] c^vv[P][b][a]
-  SBuf<float> ZH((size_t)o * nK * lv4, st, true), ZL((size_t)o * nK * lv4, st, true);
+  // Z[P][j][b] = sum_a U[j][a] c^vv[P][b][a]   (one GEMM, columns (P, b))
+  SBuf<float> ZH((size_t)nK * o * lv4, st, true), ZL((size_t)nK * o * lv4, st, true);
   {
-    TcEpilogue e = ep_split(ZH.p, ZL.p, (long long)nK * lv4);
+    TcEpilogue e = ep_split(ZH.p, ZL.p, lv4);
     e.cin = v;
-    e.cld = lv4;
+    e.cld = (long long)o * lv4;
     tcg(o, nK * v, v, USh, USl, lv4, cvvH.p, cvvL.p, lv4, 0, 1, e, d_tcerr, st);
   }
-  // G[P][k][j] = sum_b V[k][b] Z[j][P][b]   (batch j)
+  // G[P][k][j] = sum_b V[k][b] Z[P][j][b]   (batch P, coalesced rows)
   SBuf<float> GH((size_t)nK * o * lo4, st, true), GL((size_t)nK * o * lo4, st, true);
-  tcg(o, nK, lv4, VSh, VSl, lv4, ZH.p, ZL.p, lv4, (long long)nK * lv4, o,
-      ep_split(GH.p, GL.p, lo4, (long long)o * lo4, 1), d_tcerr, st);
+  tcg(o, o, v, VSh, VSl, lv4, ZH.p, ZL.p, lv4, (long long)o * lv4, nK,
+      ep_split(GH.p, GL.p, lo4, 1, (long long)o * lo4), d_tcerr, st);
   // M1[mu][P][k'] : k' < o  sum_i Q_U[i][mu] c^oo[P][i][k]
-  //                 k' >= o sum_j C_o[mu][j] G[P][k][j]          (batch P)
+  //                 k' >= o sum_j C_o[mu][j] G[P][k][j]
+  // each one GEMM over the columns (P, k)
   SBuf<float> MH((size_t)nn * nK * kp, st, true), ML((size_t)nn * nK * kp, st, true);
-  tcg(nn, o, o, WUh, WUl, kp, cooH.p, cooL.p, lo4, (long long)o * lo4, nK,
-      ep_split(MH.p, ML.p, (long long)nK * kp, 1, kp), d_tcerr, st);
-  tcg(nn, o, o, CoH.p, CoL.p, lo4, GH.p, GL.p, lo4, (long long)o * lo4, nK,
-      ep_split(MH.p + o, ML.p + o, (long long)nK * kp, 1, kp), d_tcerr, st);
-  // Gamma[mu][nu][P] += f sum_k' W_V[nu][k'] M1[mu][P][k']   (batch mu)
-  if (Gam32) {
-    TcEpilogue e;
-    e.mode = kOutF32; e.c32 = Gam32; e.rs = nK; e.bsc = (long long)nn * nK; e.alpha = f; e.beta = 1.0;
-    tcg(nn, nK, 2 * o, WVh, WVl, kp, MH.p, ML.p, kp, (long long)nK * kp, nn, e, d_tcerr, st);
-  } else {
-    tcg(nn, nK, 2 * o, WVh, WVl, kp, MH.p, ML.p, kp, (long long)nK * kp, nn,
-        ep_f64(Gam, nK, (long long)nn * nK, f, 1.0), d_tcerr, st);
+  {
+    TcEpilogue e = ep_split(MH.p, ML.p, (long long)nK * kp);
+    e.cin = o;
+    e.cld = kp;
+    tcg(nn, nK * o, o, WUh, WUl, kp, cooH.p, cooL.p, lo4, 0, 1, e, d_tcerr, st);
+    e.chi = MH.p + o;
+    e.clo = ML.p + o;
+    tcg(nn, nK * o, o, CoH.p, CoL.p, lo4, GH.p, GL.p, lo4, 0, 1, e, d_tcerr, st);
+  }
+  // Gamma[mu][nu][P] += f sum_k' W_V[nu][k'] M1[mu][P][k']: one GEMM, rows nu,
+  // columns (mu, P)
+  {
+    TcEpilogue e = Gam32 ? TcEpilogue() : ep_f64(Gam, nK, 0, f, 1.0);
+    if (Gam32) {
+      e.mode = kOutF32;
+      e.c32 = Gam32;
+      e.alpha = f;
+      e.beta = 1.0;
+    }
+    e.rs = nK;
+    e.cin = nK;
+    e.cld = (long long)nn * nK;
+    tcg(nn, nn * nK, 2 * o, WVh, WVl, kp, MH.p, ML.p, kp, 0, 1, e, d_tcerr, st);
   }
   // Omega[A][B] += f sum_{k,j} c^oo[A][k][j] G[B][k][j]
   tcg(nK, nK, o * lo4, cooH.p, cooL.p, o * lo4, GH.p, GL.p, o * lo4, 0, 1, ep_f64(Om, nU, 0, f, 1.0),
