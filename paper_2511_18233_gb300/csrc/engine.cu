@@ -1232,11 +1232,11 @@ void Engine::gamma_K_mixed(const float* USh, const float* USl, const float* VSh,
   // columns (mu, P)
   {
     TcEpilogue e = Gam32 ? TcEpilogue() : ep_f64(Gam, nK, 0, f, 1.0);
-    if (Gam32) {
+    if (Gam32) {  // sole writer of the FP32 G^K: plain stores, no read-modify-write
       e.mode = kOutF32;
       e.c32 = Gam32;
       e.alpha = f;
-      e.beta = 1.0;
+      e.beta = 0.0;
     }
     e.rs = nK;
     e.cin = nK;
@@ -2026,10 +2026,8 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
   const double cx = opt.cx;
   for (int g0 = 0; g0 < npair; g0 += NB) {
     const int nb = std::min(NB, npair - g0);
-    if (gk32)
-      RIS_CUDA(cudaMemsetAsync(GK32.p, 0, sizeof(float) * nb * gk, st));
-    else
-      RIS_CUDA(cudaMemsetAsync(GK.p, 0, sizeof(double) * nb * gk, st));
+    // (in mixed TDA the single exchange GEMM writes every element of G^K)
+    if (!gk32) RIS_CUDA(cudaMemsetAsync(GK.p, 0, sizeof(double) * nb * gk, st));
     RIS_CUDA(cudaMemsetAsync(OmB.p, 0, sizeof(double) * nb * nU * nU, st));
     std::vector<int> h_pst(2 * nb);
     for (int b = 0; b < nb; b++) {

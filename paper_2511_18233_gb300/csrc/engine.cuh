@@ -150,7 +150,8 @@ struct Engine : StreamOwner {
   void build_Kvv_tc(double* out);
   // exchange part of Gamma / Omega for one (U,V) pair with weight f (3xTF32);
   // US/VS: splits of U, V [i][a]; WU/WV: [Q^T | C_o] splits of U and V;
-  // Gamma accumulated in FP64 (Gam) or, when Gam32 is given, in FP32
+  // Gamma accumulated in FP64 (Gam) or, when Gam32 is given, written in FP32
+  // (overwritten: the caller's only exchange term)
   void gamma_K_mixed(const float* USh, const float* USl, const float* VSh, const float* VSl,
                      const float* WUh, const float* WUl, const float* WVh, const float* WVl,
                      double f, double* Gam, float* Gam32, double* Om);

@@ -409,13 +409,27 @@ constexpr int kEigT = 512;
 
 size_t eig_work_size(int m) { return (size_t)m * m + 3 * (size_t)m + 64 + 64 * (size_t)m; }
 
-__device__ int sturm_count(const double* d, const double* e, int m, double x) {
+// 1/q from the FP32 reciprocal refined by two Newton steps in FP64 (relative
+// error ~1e-15), far cheaper than an FP64 division on this part; q outside the
+// FP32 range takes the division.
+__device__ __forceinline__ double rcp64(double q) {
+  const double aq = fabs(q);
+  if (!(aq > 1e-30 && aq < 1e30)) return 1.0 / q;
+  double r = (double)__frcp_rn((float)q);
+  r = r * fma(-q, r, 2.0);
+  r = r * fma(-q, r, 2.0);
+  return r;
+}
+
+// Number of eigenvalues of the tridiagonal (d, e) below x: negative pivots of
+// the LDL^T factorisation of T - x I.  e2 holds e[i]^2.
+__device__ int sturm_count(const double* d, const double* e2, int m, double x) {
   int c = 0;
   double q = d[0] - x;
   if (q < 0) c++;
   for (int i = 1; i < m; i++) {
     if (q == 0.0) q = -1e-300;
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    q = d[i] - x - e2[i - 1] * rcp64(q);
     if (q < 0) c++;
   }
   return c;
@@ -533,8 +547,9 @@ constexpr int kSectLanes = 8;  // Sturm counts per multisection step
 // counts (kSectLanes points per step shrink the bracket 9-fold), the
 // eigenvector of T by inverse iteration (Gaussian elimination with partial
 // pivoting of T - lambda_j I, three solves), and its back-transformation
-// x = H_0 ... H_{m-3} z.
-__global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work) {
+// x = H_0 ... H_{m-3} z.  Householder vectors in shared memory when
+// a_smem is set (m x m doubles).
+__global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work, int a_smem) {
   extern __shared__ double sm[];
   __shared__ double red[33];
   __shared__ double sh_lo, sh_hi;
@@ -543,16 +558,22 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work) {
   const int tid = threadIdx.x;
   double* d = sm;
   double* e = d + m;
-  double* z = e + m;
+  double* e2 = e + m;
+  double* z = e2 + m;
   double* dl = z + m;
   double* dd = dl + m;
   double* du = dd + m;
   double* du2 = du + m;
   double* piv = du2 + m;
+  double* As = piv + m;
   for (int i = tid; i < m; i += kEigVecT) {
     d[i] = W.d[i];
     e[i] = W.e[i];
+    e2[i] = W.e[i] * W.e[i];
   }
+  if (a_smem)
+    for (size_t t = tid; t < (size_t)m * m; t += kEigVecT) As[t] = W.A[t];
+  const double* A = a_smem ? As : W.A;
   __syncthreads();
   double glo = 0.0, ghi = 0.0;
   tri_bounds(d, e, m, glo, ghi);
@@ -566,7 +587,7 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work) {
       bool above = false;
       if (lane < kSectLanes) {
         const double x = lo + h * (lane + 1);
-        above = sturm_count(d, e, m, x) > j;  // lambda_j < x
+        above = sturm_count(d, e2, m, x) > j;  // lambda_j < x
       }
       const unsigned mask = __ballot_sync(0xffffffffu, above) & ((1u << kSectLanes) - 1u);
       const int f = mask ? __ffs(mask) - 1 : kSectLanes;  // first point above lambda_j
@@ -594,11 +615,11 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work) {
     for (int i = 0; i + 1 < m; i++) {
       if (fabs(dd[i]) >= fabs(dl[i])) {
         if (dd[i] == 0.0) dd[i] = tiny;
-        const double f = dl[i] / dd[i];
+        const double f = dl[i] * rcp64(dd[i]);
         dl[i] = f;
         dd[i + 1] -= f * du[i];
       } else {
-        const double f = dd[i] / dl[i];
+        const double f = dd[i] * rcp64(dl[i]);
         dd[i] = dl[i];
         dl[i] = f;
         const double tmp = du[i];
@@ -612,6 +633,7 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work) {
       }
     }
     if (dd[m - 1] == 0.0) dd[m - 1] = tiny;
+    for (int i = 0; i < m; i++) dd[i] = rcp64(dd[i]);  // pivots kept as reciprocals
     for (int i = 0; i < m; i++) z[i] = 1.0 + 0.01 * (double)(i % 7);
     for (int it = 0; it < 3; it++) {
       for (int i = 0; i + 1 < m; i++) {
@@ -623,9 +645,9 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work) {
           z[i + 1] = t0 - dl[i] * z[i];
         }
       }
-      z[m - 1] /= dd[m - 1];
-      if (m >= 2) z[m - 2] = (z[m - 2] - du[m - 2] * z[m - 1]) / dd[m - 2];
-      for (int i = m - 3; i >= 0; i--) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / dd[i];
+      z[m - 1] *= dd[m - 1];
+      if (m >= 2) z[m - 2] = (z[m - 2] - du[m - 2] * z[m - 1]) * dd[m - 2];
+      for (int i = m - 3; i >= 0; i--) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) * dd[i];
       double nrm = 0.0;
       for (int i = 0; i < m; i++) nrm += z[i] * z[i];
       nrm = 1.0 / sqrt(nrm);
@@ -639,9 +661,9 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work) {
     const double t = W.tau[c];
     if (t == 0.0) continue;
     double part = 0.0;
-    for (int i = c + 1 + tid; i < m; i += kEigVecT) part += W.A[(size_t)i * m + c] * z[i];
+    for (int i = c + 1 + tid; i < m; i += kEigVecT) part += A[(size_t)i * m + c] * z[i];
     const double f = t * block_sum<kEigVecT>(part, red);
-    for (int i = c + 1 + tid; i < m; i += kEigVecT) z[i] -= f * W.A[(size_t)i * m + c];
+    for (int i = c + 1 + tid; i < m; i += kEigVecT) z[i] -= f * A[(size_t)i * m + c];
     __syncthreads();
   }
   for (int i = tid; i < m; i += kEigVecT) W.Z[(size_t)j * m + i] = z[i];
@@ -685,13 +707,15 @@ void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V
   ensure_smem_attr((const void*)k_eig_tridiag, (int)smem_max);
   const size_t need = (size_t)m * m * sizeof(double);
   const int use_smem = need <= smem_max;
-  const size_t vec_smem = 8 * (size_t)m * sizeof(double);
+  size_t vec_smem = 9 * (size_t)m * sizeof(double);
   RIS_REQUIRE(vec_smem <= 200 * 1024, RIS_ERR_ARG, "sym_eig_lowest: subspace too large");
-  if (vec_smem > 48 * 1024) ensure_smem_attr((const void*)k_eig_vec, (int)(200 * 1024));
+  const int a_smem = vec_smem + need <= 200 * 1024;
+  if (a_smem) vec_smem += need;
+  ensure_smem_attr((const void*)k_eig_vec, (int)(200 * 1024));
   prof_begin(kProfEig, st);
   k_eig_tridiag<<<1, kEigT, use_smem ? need : 0, st>>>(H, ldH, m, work, use_smem);
   RIS_CHECK_LAUNCH();
-  k_eig_vec<<<k, kEigVecT, vec_smem, st>>>(m, work);
+  k_eig_vec<<<k, kEigVecT, vec_smem, st>>>(m, work, a_smem);
   RIS_CHECK_LAUNCH();
   k_eig_finish<<<1, kEigT, 0, st>>>(m, k, w, V, work);
   RIS_CHECK_LAUNCH();
