@@ -243,7 +243,7 @@ __global__ void k_transpose_last2(const double* __restrict__ in, int nb, int na,
                                   double* __restrict__ out) {
   __shared__ double tile[32][33];
   const int b = blockIdx.z;
-  const int a0 = blockIdx.y * 32, r0 = blockIdx.x * 32;
+  const int a0 = blockIdx.x * 32, r0 = blockIdx.y * 32;  // the long index on grid.x
   const double* src = in + (size_t)b * na * nr;
   double* dst = out + (size_t)b * na * nr;
   for (int k = threadIdx.y; k < 32; k += 8) {
@@ -257,7 +257,8 @@ __global__ void k_transpose_last2(const double* __restrict__ in, int nb, int na,
   }
 }
 static void transpose_last2(const double* in, int nb, int na, int nr, double* out, cudaStream_t st) {
-  dim3 g(cdiv(nr, 32), cdiv(na, 32), nb);
+  RIS_REQUIRE(cdiv(nr, 32) <= 65535 && nb <= 65535, RIS_ERR_ARG, "transpose: shape too large");
+  dim3 g(cdiv(na, 32), cdiv(nr, 32), nb);
   k_transpose_last2<<<g, dim3(32, 8), 0, st>>>(in, nb, na, nr, out);
   RIS_CHECK_LAUNCH();
 }

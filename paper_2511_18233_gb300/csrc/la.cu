@@ -60,7 +60,9 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
   __shared__ double Bs[kBK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % THX, ty = tid / THX;
-  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  // tiles linearised on grid.x (column tiles fastest): no 65535 limit on rows
+  const int ntn = (n + BN - 1) / BN;
+  const int row0 = (int)(blockIdx.x / ntn) * BM, col0 = (int)(blockIdx.x % ntn) * BN;
   double acc[TM][TN];
 #pragma unroll
   for (int r = 0; r < TM; r++)
@@ -216,7 +218,9 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
   double* ws = nullptr;
   MemTrack* ws_tr = nullptr;
   if (ksplit > 1) ws = (double*)dev_alloc(sizeof(double) * (size_t)ksplit * m * n, st, &ws_tr);
-  dim3 grid(cdiv(n, sh.bn()), cdiv(m, sh.bm()), ksplit > 1 ? ksplit : nb);
+  const long long ntiles = (long long)cdiv(n, sh.bn()) * cdiv(m, sh.bm());
+  RIS_REQUIRE(ntiles < (1LL << 31), RIS_ERR_ARG, "dgemm: too many tiles");
+  dim3 grid((unsigned)ntiles, 1, ksplit > 1 ? ksplit : nb);
   double* Cout = ksplit > 1 ? ws : C;
   prof_begin(kProfGemm, st);
   if (!transA && !transB)
@@ -421,6 +425,21 @@ __device__ __forceinline__ double rcp64(double q) {
   return r;
 }
 
+// FP32 Sturm count (for the coarse bracket only): exact for T + dT with
+// |dT| of a few FP32 ulps of ||T||, i.e. correct for every x farther than
+// ~1e-6 ||T|| from an eigenvalue.
+__device__ int sturm_count_f(const float* d, const float* e2, int m, float x) {
+  int c = 0;
+  float q = d[0] - x;
+  if (q < 0.f) c++;
+  for (int i = 1; i < m; i++) {
+    if (q == 0.f) q = -1e-30f;
+    q = d[i] - x - __fdividef(e2[i - 1], q);
+    if (q < 0.f) c++;
+  }
+  return c;
+}
+
 // Number of eigenvalues of the tridiagonal (d, e) below x: negative pivots of
 // the LDL^T factorisation of T - x I.  e2 holds e[i]^2.
 __device__ int sturm_count(const double* d, const double* e2, int m, double x) {
@@ -540,11 +559,12 @@ __global__ void __launch_bounds__(kEigT) k_eig_tridiag(const double* H, int ldH,
 }
 
 constexpr int kEigVecT = 128;
-constexpr int kSectLanes = 8;  // Sturm counts per multisection step
 
 // Stage 2 (one CTA per wanted eigenvalue j, so that the FP64 work of the
 // eigenvalues runs on as many SMs): lambda_j by multisection on Sturm
-// counts (kSectLanes points per step shrink the bracket 9-fold), the
+// counts, 32 points per step (33-fold shrink): FP32 counts down to a
+// bracket of 1e-5 ||T||, widened by 1e-5 ||T|| on each side (over 100 times
+// the FP32 count error), then FP64 counts to full precision; the
 // eigenvector of T by inverse iteration (Gaussian elimination with partial
 // pivoting of T - lambda_j I, three solves), and its back-transformation
 // x = H_0 ... H_{m-3} z.  Householder vectors in shared memory when
@@ -565,11 +585,15 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work, int a
   double* du = dd + m;
   double* du2 = du + m;
   double* piv = du2 + m;
-  double* As = piv + m;
+  float* df = (float*)(piv + m);
+  float* e2f = df + m;
+  double* As = piv + m + m;  // after the two float arrays (m doubles)
   for (int i = tid; i < m; i += kEigVecT) {
     d[i] = W.d[i];
     e[i] = W.e[i];
     e2[i] = W.e[i] * W.e[i];
+    df[i] = (float)W.d[i];
+    e2f[i] = (float)(W.e[i] * W.e[i]);
   }
   if (a_smem)
     for (size_t t = tid; t < (size_t)m * m; t += kEigVecT) As[t] = W.A[t];
@@ -581,18 +605,31 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work, int a
   if (tid < 32) {
     const int lane = tid;
     double lo = glo - 1e-12 * tnorm, hi = ghi + 1e-12 * tnorm;
-    for (int it = 0; it < 80; it++) {
-      const double h = (hi - lo) / (kSectLanes + 1);
-      if (!(h > 0.0) || lo + h <= lo) break;
-      bool above = false;
-      if (lane < kSectLanes) {
-        const double x = lo + h * (lane + 1);
-        above = sturm_count(d, e2, m, x) > j;  // lambda_j < x
-      }
-      const unsigned mask = __ballot_sync(0xffffffffu, above) & ((1u << kSectLanes) - 1u);
-      const int f = mask ? __ffs(mask) - 1 : kSectLanes;  // first point above lambda_j
+    // coarse: FP32 counts while the bracket is wider than 1e-5 ||T||
+    const double coarse = 1e-5 * tnorm;
+    for (int it = 0; it < 12 && hi - lo > coarse; it++) {
+      const double h = (hi - lo) / 33.0;
+      const float x = (float)(lo + h * (lane + 1));
+      const bool above = sturm_count_f(df, e2f, m, x) > j;
+      const unsigned mask = __ballot_sync(0xffffffffu, above);
+      const int f = mask ? __ffs(mask) - 1 : 32;
       const double nlo = f == 0 ? lo : lo + h * f;
-      const double nhi = f == kSectLanes ? hi : lo + h * (f + 1);
+      const double nhi = f == 32 ? hi : lo + h * (f + 1);
+      lo = nlo;
+      hi = nhi;
+    }
+    lo = fmax(lo - coarse, glo - 1e-12 * tnorm);
+    hi = fmin(hi + coarse, ghi + 1e-12 * tnorm);
+    // fine: FP64 counts (the counts that decide the final bracket)
+    for (int it = 0; it < 40; it++) {
+      const double h = (hi - lo) / 33.0;
+      if (!(h > 0.0) || lo + h <= lo) break;
+      const double x = lo + h * (lane + 1);
+      const bool above = sturm_count(d, e2, m, x) > j;  // lambda_j < x
+      const unsigned mask = __ballot_sync(0xffffffffu, above);
+      const int f = mask ? __ffs(mask) - 1 : 32;  // first point above lambda_j
+      const double nlo = f == 0 ? lo : lo + h * f;
+      const double nhi = f == 32 ? hi : lo + h * (f + 1);
       lo = nlo;
       hi = nhi;
     }
@@ -707,7 +744,7 @@ void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V
   ensure_smem_attr((const void*)k_eig_tridiag, (int)smem_max);
   const size_t need = (size_t)m * m * sizeof(double);
   const int use_smem = need <= smem_max;
-  size_t vec_smem = 9 * (size_t)m * sizeof(double);
+  size_t vec_smem = 10 * (size_t)m * sizeof(double);
   RIS_REQUIRE(vec_smem <= 200 * 1024, RIS_ERR_ARG, "sym_eig_lowest: subspace too large");
   const int a_smem = vec_smem + need <= 200 * 1024;
   if (a_smem) vec_smem += need;

@@ -367,6 +367,15 @@ def workload(idx: int, with_mo: bool = True) -> Molecule:
     raise ValueError(idx)
 
 
+def packed_cutdown(ncopy: int = 2, with_mo: bool = True) -> Molecule:
+    """The first ncopy chains of the packed 12 x C20H22 workload (same seeds and
+    placement draws, so the chains coincide with the first ncopy there)."""
+    seed = 1001 + 3
+    rng = np.random.default_rng(seed + 1_000_000)
+    el, xyz = packed_chains(ncopy, 20, 40.0, 3.0, rng)
+    return make_molecule(f"{ncopy}xC20H22", el, xyz, seed, True, with_mo)
+
+
 # Overlap-eigenvalue cutoff of the serving molecules' MOs.  Their C stays fixed
 # along a trajectory while the geometry moves by 0.05 A per component; with
 # Loewdin MOs over the near-dependent combinations of this basis C^T S C then
