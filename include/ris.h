@@ -154,6 +154,22 @@ ris_status ris_excite_guess(ris_ctx* ctx, int nstates, const double* X_guess, do
                             double* X, double* Y);
 
 /*
+ * The ris-approximated Z-vector solve: (A + B) Z = rhs (Eq. Z_vector, with
+ * the ris kernel of Eq. ris in A + B — the solver of the section "Ris
+ * approximation for Z-vector Solver"), for nrhs <= 64 right-hand sides at
+ * once.  rhs, Z: [nrhs][nocc][nvir] (host or device).  Preconditioned
+ * conjugate gradients (A + B is symmetric positive definite for a stable
+ * ground state); preconditioner: orbital-energy differences plus the exact
+ * Coulomb part 4 B^J B^J^T (Woodbury).  Converged when every residual
+ * satisfies |rhs - (A+B) Z| <= tol |rhs| with tol = conv_tol (RIS_FP64) or
+ * max(conv_tol, mixed_tol) (RIS_MIXED, 3xTF32 (ij|ab) products); otherwise
+ * RIS_ERR_NOT_CONVERGED after max_iter iterations.  Stats [4] products, [5]
+ * iterations, [7] largest relative residual.  Works for TDA and RPA contexts
+ * (the (ib|P) block is built on first use).
+ */
+ris_status ris_zvector(ris_ctx* ctx, int nrhs, const double* rhs, double* Z);
+
+/*
  * The response operator applied to nvec vectors (the Davidson product of
  * Eqs. (A_matrix)/(B_matrix) with the ris kernel): TDA: out = A X; RPA
  * (rpa option set): out = (A+B) X followed by out2 = (A-B) X.
@@ -189,9 +205,10 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
 
 /*
  * Statistics, copied into out[0..n-1] (n <= 32):
- *   [0] aux, [1] B, [2] excite, [3] gradient/nac: milliseconds of the last
- *       call of each kind (CUDA events on the context's stream);
- *   [4] A-products and [5] Davidson iterations of the last excite,
+ *   [0] aux, [1] B, [2] excite (or Z-vector), [3] gradient/nac: milliseconds
+ *       of the last call of each kind (CUDA events on the context's stream);
+ *   [4] A-products and [5] Davidson iterations of the last excite (or the
+ *   (A+B) products and CG iterations of the last Z-vector solve),
  *   [6] FP64 products of its refinement phase (mixed with refine), [7] the
  *   largest residual norm |A x - omega x| at its last iteration (TDA);
  *   [15] kernels launched by the library since it was loaded (all contexts);

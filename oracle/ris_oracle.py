@@ -246,6 +246,20 @@ class RisOracle:
         B = (2.0 * J - self.cx * Kb).reshape(n, n)
         return A, B
 
+    # -- Z-vector equation with the ris kernel
+    def zvector(self, rhs: np.ndarray) -> np.ndarray:
+        """Solve (A + B) Z = rhs (Eq. Z_vector with the ris kernel of Eq. ris in
+        A + B) by a dense solve; rhs [n][nocc][nvir] (small systems only)."""
+        A, B = self.dense_AB()
+        n = self.nocc * self.nvir
+        R = np.asarray(rhs).reshape(-1, n)
+        Z = np.linalg.solve(A + B, R.T).T
+        return Z.reshape(np.asarray(rhs).shape)
+
+    def apb_form(self, U, V) -> float:
+        """U . (A + B) . V through the integral-level kernels (no dense matrix)."""
+        return float(np.sum(self.de * U * V)) + self._kernel_ApB(U, V)
+
     # -- excitation energies
     def tda_dense(self, nstates: int):
         A, _ = self.dense_AB()

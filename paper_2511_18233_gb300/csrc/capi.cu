@@ -214,6 +214,14 @@ ris_status ris_excite_guess(ris_ctx* ctx, int nstates, const double* X_guess, do
   });
 }
 
+ris_status ris_zvector(ris_ctx* ctx, int nrhs, const double* rhs, double* Z) {
+  return guarded(ctx, [&] {
+    StageTimer t(ctx->eng, 2);
+    ctx->eng.zvector(nrhs, rhs, Z);
+    t.stop();
+  });
+}
+
 ris_status ris_gradient(ris_ctx* ctx, int n, const int* states, int nx, const double* X_in,
                         const double* Y_in, double* grad) {
   return guarded(ctx, [&] {

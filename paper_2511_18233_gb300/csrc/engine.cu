@@ -448,21 +448,22 @@ __global__ void k_add_identity(double* __restrict__ A, int n) {
   if (i < n) A[(size_t)i * n + i] += 1.0;
 }
 
-// T[j] = R[u_j] * dinv
+// T[j] = R[u_j] * dinv   (u null: row j)
 __global__ void k_precond_scale(const double* __restrict__ R, const double* __restrict__ dinv,
                                 const int* __restrict__ u, long long n, int nt, double* __restrict__ T) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * nt) return;
   const long long i = t % n;
-  T[t] = R[(size_t)u[t / n] * n + i] * dinv[i];
+  const int row = u ? u[t / n] : (int)(t / n);
+  T[t] = R[(size_t)row * n + i] * dinv[i];
 }
 
-// T -= 2 dinv * P (rows of length n)
+// T -= f dinv * P (rows of length n)
 __global__ void k_precond_update(double* __restrict__ T, const double* __restrict__ P,
-                                 const double* __restrict__ dinv, long long n, int nt) {
+                                 const double* __restrict__ dinv, long long n, int nt, double f) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * nt) return;
-  T[t] -= 2.0 * dinv[t % n] * P[t];
+  T[t] -= f * dinv[t % n] * P[t];
 }
 
 __global__ void k_scale_rows(double* __restrict__ X, long long n, int nrow, const double* __restrict__ nrm2) {
@@ -854,6 +855,50 @@ void divide_pairs(double* out, const double* num, const double* den, int npair, 
   RIS_CHECK_LAUNCH();
 }
 
+// out[j] = A_j . B_j (rows of length n), one block per row
+__global__ void k_row_dots(const double* __restrict__ A, const double* __restrict__ B, long long n,
+                           double* __restrict__ out) {
+  __shared__ double red[8];
+  const double* a = A + (size_t)blockIdx.x * n;
+  const double* b = B + (size_t)blockIdx.x * n;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += 256) s += a[i] * b[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; w++) t += red[w];
+    out[blockIdx.x] = t;
+  }
+}
+
+// CG update for row j with step a[j] = rz[j] / pq[j] (0 for frozen rows):
+//   x_j += a p_j,  r_j -= a q_j
+__global__ void k_cg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                        const double* __restrict__ q, const double* __restrict__ rz,
+                        const double* __restrict__ pq, const int* __restrict__ active, long long n,
+                        int nr) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nr) return;
+  const int j = (int)(t / n);
+  if (!active[j]) return;
+  const double a = rz[j] / pq[j];
+  x[t] += a * p[t];
+  r[t] -= a * q[t];
+}
+
+// p_j = z_j + (rz_new[j] / rz[j]) p_j for active rows
+__global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z,
+                       const double* __restrict__ rzn, const double* __restrict__ rz,
+                       const int* __restrict__ active, long long n, int nr) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nr) return;
+  const int j = (int)(t / n);
+  if (!active[j]) return;
+  p[t] = z[t] + (rzn[j] / rz[j]) * p[t];
+}
+
 // RPA operators from their parts: P = de Z + 4 J - cx (K1 + K2), M = de Z - cx (K1 - K2);
 // on entry outP holds J.
 __global__ void k_rpa_combine(const double* __restrict__ de, const double* __restrict__ Z,
@@ -864,7 +909,7 @@ __global__ void k_rpa_combine(const double* __restrict__ de, const double* __res
   if (t >= nov * nvec) return;
   const double dz = de[t % nov] * Z[t];
   outP[t] = dz + 4.0 * outP[t] - cx * (K1[t] + K2[t]);
-  outM[t] = dz - cx * (K1[t] - K2[t]);
+  if (outM) outM[t] = dz - cx * (K1[t] - K2[t]);
 }
 
 // ------------------------------------------------------------------ setup
@@ -1434,6 +1479,58 @@ void Engine::davidson_tda(int ns, const double* guess) {
   RIS_REQUIRE(h_err == 0, RIS_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait timed out");
 }
 
+// M = D - s + f B^J B^J^T (orbital-energy differences plus the Coulomb part
+// of A (f = 2, Eq. A_matrix) or of A + B (f = 4, Eq. Z_vector)), inverted
+// exactly by the Woodbury identity with D' = D - s:
+//   M^-1 r = D'^-1 r - f D'^-1 B (I + f B^T D'^-1 B)^-1 B^T D'^-1 r.
+// shifted: s just below the smallest difference (Davidson: one shift for
+// all states); otherwise s = 0.  The capacitance matrix (nJ x nJ) is
+// Cholesky-factored once; each application is three skinny GEMMs.
+void CoulPrecond::setup(Engine& e, bool shifted, double f_, int nmax) {
+  const long long n = (long long)e.nocc * e.nvir;
+  const int nJ = e.nJ;
+  cudaStream_t st = e.st;
+  f = f_;
+  dinv.ensure(n, st);
+  capinv.ensure((size_t)nJ * nJ, st);
+  pY.ensure((size_t)nmax * nJ, st);
+  pZ.ensure((size_t)nmax * nJ, st);
+  pP.ensure((size_t)nmax * n, st);
+  SBuf<double> W((size_t)n * nJ, st), cap((size_t)nJ * nJ, st), Li((size_t)nJ * nJ, st),
+      dm(1, st, true);
+  SBuf<int> info(1, st);
+  if (shifted) {
+    k_min<<<1, 1024, 0, st>>>(e.de.p, n, dm.p);
+    RIS_CHECK_LAUNCH();
+  }
+  k_precond_setup<<<cdiv(n * nJ, 256), 256, 0, st>>>(e.de.p, dm.p, n, shifted ? kPrecondGap : 0.0,
+                                                      e.BJ.p, nJ, dinv.p, W.p);
+  RIS_CHECK_LAUNCH();
+  dgemm(true, false, nJ, nJ, (int)n, f, e.BJ.p, nJ, W.p, nJ, 0.0, cap.p, nJ, st);
+  k_add_identity<<<cdiv(nJ, 128), 128, 0, st>>>(cap.p, nJ);
+  RIS_CHECK_LAUNCH();
+  cholesky(cap.p, nJ, info.p, st);
+  tri_inverse(cap.p, Li.p, nJ, st);
+  dgemm(true, false, nJ, nJ, nJ, 1.0, Li.p, nJ, Li.p, nJ, 0.0, capinv.p, nJ, st);
+  int h_info = 0;
+  RIS_CUDA(cudaMemcpyAsync(&h_info, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RIS_CUDA(cudaStreamSynchronize(st));
+  RIS_REQUIRE(h_info == 0, RIS_ERR_ARG, "preconditioner capacitance matrix not positive definite");
+}
+
+void CoulPrecond::apply(Engine& e, const double* R, const int* idx, int nt, double* T) {
+  const long long n = (long long)e.nocc * e.nvir;
+  const int nJ = e.nJ;
+  cudaStream_t st = e.st;
+  k_precond_scale<<<cdiv(n * nt, 256), 256, 0, st>>>(R, dinv.p, idx, n, nt, T);
+  RIS_CHECK_LAUNCH();
+  dgemm(false, false, nt, nJ, (int)n, 1.0, T, (int)n, e.BJ.p, nJ, 0.0, pY.p, nJ, st);
+  dgemm(false, false, nt, nJ, nJ, 1.0, pY.p, nJ, capinv.p, nJ, 0.0, pZ.p, nJ, st);
+  dgemm(false, true, nt, (int)n, nJ, 1.0, pZ.p, nJ, e.BJ.p, nJ, 0.0, pP.p, (int)n, st);
+  k_precond_update<<<cdiv(n * nt, 256), 256, 0, st>>>(T, pP.p, dinv.p, n, nt, f);
+  RIS_CHECK_LAUNCH();
+}
+
 // Block Davidson for the lowest ns eigenpairs of the TDA A.  Starts from
 // unit vectors on the lowest orbital-energy differences, or from nguess
 // given vectors (augment: plus unit vectors up to the usual block size);
@@ -1460,47 +1557,18 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
       apply_A_tda(x, nv, y);
   };
   // Preconditioner M = D - s + 2 B^J B^J^T (the orbital-energy differences and
-  // the Coulomb part of A, Eq. A_matrix), inverted exactly by the Woodbury
-  // identity: M^-1 r = D'^-1 r - 2 D'^-1 B (I + 2 B^T D'^-1 B)^-1 B^T D'^-1 r,
-  // D' = D - s, with one shift s below the smallest difference for all states.
+  // the Coulomb part of A, Eq. A_matrix), one shift s below the smallest
+  // difference for all states (see CoulPrecond).
   const bool cprec = opt.precond == 0 && nJ > 0;
-  SBuf<double> dinv, capinv, pY, pZ, pP;
-  if (cprec) {
-    dinv.ensure(n, st);
-    capinv.ensure((size_t)nJ * nJ, st);
-    pY.ensure((size_t)ns * nJ, st);
-    pZ.ensure((size_t)ns * nJ, st);
-    pP.ensure((size_t)ns * n, st);
-    SBuf<double> W((size_t)n * nJ, st), cap((size_t)nJ * nJ, st), Li((size_t)nJ * nJ, st), dm(1, st);
-    SBuf<int> info(1, st);
-    k_min<<<1, 1024, 0, st>>>(de.p, n, dm.p);
-    RIS_CHECK_LAUNCH();
-    k_precond_setup<<<cdiv(n * nJ, 256), 256, 0, st>>>(de.p, dm.p, n, kPrecondGap, BJ.p, nJ, dinv.p, W.p);
-    RIS_CHECK_LAUNCH();
-    dgemm(true, false, nJ, nJ, (int)n, 2.0, BJ.p, nJ, W.p, nJ, 0.0, cap.p, nJ, st);
-    k_add_identity<<<cdiv(nJ, 128), 128, 0, st>>>(cap.p, nJ);
-    RIS_CHECK_LAUNCH();
-    cholesky(cap.p, nJ, info.p, st);
-    tri_inverse(cap.p, Li.p, nJ, st);
-    dgemm(true, false, nJ, nJ, nJ, 1.0, Li.p, nJ, Li.p, nJ, 0.0, capinv.p, nJ, st);
-    int h_info = 0;
-    RIS_CUDA(cudaMemcpyAsync(&h_info, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    RIS_CUDA(cudaStreamSynchronize(st));
-    RIS_REQUIRE(h_info == 0, RIS_ERR_ARG, "preconditioner capacitance matrix not positive definite");
-  }
+  CoulPrecond cp;
+  if (cprec) cp.setup(*this, true, 2.0, ns);
   auto precondition = [&](int nt) {  // T[j] = M^-1 R[d_idx[j]]
     if (!cprec) {
       k_precond<<<cdiv(n * nt, 256), 256, 0, st>>>(Rr.p, de.p, w.p, d_idx, n, nt, T.p);
       RIS_CHECK_LAUNCH();
       return;
     }
-    k_precond_scale<<<cdiv(n * nt, 256), 256, 0, st>>>(Rr.p, dinv.p, d_idx, n, nt, T.p);
-    RIS_CHECK_LAUNCH();
-    dgemm(false, false, nt, nJ, (int)n, 1.0, T.p, (int)n, BJ.p, nJ, 0.0, pY.p, nJ, st);
-    dgemm(false, false, nt, nJ, nJ, 1.0, pY.p, nJ, capinv.p, nJ, 0.0, pZ.p, nJ, st);
-    dgemm(false, true, nt, (int)n, nJ, 1.0, pZ.p, nJ, BJ.p, nJ, 0.0, pP.p, (int)n, st);
-    k_precond_update<<<cdiv(n * nt, 256), 256, 0, st>>>(T.p, pP.p, dinv.p, n, nt);
-    RIS_CHECK_LAUNCH();
+    cp.apply(*this, Rr.p, d_idx, nt, T.p);
   };
   int m = nb0;
   if (guess) {
@@ -2160,6 +2228,128 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
     RIS_CUDA(cudaStreamSynchronize(st));
     RIS_REQUIRE(h_err == 0, RIS_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait timed out");
   }
+}
+
+
+// ------------------------------------------------------------------ Z-vector
+// (ib|P)_K block B^K_ov as [R][i][a], built on demand when the context was
+// not created for RPA (the (A+B) products of the Z-vector need it).
+void Engine::ensure_Kov() {
+  const int o = nocc, v = nvir, n = nao;
+  const long long nov = (long long)o * v;
+  if (BKovR.p && BKovR.n >= (size_t)nov * nK) return;
+  RIS_REQUIRE(TK.p, RIS_ERR_STATE, "three-centre integrals not available (trimmed context)");
+  const double* Co = C.p;
+  const double* Cv = C.p + o;
+  SBuf<double> H((size_t)o * n * nK, st), Bia((size_t)nov * nK, st), Bm((size_t)nov * nK, st);
+  dgemm(true, false, o, n * nK, n, 1.0, Co, nmo, TK.p, n * nK, 0.0, H.p, n * nK, st);
+  GemmBatch bt;
+  bt.nb1 = o;
+  bt.sB1 = (long long)n * nK;
+  bt.sC1 = (long long)v * nK;
+  dgemm(true, false, v, nK, n, 1.0, Cv, nmo, H.p, nK, 0.0, Bia.p, nK, st, bt);
+  dgemm(false, true, (int)nov, nK, nK, 1.0, Bia.p, nK, LKinv.p, nK, 0.0, Bm.p, nK, st);  // [i][a][R]
+  BKovR.ensure((size_t)nov * nK, st);
+  transpose_last2(Bm.p, 1, (int)nov, nK, BKovR.p, st);  // [R][ia]
+}
+
+// Preconditioned conjugate gradients on (A+B)_ris Z = rhs (Eq. Z_vector with
+// the ris kernel of Eq. ris in A+B, the ris-approximated Z-vector solver), all
+// right-hand sides at once; preconditioner D + 4 B^J B^J^T (CoulPrecond).
+// Converged when |r_j| <= tol |rhs_j| for every j.
+void Engine::zvector(int nr, const double* rhs_in, double* Z_out) {
+  RIS_REQUIRE(stage >= 2, RIS_ERR_STATE, "ris_zvector before ris_build_B");
+  RIS_REQUIRE(nr >= 1 && nr <= 64 && rhs_in && Z_out, RIS_ERR_ARG, "bad Z-vector arguments");
+  ensure_Kov();
+  const long long n = (long long)nocc * nvir;
+  const size_t sz = (size_t)nr * n;
+  SBuf<double> b(sz, st), x(sz, st, true), r(sz, st), z(sz, st), p(sz, st), q(sz, st);
+  SBuf<double> sc(5 * (size_t)nr, st);  // rz, pq, rzn, |r|^2, |b|^2
+  double* rz = sc.p;
+  double* pq = sc.p + nr;
+  double* rzn = sc.p + 2 * nr;
+  double* rr = sc.p + 3 * nr;
+  double* bb = sc.p + 4 * nr;
+  SBuf<int> act(nr, st);
+  copy_in(b.p, rhs_in, sz, st);
+  RIS_CUDA(cudaMemcpyAsync(r.p, b.p, sizeof(double) * sz, cudaMemcpyDeviceToDevice, st));
+  const bool mixed = opt.precision == RIS_MIXED;
+  const double tol = mixed ? std::max(opt.conv_tol, opt.mixed_tol) : opt.conv_tol;
+  CoulPrecond cp;
+  const bool cprec = nJ > 0;
+  auto precondition = [&](const double* R, double* T) {
+    if (cprec) {
+      cp.apply(*this, R, nullptr, nr, T);
+    } else {  // diagonal
+      SBuf<double> w0(nr, st, true);
+      SBuf<int> idx(nr, st);
+      std::vector<int> h(nr);
+      for (int j = 0; j < nr; j++) h[j] = j;
+      RIS_CUDA(cudaMemcpyAsync(idx.p, h.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+      k_precond<<<cdiv(n * nr, 256), 256, 0, st>>>(R, de.p, w0.p, idx.p, n, nr, T);
+      RIS_CHECK_LAUNCH();
+      RIS_CUDA(cudaStreamSynchronize(st));
+    }
+  };
+  if (cprec) cp.setup(*this, false, 4.0, nr);
+  std::vector<int> h_act(nr, 1);
+  std::vector<double> h_rr(nr), h_bb(nr);
+  k_row_dots<<<nr, 256, 0, st>>>(b.p, b.p, n, bb);
+  RIS_CHECK_LAUNCH();
+  RIS_CUDA(cudaMemcpyAsync(h_bb.data(), bb, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+  precondition(r.p, z.p);
+  RIS_CUDA(cudaMemcpyAsync(p.p, z.p, sizeof(double) * sz, cudaMemcpyDeviceToDevice, st));
+  k_row_dots<<<nr, 256, 0, st>>>(r.p, z.p, n, rz);
+  RIS_CHECK_LAUNCH();
+  RIS_CUDA(cudaStreamSynchronize(st));
+  for (int j = 0; j < nr; j++) h_act[j] = h_bb[j] > 0.0;
+  int it = 0, nprod = 0;
+  bool converged = false;
+  for (it = 0; it < opt.max_iter; it++) {
+    RIS_CUDA(cudaMemcpyAsync(act.p, h_act.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+    apply_ApB_AmB(p.p, nr, q.p, nullptr);
+    nprod += nr;
+    k_row_dots<<<nr, 256, 0, st>>>(p.p, q.p, n, pq);
+    RIS_CHECK_LAUNCH();
+    k_cg_xr<<<cdiv(n * nr, 256), 256, 0, st>>>(x.p, r.p, p.p, q.p, rz, pq, act.p, n, nr);
+    RIS_CHECK_LAUNCH();
+    k_row_dots<<<nr, 256, 0, st>>>(r.p, r.p, n, rr);
+    RIS_CHECK_LAUNCH();
+    RIS_CUDA(cudaMemcpyAsync(h_rr.data(), rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int j = 0; j < nr; j++) {
+      if (h_act[j] && sqrt(h_rr[j]) <= tol * sqrt(h_bb[j])) h_act[j] = 0;
+      any = any || h_act[j];
+    }
+    if (!any) {
+      converged = true;
+      break;
+    }
+    RIS_CUDA(cudaMemcpyAsync(act.p, h_act.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, st));
+    precondition(r.p, z.p);
+    k_row_dots<<<nr, 256, 0, st>>>(r.p, z.p, n, rzn);
+    RIS_CHECK_LAUNCH();
+    k_cg_p<<<cdiv(n * nr, 256), 256, 0, st>>>(p.p, z.p, rzn, rz, act.p, n, nr);
+    RIS_CHECK_LAUNCH();
+    RIS_CUDA(cudaMemcpyAsync(rz, rzn, sizeof(double) * nr, cudaMemcpyDeviceToDevice, st));
+  }
+  stats[4] = nprod;
+  stats[5] = it + 1;
+  double worst = 0.0;
+  for (int j = 0; j < nr; j++)
+    if (h_bb[j] > 0) worst = std::max(worst, sqrt(h_rr[j] / h_bb[j]));
+  stats[7] = worst;
+  RIS_REQUIRE(converged, RIS_ERR_NOT_CONVERGED,
+              "Z-vector CG did not converge in " + std::to_string(it) + " iterations");
+  if (opt.precision == RIS_MIXED) {
+    int h_err = 0;
+    RIS_CUDA(cudaMemcpyAsync(&h_err, d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+    RIS_REQUIRE(h_err == 0, RIS_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait timed out");
+  }
+  copy_out(Z_out, x.p, sz, st);
+  RIS_CUDA(cudaStreamSynchronize(st));
 }
 
 }  // namespace ris

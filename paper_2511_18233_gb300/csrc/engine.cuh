@@ -71,6 +71,17 @@ struct StreamOwner {
   }
 };
 
+struct Engine;
+
+// Coulomb-exact preconditioner (definition and formula in engine.cu).
+struct CoulPrecond {
+  SBuf<double> dinv, capinv, pY, pZ, pP;
+  double f = 2.0;
+  void setup(Engine& e, bool shifted, double f, int nmax);
+  // T[j] = M^-1 R[idx ? idx[j] : j], j < nt <= nmax
+  void apply(Engine& e, const double* R, const int* idx, int nt, double* T);
+};
+
 struct Engine : StreamOwner {
   ris_options opt{};
   int device = 0;
@@ -160,6 +171,9 @@ struct Engine : StreamOwner {
   void apply_ApB_AmB(const double* Zin, int nvec, double* outP, double* outM);
   void davidson_tda(int ns, const double* guess = nullptr);
   void davidson_rpa(int ns);
+  // ris Z-vector solve (A+B) Z = rhs for nr right-hand sides (PCG)
+  void zvector(int nr, const double* rhs, double* Z);
+  void ensure_Kov();
   // exchange (ij|ab) and (ib|ja) contractions of nvec vectors: K1, K2 [nvec][nov]
   void exchange_terms(const double* Z, int nvec, double* K1, double* K2, bool mixed);
 };

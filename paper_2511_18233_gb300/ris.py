@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_excite_guess", "ris_trim", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_debug_dgemm",
+           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_debug_dgemm",
            "ris_gemm_tf32x3_noalloc",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
     L.ris_excite.argtypes = [P, i, P, P, P]
     L.ris_excite_guess.argtypes = [P, i, P, P, P, P]
     L.ris_trim.argtypes = [P]
+    L.ris_zvector.argtypes = [P, i, P, P]
     L.ris_apply.argtypes = [P, i, P, P, P]
     L.ris_gradient.argtypes = [P, i, P, i, P, P, P]
     L.ris_nac.argtypes = [P, i, P, i, P, P, P, P, P]
@@ -216,6 +217,12 @@ class Context:
         self._check(self.L.ris_nac(self.h, len(pr), _ptr(pr), nx, _ptr(X), _ptr(Y), _ptr(omega),
                                    _ptr(n), _ptr(numerator)))
         return n
+
+    def zvector(self, rhs, out=None):
+        """Solve (A+B) Z = rhs (ris_zvector); rhs [n][nocc][nvir], host or device."""
+        Z = np.zeros(rhs.shape) if out is None else out
+        self._check(self.L.ris_zvector(self.h, int(rhs.shape[0]), _ptr(rhs), _ptr(Z)))
+        return Z
 
     def trim(self):
         """Release every device buffer of the context (ris_trim)."""

@@ -252,3 +252,21 @@ def test_rpa_gradient_and_nac_fd(oracle, mol0, orc0):
             s = np.sign(np.sum(Xd[1] * X[1]) - np.sum(Yd[1] * Y[1]))
             return np.sum(X[0] * Xd[1] * s) - np.sum(Y[0] * Yd[1] * s)
         assert nac[3, x] == pytest.approx(_fd5(ov), rel=1e-5, abs=1e-8)
+
+
+def test_zvector_solution_against_integral_level_forms(orc0, mol0):
+    """The oracle's Z-vector (dense solve of (A+B) Z = rhs) checked through the
+    integral-level kernels instead of the dense matrices: for random V,
+    V.(A+B).Z must equal V.rhs; A+B must be positive definite (CG applies)."""
+    rhs = synth.random_amplitudes(3, mol0.nocc, mol0.nvir, seed=11)
+    Z = orc0.zvector(rhs)
+    A, B = orc0.dense_AB()
+    assert np.linalg.eigvalsh(A + B)[0] > 0
+    V = synth.random_amplitudes(2, mol0.nocc, mol0.nvir, seed=12)
+    for k in range(3):
+        for v in V:
+            lhs = orc0.apb_form(v, Z[k])
+            assert abs(lhs - float(np.sum(v * rhs[k]))) <= 1e-11 * max(1.0, abs(lhs))
+    # the dense A+B agrees with the integral-level bilinear form
+    u, w = V
+    assert abs(u.reshape(-1) @ (A + B) @ w.reshape(-1) - orc0.apb_form(u, w)) <= 1e-12
