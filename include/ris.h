@@ -154,6 +154,20 @@ ris_status ris_excite_guess(ris_ctx* ctx, int nstates, const double* X_guess, do
                             double* X, double* Y);
 
 /*
+ * Phase tracking along a trajectory (Sec. 2, phase determination for
+ * derivative couplings along a geometric path): for each of the first
+ * nstates states of the last ris_excite, the overlap with the previous
+ * step's state over its five most dominant determinants (the five largest
+ * |X_prev| elements, ties by index; MOs common to both steps) decides the
+ * sign, and a negative overlap flips the state's X (and Y).  Later
+ * ris_gradient / ris_nac calls without explicit amplitudes use the aligned
+ * phases.  X_prev: [nstates][nocc][nvir] (host or device); sign: [nstates]
+ * +1 / -1 (host or device, may be NULL); X_out: aligned X (may be NULL).
+ */
+ris_status ris_phase_align(ris_ctx* ctx, int nstates, const double* X_prev, int* sign,
+                           double* X_out);
+
+/*
  * The ris-approximated Z-vector solve: (A + B) Z = rhs (Eq. Z_vector, with
  * the ris kernel of Eq. ris in A + B — the solver of the section "Ris
  * approximation for Z-vector Solver"), for nrhs <= 64 right-hand sides at

@@ -214,6 +214,11 @@ ris_status ris_excite_guess(ris_ctx* ctx, int nstates, const double* X_guess, do
   });
 }
 
+ris_status ris_phase_align(ris_ctx* ctx, int nstates, const double* X_prev, int* sign,
+                           double* X_out) {
+  return guarded(ctx, [&] { ctx->eng.phase_align(nstates, X_prev, sign, X_out); });
+}
+
 ris_status ris_zvector(ris_ctx* ctx, int nrhs, const double* rhs, double* Z) {
   return guarded(ctx, [&] {
     StageTimer t(ctx->eng, 2);

@@ -899,6 +899,77 @@ __global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z,
   p[t] = z[t] + (rzn[j] / rz[j]) * p[t];
 }
 
+// Phase of state blockIdx.x against the previous step: the overlap over the
+// five largest |X_prev| determinants (ties by index); a negative overlap
+// flips X (and Y) of the state.  sign[I] = +1 or -1.
+__global__ void __launch_bounds__(256) k_phase_align(double* __restrict__ X, double* __restrict__ Y,
+                                                     const double* __restrict__ Xp, long long n,
+                                                     int* __restrict__ sign) {
+  __shared__ unsigned long long bk[8];
+  __shared__ long long bi[8];
+  __shared__ long long top[5];
+  __shared__ double ov;
+  if (threadIdx.x < 5) top[threadIdx.x] = -1;
+  __syncthreads();
+  const int I = blockIdx.x;
+  const double* xp = Xp + (size_t)I * n;
+  double* x = X + (size_t)I * n;
+  unsigned long long lastk = ~0ull;
+  long long lasti = -1;
+  for (int r = 0; r < 5; r++) {
+    // largest |xp| strictly after (lastk, lasti) in the order (|x| desc, index asc)
+    unsigned long long best = 0;
+    long long besti = -1;
+    for (long long i = threadIdx.x; i < n; i += 256) {
+      const unsigned long long k = (unsigned long long)__double_as_longlong(fabs(xp[i]));
+      const bool after = lasti < 0 || k < lastk || (k == lastk && i > lasti);
+      if (after && (besti < 0 || k > best || (k == best && i < besti))) {
+        best = k;
+        besti = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
+      const long long oi = __shfl_xor_sync(0xffffffffu, besti, o);
+      if (oi >= 0 && (besti < 0 || ok > best || (ok == best && oi < besti))) {
+        best = ok;
+        besti = oi;
+      }
+    }
+    if ((threadIdx.x & 31) == 0) {
+      bk[threadIdx.x >> 5] = best;
+      bi[threadIdx.x >> 5] = besti;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < 8; w++)
+        if (bi[w] >= 0 && (bi[0] < 0 || bk[w] > bk[0] || (bk[w] == bk[0] && bi[w] < bi[0]))) {
+          bk[0] = bk[w];
+          bi[0] = bi[w];
+        }
+      top[r] = bi[0];
+    }
+    __syncthreads();
+    lastk = bk[0];
+    lasti = bi[0];
+    __syncthreads();
+    if (lasti < 0) break;  // fewer than five elements
+  }
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int r = 0; r < 5; r++)
+      if (top[r] >= 0) s += x[top[r]] * xp[top[r]];
+    ov = s;
+    sign[I] = s < 0.0 ? -1 : 1;
+  }
+  __syncthreads();
+  if (ov < 0.0) {
+    for (long long i = threadIdx.x; i < n; i += 256) x[i] = -x[i];
+    if (Y)
+      for (long long i = threadIdx.x; i < n; i += 256) Y[(size_t)I * n + i] = -Y[(size_t)I * n + i];
+  }
+}
+
 // RPA operators from their parts: P = de Z + 4 J - cx (K1 + K2), M = de Z - cx (K1 - K2);
 // on entry outP holds J.
 __global__ void k_rpa_combine(const double* __restrict__ de, const double* __restrict__ Z,
@@ -2349,6 +2420,32 @@ void Engine::zvector(int nr, const double* rhs_in, double* Z_out) {
     RIS_REQUIRE(h_err == 0, RIS_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait timed out");
   }
   copy_out(Z_out, x.p, sz, st);
+  RIS_CUDA(cudaStreamSynchronize(st));
+}
+
+
+// ------------------------------------------------------------------ phase tracking
+// Align the phases of the current states with those of the previous step
+// (X_prev, host or device, [ns][nocc][nvir]); optional copies of the aligned
+// amplitudes and of the signs (host or device).
+void Engine::phase_align(int ns, const double* Xprev_in, int* sign_out, double* Xout) {
+  RIS_REQUIRE(stage >= 2 && nstates > 0 && X.p, RIS_ERR_STATE, "ris_phase_align before ris_excite");
+  RIS_REQUIRE(ns >= 1 && ns <= nstates && Xprev_in, RIS_ERR_ARG, "bad phase-alignment arguments");
+  const long long n = (long long)nocc * nvir;
+  SBuf<double> xp((size_t)ns * n, st);
+  copy_in(xp.p, Xprev_in, (size_t)ns * n, st);
+  SBuf<int> sg(ns, st);
+  k_phase_align<<<ns, 256, 0, st>>>(X.p, opt.rpa ? Y.p : nullptr, xp.p, n, sg.p);
+  RIS_CHECK_LAUNCH();
+  if (sign_out) {
+    cudaPointerAttributes a;
+    const bool dev = cudaPointerGetAttributes(&a, sign_out) == cudaSuccess &&
+                     (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    RIS_CUDA(cudaMemcpyAsync(sign_out, sg.p, sizeof(int) * ns,
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (Xout) copy_out(Xout, X.p, (size_t)ns * n, st);
   RIS_CUDA(cudaStreamSynchronize(st));
 }
 

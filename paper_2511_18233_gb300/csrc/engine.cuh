@@ -174,6 +174,8 @@ struct Engine : StreamOwner {
   // ris Z-vector solve (A+B) Z = rhs for nr right-hand sides (PCG)
   void zvector(int nr, const double* rhs, double* Z);
   void ensure_Kov();
+  // phases of the current states against the previous step (five dominant determinants)
+  void phase_align(int ns, const double* Xprev, int* sign, double* Xout);
   // exchange (ij|ab) and (ib|ja) contractions of nvec vectors: K1, K2 [nvec][nov]
   void exchange_terms(const double* Z, int nvec, double* K1, double* K2, bool mixed);
 };

@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_debug_dgemm",
+           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_debug_dgemm",
            "ris_gemm_tf32x3_noalloc",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH):
     L.ris_excite_guess.argtypes = [P, i, P, P, P, P]
     L.ris_trim.argtypes = [P]
     L.ris_zvector.argtypes = [P, i, P, P]
+    L.ris_phase_align.argtypes = [P, i, P, P, P]
     L.ris_apply.argtypes = [P, i, P, P, P]
     L.ris_gradient.argtypes = [P, i, P, i, P, P, P]
     L.ris_nac.argtypes = [P, i, P, i, P, P, P, P, P]
@@ -223,6 +224,13 @@ class Context:
         Z = np.zeros(rhs.shape) if out is None else out
         self._check(self.L.ris_zvector(self.h, int(rhs.shape[0]), _ptr(rhs), _ptr(Z)))
         return Z
+
+    def phase_align(self, X_prev, X_out=None):
+        """Align the current states' phases with X_prev (ris_phase_align); returns the signs."""
+        ns = int(X_prev.shape[0])
+        sign = np.zeros(ns, dtype=np.int32)
+        self._check(self.L.ris_phase_align(self.h, ns, _ptr(X_prev), _ptr(sign), _ptr(X_out)))
+        return sign
 
     def trim(self):
         """Release every device buffer of the context (ris_trim)."""

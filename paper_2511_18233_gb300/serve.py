@@ -17,6 +17,11 @@ module serves such a stream on one GPU:
   of all running requests plus all resident trajectory state fit the
   budget; a request's footprint is estimated from its dimensions on a
   trajectory's first step and measured by the library afterwards;
+* phases: from its second step on, each state's sign follows the previous
+  step (overlap over the five most dominant determinants, ris_phase_align),
+  so the couplings keep a consistent sign along the trajectory, and the
+  time-derivative coupling T_IJ = d_IJ . v (v: the step's nuclear
+  velocities) is returned with them;
 * latency is arrival -> results on the host; p50/p99 and throughput are
   reported.
 
@@ -161,6 +166,20 @@ def step_coords(ref: np.ndarray, spec: TrajectorySpec, step: int,
     (trajectory, step)."""
     rng = np.random.default_rng([spec.seed, step])
     return synth.perturb(ref, sigma_ang, rng)
+
+
+# atomic masses (electron masses) and k_B T at 300 K (Hartree)
+_MASS = {"H": 1.00794 * 1822.888486, "C": 12.0107 * 1822.888486}
+_KT300 = 300.0 * 3.166811563e-6
+
+
+def step_velocities(elements: Sequence[str], spec: TrajectorySpec, step: int) -> np.ndarray:
+    """Nuclear velocities of a step (bohr per atomic time unit): Maxwell-Boltzmann
+    at 300 K per Cartesian component, seeded per (trajectory, step); they enter
+    only T_IJ = d_IJ . v, the quantity surface hopping uses."""
+    rng = np.random.default_rng([spec.seed, step, 1])
+    m = np.array([_MASS[e] for e in elements])
+    return rng.normal(size=(len(elements), 3)) * np.sqrt(_KT300 / m)[:, None]
 
 
 def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
@@ -521,6 +540,9 @@ class RisExecutor:
                 ctx.excite_guess(ns, s["X"][s["cur"]], out=(s["om"], out, None))
             else:
                 ctx.excite(ns, out=(s["om"], out, None))
+            signs = np.ones(ns, dtype=np.int32)
+            if s["have_X"]:  # phases consistent with the previous step
+                signs = ctx.phase_align(s["X"][s["cur"]], X_out=out)
             s["cur"] = 1 - s["cur"]
             s["have_X"] = True
             grad = ctx.gradient([spec.active])[0]
@@ -529,8 +551,11 @@ class RisExecutor:
             st = ctx.stats()
         finally:
             ctx.trim()
-        return ({"omega": omega, "grad": grad, "nac": nac, "n_iter": int(st["n_iter"]),
-                 "n_products": int(st["n_products"])}, int(st["bytes_peak"]))
+        v = step_velocities(tr.mol.elements, spec, req.step)
+        T = np.einsum("pax,ax->p", nac, v) if len(spec.pairs) else np.zeros(0)
+        return ({"omega": omega, "grad": grad, "nac": nac, "T": T, "signs": signs,
+                 "n_iter": int(st["n_iter"]), "n_products": int(st["n_products"])},
+                int(st["bytes_peak"]))
 
 
 def build_trajectories(specs: Sequence[TrajectorySpec]) -> List[Trajectory]:
