@@ -94,6 +94,10 @@ typedef struct {
   int precond;        /* TDA Davidson preconditioner: 0 (default) = (D - s + 2 B^J B^J^T)^-1
                          applied exactly (Woodbury) with one shift s just below the smallest
                          orbital-energy difference; 1 = diagonal (D - omega_k)^-1 per state */
+  double mo_window;   /* > 0: keep only occupied MOs with e_i >= e_HOMO - mo_window and virtual
+                         MOs with e_a <= e_LUMO + mo_window (Hartree; orbital energies sorted
+                         within each block); amplitudes are then [nocc_act][nvir_act]
+                         (ris_get_mo_window).  0 (default): all MOs */
 } ris_options;
 
 typedef struct {
@@ -212,6 +216,13 @@ ris_status ris_gradient(ris_ctx* ctx, int n, const int* states, int nx, const do
  */
 ris_status ris_nac(ris_ctx* ctx, int npair, const int* pairs, int nx, const double* X_in,
                    const double* Y_in, const double* omega_in, double* nac, double* numerator);
+
+/*
+ * The active MO range after ris_build_B: occupied MOs first_occ .. nocc-1 and
+ * the first nvir_act virtual MOs (all of them without mo_window); the
+ * amplitudes of every call are [nocc_act][nvir_act].  Any pointer may be NULL.
+ */
+ris_status ris_get_mo_window(const ris_ctx* ctx, int* first_occ, int* nocc_act, int* nvir_act);
 
 /* Sizes of the current problem (any pointer may be NULL). */
 ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int* nauxJ,

@@ -384,7 +384,7 @@ void oracle_int3c_deriv_atom(int atom, const double* coords, int nsh, const int*
 #pragma omp parallel
   {
     double* scr = (double*)malloc(sizeof(double) * scratch_size(4, 4, 3));
-    double* d = (double*)malloc(sizeof(double) * 9 * 6 * 6 * 3);
+    double* d = (double*)malloc(sizeof(double) * 9 * 6 * 6 * 6);  /* AO and aux shells up to d */
     double na_[10], nb_[10], nc_[10];
 #pragma omp for schedule(dynamic)
     for (int sab = 0; sab < nsh * nsh; sab++) {

@@ -134,6 +134,7 @@ ris_status ris_options_default(ris_options* opt) {
   opt->mixed_tol = 1e-6;
   opt->refine = 0;
   opt->precond = 0;
+  opt->mo_window = 0.0;
   return RIS_OK;
 }
 
@@ -149,6 +150,7 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
   if (!(o.conv_tol > 0) || o.max_iter <= 0 || !(o.screen_thr >= 0)) return RIS_ERR_ARG;
   if (o.precision == RIS_MIXED && !(o.mixed_tol > 0)) return RIS_ERR_ARG;
   if (o.precond != 0 && o.precond != 1) return RIS_ERR_ARG;
+  if (!(o.mo_window >= 0.0)) return RIS_ERR_ARG;
   c->eng.opt = o;
   c->eng.device = o.device;
   if (o.profile) ris::prof_enable(true);
@@ -283,6 +285,15 @@ ris_status ris_nac(ris_ctx* ctx, int npair, const int* pairs, int nx, const doub
     return RIS_ERR_DEGENERATE;
   }
   return s;
+}
+
+ris_status ris_get_mo_window(const ris_ctx* ctx, int* first_occ, int* nocc_act, int* nvir_act) {
+  if (!ctx) return RIS_ERR_ARG;
+  const ris::Engine& e = ctx->eng;
+  if (first_occ) *first_occ = e.first_occ;
+  if (nocc_act) *nocc_act = e.nocc;
+  if (nvir_act) *nvir_act = e.nvir;
+  return RIS_OK;
 }
 
 ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int* nauxJ,

@@ -14,7 +14,7 @@ namespace ris {
 
 // Highest angular momenta handled by the integral kernels.
 constexpr int kMaxLAO = 2;   // AO shells up to d
-constexpr int kMaxLAux = 1;  // auxiliary shells up to p
+constexpr int kMaxLAux = 2;  // auxiliary shells up to d
 // Boys table: F_m(k*dT) for m <= kBoysM, k*dT <= kBoysTmax.
 constexpr int kBoysM = 16;
 constexpr double kBoysDT = 0.05;

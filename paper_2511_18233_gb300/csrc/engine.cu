@@ -93,7 +93,8 @@ void FBuf::release() {
 }
 
 static void free_shells(ShellSet& s, cudaStream_t st) {
-  int** ip[] = {&s.atom, &s.l, &s.off, &s.jmap, &s.kmap, &s.fun_atom, &s.d_by_l[0], &s.d_by_l[1]};
+  int** ip[] = {&s.atom, &s.l, &s.off, &s.jmap, &s.kmap, &s.fun_atom, &s.d_by_l[0], &s.d_by_l[1],
+                &s.d_by_l[2]};
   for (auto q : ip)
     if (*q) {
       cudaFreeAsync(*q, st);
@@ -1144,16 +1145,36 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
   RIS_REQUIRE(nocc_ > 0 && nocc_ < nmo_, RIS_ERR_ARG, "need 0 < nocc < nmo");
   RIS_REQUIRE(Cin && eps_in, RIS_ERR_ARG, "null pointer");
   stage = 1;
-  nmo = nmo_;
-  nocc = nocc_;
+  // active MO range: all MOs, or the energy window around the frontier
+  // orbitals (a contiguous column range [i0, a1) of C)
+  int i0 = 0, a1 = nmo_;
+  if (opt.mo_window > 0.0) {
+    std::vector<double> he(nmo_);
+    copy_to_host(he.data(), eps_in, nmo_, st);
+    for (int i = 1; i < nmo_; i++)
+      RIS_REQUIRE(i == nocc_ || he[i] >= he[i - 1], RIS_ERR_ARG,
+                  "mo_window needs orbital energies sorted within the occupied and virtual blocks");
+    const double lo = he[nocc_ - 1] - opt.mo_window, hi = he[nocc_] + opt.mo_window;
+    while (i0 < nocc_ - 1 && he[i0] < lo) i0++;
+    while (a1 > nocc_ + 1 && he[a1 - 1] > hi) a1--;
+  }
+  first_occ = i0;
+  nmo = a1 - i0;
+  nocc = nocc_ - i0;
   nvir = nmo - nocc;
   const int o = nocc, v = nvir, n = nao;
   const long long nov = (long long)o * v;
   C.ensure((size_t)n * nmo, st);
   eps.ensure(nmo, st);
   de.ensure(nov, st);
-  copy_in(C.p, Cin, (size_t)n * nmo, st);
-  copy_in(eps.p, eps_in, nmo, st);
+  if (i0 == 0 && a1 == nmo_) {
+    copy_in(C.p, Cin, (size_t)n * nmo, st);
+    copy_in(eps.p, eps_in, nmo, st);
+  } else {  // columns i0 .. a1-1 of C [nao][nmo_]
+    RIS_CUDA(cudaMemcpy2DAsync(C.p, sizeof(double) * nmo, Cin + i0, sizeof(double) * nmo_,
+                               sizeof(double) * nmo, n, cudaMemcpyDefault, st));
+    copy_in(eps.p, eps_in + i0, nmo, st);
+  }
   k_orb_diff<<<cdiv(nov, 256), 256, 0, st>>>(eps.p, o, v, de.p);
   RIS_CHECK_LAUNCH();
   const double* Co = C.p;

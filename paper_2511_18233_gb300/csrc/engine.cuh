@@ -109,7 +109,8 @@ struct Engine : StreamOwner {
   int* d_info = nullptr;
 
   // MO data
-  int nao = 0, nmo = 0, nocc = 0, nvir = 0;
+  int nao = 0, nmo = 0, nocc = 0, nvir = 0;  // active sizes (after mo_window)
+  int first_occ = 0;                           // first active occupied MO of the input
   DBuf C, eps, de;
   DBuf BJ;        // [ov][RJ]
   DBuf BKoo;      // [i][j][R]

@@ -239,6 +239,28 @@ __host__ __device__ constexpr double cfac(int l, int c) {
   return (l == 2 && (c == 0 || c == 3 || c == 5)) ? 0.57735026918962576451 : 1.0;
 }
 
+// Hermite expansion of one Cartesian factor x^k exp(-g x^2) of a Gaussian in
+// Hermite Gaussians Lambda_tau = (d/dC_x)^tau exp(-g (x - C_x)^2):
+//   x^0 = Lambda_0, x^1 = Lambda_1 / (2g), x^2 = Lambda_0 / (2g) + Lambda_2 / (4g^2);
+// sgn = -1 applies the ket sign (-1)^tau of the McMurchie-Davidson formula.
+__device__ __forceinline__ int herm1(int k, double g, double sgn, int* tau, double* c) {
+  if (k == 0) {
+    tau[0] = 0;
+    c[0] = 1.0;
+    return 1;
+  }
+  if (k == 1) {
+    tau[0] = 1;
+    c[0] = sgn * 0.5 / g;
+    return 1;
+  }
+  tau[0] = 0;
+  c[0] = 0.5 / g;
+  tau[1] = 2;
+  c[1] = 0.25 / (g * g);
+  return 2;
+}
+
 struct PairGeom {
   double p, PA[3], PB[3], P[3], pref_ab;  // pref_ab = K_ab * nbase_a * nbase_b
 };
@@ -307,21 +329,31 @@ __global__ void __launch_bounds__(128) k_int3c(const int* __restrict__ pa, const
       const double nab = pref * cfac(LA, ia) * cfac(LB, ib);
 #pragma unroll 1
       for (int ic = 0; ic < (LC + 1) * (LC + 2) / 2; ic++) {
-        const int kx = cx_(LC, ic), ky = cy_(LC, ic), kz = cz_(LC, ic);
+        int tx[2], ty[2], tz[2];
+        double fx[2], fy[2], fz[2];
+        const int nx = herm1(cx_(LC, ic), gam, -1.0, tx, fx);
+        const int ny = herm1(cy_(LC, ic), gam, -1.0, ty, fy);
+        const int nz = herm1(cz_(LC, ic), gam, -1.0, tz, fz);
         double s = 0.0;
+        for (int jx = 0; jx < nx; jx++)
+          for (int jy = 0; jy < ny; jy++)
+            for (int jz = 0; jz < nz; jz++) {
+              const int kx = tx[jx], ky = ty[jy], kz = tz[jz];
+              double sub = 0.0;
 #pragma unroll 1
-        for (int t = 0; t <= ax + bx; t++) {
-          const double et = E[0][ax][bx][t];
+              for (int t = 0; t <= ax + bx; t++) {
+                const double et = E[0][ax][bx][t];
 #pragma unroll 1
-          for (int u = 0; u <= ay + by; u++) {
-            const double eu = et * E[1][ay][by][u];
+                for (int u = 0; u <= ay + by; u++) {
+                  const double eu = et * E[1][ay][by][u];
 #pragma unroll 1
-            for (int v = 0; v <= az + bz; v++)
-              s += eu * E[2][az][bz][v] * R[hidx(t + kx, u + ky, v + kz)];
-          }
-        }
-        if (LC == 1) s *= -0.5 / gam;
-        s *= nab;
+                  for (int v = 0; v <= az + bz; v++)
+                    sub += eu * E[2][az][bz][v] * R[hidx(t + kx, u + ky, v + kz)];
+                }
+              }
+              s += fx[jx] * fy[jy] * fz[jz] * sub;
+            }
+        s *= nab * cfac(LC, ic);
         const int mu = oa + ia, nu = ob + ib;
         if (jm >= 0) {
           TJ[((size_t)mu * nao + nu) * nJ + jm + ic] = s;
@@ -381,8 +413,12 @@ __global__ void __launch_bounds__(128) k_int3c_deriv(
       const double nab = pref * cfac(LA, ia) * cfac(LB, ib);
 #pragma unroll 1
       for (int ic = 0; ic < (LC + 1) * (LC + 2) / 2; ic++) {
-        const int k_[3] = {cx_(LC, ic), cy_(LC, ic), cz_(LC, ic)};
-        const double sc_ = (LC == 1 ? -0.5 / gam : 1.0) * nab;
+        int th[3][2];
+        double fh[3][2];
+        const int nh[3] = {herm1(cx_(LC, ic), gam, -1.0, th[0], fh[0]),
+                           herm1(cy_(LC, ic), gam, -1.0, th[1], fh[1]),
+                           herm1(cz_(LC, ic), gam, -1.0, th[2], fh[2])};
+        const double sc_ = cfac(LC, ic) * nab;
         const int mu = oa + ia, nu = ob + ib, P = oc + ic;
 #pragma unroll 1
         for (int x = 0; x < 3; x++) {
@@ -400,18 +436,25 @@ __global__ void __launch_bounds__(128) k_int3c_deriv(
             const double eA = 2.0 * alpha * up - a_[x] * dn;
             const double eB = 2.0 * beta * upb - b_[x] * dnb;
             double r = 0.0;
+            for (int jx = 0; jx < nh[x]; jx++)
+              for (int jy = 0; jy < nh[y]; jy++)
+                for (int jz = 0; jz < nh[z]; jz++) {
+                  const double fc = fh[x][jx] * fh[y][jy] * fh[z][jz];
+                  double rr = 0.0;
 #pragma unroll 1
-            for (int u = 0; u <= a_[y] + b_[y]; u++) {
-              const double eu = E[y][a_[y]][b_[y]][u];
+                  for (int u = 0; u <= a_[y] + b_[y]; u++) {
+                    const double eu = E[y][a_[y]][b_[y]][u];
 #pragma unroll 1
-              for (int v = 0; v <= a_[z] + b_[z]; v++) {
-                int tuv[3];
-                tuv[x] = t + k_[x];
-                tuv[y] = u + k_[y];
-                tuv[z] = v + k_[z];
-                r += eu * E[z][a_[z]][b_[z]][v] * R[hidx(tuv[0], tuv[1], tuv[2])];
-              }
-            }
+                    for (int v = 0; v <= a_[z] + b_[z]; v++) {
+                      int tuv[3];
+                      tuv[x] = t + th[x][jx];
+                      tuv[y] = u + th[y][jy];
+                      tuv[z] = v + th[z][jz];
+                      rr += eu * E[z][a_[z]][b_[z]][v] * R[hidx(tuv[0], tuv[1], tuv[2])];
+                    }
+                  }
+                  r += fc * rr;
+                }
             sA += eA * r;
             sB += eB * r;
           }
@@ -438,31 +481,48 @@ __global__ void k_int2c(int nsh, const int* __restrict__ atom, const int* __rest
   const double* Cc = xyz + 3 * atom[sq];
   const double rho = a * c / (a + c);
   const double X = A[0] - Cc[0], Y = A[1] - Cc[1], Z = A[2] - Cc[2];
-  double F[4];
-  boys<3>(rho * (X * X + Y * Y + Z * Z), boys_tab, F);
-  double R[NH<3>::n];
-  hermite_R<3>(rho, X, Y, Z, F, R);
+  constexpr int LM = 2 * kMaxLAux + 1;  // (P|Q) and its first derivative
+  double F[LM + 1];
+  boys<LM>(rho * (X * X + Y * Y + Z * Z), boys_tab, F);
+  double R[NH<LM>::n];
+  hermite_R<LM>(rho, X, Y, Z, F, R);
   const double pref = 2.0 * 17.493418327624862 / (a * c * sqrt(a + c)) * nbase[sp] * nbase[sq];
   const int l1 = lq[sp], l2 = lq[sq];
   for (int i = 0; i < ncart(l1); i++) {
+    int t1[3][2], n1[3];
+    double f1[3][2];
+    n1[0] = herm1(cx_(l1, i), a, 1.0, t1[0], f1[0]);
+    n1[1] = herm1(cy_(l1, i), a, 1.0, t1[1], f1[1]);
+    n1[2] = herm1(cz_(l1, i), a, 1.0, t1[2], f1[2]);
     for (int k = 0; k < ncart(l2); k++) {
-      int e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
-      double f = 1.0;
-      if (l1 == 1) {
-        e1[i] = 1;
-        f *= 0.5 / a;
-      }
-      if (l2 == 1) {
-        e2[k] = 1;
-        f *= -0.5 / c;
-      }
-      const int t = e1[0] + e2[0], u = e1[1] + e2[1], v = e1[2] + e2[2];
+      int t2[3][2], n2[3];
+      double f2[3][2];
+      n2[0] = herm1(cx_(l2, k), c, -1.0, t2[0], f2[0]);
+      n2[1] = herm1(cy_(l2, k), c, -1.0, t2[1], f2[1]);
+      n2[2] = herm1(cz_(l2, k), c, -1.0, t2[2], f2[2]);
+      double m = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
+      for (int ax = 0; ax < n1[0]; ax++)
+        for (int ay = 0; ay < n1[1]; ay++)
+          for (int az = 0; az < n1[2]; az++)
+            for (int bx = 0; bx < n2[0]; bx++)
+              for (int by = 0; by < n2[1]; by++)
+                for (int bz = 0; bz < n2[2]; bz++) {
+                  const double f = f1[0][ax] * f1[1][ay] * f1[2][az] * f2[0][bx] * f2[1][by] *
+                                   f2[2][bz];
+                  const int t = t1[0][ax] + t2[0][bx], u = t1[1][ay] + t2[1][by],
+                            v = t1[2][az] + t2[2][bz];
+                  m += f * R[hidx(t, u, v)];
+                  // d/dA_x R_tuv(A - C) = R_{t+1,u,v}
+                  d0 += f * R[hidx(t + 1, u, v)];
+                  d1 += f * R[hidx(t, u + 1, v)];
+                  d2 += f * R[hidx(t, u, v + 1)];
+                }
+      const double nf = pref * cfac(l1, i) * cfac(l2, k);
       const size_t o = (size_t)(off[sp] + i) * naux + off[sq] + k;
-      M[o] = pref * f * R[hidx(t, u, v)];
-      // d/dA_x R_tuv(A - C) = R_{t+1,u,v}
-      dM[o] = pref * f * R[hidx(t + 1, u, v)];
-      dM[(size_t)naux * naux + o] = pref * f * R[hidx(t, u + 1, v)];
-      dM[(size_t)2 * naux * naux + o] = pref * f * R[hidx(t, u, v + 1)];
+      M[o] = nf * m;
+      dM[o] = nf * d0;
+      dM[(size_t)naux * naux + o] = nf * d1;
+      dM[(size_t)2 * naux * naux + o] = nf * d2;
     }
   }
 }
@@ -651,7 +711,13 @@ static void launch_int3c_deriv(const ShellSet& ao, const ShellSet& aux, const Pa
   M<1, 1, 1>(__VA_ARGS__);        \
   M<2, 0, 1>(__VA_ARGS__);        \
   M<2, 1, 1>(__VA_ARGS__);        \
-  M<2, 2, 1>(__VA_ARGS__);
+  M<2, 2, 1>(__VA_ARGS__);        \
+  M<0, 0, 2>(__VA_ARGS__);        \
+  M<1, 0, 2>(__VA_ARGS__);        \
+  M<1, 1, 2>(__VA_ARGS__);        \
+  M<2, 0, 2>(__VA_ARGS__);        \
+  M<2, 1, 2>(__VA_ARGS__);        \
+  M<2, 2, 2>(__VA_ARGS__);
 
 void int3c(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const double* xyz, int nJ,
            int nK, double* TJ, double* TK, cudaStream_t st) {

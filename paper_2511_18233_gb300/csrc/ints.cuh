@@ -21,7 +21,7 @@ struct ShellSet {
   std::vector<int> h_atom, h_l, h_off, h_jmap, h_kmap;
   std::vector<double> h_ex;
   std::vector<int> by_l[kMaxLAux + 1];  // auxiliary shells grouped by l
-  int* d_by_l[kMaxLAux + 1] = {nullptr, nullptr};
+  int* d_by_l[kMaxLAux + 1] = {nullptr, nullptr, nullptr};
   int* fun_atom = nullptr;   // atom of each function
 };
 

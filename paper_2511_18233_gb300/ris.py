@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_debug_dgemm",
+           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_debug_dgemm",
            "ris_gemm_tf32x3_noalloc",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
                 ("mem_budget", ctypes.c_size_t), ("occ_block", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("profile", ctypes.c_int), ("mixed_tol", ctypes.c_double), ("refine", ctypes.c_int),
-                ("precond", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("mo_window", ctypes.c_double)]
 
 
 class Shell(ctypes.Structure):
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
     L.ris_trim.argtypes = [P]
     L.ris_zvector.argtypes = [P, i, P, P]
     L.ris_phase_align.argtypes = [P, i, P, P, P]
+    L.ris_get_mo_window.argtypes = [P, P, P, P]
     L.ris_apply.argtypes = [P, i, P, P, P]
     L.ris_gradient.argtypes = [P, i, P, i, P, P, P]
     L.ris_nac.argtypes = [P, i, P, i, P, P, P, P, P]
@@ -166,8 +167,14 @@ class Context:
             C = np.ascontiguousarray(C, dtype=np.float64)
             mo_energy = np.ascontiguousarray(mo_energy, dtype=np.float64)
         nao, nmo = C.shape
-        self.nocc, self.nvir = int(nocc), int(nmo - nocc)
         self._check(self.L.ris_build_B(self.h, nao, nmo, int(nocc), _ptr(C), _ptr(mo_energy)))
+        self.first_occ, self.nocc, self.nvir = self.mo_window()
+
+    def mo_window(self):
+        """(first active occupied MO, active nocc, active nvir) after build_B."""
+        v = [ctypes.c_int() for _ in range(3)]
+        self._check(self.L.ris_get_mo_window(self.h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def excite(self, nstates: int, out=None):
         """Returns (omega, X[, Y]) as numpy arrays, or fills `out` (omega, X, Y)

@@ -160,7 +160,8 @@ def _coulomb_quad(ca, a, A, cb, b, B, cc, g, Cc):
     return 2.0 / math.sqrt(PI) * (val1 + val2) * nr
 
 
-@pytest.mark.parametrize("la,lb,lc", [(0, 0, 0), (1, 0, 1), (2, 1, 0), (2, 2, 1), (1, 2, 1)])
+@pytest.mark.parametrize("la,lb,lc", [(0, 0, 0), (1, 0, 1), (2, 1, 0), (2, 2, 1), (1, 2, 1),
+                                      (0, 0, 2), (1, 1, 2), (2, 2, 2)])
 def test_three_centre_against_quadrature(oracle, la, lb, lc):
     rng = np.random.default_rng(100 + 9 * la + 3 * lb + lc)
     a, b, g = rng.uniform(0.15, 2.0, 3)
@@ -176,7 +177,8 @@ def test_three_centre_against_quadrature(oracle, la, lb, lc):
 
 
 # ------------------------------------------------------------------ derivatives
-@pytest.mark.parametrize("la,lb,lc", [(0, 0, 0), (1, 1, 0), (2, 1, 1), (2, 2, 1), (2, 0, 0)])
+@pytest.mark.parametrize("la,lb,lc", [(0, 0, 0), (1, 1, 0), (2, 1, 1), (2, 2, 1), (2, 0, 0),
+                                      (1, 0, 2), (2, 2, 2)])
 def test_centre_derivatives_fd_and_translation(oracle, la, lb, lc):
     rng = np.random.default_rng(200 + 9 * la + 3 * lb + lc)
     a, b, g = rng.uniform(0.15, 2.5, 3)

@@ -270,3 +270,30 @@ def test_zvector_solution_against_integral_level_forms(orc0, mol0):
     # the dense A+B agrees with the integral-level bilinear form
     u, w = V
     assert abs(u.reshape(-1) @ (A + B) @ w.reshape(-1) - orc0.apb_form(u, w)) <= 1e-12
+
+
+def test_d_aux_gradient_is_hellmann_feynman(oracle, mol0):
+    """With d auxiliary shells on carbon and K-fit exponents distinct from the
+    J-fit ones, the oracle's analytic gradient equals the 5-point finite
+    difference of re-solved eigenvalues (pins its l = 2 auxiliary integrals,
+    metric and derivative paths end to end)."""
+    aj = synth.build_aux(mol0.elements, True)
+    carb = [k for k, e in enumerate(mol0.elements) if e == "C"]
+    d = np.array([(a, 2, 0.3 / 1.32 ** 2) for a in carb], dtype=synth.SHELL_DTYPE)
+    aux_j = np.concatenate([aj, d])
+    aux_k = synth.build_aux(mol0.elements, False).copy()
+    aux_k["exp"] *= 1.3
+
+    def make(coords):
+        return oracle.RisOracle(coords, mol0.shells, aux_j, aux_k, mol0.C, mol0.mo_energy,
+                                mol0.nocc)
+
+    nst = 3
+    w, X = make(mol0.coords).tda_dense(nst)
+    g = make(mol0.coords).gradients(range(nst), X, atoms=[1])
+    for x in (0, 2):
+        def om(dd):
+            c = mol0.coords.copy()
+            c[1, x] += dd
+            return make(c).tda_dense(nst)[0]
+        np.testing.assert_allclose(g[:, 1, x], _fd5(om), rtol=1e-6, atol=1e-9)
