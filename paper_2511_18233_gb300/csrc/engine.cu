@@ -266,11 +266,12 @@ static void transpose_last2(const double* in, int nb, int na, int nr, double* ou
 
 // dst[r][c0 + c] = src[r][c] for c < ncol (FP32, row strides lds / ldd)
 __global__ void k_copy_cols(const float* __restrict__ src, int lds, float* __restrict__ dst, int ldd,
-                            int c0, int nrow, int ncol) {
+                            int c0, int nrow, int ncol, long long dbatch) {
+  // batch blockIdx.y: dst + blockIdx.y * dbatch (the same src for every batch)
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)nrow * ncol) return;
   const int r = (int)(t / ncol), c = (int)(t % ncol);
-  dst[(size_t)r * ldd + c0 + c] = src[(size_t)r * lds + c];
+  dst[(size_t)blockIdx.y * dbatch + (size_t)r * ldd + c0 + c] = src[(size_t)r * lds + c];
 }
 
 // out[c][a][b] = in[a][b][c]
@@ -1284,7 +1285,8 @@ static void tcg(int M, int N, int K, const float* ah, const float* al, int lda, 
                 cudaStream_t st, long long bsa = 0, int nba = 1) {
   TcOperand A, B;
   A.hi = ah; A.lo = al; A.rows = M; A.ld = lda; A.bstride = bsa; A.nb = nba;
-  B.hi = bh; B.lo = bl; B.rows = N; B.ld = ldb; B.bstride = bsb; B.nb = nb > 1 ? nb : 1;
+  B.hi = bh; B.lo = bl; B.rows = N; B.ld = ldb; B.bstride = bsb;
+  B.nb = (nb > 1 && bsb != 0) ? nb : 1;  // bsb == 0: one B shared by every batch
   tc_gemm(M, N, K, A, B, nb, e, err, st);
 }
 static TcEpilogue ep_split(float* h, float* l, long long rs, long long cs = 1, long long bsc = 0) {
@@ -2093,27 +2095,28 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
     WLl.ensure((size_t)nsu * nn * kp, st, true);
     split_f64(Rs.p, nsu * o, v, v, RSh.p, RSl.p, lv4, st);
     split_f64(Ls.p, nsu * o, v, v, LSh.p, LSl.p, lv4, st);
-    SBuf<float> RtH((size_t)v * lo4, st), RtL((size_t)v * lo4, st), t1H((size_t)nn * lv4, st),
-        t1L((size_t)nn * lv4, st);
-    for (int s = 0; s < nsu; s++) {
-      // D^R_s = C_o R_s C_v^T: t1 = C_o R_s (split), D = t1 C_v^T
-      split_f64_t(Rs.p + s * nov, o, v, v, RtH.p, RtL.p, lo4, st);
-      tcg(nn, v, o, CoH.p, CoL.p, lo4, RtH.p, RtL.p, lo4, 0, 1, ep_split(t1H.p, t1L.p, lv4), d_tcerr,
-          st);
-      tcg(nn, nn, v, t1H.p, t1L.p, lv4, CvH.p, CvL.p, lv4, 0, 1,
-          ep_f64(DR.p + (size_t)s * nn * nn, nn), d_tcerr, st);
-      // Q^T[nu][i] = sum_a C_v[nu][a] U[i][a] into W[:, 0:o]; C_o into W[:, o:2o]
-      for (int w = 0; w < (rpa ? 2 : 1); w++) {
-        float* Wh = (w == 0 ? WRh.p : WLh.p) + (size_t)s * nn * kp;
-        float* Wl = (w == 0 ? WRl.p : WLl.p) + (size_t)s * nn * kp;
-        const float* Uh = (w == 0 ? RSh.p : LSh.p) + (size_t)s * o * lv4;
-        const float* Ul = (w == 0 ? RSl.p : LSl.p) + (size_t)s * o * lv4;
-        tcg(nn, o, v, CvH.p, CvL.p, lv4, Uh, Ul, lv4, 0, 1, ep_split(Wh, Wl, kp), d_tcerr, st);
-        k_copy_cols<<<cdiv((long long)nn * o, 256), 256, 0, st>>>(CoH.p, lo4, Wh, kp, o, nn, o);
-        RIS_CHECK_LAUNCH();
-        k_copy_cols<<<cdiv((long long)nn * o, 256), 256, 0, st>>>(CoL.p, lo4, Wl, kp, o, nn, o);
-        RIS_CHECK_LAUNCH();
-      }
+    // every state in one launch per kind (batch index = state)
+    // D^R_s = C_o R_s C_v^T: t1_s = C_o R_s (split), D^R_s = t1_s C_v^T
+    SBuf<float> RtH((size_t)nsu * v * lo4, st), RtL((size_t)nsu * v * lo4, st),
+        t1H((size_t)nsu * nn * lv4, st), t1L((size_t)nsu * nn * lv4, st);
+    split_f64_t(Rs.p, o, v, v, RtH.p, RtL.p, lo4, st, nsu, nov, (long long)v * lo4);
+    tcg(nn, v, o, CoH.p, CoL.p, lo4, RtH.p, RtL.p, lo4, (long long)v * lo4, nsu,
+        ep_split(t1H.p, t1L.p, lv4, 1, (long long)nn * lv4), d_tcerr, st);
+    tcg(nn, nn, v, t1H.p, t1L.p, lv4, CvH.p, CvL.p, lv4, 0, nsu,
+        ep_f64(DR.p, nn, (long long)nn * nn), d_tcerr, st, (long long)nn * lv4, nsu);
+    // Q^T_s[nu][i] = sum_a C_v[nu][a] U_s[i][a] into W_s[:, 0:o]; C_o into W_s[:, o:2o]
+    for (int w = 0; w < (rpa ? 2 : 1); w++) {
+      float* Wh = w == 0 ? WRh.p : WLh.p;
+      float* Wl = w == 0 ? WRl.p : WLl.p;
+      const float* Uh = w == 0 ? RSh.p : LSh.p;
+      const float* Ul = w == 0 ? RSl.p : LSl.p;
+      tcg(nn, o, v, CvH.p, CvL.p, lv4, Uh, Ul, lv4, (long long)o * lv4, nsu,
+          ep_split(Wh, Wl, kp, 1, (long long)nn * kp), d_tcerr, st);
+      const dim3 gc(cdiv((long long)nn * o, 256), nsu);
+      k_copy_cols<<<gc, 256, 0, st>>>(CoH.p, lo4, Wh, kp, o, nn, o, (long long)nn * kp);
+      RIS_CHECK_LAUNCH();
+      k_copy_cols<<<gc, 256, 0, st>>>(CoL.p, lo4, Wl, kp, o, nn, o, (long long)nn * kp);
+      RIS_CHECK_LAUNCH();
     }
   }
   if (!mixed || rpa) {

@@ -244,17 +244,12 @@ __host__ __device__ constexpr double cfac(int l, int c) {
 //   x^0 = Lambda_0, x^1 = Lambda_1 / (2g), x^2 = Lambda_0 / (2g) + Lambda_2 / (4g^2);
 // sgn = -1 applies the ket sign (-1)^tau of the McMurchie-Davidson formula.
 __device__ __forceinline__ int herm1(int k, double g, double sgn, int* tau, double* c) {
-  if (k == 0) {
-    tau[0] = 0;
-    c[0] = 1.0;
+  if (k <= 1) {  // one term: the s and p auxiliary shells
+    tau[0] = k;
+    c[0] = k == 0 ? 1.0 : sgn * 0.5 / g;
     return 1;
   }
-  if (k == 1) {
-    tau[0] = 1;
-    c[0] = sgn * 0.5 / g;
-    return 1;
-  }
-  tau[0] = 0;
+  tau[0] = 0;  // k == 2
   c[0] = 0.5 / g;
   tau[1] = 2;
   c[1] = 0.25 / (g * g);
@@ -335,9 +330,10 @@ __global__ void __launch_bounds__(128) k_int3c(const int* __restrict__ pa, const
         const int ny = herm1(cy_(LC, ic), gam, -1.0, ty, fy);
         const int nz = herm1(cz_(LC, ic), gam, -1.0, tz, fz);
         double s = 0.0;
-        for (int jx = 0; jx < nx; jx++)
-          for (int jy = 0; jy < ny; jy++)
-            for (int jz = 0; jz < nz; jz++) {
+        const int mx = LC <= 1 ? 1 : nx, my = LC <= 1 ? 1 : ny, mz = LC <= 1 ? 1 : nz;
+        for (int jx = 0; jx < mx; jx++)
+          for (int jy = 0; jy < my; jy++)
+            for (int jz = 0; jz < mz; jz++) {
               const int kx = tx[jx], ky = ty[jy], kz = tz[jz];
               double sub = 0.0;
 #pragma unroll 1
@@ -436,9 +432,11 @@ __global__ void __launch_bounds__(128) k_int3c_deriv(
             const double eA = 2.0 * alpha * up - a_[x] * dn;
             const double eB = 2.0 * beta * upb - b_[x] * dnb;
             double r = 0.0;
-            for (int jx = 0; jx < nh[x]; jx++)
-              for (int jy = 0; jy < nh[y]; jy++)
-                for (int jz = 0; jz < nh[z]; jz++) {
+            // LC <= 1: one Hermite term per axis (loops of length 1 at compile time)
+            const int mx = LC <= 1 ? 1 : nh[x], my = LC <= 1 ? 1 : nh[y], mz = LC <= 1 ? 1 : nh[z];
+            for (int jx = 0; jx < mx; jx++)
+              for (int jy = 0; jy < my; jy++)
+                for (int jz = 0; jz < mz; jz++) {
                   const double fc = fh[x][jx] * fh[y][jy] * fh[z][jz];
                   double rr = 0.0;
 #pragma unroll 1
