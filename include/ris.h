@@ -98,6 +98,10 @@ typedef struct {
                          MOs with e_a <= e_LUMO + mo_window (Hartree; orbital energies sorted
                          within each block); amplitudes are then [nocc_act][nvir_act]
                          (ris_get_mo_window).  0 (default): all MOs */
+  int deriv_prefetch; /* 1 (default): ris_build_aux also starts the derivative integrals on a
+                         second, low-priority stream, overlapping the B build and the
+                         Davidson; the first gradient / coupling call waits for them.
+                         0: computed by the first derivative call */
 } ris_options;
 
 typedef struct {

@@ -135,6 +135,7 @@ ris_status ris_options_default(ris_options* opt) {
   opt->refine = 0;
   opt->precond = 0;
   opt->mo_window = 0.0;
+  opt->deriv_prefetch = 1;
   return RIS_OK;
 }
 
@@ -151,6 +152,7 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
   if (o.precision == RIS_MIXED && !(o.mixed_tol > 0)) return RIS_ERR_ARG;
   if (o.precond != 0 && o.precond != 1) return RIS_ERR_ARG;
   if (!(o.mo_window >= 0.0)) return RIS_ERR_ARG;
+  if (o.deriv_prefetch != 0 && o.deriv_prefetch != 1) return RIS_ERR_ARG;
   c->eng.opt = o;
   c->eng.device = o.device;
   if (o.profile) ris::prof_enable(true);
@@ -169,6 +171,13 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
     RIS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
     RIS_CUDA(cudaEventCreate(&c->eng.ev0));
     RIS_CUDA(cudaEventCreate(&c->eng.ev1));
+    if (o.deriv_prefetch) {
+      int lo = 0, hi = 0;
+      RIS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      RIS_CUDA(cudaStreamCreateWithPriority(&c->eng.st2, cudaStreamNonBlocking, lo));
+      RIS_CUDA(cudaEventCreateWithFlags(&c->eng.evA, cudaEventDisableTiming));
+      RIS_CUDA(cudaEventCreateWithFlags(&c->eng.evD, cudaEventDisableTiming));
+    }
   });
   if (s != RIS_OK) return s;
   *out = c.release();

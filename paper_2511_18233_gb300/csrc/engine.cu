@@ -109,6 +109,7 @@ static void free_shells(ShellSet& s, cudaStream_t st) {
 }
 
 void Engine::trim() {
+  join_D();
   free_shells(ao, st);
   free_shells(aux, st);
   free_pairs(pl, st);
@@ -139,6 +140,9 @@ Engine::~Engine() {
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   if (st) cudaStreamSynchronize(st);
+  if (st2) cudaStreamSynchronize(st2);
+  if (evA) cudaEventDestroy(evA);
+  if (evD) cudaEventDestroy(evD);
 }
 
 template <class T>
@@ -1006,6 +1010,7 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
   check(aos, nshell, kMaxLAO, "AO shell");
   check(auxJ, nJs, kMaxLAux, "J auxiliary shell");
   check(auxK, nKs, kMaxLAux, "K auxiliary shell");
+  join_D();  // a previous geometry's derivative integrals may still read the shells
   stage = 0;
   have_D = false;
   natm = natm_;
@@ -1137,6 +1142,14 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
                   std::to_string(info[0] ? info[0] : info[1]) + ")");
   nao = nao_;
   stage = 1;
+  if (opt.deriv_prefetch && st2) {  // derivative integrals behind the B build and Davidson
+    RIS_CUDA(cudaEventRecord(evA, st));
+    RIS_CUDA(cudaStreamWaitEvent(st2, evA, 0));
+    start_D(st2);
+    RIS_CUDA(cudaEventRecord(evD, st2));
+    D_pending = true;
+    have_D = true;
+  }
 }
 
 void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const double* eps_in) {
@@ -2010,19 +2023,35 @@ void Engine::davidson_rpa(int ns) {
 // ------------------------------------------------------------------ derivatives
 // Derivative integrals for the current geometry: FP64 storage, or FP32 in
 // mixed precision (the integral recursion itself is FP64 either way).
-void Engine::ensure_D() {
-  if (have_D) return;
+void Engine::start_D(cudaStream_t s) {
   const size_t plane = (size_t)nao * nao * nU;
   if (opt.precision == RIS_MIXED) {
     D.release();
-    Df.ensure(3 * plane, st);
-    RIS_CUDA(cudaMemsetAsync(Df.p, 0, sizeof(float) * 3 * plane, st));
-    int3c_deriv<float>(ao, aux, pl, xyz.p, Df.p, st);
+    Df.ensure(3 * plane, s);
+    RIS_CUDA(cudaMemsetAsync(Df.p, 0, sizeof(float) * 3 * plane, s));
+    int3c_deriv<float>(ao, aux, pl, xyz.p, Df.p, s);
   } else {
-    D.ensure(3 * plane, st);
-    RIS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * 3 * plane, st));
-    int3c_deriv<double>(ao, aux, pl, xyz.p, D.p, st);
+    D.ensure(3 * plane, s);
+    RIS_CUDA(cudaMemsetAsync(D.p, 0, sizeof(double) * 3 * plane, s));
+    int3c_deriv<double>(ao, aux, pl, xyz.p, D.p, s);
   }
+}
+
+// The main stream waits for derivative integrals started on st2; from then
+// on the buffer belongs to the main stream (its eventual free is ordered
+// after every use there).
+void Engine::join_D() {
+  if (!D_pending) return;
+  RIS_CUDA(cudaStreamWaitEvent(st, evD, 0));
+  if (D.p) D.st = st;
+  if (Df.p) Df.st = st;
+  D_pending = false;
+}
+
+void Engine::ensure_D() {
+  join_D();
+  if (have_D) return;
+  start_D(st);
   have_D = true;
 }
 

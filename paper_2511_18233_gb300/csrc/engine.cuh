@@ -66,7 +66,9 @@ struct FBuf {
 struct StreamOwner {
   cudaStream_t st = nullptr;
   bool own_stream = false;
+  cudaStream_t st2 = nullptr;  // low-priority side stream (derivative integrals)
   ~StreamOwner() {
+    if (st2) cudaStreamDestroy(st2);
     if (own_stream && st) cudaStreamDestroy(st);
   }
 };
@@ -106,6 +108,8 @@ struct Engine : StreamOwner {
   DBuf D;                   // derivative integrals [3][mu][nu][P_U] (FP64 path)
   FBuf Df;                  // the same in FP32 storage (mixed precision)
   bool have_D = false;
+  bool D_pending = false;             // D being computed on st2 (event evD)
+  cudaEvent_t evA = nullptr, evD = nullptr;
   int* d_info = nullptr;
 
   // MO data
@@ -152,6 +156,8 @@ struct Engine : StreamOwner {
   void pair_derivs(int npair, const int* pairs, int nx, const double* X_in, const double* Y_in,
                    double* out_dev);
   void ensure_D();
+  void start_D(cudaStream_t s);  // derivative integrals on stream s
+  void join_D();                 // make st wait for a pending D
   void apply(int nvec, const double* X, double* out, double* out2);
 
   // helpers

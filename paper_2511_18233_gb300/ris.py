@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("mem_budget", ctypes.c_size_t), ("occ_block", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("profile", ctypes.c_int), ("mixed_tol", ctypes.c_double), ("refine", ctypes.c_int),
-                ("precond", ctypes.c_int), ("mo_window", ctypes.c_double)]
+                ("precond", ctypes.c_int), ("mo_window", ctypes.c_double),
+                ("deriv_prefetch", ctypes.c_int)]
 
 
 class Shell(ctypes.Structure):

@@ -60,7 +60,9 @@ def footprint_bytes(nao: int, nocc: int, nJ: int, nK: int, nU: int, nstates: int
     precision, their FP32 hi/lo splits and the tensor-core operands of the
     (ab|P)_K transform) plus the larger of the Davidson work space and the
     derivative stage (the derivative integrals d(mu nu|P)/dR, the exchange
-    parts of a batch of pair densities and per-state densities).
+    parts of a batch of pair densities and per-state densities).  The
+    derivative integrals d(mu nu|P)/dR (FP32 in mixed precision) are computed
+    on a side stream from the auxiliary build on, so they count as persistent.
     """
     n, o = nao, nocc
     v = n - o
@@ -84,11 +86,12 @@ def footprint_bytes(nao: int, nocc: int, nJ: int, nK: int, nU: int, nstates: int
         dav += f * 2 * nb0 * v * _ld4(o)
     s = nstate_deriv
     nbp = min(s, 8)  # pairs sharing one pass over the derivative integrals
-    deriv = d * (3 * n * n * nU + nbp * (n * n * nK + 3 * n * nK + nU * nU) + s * n * n
+    dint = (f if mixed else d) * 3 * n * n * nU
+    deriv = d * (nbp * (n * n * nK + 3 * n * nK + nU * nU) + s * n * n
                  + 3 * s * n * nU + 4 * s * o * n + n * v + 2 * o * v * nK + 2 * n * o * nK)
     if mixed:
         deriv += f * 4 * s * (o * _ld4(v) + n * _ld4(2 * o))
-    total = aux + B + d * 2 * ns * nov + max(dav, deriv)
+    total = aux + B + dint + d * 2 * ns * nov + max(dav, deriv)
     return int(1.25 * total) + (32 << 20)
 
 

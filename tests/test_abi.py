@@ -44,6 +44,7 @@ def test_options_defaults(lib):
     assert o.cx == 0.25 and o.conv_tol == 1e-10 and o.max_iter == 100
     assert o.precision == ris.FP64 and o.rpa == 0 and o.screen_thr == 1e-14
     assert o.mixed_tol == 1e-6 and o.refine == 0 and o.profile == 0
+    assert o.precond == 0 and o.mo_window == 0.0 and o.deriv_prefetch == 1
 
 
 def test_create_rejects_bad_options(lib):
@@ -53,6 +54,10 @@ def test_create_rejects_bad_options(lib):
     o = ris.options(precision=7)
     assert lib.ris_create(ctypes.byref(h), ctypes.byref(o)) == -1
     o = ris.options(conv_tol=-1.0)
+    assert lib.ris_create(ctypes.byref(h), ctypes.byref(o)) == -1
+    o = ris.options(deriv_prefetch=2)
+    assert lib.ris_create(ctypes.byref(h), ctypes.byref(o)) == -1
+    o = ris.options(precond=3)
     assert lib.ris_create(ctypes.byref(h), ctypes.byref(o)) == -1
     assert lib.ris_create(None, None) == -1
     assert lib.ris_get_stats(None, None, 1) == -1

@@ -159,6 +159,36 @@ def test_full_pipeline_small(ris_mod, small):
     assert _rel(nac, nref) <= 1e-9
 
 
+def _grad_nac(c, ns):
+    om, Xg = c.excite(ns)
+    return om, c.gradient(range(ns)), c.nac([(0, 1), (1, 2)])
+
+
+@gpu
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_derivative_prefetch_same_results(ris_mod, small, precision):
+    """Derivative integrals started on the side stream at ris_build_aux give
+    the results of computing them in the first gradient call (same kernels,
+    same order: equal up to a 1e-10 relative margin), and a context reused
+    over a second geometry matches a fresh one."""
+    mol = small[0]
+    prec = ris_mod.MIXED if precision == "mixed" else ris_mod.FP64
+    a = _grad_nac(_ctx(ris_mod, mol, precision=prec, deriv_prefetch=0), 4)
+    c = _ctx(ris_mod, mol, precision=prec, deriv_prefetch=1)
+    b = _grad_nac(c, 4)
+    for x, y in zip(a, b):
+        assert _rel(x, y) <= 1e-10
+    xyz = mol.coords + 0.02 * np.random.default_rng(4).standard_normal(mol.coords.shape)
+    c.build_aux(xyz, mol.shells, mol.aux_j, mol.aux_k)
+    c.build_B(mol.C, mol.mo_energy, mol.nocc)
+    again = _grad_nac(c, 4)
+    f = ris_mod.Context(precision=prec, deriv_prefetch=0)
+    f.build_aux(xyz, mol.shells, mol.aux_j, mol.aux_k)
+    f.build_B(mol.C, mol.mo_energy, mol.nocc)
+    for x, y in zip(again, _grad_nac(f, 4)):
+        assert _rel(x, y) <= 1e-10
+
+
 @gpu
 def test_random_amplitudes_and_device_pointers(ris_mod, small):
     import torch

@@ -66,8 +66,9 @@ def test_footprint_estimate_grows_with_size():
     assert serve.footprint_bytes(1024, 162, 204, 84, 204, 10, 3, True) > 8 * base * 0.9
     assert serve.footprint_bytes(512, 81, 102, 42, 102, 10, 3, True) >= \
         serve.footprint_bytes(512, 81, 102, 42, 102, 5, 3, True)
-    # the derivative integrals alone, 3 nao^2 nU doubles, are a lower bound
-    assert base > 3 * 512 * 512 * 102 * 8
+    # the derivative integrals alone (3 nao^2 nU, FP32 in mixed precision) are a lower bound
+    assert base > 3 * 512 * 512 * 102 * 4
+    assert serve.footprint_bytes(512, 81, 102, 42, 102, 10, 3, False) > 3 * 512 * 512 * 102 * 8
 
 
 def test_molecule_dims_union_aux():
