@@ -358,6 +358,11 @@ def measure(precision, mol, args, world, local, dist):
                            f"of {src} bf16 x nominal TF32/BF16 (1.1/2.25); achieved counts the 3 TF32 passes"),
         "dgemm_fp64": (st["gemm_ms"], st["gemm_flops"] / 1e12, "tensor", "TFLOP/s", fp64_peak,
                        f"of {src} bf16 x nominal FP64/BF16 (1.25/2250)"),
+        # FP64-accurate products on the FP16 tensor cores: 55 digit-slice
+        # products per FP64 product, counted as FP16 tensor work
+        "emu_gemm_f64": (st["emu_gemm_ms"], 55 * st["emu_gemm_flops"] / 1e12, "tensor", "TFLOP/s",
+                         peaks["bf16_tflops"], f"of {src} bf16 (FP16 runs at the same rate); "
+                         "achieved counts the 55 slice products"),
         "int3c_deriv": (st["int3c_deriv_ms"], None, "alu", None, None,
                         "side stream: runs under the B build and Davidson, time not additive"),
         "int3c": (st["int3c_ms"], None, "alu", None, None, ""),

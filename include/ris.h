@@ -102,6 +102,9 @@ typedef struct {
                          second, low-priority stream, overlapping the B build and the
                          Davidson; the first gradient / coupling call waits for them.
                          0: computed by the first derivative call */
+  int emu_f64;        /* mixed precision: 1 (default) runs the Coulomb B transforms
+                         (the two MO transforms of (mu nu|P)_J) as FP64-accurate products
+                         on the FP16 tensor cores by exact operand splitting; 0: FP64 */
 } ris_options;
 
 typedef struct {
@@ -248,7 +251,9 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
  *   [26] 3xTF32 tensor-core GEMM ms, [27] its algorithmic flops (one per
  *   multiply-add pair of the product, the three TF32 passes counted once);
  *   [28] device bytes the context holds now, [29] the most it has held
- *   since it was created or last trimmed (its HBM footprint).
+ *   since it was created or last trimmed (its HBM footprint);
+ *   [30] FP64-emulating tensor-core GEMM ms, [31] its algorithmic FP64
+ *   flops (profile option, as [16]..[27]).
  */
 ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n);
 
@@ -299,6 +304,19 @@ int ris_debug_sym_eig(int m, int k, const double* H, double* w, double* V);
  * timed out, or another ris_status.
  */
 int ris_debug_gemm_tf32x3(int M, int N, int K, const double* A, const double* B, double* C);
+
+/*
+ * Test hook: C = A . B^T with the library's FP64-emulating tensor-core GEMM
+ * (the kernel behind the Coulomb transforms of RIS_MIXED): both operands are
+ * split exactly into ten 6-bit digit slices per row frame (Ozaki's
+ * error-free transformation) and multiplied on the FP16 tensor cores with
+ * exact FP32 accumulation.  Error per element below about
+ * K 2^-54 max_k|A_rk| max_k|B_ck| plus FP64 rounding of the result.
+ * A: [M][K], B: [N][K], C: [M][N], FP64 DEVICE pointers on the current
+ * device, finite values.  Synchronises the device; returns 0,
+ * RIS_ERR_TIMEOUT if a pipeline wait timed out, or another ris_status.
+ */
+int ris_debug_gemm_f64emu(int M, int N, int K, const double* A, const double* B, double* C);
 
 /*
  * Allocation-free 3xTF32 GEMM: C = A . B^T computed exactly like

@@ -136,6 +136,7 @@ ris_status ris_options_default(ris_options* opt) {
   opt->precond = 0;
   opt->mo_window = 0.0;
   opt->deriv_prefetch = 1;
+  opt->emu_f64 = 1;
   return RIS_OK;
 }
 
@@ -153,6 +154,7 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
   if (o.precond != 0 && o.precond != 1) return RIS_ERR_ARG;
   if (!(o.mo_window >= 0.0)) return RIS_ERR_ARG;
   if (o.deriv_prefetch != 0 && o.deriv_prefetch != 1) return RIS_ERR_ARG;
+  if (o.emu_f64 != 0 && o.emu_f64 != 1) return RIS_ERR_ARG;
   c->eng.opt = o;
   c->eng.device = o.device;
   if (o.profile) ris::prof_enable(true);
@@ -328,8 +330,9 @@ ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n) {
     double ms[ris::kProfN], work[ris::kProfN];
     ris::prof_collect(ms, work);
     for (int c = 0; c < ris::kProfN; c++) {
-      all[16 + 2 * c] = ms[c];
-      all[17 + 2 * c] = work[c];
+      const int slot = c == ris::kProfEmuGemm ? 30 : 16 + 2 * c;
+      all[slot] = ms[c];
+      all[slot + 1] = work[c];
     }
   } catch (const ris::Error&) {
     return RIS_ERR_CUDA;

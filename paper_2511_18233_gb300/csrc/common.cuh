@@ -44,7 +44,9 @@ extern std::atomic<long long> g_launches;
 
 // Optional per-kernel-class timing with CUDA events on the launching stream
 // (enabled by the profile option; off by default).
-enum ProfClass { kProfGemm = 0, kProfInt3c, kProfInt3cDeriv, kProfContract, kProfEig, kProfTcGemm, kProfN };
+enum ProfClass {
+  kProfGemm = 0, kProfInt3c, kProfInt3cDeriv, kProfContract, kProfEig, kProfTcGemm, kProfEmuGemm, kProfN
+};
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st, double work);
 void prof_enable(bool on);

@@ -115,7 +115,8 @@ void Engine::trim() {
   free_pairs(pl, st);
   if (d_jU) cudaFreeAsync(d_jU, st);
   if (d_kU) cudaFreeAsync(d_kU, st);
-  d_jU = d_kU = nullptr;
+  if (d_kJ) cudaFreeAsync(d_kJ, st);
+  d_jU = d_kU = d_kJ = nullptr;
   DBuf* dbs[] = {&xyz, &TJ, &TK, &MU, &dMU, &LJinv, &LKinv, &D, &C, &eps, &de, &BJ, &BKoo,
                  &BKvvD, &BKovR, &cKovP, &cKoo, &cKvv, &cKov, &cKooP, &omega, &X, &Y,
                  &w1, &w2, &w3, &w4, &w5, &w6, &w7, &w8};
@@ -235,6 +236,20 @@ __global__ void k_gather_sq(const double* __restrict__ src, int lds, const int* 
   if (t >= n * n) return;
   const int i = t / n, j = t % n;
   dst[t] = src[(size_t)map[i] * lds + map[j]];
+}
+
+// dst[r][c] = src[r'][map[c]] (rows of length lds), c < nc, with r' = r, or,
+// when n1 > 0, r = (i, j) -> r' = (j, i) for i < n0, j < n1 (row blocks
+// transposed).
+__global__ void k_gather_cols(const double* __restrict__ src, long long rows, int lds,
+                              const int* __restrict__ map, int nc, double* __restrict__ dst, int n1,
+                              int n0) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * nc) return;
+  long long r = t / nc;
+  const int c = (int)(t % nc);
+  if (n1 > 0) r = (r % n1) * n0 + r / n1;
+  dst[t] = src[(size_t)r * lds + map[c]];
 }
 
 __global__ void k_orb_diff(const double* __restrict__ eps, int nocc, int nvir, double* __restrict__ de) {
@@ -1099,8 +1114,24 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
       }
     if (d_jU) cudaFreeAsync(d_jU, st);
     if (d_kU) cudaFreeAsync(d_kU, st);
+    if (d_kJ) cudaFreeAsync(d_kJ, st);
     d_jU = upload(h_jU, st);
     d_kU = upload(h_kU, st);
+    // K fitting functions that are also J fitting functions (the minimal
+    // K set of s functions inside the s+p J set): the K half transform is
+    // then a column subset of the J one
+    d_kJ = nullptr;
+    {
+      std::vector<int> uJ(nU, -1);
+      for (int j = 0; j < nJ; j++) uJ[h_jU[j]] = j;
+      h_kJ.assign(nK, -1);
+      bool subset = true;
+      for (int k = 0; k < nK; k++) {
+        h_kJ[k] = uJ[h_kU[k]];
+        subset = subset && h_kJ[k] >= 0;
+      }
+      if (subset) d_kJ = upload(h_kJ, st);
+    }
   }
   // screened pair list; the estimate is scaled by the largest auxiliary
   // potential |V_P| <= N_P 2 pi / g (times g^-1/2 for p)
@@ -1194,10 +1225,15 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
   const double* Co = C.p;
   const double* Cv = C.p + o;
   // Coulomb: H[i][nu][P] = sum_mu C_mu,i T[mu][nu][P]; B[i][a][P]; B L^-T
+  // (mixed form: H as [nu][i][P], both transforms FP64-accurate on the
+  // tensor cores)
+  const bool emu = opt.precision == RIS_MIXED && opt.emu_f64;
   w2.ensure((size_t)o * n * std::max(nJ, nK), st);
-  dgemm(true, false, o, n * nJ, n, 1.0, Co, nmo, TJ.p, n * nJ, 0.0, w2.p, n * nJ, st);
   w3.ensure((size_t)std::max(nov, (long long)o * o) * std::max(nJ, nK), st);
-  {
+  if (emu) {
+    coulomb_emu(w2.p, w3.p);
+  } else {
+    dgemm(true, false, o, n * nJ, n, 1.0, Co, nmo, TJ.p, n * nJ, 0.0, w2.p, n * nJ, st);
     GemmBatch bt;
     bt.nb1 = o;
     bt.sB1 = (long long)n * nJ;
@@ -1207,13 +1243,23 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
   BJ.ensure((size_t)nov * nJ, st);
   dgemm(false, true, (int)nov, nJ, nJ, 1.0, w3.p, nJ, LJinv.p, nJ, 0.0, BJ.p, nJ, st);
   // exchange: oo and ov from C_o^T T^K, vv from C_v^T T^K
-  dgemm(true, false, o, n * nK, n, 1.0, Co, nmo, TK.p, n * nK, 0.0, w2.p, n * nK, st);
+  const double* HK = w2.p;
+  if (d_kJ) {  // C_o^T T^K: columns of C_o^T T^J
+    w5.ensure((size_t)o * n * nK, st);
+    const long long rows = (long long)o * n;
+    k_gather_cols<<<(unsigned)cdiv(rows * nK, 256), 256, 0, st>>>(w2.p, rows, nJ, d_kJ, nK, w5.p,
+                                                                  emu ? n : 0, o);
+    RIS_CHECK_LAUNCH();
+    HK = w5.p;
+  } else {
+    dgemm(true, false, o, n * nK, n, 1.0, Co, nmo, TK.p, n * nK, 0.0, w2.p, n * nK, st);
+  }
   {
     GemmBatch bt;
     bt.nb1 = o;
     bt.sB1 = (long long)n * nK;
     bt.sC1 = (long long)o * nK;
-    dgemm(true, false, o, nK, n, 1.0, Co, nmo, w2.p, nK, 0.0, w3.p, nK, st, bt);
+    dgemm(true, false, o, nK, n, 1.0, Co, nmo, HK, nK, 0.0, w3.p, nK, st, bt);
   }
   BKoo.ensure((size_t)o * o * nK, st);
   dgemm(false, true, o * o, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, BKoo.p, nK, st);
@@ -1224,7 +1270,7 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
     bt.nb1 = o;
     bt.sB1 = (long long)n * nK;
     bt.sC1 = (long long)v * nK;
-    dgemm(true, false, v, nK, n, 1.0, Cv, nmo, w2.p, nK, 0.0, w3.p, nK, st, bt);
+    dgemm(true, false, v, nK, n, 1.0, Cv, nmo, HK, nK, 0.0, w3.p, nK, st, bt);
     w4.ensure((size_t)nov * nK, st);
     dgemm(false, true, (int)nov, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // [i][a][R]
     cKov.ensure((size_t)nov * nK, st);
@@ -1312,6 +1358,42 @@ static TcEpilogue ep_f64(double* c, long long rs, long long bsc = 0, double alph
   TcEpilogue e;
   e.mode = kOutF64; e.c64 = c; e.rs = rs; e.cs = cs; e.bsc = bsc; e.alpha = alpha; e.beta = beta;
   return e;
+}
+
+// Mixed precision, Coulomb transforms (ia|P)_J = sum_mu,nu C_mu,i C_nu,a
+// (mu nu|P) as FP64-accurate products on the FP16 tensor cores (exact
+// operand splitting, gemm_emu.cu).  The J metric is ill-conditioned and the
+// MO transforms cancel heavily, so these stay at FP64 accuracy.
+// Transform 1: H[(nu,P)][i] = sum_mu T[(nu,P)][mu] C_o[mu][i], stored as
+// H[nu][i][P] (T symmetric in mu, nu; read through (mu nu|P) = T[mu][nu][P]);
+// transform 2: W[(i,P)][a] = sum_nu H[(i,P)][nu] C_v[nu][a], stored as
+// W[i][a][P].
+void Engine::coulomb_emu(double* H, double* W) {
+  const int o = nocc, v = nvir, n = nao;
+  if (!d_tcerr) {
+    RIS_CUDA(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
+    RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
+  }
+  const long long rT = (long long)n * nJ, rH = (long long)o * nJ;
+  RIS_REQUIRE(rT < (1ll << 31), RIS_ERR_ARG, "Coulomb transform too large for one product");
+  const int lk = ld8(n);
+  SBuf<__half> sT((size_t)kEmuSlices * rT * lk, st), sC((size_t)kEmuSlices * std::max(o, v) * lk, st);
+  SBuf<int> eT(rT, st), eC(std::max(o, v), st);
+  EmuOperand A, B;
+  A.s = sT.p; A.e = eT.p;
+  B.s = sC.p; B.e = eC.p;
+  // A[(nu,P)][mu] = T[mu][(nu,P)], B[i][mu] = C[mu][i]
+  emu_slice(TJ.p, (int)rT, n, 1, rT, A, st);
+  emu_slice(C.p, o, n, 1, nmo, B, st);
+  EmuEpilogue e1;
+  e1.c64 = H; e1.rin = nJ; e1.rld = rH; e1.rs = 1; e1.cs = nJ;
+  emu_gemm((int)rT, o, A, B, e1, d_tcerr, st);
+  // A[(i,P)][nu] = H[nu][(i,P)], B[a][nu] = C[nu][o + a]
+  emu_slice(H, (int)rH, n, 1, rH, A, st);
+  emu_slice(C.p + o, v, n, 1, nmo, B, st);
+  EmuEpilogue e2;
+  e2.c64 = W; e2.rin = nJ; e2.rld = (long long)v * nJ; e2.rs = 1; e2.cs = nJ;
+  emu_gemm((int)rH, v, A, B, e2, d_tcerr, st);
 }
 
 // Mixed precision: (ab|P)_K = sum_mu,nu C_mu,a C_nu,b (mu nu|P) by two

@@ -3,6 +3,7 @@
 #include <string>
 #include <vector>
 
+#include "gemm_emu.cuh"
 #include "gemm_tc.cuh"
 #include "ints.cuh"
 #include "la.cuh"
@@ -97,8 +98,10 @@ struct Engine : StreamOwner {
   ShellSet ao, aux;   // aux = union of the J and K sets, K functions first
   int nJ = 0, nK = 0, nU = 0;
   std::vector<int> h_jU, h_kU;  // J / K function -> union function
+  std::vector<int> h_kJ;        // K function -> J function (-1: none)
   int* d_jU = nullptr;
   int* d_kU = nullptr;
+  int* d_kJ = nullptr;  // K function -> J column, when every K function is also a J function
   // functions of each atom (CSR): AO functions and union auxiliary functions
   SBuf<int> aoPtr, aoList, axPtr, axList;
   PairList pl;
@@ -166,6 +169,7 @@ struct Engine : StreamOwner {
   void apply_exchange_mixed(const double* Z, int nvec, double* out, double alpha, double beta);
   void prepare_mixed();
   void build_Kvv_tc(double* out);
+  void coulomb_emu(double* H, double* W);  // H [nu][i][P], W [i][a][P] (mixed form)
   // exchange part of Gamma / Omega for one (U,V) pair with weight f (3xTF32);
   // US/VS: splits of U, V [i][a]; WU/WV: [Q^T | C_o] splits of U and V;
   // Gamma accumulated in FP64 (Gam) or, when Gam32 is given, written in FP32

@@ -23,35 +23,17 @@
 #include <mutex>
 
 #include "gemm_tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace ris {
 
 namespace {
+using namespace tcx;
 
 constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
 constexpr int TILE_BYTES = BM * BK * 4;                      // 16 KB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;                  // hi/lo of A and B
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr long long kWaitCycles = 2000000000LL;
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static std::mutex mu;
-  static EncodeTiledFn fn = nullptr;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    RIS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-    RIS_REQUIRE(p && q == cudaDriverEntryPointSuccess, RIS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    fn = (EncodeTiledFn)p;
-  }
-  return fn;
-}
 
 // 3-D map {K, rows, batch} of FP32, box {32, 128, 1}, 128-byte swizzle.
 CUtensorMap make_map(const float* base, int K, int rows, int ld, long long bstride, int nb) {
@@ -68,45 +50,6 @@ CUtensorMap make_map(const float* base, int K, int rows, int ld, long long bstri
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   RIS_REQUIRE(r == CUDA_SUCCESS, RIS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return m;
-}
-
-__device__ __forceinline__ uint32_t sa(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(sa(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_test(b, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* m, uint64_t* bar, int x, int y,
-                                         int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sa(dst)),
-      "l"(m), "r"(sa(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
 }
 
 // K-major operand tile of 128 rows x 128 bytes with 128-byte swizzle:
@@ -130,11 +73,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
       : "memory");
 }
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
-               : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
   asm volatile(

@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_sym_eig", "ris_debug_dgemm",
+           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_gemm_f64emu", "ris_debug_sym_eig", "ris_debug_dgemm",
            "ris_gemm_tf32x3_noalloc",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("profile", ctypes.c_int), ("mixed_tol", ctypes.c_double), ("refine", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mo_window", ctypes.c_double),
-                ("deriv_prefetch", ctypes.c_int)]
+                ("deriv_prefetch", ctypes.c_int), ("emu_f64", ctypes.c_int)]
 
 
 class Shell(ctypes.Structure):
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
     L.ris_get_stats.argtypes = [P, ctypes.POINTER(d), i]
     L.ris_debug_boys.argtypes = [i, P, P, P]
     L.ris_debug_gemm_tf32x3.argtypes = [i, i, i, P, P, P]
+    L.ris_debug_gemm_f64emu.argtypes = [i, i, i, P, P, P]
     L.ris_debug_sym_eig.argtypes = [i, i, P, P, P]
     d = ctypes.c_double
     L.ris_debug_dgemm.argtypes = [i, i, i, i, i, d, P, i, P, i, d, P, i]
@@ -255,7 +256,8 @@ class Context:
                  19: "int3c_triples", 20: "int3c_deriv_ms", 21: "int3c_deriv_triples",
                  22: "contract_ms", 23: "contract_bytes", 24: "eig_ms", 25: "eig_calls",
                  26: "tc_gemm_ms", 27: "tc_gemm_flops", 6: "refine_products",
-                 28: "bytes_held", 29: "bytes_peak", 7: "residual_max"}
+                 28: "bytes_held", 29: "bytes_peak", 7: "residual_max", 30: "emu_gemm_ms",
+                 31: "emu_gemm_flops"}
 
     def stats(self):
         out = (ctypes.c_double * 32)()
@@ -287,6 +289,22 @@ def debug_gemm_tf32x3(A, B):
     torch.cuda.synchronize()
     if st != 0:
         raise RisError(st, "ris_debug_gemm_tf32x3 failed")
+    return C_t.cpu().numpy()
+
+
+def debug_gemm_f64emu(A, B):
+    """C = A B^T through the library's FP64-emulating tensor-core GEMM
+    (numpy in/out)."""
+    import torch
+    A_t = torch.as_tensor(np.ascontiguousarray(A, dtype=np.float64), device="cuda")
+    B_t = torch.as_tensor(np.ascontiguousarray(B, dtype=np.float64), device="cuda")
+    M, K = A_t.shape
+    N = B_t.shape[0]
+    C_t = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    st = load().ris_debug_gemm_f64emu(M, N, K, A_t.data_ptr(), B_t.data_ptr(), C_t.data_ptr())
+    torch.cuda.synchronize()
+    if st != 0:
+        raise RisError(st, "ris_debug_gemm_f64emu failed")
     return C_t.cpu().numpy()
 
 

@@ -45,6 +45,10 @@ from . import synth
 ANGSTROM = synth.ANGSTROM
 
 
+def _ld8(k: int) -> int:
+    return (k + 7) & ~7
+
+
 def _ld4(n: int) -> int:
     return (n + 3) // 4 * 4
 
@@ -70,7 +74,7 @@ def footprint_bytes(nao: int, nocc: int, nJ: int, nK: int, nU: int, nstates: int
     M = max(nJ, nK)
     d, f = 8, 4
     aux = d * (n * n * (nJ + nK) + 4 * nU * nU + nJ * nJ + nK * nK + M * M)
-    B = d * (n * n + 3 * n + nov + o * n * M + max(v * n * nK, o * n * M)
+    B = d * (n * n + 3 * n + nov + o * n * M + o * n * nK + max(v * n * nK, o * n * M)
              + max(max(nov, o * o) * M, v * v * nK) + nov * nJ + 2 * o * o * nK
              + 3 * v * v * nK)
     if mixed:
@@ -78,6 +82,9 @@ def footprint_bytes(nao: int, nocc: int, nJ: int, nK: int, nU: int, nstates: int
                   + 2 * n * (_ld4(o) + _ld4(v))) + d * o * o * nK
         # (ab|P)_K on tensor cores: T^K and H splits, C_v^T split, FP64 G
         B += f * 2 * _ld4(n) * (nK * n + v * nK + v) + d * v * nK * v
+        # Coulomb transforms on the tensor cores: ten FP16 digit slices of T^J
+        # and of C, row exponents
+        B += 2 * 10 * (n * nJ + max(o, v)) * _ld8(n) + 4 * (n * nJ + max(o, v))
     ns = nstates
     nb0 = min(nov, ns + min(ns, 8))
     maxsp = min(max(nb0 + 2 * ns, 8 * ns), 256, nov)

@@ -71,3 +71,37 @@ def test_d_aux_mixed_stated_error(ris_mod, case):
     assert np.max(np.abs(om - w[:4])) <= 1e-6
     g = c.gradient([0, 2])
     assert np.max(np.abs(g - orc.gradients([0, 2], X[:4]))) <= 1e-5
+
+
+@gpu
+@pytest.mark.parametrize("rpa", [0, 1])
+def test_k_set_inside_j_set_in_another_order(ris_mod, oracle, rpa):
+    """K functions that are J functions listed in another order: the K half
+    transforms are then gathered from the J ones (TDA: A X, energies and
+    gradients; RPA: (A + B) X and (A - B) X, whose B part reads the gathered
+    ov block)."""
+    mol = synth.workload(0)
+    aux_j = synth.build_aux(mol.elements, True)
+    aux_k = synth.build_aux(mol.elements, False)[::-1].copy()
+    orc = oracle.RisOracle(mol.coords, mol.shells, aux_j, aux_k, mol.C, mol.mo_energy, mol.nocc)
+    c = ris_mod.Context(rpa=rpa)
+    c.build_aux(mol.coords, mol.shells, aux_j, aux_k)
+    c.build_B(mol.C, mol.mo_energy, mol.nocc)
+    Xr = synth.random_amplitudes(3, mol.nocc, mol.nvir, seed=21)
+    A, B = orc.dense_AB()
+    x = Xr.reshape(3, -1)
+    if rpa:
+        p, m = c.apply(Xr)
+        for got, M in ((p, A + B), (m, A - B)):
+            ref = (x @ M.T).reshape(Xr.shape)
+            assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+        return
+    got = c.apply(Xr)
+    ref = (x @ A.T).reshape(Xr.shape)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    w, X = orc.tda_dense(4)
+    om, Xg = c.excite(3)
+    np.testing.assert_allclose(om, w[:3], rtol=1e-9)
+    g = c.gradient([0, 2], X=np.ascontiguousarray(X[:3]))
+    gr = orc.gradients([0, 2], X[:3])
+    assert np.max(np.abs(g - gr)) <= 1e-9 * np.max(np.abs(gr))
