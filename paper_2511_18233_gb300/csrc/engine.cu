@@ -1241,7 +1241,13 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
     dgemm(true, false, v, nJ, n, 1.0, Cv, nmo, w2.p, nJ, 0.0, w3.p, nJ, st, bt);
   }
   BJ.ensure((size_t)nov * nJ, st);
-  dgemm(false, true, (int)nov, nJ, nJ, 1.0, w3.p, nJ, LJinv.p, nJ, 0.0, BJ.p, nJ, st);
+  if (emu) {  // B[(i,a)][R] = sum_P W[(i,a)][P] L_J^-1[R][P]
+    EmuEpilogue e;
+    e.c64 = BJ.p; e.rs = nJ; e.cs = 1;
+    emu_abt((int)nov, nJ, nJ, w3.p, nJ, 1, LJinv.p, nJ, 1, e);
+  } else {
+    dgemm(false, true, (int)nov, nJ, nJ, 1.0, w3.p, nJ, LJinv.p, nJ, 0.0, BJ.p, nJ, st);
+  }
   // exchange: oo and ov from C_o^T T^K, vv from C_v^T T^K
   const double* HK = w2.p;
   if (d_kJ) {  // C_o^T T^K: columns of C_o^T T^J
@@ -1295,7 +1301,13 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
     dgemm(false, true, v * v, nK, nK, 1.0, w3.p, nK, LKinv.p, nK, 0.0, w4.p, nK, st);  // B[a][b][R]
   }
   cKvv.ensure((size_t)v * v * nK, st);
-  dgemm(false, false, v * v, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKvv.p, nK, st);
+  if (emu) {  // c[(a,b)][Q] = sum_R B[(a,b)][R] L_K^-1[R][Q]
+    EmuEpilogue e;
+    e.c64 = cKvv.p; e.rs = nK; e.cs = 1;
+    emu_abt(v * v, nK, nK, w4.p, nK, 1, LKinv.p, 1, nK, e);
+  } else {
+    dgemm(false, false, v * v, nK, nK, 1.0, w4.p, nK, LKinv.p, nK, 0.0, cKvv.p, nK, st);
+  }
   BKvvD.ensure((size_t)v * v * nK, st);
   transpose_last2(w4.p, v, v, nK, BKvvD.p, st);  // [b][R][a]
   if (opt.precision == RIS_MIXED) prepare_mixed();
@@ -1370,30 +1382,33 @@ static TcEpilogue ep_f64(double* c, long long rs, long long bsc = 0, double alph
 // W[i][a][P].
 void Engine::coulomb_emu(double* H, double* W) {
   const int o = nocc, v = nvir, n = nao;
+  const long long rT = (long long)n * nJ, rH = (long long)o * nJ;
+  RIS_REQUIRE(rT < (1ll << 31), RIS_ERR_ARG, "Coulomb transform too large for one product");
+  // H[(nu,P)][i]: A[(nu,P)][mu] = T[mu][(nu,P)], B[i][mu] = C[mu][i]
+  EmuEpilogue e1;
+  e1.c64 = H; e1.rin = nJ; e1.rld = rH; e1.rs = 1; e1.cs = nJ;
+  emu_abt((int)rT, o, n, TJ.p, 1, rT, C.p, 1, nmo, e1);
+  // W[(i,P)][a]: A[(i,P)][nu] = H[nu][(i,P)], B[a][nu] = C[nu][o + a]
+  EmuEpilogue e2;
+  e2.c64 = W; e2.rin = nJ; e2.rld = (long long)v * nJ; e2.rs = 1; e2.cs = nJ;
+  emu_abt((int)rH, v, n, H, 1, rH, C.p + o, 1, nmo, e2);
+}
+
+void Engine::emu_abt(int M, int N, int K, const double* A, long long rsA, long long ksA,
+                     const double* B, long long rsB, long long ksB, const EmuEpilogue& ep) {
   if (!d_tcerr) {
     RIS_CUDA(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
     RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
   }
-  const long long rT = (long long)n * nJ, rH = (long long)o * nJ;
-  RIS_REQUIRE(rT < (1ll << 31), RIS_ERR_ARG, "Coulomb transform too large for one product");
-  const int lk = ld8(n);
-  SBuf<__half> sT((size_t)kEmuSlices * rT * lk, st), sC((size_t)kEmuSlices * std::max(o, v) * lk, st);
-  SBuf<int> eT(rT, st), eC(std::max(o, v), st);
-  EmuOperand A, B;
-  A.s = sT.p; A.e = eT.p;
-  B.s = sC.p; B.e = eC.p;
-  // A[(nu,P)][mu] = T[mu][(nu,P)], B[i][mu] = C[mu][i]
-  emu_slice(TJ.p, (int)rT, n, 1, rT, A, st);
-  emu_slice(C.p, o, n, 1, nmo, B, st);
-  EmuEpilogue e1;
-  e1.c64 = H; e1.rin = nJ; e1.rld = rH; e1.rs = 1; e1.cs = nJ;
-  emu_gemm((int)rT, o, A, B, e1, d_tcerr, st);
-  // A[(i,P)][nu] = H[nu][(i,P)], B[a][nu] = C[nu][o + a]
-  emu_slice(H, (int)rH, n, 1, rH, A, st);
-  emu_slice(C.p + o, v, n, 1, nmo, B, st);
-  EmuEpilogue e2;
-  e2.c64 = W; e2.rin = nJ; e2.rld = (long long)v * nJ; e2.rs = 1; e2.cs = nJ;
-  emu_gemm((int)rH, v, A, B, e2, d_tcerr, st);
+  const int lk = ld8(K);
+  SBuf<__half> sA((size_t)kEmuSlices * M * lk, st), sB((size_t)kEmuSlices * N * lk, st);
+  SBuf<int> eA(M, st), eB(N, st);
+  EmuOperand a, b;
+  a.s = sA.p; a.e = eA.p;
+  b.s = sB.p; b.e = eB.p;
+  emu_slice(A, M, K, rsA, ksA, a, st);
+  emu_slice(B, N, K, rsB, ksB, b, st);
+  emu_gemm(M, N, a, b, ep, d_tcerr, st);
 }
 
 // Mixed precision: (ab|P)_K = sum_mu,nu C_mu,a C_nu,b (mu nu|P) by two

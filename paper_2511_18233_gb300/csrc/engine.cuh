@@ -170,6 +170,10 @@ struct Engine : StreamOwner {
   void prepare_mixed();
   void build_Kvv_tc(double* out);
   void coulomb_emu(double* H, double* W);  // H [nu][i][P], W [i][a][P] (mixed form)
+  // C = A B^T, element (r, k) of A at A[r rsA + k ksA] (B likewise), as an
+  // FP64-accurate product on the tensor cores
+  void emu_abt(int M, int N, int K, const double* A, long long rsA, long long ksA, const double* B,
+               long long rsB, long long ksB, const EmuEpilogue& ep);
   // exchange part of Gamma / Omega for one (U,V) pair with weight f (3xTF32);
   // US/VS: splits of U, V [i][a]; WU/WV: [Q^T | C_o] splits of U and V;
   // Gamma accumulated in FP64 (Gam) or, when Gam32 is given, written in FP32

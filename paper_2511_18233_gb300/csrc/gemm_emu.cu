@@ -12,7 +12,7 @@
 // for K <= 512, every V_d with d <= 9 (at most eight terms) stays below 2^24
 // and is summed exactly in its FP32 tensor-memory accumulator; V_10 and
 // V_11 (nine and ten terms) may lose their last bit, 2^-60 below the frame.
-// The epilogue combines the ten accumulators in FP64.
+// The epilogue combines the ten accumulators in 64-bit integers and FP64.
 //
 // Kernel (one 128 x BN output tile per CTA, BN <= 48, 128 threads):
 //   warp 0 / lane 0 : TMA producer, 4-stage ring; a stage is K = 16 of all
@@ -47,6 +47,7 @@ constexpr int TMEM_COLS = 512;
 static_assert(NG * EMAXBN <= TMEM_COLS, "accumulators exceed tensor memory");
 static_assert(ESMEM <= 232448, "pipeline exceeds shared memory");
 static_assert(kFracBits <= 63, "row frame exceeds 64-bit integers");
+static_assert(NG == 10 && kEmuBeta == 6, "the epilogue's integer combination assumes 10 x 6 bits");
 
 // 3-D map {K, rows, slice} of FP16 digits, box {16, box_rows, S}, 32-byte swizzle.
 CUtensorMap make_map(const EmuOperand& op, int box_rows) {
@@ -214,9 +215,16 @@ __global__ void __launch_bounds__(128, 1) k_emu_gemm(const __grid_constant__ CUt
     for (int j = 0; j < 8 && live; j++) {
       const int col = n0 + c0 + j;
       if (col >= args.N) break;
-      double s = (double)v[NG - 1][j];
+      // sum_g V_g 2^(-6g) in 64-bit integers (the V_g are integers, below
+      // 2^24 for g <= 7 and 2^25 for g = 8, 9): hi = V_0 2^12 + V_1 2^6 + V_2
+      // and lo = sum_{g>=3} V_g 2^(6(9-g)) < 2^61, both exact; then two
+      // conversions and one FMA in FP64
+      const long long hi = __float2ll_rn(v[0][j]) * 4096 + __float2ll_rn(v[1][j]) * 64 +
+                           __float2ll_rn(v[2][j]);
+      long long lo = 0;
 #pragma unroll
-      for (int g = NG - 2; g >= 0; g--) s = fma(s, 0x1p-6, (double)v[g][j]);
+      for (int g = 3; g < NG; g++) lo += __float2ll_rn(v[g][j]) * (1ll << (kEmuBeta * (NG - 1 - g)));
+      const double s = fma((double)hi, 0x1p-12, (double)lo * 0x1p-54);
       const double x = ldexp(s, er + args.eb[col] - 2 * kEmuBeta);
       double* p = ep.c64 + roff + emu_off(col, ep.cin, ep.cld, ep.cs);
       *p = ep.beta == 0.0 ? ep.alpha * x : fma(ep.alpha, x, ep.beta * *p);

@@ -409,7 +409,8 @@ void tri_inverse(const double* L, double* Linv, int n, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ eigensolver
-constexpr int kEigT = 512;
+constexpr int kEigT = 256;
+constexpr int kEigMaxM = 256;  // largest subspace (Davidson caps it at 256)
 
 size_t eig_work_size(int m) { return (size_t)m * m + 3 * (size_t)m + 64 + 64 * (size_t)m; }
 
@@ -487,12 +488,12 @@ __global__ void __launch_bounds__(kEigT) k_eig_tridiag(const double* H, int ldH,
   extern __shared__ double sm_A[];
   __shared__ double red[33];
   __shared__ double sh_alpha, sh_tau;
+  __shared__ double p[kEigMaxM];  // A_sub v of the current step
   EigWork W(work, m);
   double* A = use_smem ? sm_A : W.A;
   double* d = W.d;
   double* e = W.e;
   double* tau = W.tau;
-  double* p = W.Z;  // scratch (m) before the eigenvectors exist
   const int tid = threadIdx.x;
   for (size_t ij = tid; ij < (size_t)m * m; ij += kEigT) {
     const int i = (int)(ij / m), j = (int)(ij % m);
@@ -585,13 +586,15 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work, int a
   double* du = dd + m;
   double* du2 = du + m;
   double* piv = du2 + m;
-  float* df = (float*)(piv + m);
+  double* tau = piv + m;
+  float* df = (float*)(tau + m);
   float* e2f = df + m;
-  double* As = piv + m + m;  // after the two float arrays (m doubles)
+  double* As = tau + m + m;  // after the two float arrays (m doubles)
   for (int i = tid; i < m; i += kEigVecT) {
     d[i] = W.d[i];
     e[i] = W.e[i];
     e2[i] = W.e[i] * W.e[i];
+    tau[i] = W.tau[i];
     df[i] = (float)W.d[i];
     e2f[i] = (float)(W.e[i] * W.e[i]);
   }
@@ -693,16 +696,22 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work, int a
     W.lam[j] = lj;
   }
   __syncthreads();
-  // back-transformation, H_{m-3} applied first
-  for (int c = m - 3; c >= 0; c--) {
-    const double t = W.tau[c];
-    if (t == 0.0) continue;
-    double part = 0.0;
-    for (int i = c + 1 + tid; i < m; i += kEigVecT) part += A[(size_t)i * m + c] * z[i];
-    const double f = t * block_sum<kEigVecT>(part, red);
-    for (int i = c + 1 + tid; i < m; i += kEigVecT) z[i] -= f * A[(size_t)i * m + c];
-    __syncthreads();
+  // back-transformation, H_{m-3} applied first, by one warp (each lane owns
+  // the same elements of z in the dot product and in the update, so the
+  // steps need no barrier)
+  if (tid < 32) {
+    for (int c = m - 3; c >= 0; c--) {
+      const double t = tau[c];
+      if (t == 0.0) continue;
+      double part = 0.0;
+      for (int i = c + 1 + tid; i < m; i += 32) part += A[(size_t)i * m + c] * z[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      const double f = t * part;
+      for (int i = c + 1 + tid; i < m; i += 32) z[i] -= f * A[(size_t)i * m + c];
+    }
   }
+  __syncthreads();
   for (int i = tid; i < m; i += kEigVecT) W.Z[(size_t)j * m + i] = z[i];
 }
 
@@ -711,16 +720,23 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work, int a
 __global__ void __launch_bounds__(kEigT) k_eig_finish(int m, int k, double* w, double* V,
                                                       double* work) {
   __shared__ double red[33];
+  __shared__ double lam[64], bnd[2];
   EigWork W(work, m);
   const int tid = threadIdx.x;
-  double glo = 0.0, ghi = 0.0;
-  tri_bounds(W.d, W.e, m, glo, ghi);
-  const double tnorm = fmax(fmax(fabs(glo), fabs(ghi)), 1e-300);
+  for (int i = tid; i < k; i += kEigT) lam[i] = W.lam[i];
+  if (tid == 0) {
+    double glo = 0.0, ghi = 0.0;
+    tri_bounds(W.d, W.e, m, glo, ghi);
+    bnd[0] = glo;
+    bnd[1] = ghi;
+  }
+  __syncthreads();
+  const double tnorm = fmax(fmax(fabs(bnd[0]), fabs(bnd[1])), 1e-300);
   const double gap_tol = 1e-7 * tnorm;
   double* Z = W.Z;
   for (int j = 1; j < k; j++) {
     for (int i = 0; i < j; i++) {
-      if (fabs(W.lam[j] - W.lam[i]) > gap_tol) continue;
+      if (fabs(lam[j] - lam[i]) > gap_tol) continue;
       double part = 0.0;
       for (int q = tid; q < m; q += kEigT) part += Z[(size_t)i * m + q] * Z[(size_t)j * m + q];
       const double s = block_sum<kEigT>(part, red);
@@ -733,18 +749,19 @@ __global__ void __launch_bounds__(kEigT) k_eig_finish(int m, int k, double* w, d
       __syncthreads();
     }
   }
-  for (int j = tid; j < k; j += kEigT) w[j] = W.lam[j];
+  for (int j = tid; j < k; j += kEigT) w[j] = lam[j];
   for (size_t i = tid; i < (size_t)k * m; i += kEigT) V[i] = Z[i];
 }
 
 void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
                     cudaStream_t st) {
   RIS_REQUIRE(k >= 1 && k <= 64 && k <= m, RIS_ERR_ARG, "sym_eig_lowest: bad k");
+  RIS_REQUIRE(m <= kEigMaxM, RIS_ERR_ARG, "sym_eig_lowest: subspace larger than 256");
   const size_t smem_max = 200 * 1024;
   ensure_smem_attr((const void*)k_eig_tridiag, (int)smem_max);
   const size_t need = (size_t)m * m * sizeof(double);
   const int use_smem = need <= smem_max;
-  size_t vec_smem = 10 * (size_t)m * sizeof(double);
+  size_t vec_smem = 11 * (size_t)m * sizeof(double);
   RIS_REQUIRE(vec_smem <= 200 * 1024, RIS_ERR_ARG, "sym_eig_lowest: subspace too large");
   const int a_smem = vec_smem + need <= 200 * 1024;
   if (a_smem) vec_smem += need;

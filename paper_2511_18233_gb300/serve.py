@@ -85,6 +85,8 @@ def footprint_bytes(nao: int, nocc: int, nJ: int, nK: int, nU: int, nstates: int
         # Coulomb transforms on the tensor cores: ten FP16 digit slices of T^J
         # and of C, row exponents
         B += 2 * 10 * (n * nJ + max(o, v)) * _ld8(n) + 4 * (n * nJ + max(o, v))
+        # and of the metric products B^J = W L_J^-T, c^K_vv = B^K_vv L_K^-1
+        B += 2 * 10 * (max(nov, v * v) + M) * _ld8(M) + 4 * (max(nov, v * v) + M)
     ns = nstates
     nb0 = min(nov, ns + min(ns, 8))
     maxsp = min(max(nb0 + 2 * ns, 8 * ns), 256, nov)
