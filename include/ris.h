@@ -297,6 +297,16 @@ int ris_debug_dgemm(int transA, int transB, int m, int n, int k, double alpha, c
 int ris_debug_sym_eig(int m, int k, const double* H, double* w, double* V);
 
 /*
+ * Test hook: the same with the FP32 form of the eigensolver used by the
+ * mixed precision Davidson (m <= 200): FP32 Householder reduction,
+ * multisection and inverse iteration; FP64 normalisation and Rayleigh
+ * quotients; vectors of eigenvalues closer than 1e-4 ||H|| orthonormalised
+ * and rotated onto the Ritz vectors of their span in FP64.  Residuals
+ * |H v - w v| of a few FP32 ulps of ||H||.  Returns RIS_ERR_ARG for m > 200.
+ */
+int ris_debug_sym_eig_f32(int m, int k, const double* H, double* w, double* V);
+
+/*
  * Test hook: C = A . B^T with the library's 3xTF32 tensor-core GEMM (the
  * kernel behind RIS_MIXED).  A: [M][K], B: [N][K], C: [M][N], FP64 DEVICE
  * pointers on the current device (inputs are rounded to FP32 and split).

@@ -1754,6 +1754,12 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
       ework(eig_work_size(maxsp), st);
   SBuf<int> idxbuf((size_t)std::max(nb0, ns) + 8, st);
   int* d_idx = idxbuf.p;
+  // Mixed form: the subspace eigenproblem in FP32 (Ritz residuals of about
+  // 1e-7 ||H||, below its tolerance), back to FP64 if the residuals stall.
+  bool eig32 = mixed && maxsp <= 200;
+  bool s32 = false;  // S came from the FP32 solver
+  int stall = 0;
+  double rprev = 0.0;
   auto product = [&](const double* x, int nv, double* y) {
     if (mixed)
       apply_A_mixed(x, nv, y);
@@ -1821,7 +1827,8 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
   const double drop = 1e-10;
   for (it = 0; it < opt.max_iter; it++) {
     const int nk = std::min(m, std::max(ns, kkeep));
-    sym_eig_lowest(Hs.p, maxsp, m, nk, w.p, S.p, ework.p, st);
+    s32 = eig32 && sym_eig_lowest_f32(Hs.p, maxsp, m, nk, w.p, S.p, ework.p, st);
+    if (!s32) sym_eig_lowest(Hs.p, maxsp, m, nk, w.p, S.p, ework.p, st);
     dgemm(false, false, ns, (int)n, m, 1.0, S.p, m, V.p, (int)n, 0.0, Xr.p, (int)n, st);
     dgemm(false, false, ns, (int)n, m, 1.0, S.p, m, AV.p, (int)n, 0.0, AXr.p, (int)n, st);
     k_residual<<<cdiv(n * ns, 256), 256, 0, st>>>(AXr.p, Xr.p, w.p, n, ns, Rr.p);
@@ -1839,17 +1846,45 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
       converged = true;
       break;
     }
+    if (s32) {  // three iterations without a 10% drop of the largest residual
+      stall = it > 0 && rmax > 0.9 * rprev ? stall + 1 : 0;
+      if (stall >= 3) eig32 = false;
+    }
+    rprev = rmax;
     int nt = (int)u.size();
     RIS_CUDA(cudaMemcpyAsync(d_idx, u.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
     precondition(nt);
     if (m + nt > maxsp) {  // restart with the lowest Ritz vectors
-      const int keep = std::min(nk, maxsp - nt);
-      dgemm(false, false, keep, (int)n, m, 1.0, S.p, m, V.p, (int)n, 0.0, tmp.p, (int)n, st);
+      int keep = std::min(nk, maxsp - nt);
+      const double* Sk = S.p;
+      SBuf<double> S2(s32 ? (size_t)keep * m : 1, st), T1(s32 ? (size_t)keep * m : 1, st),
+          G2(s32 ? (size_t)keep * keep + 64 : 1, st), P2(s32 ? (size_t)keep * keep + 64 : 1, st);
+      if (s32) {
+        // FP32 Ritz vectors are orthogonal only to FP32 level: orthonormalise
+        // them in FP64 (CholQR) and project H on them instead of taking diag(w)
+        dgemm(false, true, keep, keep, m, 1.0, S.p, m, S.p, m, 0.0, G2.p, keep, st);
+        cholqr_small(G2.p, keep, 1e-10, P2.p, (int*)(P2.p + keep * keep), st);
+        int nk2 = 0;
+        RIS_CUDA(cudaMemcpyAsync(&nk2, P2.p + keep * keep, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RIS_CUDA(cudaStreamSynchronize(st));
+        RIS_REQUIRE(nk2 >= ns, RIS_ERR_NOT_CONVERGED, "Davidson restart lost Ritz vectors");
+        keep = nk2;
+        dgemm(false, false, keep, m, keep, 1.0, P2.p, keep, S.p, m, 0.0, S2.p, m, st);
+        dgemm(false, false, keep, m, m, 1.0, S2.p, m, Hs.p, maxsp, 0.0, T1.p, m, st);
+        dgemm(false, true, keep, keep, m, 1.0, T1.p, m, S2.p, m, 0.0, G2.p, keep, st);
+        Sk = S2.p;
+      }
+      dgemm(false, false, keep, (int)n, m, 1.0, Sk, m, V.p, (int)n, 0.0, tmp.p, (int)n, st);
       RIS_CUDA(cudaMemcpyAsync(V.p, tmp.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, st));
-      dgemm(false, false, keep, (int)n, m, 1.0, S.p, m, AV.p, (int)n, 0.0, tmp.p, (int)n, st);
+      dgemm(false, false, keep, (int)n, m, 1.0, Sk, m, AV.p, (int)n, 0.0, tmp.p, (int)n, st);
       RIS_CUDA(cudaMemcpyAsync(AV.p, tmp.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, st));
-      k_diag_set<<<cdiv(keep * keep, 256), 256, 0, st>>>(Hs.p, maxsp, keep, w.p);
-      RIS_CHECK_LAUNCH();
+      if (s32) {
+        RIS_CUDA(cudaMemcpy2DAsync(Hs.p, sizeof(double) * maxsp, G2.p, sizeof(double) * keep,
+                                   sizeof(double) * keep, keep, cudaMemcpyDeviceToDevice, st));
+      } else {
+        k_diag_set<<<cdiv(keep * keep, 256), 256, 0, st>>>(Hs.p, maxsp, keep, w.p);
+        RIS_CHECK_LAUNCH();
+      }
       m = keep;
     }
     // two rounds of (project out V, orthonormalise within the block)

@@ -674,7 +674,9 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work, int a
     }
     if (dd[m - 1] == 0.0) dd[m - 1] = tiny;
     for (int i = 0; i < m; i++) dd[i] = rcp64(dd[i]);  // pivots kept as reciprocals
-    for (int i = 0; i < m; i++) z[i] = 1.0 + 0.01 * (double)(i % 7);
+    // start vector depending on j: equal eigenvalues (a split T) give
+    // different vectors of their eigenspace, which stage 3 orthonormalises
+    for (int i = 0; i < m; i++) z[i] = 1.0 + 0.01 * (double)((i * (j + 1)) % 7);
     for (int it = 0; it < 3; it++) {
       for (int i = 0; i + 1 < m; i++) {
         if (piv[i] == 0.0) {
@@ -753,6 +755,406 @@ __global__ void __launch_bounds__(kEigT) k_eig_finish(int m, int k, double* w, d
   for (size_t i = tid; i < (size_t)k * m; i += kEigT) V[i] = Z[i];
 }
 
+// ---------------------------------------------------- FP32 subspace eigensolver
+// The same three stages in FP32 arithmetic for the mixed precision form: the
+// Householder reduction and the eigenvectors of T are backward stable, so
+// every returned vector has a residual |H z - theta z| of a few FP32 ulps
+// of ||H|| (about 1e-7 ||H||, below the mixed form's Davidson tolerance);
+// the Ritz values are FP64 Rayleigh quotients of the FP64-normalised
+// vectors.  Vectors of close eigenvalues (within 1e-4 ||T||) are made
+// orthonormal and rotated onto the Ritz vectors of their span in FP64.
+constexpr int kEig32MaxM = 200;  // m^2 floats in shared memory
+
+template <int NT>
+__device__ __forceinline__ float block_sumf(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Stage 1 in FP32: T = Q^T H Q; reflectors left as floats in the first m^2
+// floats of the work array's A block, d, e, tau stored as doubles.
+__global__ void __launch_bounds__(kEigT) k_eig_tridiag32(const double* H, int ldH, int m,
+                                                         double* work) {
+  extern __shared__ float sA32[];
+  __shared__ float red[33];
+  __shared__ float sh_alpha, sh_tau;
+  __shared__ float p[kEigMaxM];
+  EigWork W(work, m);
+  float* A = sA32;
+  const int tid = threadIdx.x;
+  for (size_t ij = tid; ij < (size_t)m * m; ij += kEigT) {
+    const int i = (int)(ij / m), j = (int)(ij % m);
+    A[ij] = (float)(0.5 * (H[(size_t)i * ldH + j] + H[(size_t)j * ldH + i]));
+  }
+  __syncthreads();
+  for (int c = 0; c + 2 < m; c++) {
+    float part = 0.f;
+    for (int i = c + 1 + tid; i < m; i += kEigT) part += A[(size_t)i * m + c] * A[(size_t)i * m + c];
+    const float s = block_sumf<kEigT>(part, red);
+    if (tid == 0) {
+      const float x0 = A[(size_t)(c + 1) * m + c];
+      const float nrm = sqrtf(s);
+      W.d[c] = A[(size_t)c * m + c];
+      if (nrm == 0.f) {
+        sh_alpha = 0.f;
+        sh_tau = 0.f;
+      } else {
+        const float alpha = x0 >= 0.f ? -nrm : nrm;
+        const float v0 = x0 - alpha;
+        const float vn2 = s - x0 * x0 + v0 * v0;
+        A[(size_t)(c + 1) * m + c] = v0;
+        sh_alpha = alpha;
+        sh_tau = vn2 > 0.f ? 2.f / vn2 : 0.f;
+      }
+      W.e[c] = sh_alpha;
+      W.tau[c] = sh_tau;
+    }
+    __syncthreads();
+    const float tt = sh_tau;
+    if (tt == 0.f) continue;
+    for (int i = c + 1 + tid; i < m; i += kEigT) {
+      float acc = 0.f;
+      for (int j = c + 1; j < m; j++) acc += A[(size_t)j * m + i] * A[(size_t)j * m + c];
+      p[i] = tt * acc;
+    }
+    __syncthreads();
+    part = 0.f;
+    for (int i = c + 1 + tid; i < m; i += kEigT) part += p[i] * A[(size_t)i * m + c];
+    const float K = 0.5f * tt * block_sumf<kEigT>(part, red);
+    for (int i = c + 1 + tid; i < m; i += kEigT) p[i] -= K * A[(size_t)i * m + c];
+    __syncthreads();
+    const int ms = m - c - 1;
+    for (size_t ij = tid; ij < (size_t)ms * ms; ij += kEigT) {
+      const int i = c + 1 + (int)(ij / ms), j = c + 1 + (int)(ij % ms);
+      A[(size_t)i * m + j] -= A[(size_t)i * m + c] * p[j] + p[i] * A[(size_t)j * m + c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (m >= 2) {
+      W.d[m - 2] = A[(size_t)(m - 2) * m + m - 2];
+      W.e[m - 2] = A[(size_t)(m - 1) * m + m - 2];
+      W.tau[m - 2] = 0.0;
+    }
+    W.d[m - 1] = A[(size_t)(m - 1) * m + m - 1];
+    W.e[m - 1] = 0.0;
+    W.tau[m - 1] = 0.0;
+  }
+  float* Ag = (float*)W.A;
+  for (size_t ij = tid; ij < (size_t)m * m; ij += kEigT) Ag[ij] = A[ij];
+}
+
+constexpr int kEig32VecT = 128;
+
+// Stage 2 in FP32 (one CTA per wanted eigenvalue j): multisection on FP32
+// Sturm counts down to FP32 resolution, inverse iteration, back
+// transformation; then the vector in FP64, normalised, and its FP64
+// Rayleigh quotient with H.
+__global__ void __launch_bounds__(kEig32VecT) k_eig_vec32(int m, double* work, const double* H,
+                                                          int ldH) {
+  extern __shared__ float s32[];
+  __shared__ double redd[33];
+  __shared__ float sh_lo, sh_hi;
+  EigWork W(work, m);
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x;
+  float* d = s32;
+  float* e = d + m;
+  float* e2 = e + m;
+  float* tau = e2 + m;
+  float* z = tau + m;
+  float* dl = z + m;
+  float* dd = dl + m;
+  float* du = dd + m;
+  float* du2 = du + m;
+  float* piv = du2 + m;
+  float* A = piv + m;
+  double* zd = (double*)(A + (size_t)m * m + ((m * m) & 1));  // m doubles, 8-byte aligned
+  for (int i = tid; i < m; i += kEig32VecT) {
+    d[i] = (float)W.d[i];
+    e[i] = (float)W.e[i];
+    e2[i] = e[i] * e[i];
+    tau[i] = (float)W.tau[i];
+  }
+  const float* Ag = (const float*)W.A;
+  for (size_t q = tid; q < (size_t)m * m; q += kEig32VecT) A[q] = Ag[q];
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    float glo = 0.f, ghi = 0.f;
+    for (int i = 0; i < m; i++) {
+      const float r = (i > 0 ? fabsf(e[i - 1]) : 0.f) + (i + 1 < m ? fabsf(e[i]) : 0.f);
+      if (i == 0 || d[i] - r < glo) glo = d[i] - r;
+      if (i == 0 || d[i] + r > ghi) ghi = d[i] + r;
+    }
+    const float tn = fmaxf(fmaxf(fabsf(glo), fabsf(ghi)), 1e-30f);
+    float lo = glo - 1e-6f * tn, hi = ghi + 1e-6f * tn;
+    for (int it = 0; it < 24; it++) {
+      const float h = (hi - lo) / 33.f;
+      if (!(h > 0.f) || lo + h <= lo || hi - h >= hi) break;
+      const float x = lo + h * (float)(lane + 1);
+      const bool above = sturm_count_f(d, e2, m, x) > j;
+      const unsigned mask = __ballot_sync(0xffffffffu, above);
+      const int f = mask ? __ffs(mask) - 1 : 32;
+      const float nlo = f == 0 ? lo : lo + h * (float)f;
+      const float nhi = f == 32 ? hi : lo + h * (float)(f + 1);
+      lo = nlo;
+      hi = nhi;
+    }
+    if (lane == 0) {
+      sh_lo = lo;
+      sh_hi = hi;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const float lj = 0.5f * (sh_lo + sh_hi);
+    float tn = 0.f;
+    for (int i = 0; i < m; i++) tn = fmaxf(tn, fabsf(d[i]) + 2.f * fabsf(e[i]));
+    const float tiny = 1e-7f * fmaxf(tn, 1e-30f);
+    for (int i = 0; i < m; i++) {
+      dd[i] = d[i] - lj;
+      dl[i] = i + 1 < m ? e[i] : 0.f;
+      du[i] = i + 1 < m ? e[i] : 0.f;
+      du2[i] = 0.f;
+      piv[i] = 0.f;
+    }
+    for (int i = 0; i + 1 < m; i++) {
+      if (fabsf(dd[i]) >= fabsf(dl[i])) {
+        if (dd[i] == 0.f) dd[i] = tiny;
+        const float f = dl[i] / dd[i];
+        dl[i] = f;
+        dd[i + 1] -= f * du[i];
+      } else {
+        const float f = dd[i] / dl[i];
+        dd[i] = dl[i];
+        dl[i] = f;
+        const float tmp = du[i];
+        du[i] = dd[i + 1];
+        dd[i + 1] = tmp - f * dd[i + 1];
+        if (i + 2 < m) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du[i + 1];
+        }
+        piv[i] = 1.f;
+      }
+    }
+    if (dd[m - 1] == 0.f) dd[m - 1] = tiny;
+    for (int i = 0; i < m; i++) dd[i] = 1.f / dd[i];
+    for (int i = 0; i < m; i++) z[i] = 1.f + 0.01f * (float)((i * (j + 1)) % 7);
+    for (int it = 0; it < 3; it++) {
+      for (int i = 0; i + 1 < m; i++) {
+        if (piv[i] == 0.f) {
+          z[i + 1] -= dl[i] * z[i];
+        } else {
+          const float t0 = z[i];
+          z[i] = z[i + 1];
+          z[i + 1] = t0 - dl[i] * z[i];
+        }
+      }
+      z[m - 1] *= dd[m - 1];
+      if (m >= 2) z[m - 2] = (z[m - 2] - du[m - 2] * z[m - 1]) * dd[m - 2];
+      for (int i = m - 3; i >= 0; i--) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) * dd[i];
+      float mx = 0.f;
+      for (int i = 0; i < m; i++) mx = fmaxf(mx, fabsf(z[i]));
+      const float sc = mx > 0.f ? 1.f / mx : 1.f;
+      for (int i = 0; i < m; i++) z[i] *= sc;
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {  // back-transformation by one warp, H_{m-3} first
+    for (int c = m - 3; c >= 0; c--) {
+      const float tt = tau[c];
+      if (tt == 0.f) continue;
+      float part = 0.f;
+      for (int i = c + 1 + tid; i < m; i += 32) part += A[(size_t)i * m + c] * z[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      const float f = tt * part;
+      for (int i = c + 1 + tid; i < m; i += 32) z[i] -= f * A[(size_t)i * m + c];
+    }
+  }
+  __syncthreads();
+  // FP64: normalise, Rayleigh quotient z^T H z
+  double part = 0.0;
+  for (int i = tid; i < m; i += kEig32VecT) {
+    zd[i] = (double)z[i];
+    part += zd[i] * zd[i];
+  }
+  const double nn = block_sum<kEig32VecT>(part, redd);
+  const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+  for (int i = tid; i < m; i += kEig32VecT) zd[i] *= sc;
+  __syncthreads();
+  part = 0.0;
+  for (int i = tid; i < m; i += kEig32VecT) {
+    double hz = 0.0;
+    const double* Hi = H + (size_t)i * ldH;
+    for (int q = 0; q < m; q++) hz += Hi[q] * zd[q];
+    part += zd[i] * hz;
+  }
+  const double rq = block_sum<kEig32VecT>(part, redd);
+  if (tid == 0) W.lam[j] = rq;
+  for (int i = tid; i < m; i += kEig32VecT) W.Z[(size_t)j * m + i] = zd[i];
+}
+
+// Stage 3 for the FP32 vectors (one CTA): clusters of consecutive
+// eigenvalues closer than 1e-4 ||T|| are orthonormalised (two Gram-Schmidt
+// passes) and replaced by the Ritz vectors of their span with respect to H
+// (FP64 projected matrix, cyclic Jacobi); then the output.
+constexpr int kEigMaxCluster = 16;
+__global__ void __launch_bounds__(kEigT) k_eig_finish32(int m, int k, double* w, double* V,
+                                                        double* work, const double* H, int ldH) {
+  __shared__ double red[33];
+  __shared__ double lam[64];
+  __shared__ double Hc[kEigMaxCluster][kEigMaxCluster], Qc[kEigMaxCluster][kEigMaxCluster];
+  __shared__ double bnd[2];
+  EigWork W(work, m);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < k; i += kEigT) lam[i] = W.lam[i];
+  if (tid == 0) {
+    double glo = 0.0, ghi = 0.0;
+    tri_bounds(W.d, W.e, m, glo, ghi);
+    bnd[0] = glo;
+    bnd[1] = ghi;
+  }
+  __syncthreads();
+  const double tnorm = fmax(fmax(fabs(bnd[0]), fabs(bnd[1])), 1e-300);
+  const double gap_tol = 1e-4 * tnorm;
+  double* Z = W.Z;
+  int j0 = 0;
+  while (j0 < k) {
+    int j1 = j0 + 1;
+    while (j1 < k && j1 - j0 < kEigMaxCluster && fabs(lam[j1] - lam[j1 - 1]) <= gap_tol) j1++;
+    const int c = j1 - j0;
+    if (c > 1) {
+      for (int pass = 0; pass < 2; pass++)
+        for (int a = j0; a < j1; a++) {
+          for (int b = j0; b < a; b++) {
+            double part = 0.0;
+            for (int q = tid; q < m; q += kEigT) part += Z[(size_t)a * m + q] * Z[(size_t)b * m + q];
+            const double s = block_sum<kEigT>(part, red);
+            for (int q = tid; q < m; q += kEigT) Z[(size_t)a * m + q] -= s * Z[(size_t)b * m + q];
+            __syncthreads();
+          }
+          double part = 0.0;
+          for (int q = tid; q < m; q += kEigT) part += Z[(size_t)a * m + q] * Z[(size_t)a * m + q];
+          const double nn = block_sum<kEigT>(part, red);
+          for (int q = tid; q < m; q += kEigT) Z[(size_t)a * m + q] /= sqrt(nn);
+          __syncthreads();
+        }
+      // projected matrix Hc = Zc H Zc^T
+      for (int a = 0; a < c; a++)
+        for (int b = 0; b <= a; b++) {
+          double part = 0.0;
+          for (int i = tid; i < m; i += kEigT) {
+            double hz = 0.0;
+            const double* Hi = H + (size_t)i * ldH;
+            for (int q = 0; q < m; q++) hz += Hi[q] * Z[(size_t)(j0 + b) * m + q];
+            part += Z[(size_t)(j0 + a) * m + i] * hz;
+          }
+          const double s = block_sum<kEigT>(part, red);
+          if (tid == 0) Hc[a][b] = Hc[b][a] = s;
+        }
+      __syncthreads();
+      if (tid == 0) {  // cyclic Jacobi on the c x c matrix
+        for (int a = 0; a < c; a++)
+          for (int b = 0; b < c; b++) Qc[a][b] = a == b ? 1.0 : 0.0;
+        for (int sweep = 0; sweep < 12; sweep++) {
+          double off = 0.0;
+          for (int a = 0; a < c; a++)
+            for (int b = a + 1; b < c; b++) off += Hc[a][b] * Hc[a][b];
+          if (off < 1e-30) break;
+          for (int a = 0; a < c; a++)
+            for (int b = a + 1; b < c; b++) {
+              if (Hc[a][b] == 0.0) continue;
+              const double th = 0.5 * (Hc[b][b] - Hc[a][a]) / Hc[a][b];
+              const double tq = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+              const double cs = 1.0 / sqrt(tq * tq + 1.0), sn = tq * cs;
+              for (int q = 0; q < c; q++) {  // columns a, b
+                const double x = Hc[q][a], y = Hc[q][b];
+                Hc[q][a] = cs * x - sn * y;
+                Hc[q][b] = sn * x + cs * y;
+              }
+              for (int q = 0; q < c; q++) {  // rows a, b
+                const double x = Hc[a][q], y = Hc[b][q];
+                Hc[a][q] = cs * x - sn * y;
+                Hc[b][q] = sn * x + cs * y;
+              }
+              for (int q = 0; q < c; q++) {
+                const double x = Qc[q][a], y = Qc[q][b];
+                Qc[q][a] = cs * x - sn * y;
+                Qc[q][b] = sn * x + cs * y;
+              }
+            }
+        }
+        // ascending order of the Ritz values (selection sort on the columns)
+        for (int a = 0; a < c; a++) {
+          int best = a;
+          for (int b = a + 1; b < c; b++)
+            if (Hc[b][b] < Hc[best][best]) best = b;
+          if (best != a) {
+            const double t0 = Hc[a][a];
+            Hc[a][a] = Hc[best][best];
+            Hc[best][best] = t0;
+            for (int q = 0; q < c; q++) {
+              const double t1 = Qc[q][a];
+              Qc[q][a] = Qc[q][best];
+              Qc[q][best] = t1;
+            }
+          }
+        }
+        for (int a = 0; a < c; a++) lam[j0 + a] = Hc[a][a];
+      }
+      __syncthreads();
+      // Z_c <- Qc^T Z_c, column by column of Z
+      for (int q = tid; q < m; q += kEigT) {
+        double zc[kEigMaxCluster];
+        for (int a = 0; a < c; a++) zc[a] = Z[(size_t)(j0 + a) * m + q];
+        for (int a = 0; a < c; a++) {
+          double s = 0.0;
+          for (int b = 0; b < c; b++) s += Qc[b][a] * zc[b];
+          Z[(size_t)(j0 + a) * m + q] = s;
+        }
+      }
+      __syncthreads();
+    }
+    j0 = j1;
+  }
+  for (int j = tid; j < k; j += kEigT) w[j] = lam[j];
+  for (size_t i = tid; i < (size_t)k * m; i += kEigT) V[i] = Z[i];
+}
+
+bool sym_eig_lowest_f32(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
+                        cudaStream_t st) {
+  if (m > kEig32MaxM || k > 64 || k < 1 || k > m) return false;
+  const size_t smA = (size_t)m * m * sizeof(float);
+  ensure_smem_attr((const void*)k_eig_tridiag32, 200 * 1024);
+  ensure_smem_attr((const void*)k_eig_vec32, 200 * 1024);
+  const size_t vec_smem = 10 * (size_t)m * sizeof(float) + smA + 8 + (size_t)m * sizeof(double);
+  prof_begin(kProfEig, st);
+  k_eig_tridiag32<<<1, kEigT, smA, st>>>(H, ldH, m, work);
+  RIS_CHECK_LAUNCH();
+  k_eig_vec32<<<k, kEig32VecT, vec_smem, st>>>(m, work, H, ldH);
+  RIS_CHECK_LAUNCH();
+  k_eig_finish32<<<1, kEigT, 0, st>>>(m, k, w, V, work, H, ldH);
+  RIS_CHECK_LAUNCH();
+  prof_end(kProfEig, st, 1.0);
+  return true;
+}
+
 void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
                     cudaStream_t st) {
   RIS_REQUIRE(k >= 1 && k <= 64 && k <= m, RIS_ERR_ARG, "sym_eig_lowest: bad k");
@@ -826,6 +1228,21 @@ extern "C" int ris_debug_dgemm(int transA, int transB, int m, int n, int k, doub
     return 0;
   } catch (const Error& e) {
     fprintf(stderr, "ris_debug_dgemm: %s\n", e.msg.c_str());
+    return (int)e.code;
+  }
+}
+
+extern "C" int ris_debug_sym_eig_f32(int m, int k, const double* H, double* w, double* V) {
+  using namespace ris;
+  try {
+    double* work = nullptr;
+    RIS_CUDA(cudaMalloc(&work, sizeof(double) * eig_work_size(m)));
+    const bool ok = sym_eig_lowest_f32(H, m, m, k, w, V, work, 0);
+    RIS_CUDA(cudaDeviceSynchronize());
+    cudaFree(work);
+    return ok ? 0 : (int)RIS_ERR_ARG;
+  } catch (const Error& e) {
+    fprintf(stderr, "ris_debug_sym_eig_f32: %s\n", e.msg.c_str());
     return (int)e.code;
   }
 }

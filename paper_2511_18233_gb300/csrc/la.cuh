@@ -30,6 +30,12 @@ void tri_inverse(const double* L, double* Linv, int n, cudaStream_t st);
 size_t eig_work_size(int m);
 void sym_eig_lowest(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
                     cudaStream_t st);
+// The same in FP32 arithmetic with FP64 Rayleigh quotients (residuals of a
+// few FP32 ulps of ||H||; close eigenvalues' vectors orthonormalised and
+// rotated onto Ritz vectors in FP64).  Returns false (nothing launched) when
+// m > 200.
+bool sym_eig_lowest_f32(const double* H, int ldH, int m, int k, double* w, double* V, double* work,
+                        cudaStream_t st);
 
 // Utilities
 void fill(double* x, double v, size_t n, cudaStream_t st);

@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_gemm_f64emu", "ris_debug_sym_eig", "ris_debug_dgemm",
+           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_gemm_f64emu", "ris_debug_sym_eig", "ris_debug_sym_eig_f32", "ris_debug_dgemm",
            "ris_gemm_tf32x3_noalloc",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
     L.ris_debug_gemm_tf32x3.argtypes = [i, i, i, P, P, P]
     L.ris_debug_gemm_f64emu.argtypes = [i, i, i, P, P, P]
     L.ris_debug_sym_eig.argtypes = [i, i, P, P, P]
+    L.ris_debug_sym_eig_f32.argtypes = [i, i, P, P, P]
     d = ctypes.c_double
     L.ris_debug_dgemm.argtypes = [i, i, i, i, i, d, P, i, P, i, d, P, i]
     L.ris_gemm_tf32x3_noalloc.argtypes = [i, i, i, P, P, P, P]
@@ -334,14 +335,16 @@ def debug_dgemm(A, B, C, transA=False, transB=False, alpha=1.0, beta=0.0):
     return C_t.cpu().numpy()
 
 
-def debug_sym_eig(H, k):
-    """Lowest k eigenpairs of symmetric H via the device subspace eigensolver."""
+def debug_sym_eig(H, k, fp32=False):
+    """Lowest k eigenpairs of symmetric H via the device subspace eigensolver
+    (fp32: its FP32 form with FP64 Rayleigh quotients)."""
     import torch
     H_t = torch.as_tensor(np.ascontiguousarray(H, dtype=np.float64), device="cuda")
     m = H_t.shape[0]
     w = torch.zeros(k, dtype=torch.float64, device="cuda")
     V = torch.zeros((k, m), dtype=torch.float64, device="cuda")
-    st = load().ris_debug_sym_eig(int(m), int(k), H_t.data_ptr(), w.data_ptr(), V.data_ptr())
+    fn = load().ris_debug_sym_eig_f32 if fp32 else load().ris_debug_sym_eig
+    st = fn(int(m), int(k), H_t.data_ptr(), w.data_ptr(), V.data_ptr())
     if st != 0:
         raise RisError(st, "ris_debug_sym_eig failed")
     return w.cpu().numpy(), V.cpu().numpy()
