@@ -178,7 +178,8 @@ def run_serving(args):
         with Clocks(0) as clk:
             res = serve.serve(specs, n_requests=nreq, n_warmup=nwarm, rate=args.serve_rate,
                               nslots=args.serve_slots if mixed else 1, budget_bytes=budget,
-                              precision="mixed" if mixed else "fp64", use_guess=args.serve_guess and mixed, seed=7)
+                              precision="mixed" if mixed else "fp64", use_guess=args.serve_guess and mixed, seed=7,
+                              **({"eig_fp32": 1} if mixed and args.eig_fp32 else {}))
         done = res.pop("done")
         res.pop("trajectories")
         iters = [r.result["n_iter"] for r in done if r.result]
@@ -194,7 +195,8 @@ def run_serving(args):
             "config": {"workload": f"{args.serve_trajectories} trajectories, chains C4..C40 and flakes "
                                    f"4-7 A, 5-10 states, Poisson {args.serve_rate}/s, closed pool",
                        "slots": args.serve_slots, "budget_bytes": budget,
-                       "davidson_seed": "previous step" if args.serve_guess else "cold"},
+                       "davidson_seed": "previous step" if args.serve_guess else "cold",
+                       "subspace_eig": "fp32" if args.eig_fp32 else "fp64"},
             "mixed": m, "fp64_plain": f}
     print(json.dumps(line))
     return 0
@@ -210,6 +212,8 @@ def main():
                     help="both: mixed is the headline value, FP64 reported beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead")
+    ap.add_argument("--eig-fp32", action="store_true",
+                    help="mixed form: Davidson subspace eigenproblem in FP32 (option eig_fp32)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-fp64-requests", type=int, default=100)
@@ -250,7 +254,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": head["dtype"], "data": "synthetic",
-            "config": dict(CONFIG, workload=WORKLOAD, precision=precs[0]),
+            "config": dict(CONFIG, workload=WORKLOAD, precision=precs[0],
+                           subspace_eig="fp32" if args.eig_fp32 and precs[0] == "mixed" else "fp64"),
             "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
             "stages_last_step": head["stages"], "roofline": head["roofline"],
             "roofline_classes": head["classes"], "clocks": head["clocks"]}
@@ -280,7 +285,8 @@ def measure(precision, mol, args, world, local, dist):
     from paper_2511_18233_gb300 import ris
     stream = torch.cuda.Stream()
     prec = ris.FP64 if precision == "fp64" else ris.MIXED
-    ctx = ris.Context(device=local, precision=prec, cuda_stream=stream.cuda_stream, profile=1)
+    extra = {"eig_fp32": 1} if precision == "mixed" and args.eig_fp32 else {}
+    ctx = ris.Context(device=local, precision=prec, cuda_stream=stream.cuda_stream, profile=1, **extra)
     dev = f"cuda:{local}"
     coords_d = torch.as_tensor(mol.coords, device=dev)
     C_d = torch.as_tensor(mol.C, device=dev)

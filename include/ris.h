@@ -105,6 +105,9 @@ typedef struct {
   int emu_f64;        /* mixed precision: 1 (default) runs the Coulomb B transforms
                          (the two MO transforms of (mu nu|P)_J) as FP64-accurate products
                          on the FP16 tensor cores by exact operand splitting; 0: FP64 */
+  int eig_fp32;       /* mixed precision: 1 solves the Davidson subspace eigenproblem in FP32
+                         (FP64 Rayleigh quotients, close pairs and restarts re-orthonormalised
+                         in FP64, back to FP64 if the residuals stall); 0 (default): FP64 */
 } ris_options;
 
 typedef struct {

@@ -137,6 +137,7 @@ ris_status ris_options_default(ris_options* opt) {
   opt->mo_window = 0.0;
   opt->deriv_prefetch = 1;
   opt->emu_f64 = 1;
+  opt->eig_fp32 = 0;
   return RIS_OK;
 }
 
@@ -155,6 +156,7 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
   if (!(o.mo_window >= 0.0)) return RIS_ERR_ARG;
   if (o.deriv_prefetch != 0 && o.deriv_prefetch != 1) return RIS_ERR_ARG;
   if (o.emu_f64 != 0 && o.emu_f64 != 1) return RIS_ERR_ARG;
+  if (o.eig_fp32 != 0 && o.eig_fp32 != 1) return RIS_ERR_ARG;
   c->eng.opt = o;
   c->eng.device = o.device;
   if (o.profile) ris::prof_enable(true);

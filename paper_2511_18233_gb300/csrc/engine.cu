@@ -1754,9 +1754,10 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
       ework(eig_work_size(maxsp), st);
   SBuf<int> idxbuf((size_t)std::max(nb0, ns) + 8, st);
   int* d_idx = idxbuf.p;
-  // Mixed form: the subspace eigenproblem in FP32 (Ritz residuals of about
-  // 1e-7 ||H||, below its tolerance), back to FP64 if the residuals stall.
-  bool eig32 = mixed && maxsp <= 200;
+  // Mixed form with eig_fp32: the subspace eigenproblem in FP32 (Ritz
+  // residuals of about 1e-7 ||H||, below its tolerance), back to FP64 if the
+  // residuals stall.  By default the subspace eigensolve stays FP64.
+  bool eig32 = mixed && opt.eig_fp32 && maxsp <= 200;
   bool s32 = false;  // S came from the FP32 solver
   int stall = 0;
   double rprev = 0.0;

@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("profile", ctypes.c_int), ("mixed_tol", ctypes.c_double), ("refine", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mo_window", ctypes.c_double),
-                ("deriv_prefetch", ctypes.c_int), ("emu_f64", ctypes.c_int)]
+                ("deriv_prefetch", ctypes.c_int), ("emu_f64", ctypes.c_int),
+                ("eig_fp32", ctypes.c_int)]
 
 
 class Shell(ctypes.Structure):

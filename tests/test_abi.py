@@ -45,6 +45,7 @@ def test_options_defaults(lib):
     assert o.precision == ris.FP64 and o.rpa == 0 and o.screen_thr == 1e-14
     assert o.mixed_tol == 1e-6 and o.refine == 0 and o.profile == 0
     assert o.precond == 0 and o.mo_window == 0.0 and o.deriv_prefetch == 1
+    assert o.emu_f64 == 1 and o.eig_fp32 == 0
 
 
 def test_create_rejects_bad_options(lib):
@@ -58,6 +59,8 @@ def test_create_rejects_bad_options(lib):
     o = ris.options(deriv_prefetch=2)
     assert lib.ris_create(ctypes.byref(h), ctypes.byref(o)) == -1
     o = ris.options(precond=3)
+    assert lib.ris_create(ctypes.byref(h), ctypes.byref(o)) == -1
+    o = ris.options(eig_fp32=2)
     assert lib.ris_create(ctypes.byref(h), ctypes.byref(o)) == -1
     assert lib.ris_create(None, None) == -1
     assert lib.ris_get_stats(None, None, 1) == -1

@@ -68,9 +68,12 @@ def test_mixed_apply(ris_mod, small):
 
 
 @gpu
-def test_mixed_small_stated_error(ris_mod, small):
+@pytest.mark.parametrize("eig32", [0, 1])
+def test_mixed_small_stated_error(ris_mod, small, eig32):
+    """Stated error, with the FP64 subspace eigensolver (default) and with
+    its FP32 form (option eig_fp32)."""
     mol, orc, w, X = small
-    c = _ctx(ris_mod, mol, precision=ris_mod.MIXED)
+    c = _ctx(ris_mod, mol, precision=ris_mod.MIXED, eig_fp32=eig32)
     om, Xg = c.excite(5)
     assert np.max(np.abs(om - w[:5])) <= 1e-6
     g = c.gradient(range(5))
@@ -96,14 +99,21 @@ def test_mixed_refined_to_fp64(ris_mod, small):
     assert st["n_products"] > 0
 
 
-@gpu
-@pytest.mark.slow
-def test_mixed_chain_stated_error(ris_mod, oracle):
+@pytest.fixture(scope="module")
+def chain(oracle):
     mol = synth.workload(1)
     orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy,
                            mol.nocc)
     w, X, _ = orc.tda_davidson(11, tol=1e-10)
-    c = _ctx(ris_mod, mol, precision=ris_mod.MIXED)
+    return mol, orc, w, X
+
+
+@gpu
+@pytest.mark.slow
+@pytest.mark.parametrize("eig32", [0, 1])
+def test_mixed_chain_stated_error(ris_mod, chain, eig32):
+    mol, orc, w, X = chain
+    c = _ctx(ris_mod, mol, precision=ris_mod.MIXED, eig_fp32=eig32)
     om, Xg = c.excite(10)
     assert np.max(np.abs(om - w[:10])) <= 1e-6
     g = c.gradient(range(10))
