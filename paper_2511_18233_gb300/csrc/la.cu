@@ -241,17 +241,19 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
 }
 
 // ------------------------------------------------------------------ reductions
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
+// Sum over the block (NT threads) of v, returned to every thread; red holds
+// 33 elements of shared memory.
+template <int NT, class T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = T(0);
   if (threadIdx.x < 32) {
-    s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+    s = threadIdx.x < NT / 32 ? red[threadIdx.x] : T(0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) red[32] = s;
@@ -765,25 +767,6 @@ __global__ void __launch_bounds__(kEigT) k_eig_finish(int m, int k, double* w, d
 // orthonormal and rotated onto the Ritz vectors of their span in FP64.
 constexpr int kEig32MaxM = 200;  // m^2 floats in shared memory
 
-template <int NT>
-__device__ __forceinline__ float block_sumf(float v, float* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  float s = 0.f;
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) red[32] = s;
-  }
-  __syncthreads();
-  return red[32];
-}
-
 // Stage 1 in FP32: T = Q^T H Q; reflectors left as floats in the first m^2
 // floats of the work array's A block, d, e, tau stored as doubles.
 __global__ void __launch_bounds__(kEigT) k_eig_tridiag32(const double* H, int ldH, int m,
@@ -803,7 +786,7 @@ __global__ void __launch_bounds__(kEigT) k_eig_tridiag32(const double* H, int ld
   for (int c = 0; c + 2 < m; c++) {
     float part = 0.f;
     for (int i = c + 1 + tid; i < m; i += kEigT) part += A[(size_t)i * m + c] * A[(size_t)i * m + c];
-    const float s = block_sumf<kEigT>(part, red);
+    const float s = block_sum<kEigT>(part, red);
     if (tid == 0) {
       const float x0 = A[(size_t)(c + 1) * m + c];
       const float nrm = sqrtf(s);
@@ -833,7 +816,7 @@ __global__ void __launch_bounds__(kEigT) k_eig_tridiag32(const double* H, int ld
     __syncthreads();
     part = 0.f;
     for (int i = c + 1 + tid; i < m; i += kEigT) part += p[i] * A[(size_t)i * m + c];
-    const float K = 0.5f * tt * block_sumf<kEigT>(part, red);
+    const float K = 0.5f * tt * block_sum<kEigT>(part, red);
     for (int i = c + 1 + tid; i < m; i += kEigT) p[i] -= K * A[(size_t)i * m + c];
     __syncthreads();
     const int ms = m - c - 1;
