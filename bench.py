@@ -147,7 +147,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(CONFIG, workload=WORKLOAD),
+            "config": dict(CONFIG, workload=WORKLOAD, subspace_eig="fp32" if args.eig_fp32 else "fp64"),
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
