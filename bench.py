@@ -46,6 +46,19 @@ WORKLOAD = "C20H22 chain, 42 atoms, nao 512, TDA-ris 10 states, 10 gradients + 9
 NSTATES = 10
 
 
+def replica_throughput(seconds: float, steps: int, world: int, dist=None, device="cpu") -> float:
+    """Whole-job evaluations/s of `world` replicas that each ran `steps`
+    evaluations: world * steps / the slowest rank's time (an all-reduce MAX
+    over the process group when there is one; every rank gets the value)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+        dist.barrier()
+    return world * steps / seconds
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -332,12 +345,8 @@ def measure(precision, mol, args, world, local, dist):
     stages.update({"davidson_products": int(st["n_products"]), "davidson_iterations": int(st["n_iter"])})
     torch.cuda.synchronize()
     tot = sum(times) / 1000.0
-    if dist:
-        t = torch.tensor([tot], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-        dist.barrier()
-    value = world * args.steps / tot
+    value = replica_throughput(tot, args.steps, world, dist, dev)
+    tot = world * args.steps / value  # the slowest rank's time
 
     # end to end through host buffers
     h2d = mol.coords.nbytes + mol.C.nbytes + mol.mo_energy.nbytes
