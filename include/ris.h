@@ -41,8 +41,10 @@
  *   - The caller owns every argument buffer; the context copies what it keeps
  *     and owns all device memory it allocates.
  *   - Every call returns a ris_status.  On error the outputs are untouched and
- *     ris_last_error() returns a message.  Calls made out of order
- *     (aux -> B -> excite -> gradient/nac) return RIS_ERR_STATE.
+ *     ris_last_error() returns a message; the one exception is ris_nac, which
+ *     still writes the requested numerators when it returns
+ *     RIS_ERR_DEGENERATE (the couplings themselves are untouched).  Calls made
+ *     out of order (aux -> B -> excite -> gradient/nac) return RIS_ERR_STATE.
  *   - One context per stream; contexts share no state.
  */
 #ifndef RIS_H_
@@ -352,6 +354,27 @@ int ris_debug_gemm_f64emu(int M, int N, int K, const double* A, const double* B,
  */
 int ris_gemm_tf32x3_noalloc(int M, int N, int K, const double* A, const double* B, double* C,
                             void* stream);
+
+/*
+ * Test hook: measured peak rate of one arithmetic pipe of the current
+ * device, the denominator of the roofline fractions of the kernels bound by
+ * it.  kind: 0 FP64 FMA, 1 FP32 FMA (SIMT; independent chains on every
+ * SM), 2 FP64 mma.sync m16n8k4, 3 tcgen05 kind::tf32 (M 128, N 256, K 8),
+ * 4 tcgen05 kind::f16 (M 128, N 256, K 16; one CTA per SM issuing back to
+ * back from fixed shared-memory tiles).  Best of reps timed runs after one
+ * warm-up run (CUDA events): *tflops in 10^12 flop/s (an FMA or MMA
+ * multiply-add counts 2), *ms (may be NULL) the duration of that run.
+ * Synchronises the device.  Returns 0, RIS_ERR_ARG, RIS_ERR_TIMEOUT (an MMA
+ * completion wait timed out) or RIS_ERR_CUDA.
+ */
+int ris_debug_peak_probe(int kind, int reps, double* tflops, double* ms);
+
+/*
+ * Test hook: the number of device allocations (cudaMalloc, cudaMallocAsync)
+ * the library has made since it was loaded, over all contexts, devices and
+ * hooks.  Lets a test check that a call allocated nothing.
+ */
+long long ris_debug_alloc_count(void);
 
 /* Message of the last error on this context ("" if none). */
 const char* ris_last_error(const ris_ctx* ctx);

@@ -13,6 +13,7 @@ struct ris_ctx {
 
 namespace ris {
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_allocs{0};
 
 namespace {
 struct Rec {
@@ -351,6 +352,8 @@ ris_status ris_trim(ris_ctx* ctx) {
     RIS_CUDA(cudaStreamSynchronize(ctx->eng.st));
   });
 }
+
+long long ris_debug_alloc_count(void) { return ris::g_allocs.load(); }
 
 const char* ris_last_error(const ris_ctx* ctx) { return ctx ? ctx->eng.err.c_str() : "null context"; }
 

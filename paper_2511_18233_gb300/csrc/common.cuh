@@ -36,6 +36,14 @@ struct Error {
 
 // Every kernel launch is followed by RIS_CHECK_LAUNCH, which also counts it.
 extern std::atomic<long long> g_launches;
+// Device allocations made by the library since it was loaded (every
+// cudaMalloc / cudaMallocAsync goes through RIS_ALLOC or dev_alloc).
+extern std::atomic<long long> g_allocs;
+#define RIS_ALLOC(call)  \
+  do {                   \
+    ++::ris::g_allocs;   \
+    RIS_CUDA(call);      \
+  } while (0)
 #define RIS_CHECK_LAUNCH()        \
   do {                            \
     ++::ris::g_launches;          \

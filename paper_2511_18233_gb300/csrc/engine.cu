@@ -38,6 +38,7 @@ thread_local MemTrack* t_track = nullptr;
 
 void* dev_alloc(size_t bytes, cudaStream_t st, MemTrack** owner) {
   void* p = nullptr;
+  ++g_allocs;
   cudaError_t e = cudaMallocAsync(&p, bytes, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -149,7 +150,7 @@ Engine::~Engine() {
 template <class T>
 static T* upload(const std::vector<T>& v, cudaStream_t st) {
   T* d = nullptr;
-  RIS_CUDA(cudaMallocAsync((void**)&d, sizeof(T) * std::max<size_t>(v.size(), 1), st));
+  RIS_ALLOC(cudaMallocAsync((void**)&d, sizeof(T) * std::max<size_t>(v.size(), 1), st));
   if (!v.empty())
     RIS_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
   return d;
@@ -1153,7 +1154,7 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
   dMU.ensure(3 * (size_t)nU * nU, st);
   int2c(aux, xyz.p, MU.p, dMU.p, st);
   // metric factors
-  if (!d_info) RIS_CUDA(cudaMallocAsync((void**)&d_info, sizeof(int) * 2, st));
+  if (!d_info) RIS_ALLOC(cudaMallocAsync((void**)&d_info, sizeof(int) * 2, st));
   LJinv.ensure((size_t)nJ * nJ, st);
   LKinv.ensure((size_t)nK * nK, st);
   w1.ensure((size_t)std::max(nJ, nK) * std::max(nJ, nK), st);
@@ -1319,7 +1320,7 @@ void Engine::prepare_mixed() {
   const int o = nocc, v = nvir, n = nao;
   const int lo4 = ld4(o), lv4 = ld4(v);
   if (!d_tcerr) {
-    RIS_CUDA(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
+    RIS_ALLOC(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
     RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
   }
   BooH.ensure((size_t)o * nK * lo4, st);
@@ -1397,7 +1398,7 @@ void Engine::coulomb_emu(double* H, double* W) {
 void Engine::emu_abt(int M, int N, int K, const double* A, long long rsA, long long ksA,
                      const double* B, long long rsB, long long ksB, const EmuEpilogue& ep) {
   if (!d_tcerr) {
-    RIS_CUDA(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
+    RIS_ALLOC(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
     RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
   }
   const int lk = ld8(K);
@@ -1420,7 +1421,7 @@ void Engine::build_Kvv_tc(double* out) {
   const int o = nocc, v = nvir, n = nao;
   const int ldn = ld4(n);
   if (!d_tcerr) {
-    RIS_CUDA(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
+    RIS_ALLOC(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
     RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
   }
   SBuf<float> Th((size_t)nK * n * ldn, st), Tl((size_t)nK * n * ldn, st);

@@ -392,11 +392,11 @@ extern "C" int ris_debug_gemm_f64emu(int M, int N, int K, const double* A, const
     const int lk = ld8(K);
     EmuOperand a, b;
     int* err;
-    RIS_CUDA(cudaMalloc(&a.s, sizeof(__half) * kEmuSlices * (size_t)M * lk));
-    RIS_CUDA(cudaMalloc(&b.s, sizeof(__half) * kEmuSlices * (size_t)N * lk));
-    RIS_CUDA(cudaMalloc(&a.e, sizeof(int) * (size_t)M));
-    RIS_CUDA(cudaMalloc(&b.e, sizeof(int) * (size_t)N));
-    RIS_CUDA(cudaMalloc(&err, sizeof(int)));
+    RIS_ALLOC(cudaMalloc(&a.s, sizeof(__half) * kEmuSlices * (size_t)M * lk));
+    RIS_ALLOC(cudaMalloc(&b.s, sizeof(__half) * kEmuSlices * (size_t)N * lk));
+    RIS_ALLOC(cudaMalloc(&a.e, sizeof(int) * (size_t)M));
+    RIS_ALLOC(cudaMalloc(&b.e, sizeof(int) * (size_t)N));
+    RIS_ALLOC(cudaMalloc(&err, sizeof(int)));
     RIS_CUDA(cudaMemset(err, 0, sizeof(int)));
     emu_slice(A, M, K, K, 1, a, st);
     emu_slice(B, N, K, K, 1, b, st);

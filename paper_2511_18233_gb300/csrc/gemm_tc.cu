@@ -397,11 +397,11 @@ extern "C" int ris_debug_gemm_tf32x3(int M, int N, int K, const double* A, const
     const int ld = ld4(K);
     float *ah, *al, *bh, *bl;
     int* err;
-    RIS_CUDA(cudaMalloc(&ah, sizeof(float) * (size_t)M * ld));
-    RIS_CUDA(cudaMalloc(&al, sizeof(float) * (size_t)M * ld));
-    RIS_CUDA(cudaMalloc(&bh, sizeof(float) * (size_t)N * ld));
-    RIS_CUDA(cudaMalloc(&bl, sizeof(float) * (size_t)N * ld));
-    RIS_CUDA(cudaMalloc(&err, sizeof(int)));
+    RIS_ALLOC(cudaMalloc(&ah, sizeof(float) * (size_t)M * ld));
+    RIS_ALLOC(cudaMalloc(&al, sizeof(float) * (size_t)M * ld));
+    RIS_ALLOC(cudaMalloc(&bh, sizeof(float) * (size_t)N * ld));
+    RIS_ALLOC(cudaMalloc(&bl, sizeof(float) * (size_t)N * ld));
+    RIS_ALLOC(cudaMalloc(&err, sizeof(int)));
     RIS_CUDA(cudaMemset(err, 0, sizeof(int)));
     split_f64(A, M, K, K, ah, al, ld, st);
     split_f64(B, N, K, K, bh, bl, ld, st);

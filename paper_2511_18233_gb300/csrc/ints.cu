@@ -102,7 +102,7 @@ const double* boys_table_device(int device) {
   if (it != per_dev.end()) return it->second;
   if (host.empty()) host = make_boys_table();
   double* d = nullptr;
-  RIS_CUDA(cudaMalloc(&d, host.size() * sizeof(double)));
+  RIS_ALLOC(cudaMalloc(&d, host.size() * sizeof(double)));
   RIS_CUDA(cudaMemcpy(d, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice));
   per_dev[device] = d;
   return d;
@@ -632,9 +632,9 @@ void build_pairs(const ShellSet& ao, const double* d_coords, double thr, PairLis
   const int nitem = nsh * nsh;
   const int nblk = cdiv(nitem, kPairBlock);
   int *counts = nullptr, *offs = nullptr, *totals = nullptr;
-  RIS_CUDA(cudaMallocAsync(&counts, sizeof(int) * 8 * nblk, st));
-  RIS_CUDA(cudaMallocAsync(&offs, sizeof(int) * 8 * nblk, st));
-  RIS_CUDA(cudaMallocAsync(&totals, sizeof(int) * 8, st));
+  RIS_ALLOC(cudaMallocAsync(&counts, sizeof(int) * 8 * nblk, st));
+  RIS_ALLOC(cudaMallocAsync(&offs, sizeof(int) * 8 * nblk, st));
+  RIS_ALLOC(cudaMallocAsync(&totals, sizeof(int) * 8, st));
   k_pair_count<<<nblk, kPairBlock, 0, st>>>(nsh, ao.l, ao.atom, ao.ex, ao.nbase, d_coords, thr,
                                            counts);
   RIS_CHECK_LAUNCH();
@@ -650,8 +650,8 @@ void build_pairs(const ShellSet& ao, const double* d_coords, double thr, PairLis
     pl.class_off[k + 1] = n;
   }
   pl.npair = n;
-  RIS_CUDA(cudaMallocAsync((void**)&pl.a, sizeof(int) * std::max(n, 1), st));
-  RIS_CUDA(cudaMallocAsync((void**)&pl.b, sizeof(int) * std::max(n, 1), st));
+  RIS_ALLOC(cudaMallocAsync((void**)&pl.a, sizeof(int) * std::max(n, 1), st));
+  RIS_ALLOC(cudaMallocAsync((void**)&pl.b, sizeof(int) * std::max(n, 1), st));
   k_pair_scatter<<<nblk, kPairBlock, 0, st>>>(nsh, ao.l, ao.atom, ao.ex, ao.nbase, d_coords,
                                              thr, offs, pl.a, pl.b);
   RIS_CHECK_LAUNCH();

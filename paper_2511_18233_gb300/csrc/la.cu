@@ -1219,7 +1219,7 @@ extern "C" int ris_debug_sym_eig_f32(int m, int k, const double* H, double* w, d
   using namespace ris;
   try {
     double* work = nullptr;
-    RIS_CUDA(cudaMalloc(&work, sizeof(double) * eig_work_size(m)));
+    RIS_ALLOC(cudaMalloc(&work, sizeof(double) * eig_work_size(m)));
     const bool ok = sym_eig_lowest_f32(H, m, m, k, w, V, work, 0);
     RIS_CUDA(cudaDeviceSynchronize());
     cudaFree(work);
@@ -1234,7 +1234,7 @@ extern "C" int ris_debug_sym_eig(int m, int k, const double* H, double* w, doubl
   using namespace ris;
   try {
     double* work = nullptr;
-    RIS_CUDA(cudaMalloc(&work, sizeof(double) * eig_work_size(m)));
+    RIS_ALLOC(cudaMalloc(&work, sizeof(double) * eig_work_size(m)));
     sym_eig_lowest(H, m, m, k, w, V, work, 0);
     RIS_CUDA(cudaDeviceSynchronize());
     cudaFree(work);

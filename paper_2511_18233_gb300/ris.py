@@ -24,7 +24,7 @@ FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
            "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_gemm_f64emu", "ris_debug_sym_eig", "ris_debug_sym_eig_f32", "ris_debug_dgemm",
-           "ris_gemm_tf32x3_noalloc",
+           "ris_gemm_tf32x3_noalloc", "ris_debug_alloc_count", "ris_debug_peak_probe",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
 
@@ -87,12 +87,15 @@ def load(path: str = LIB_PATH):
     d = ctypes.c_double
     L.ris_debug_dgemm.argtypes = [i, i, i, i, i, d, P, i, P, i, d, P, i]
     L.ris_gemm_tf32x3_noalloc.argtypes = [i, i, i, P, P, P, P]
+    L.ris_debug_alloc_count.argtypes = []
+    L.ris_debug_peak_probe.argtypes = [i, i, P, P]
     L.ris_last_error.argtypes = [P]
     L.ris_last_error.restype = ctypes.c_char_p
     L.ris_destroy.argtypes = [P]
     for f in EXPORTS:
-        if f not in ("ris_last_error", "ris_destroy"):
+        if f not in ("ris_last_error", "ris_destroy", "ris_debug_alloc_count"):
             getattr(L, f).restype = ctypes.c_int
+    L.ris_debug_alloc_count.restype = ctypes.c_longlong
     L.ris_destroy.restype = None
     _lib = L
     return L
@@ -311,12 +314,49 @@ def debug_gemm_f64emu(A, B):
 
 
 def gemm_tf32x3_noalloc(A_t, B_t, C_t, stream=None) -> int:
-    """C_t = A_t B_t^T (CUDA float64 tensors) through the allocation-free
-    entry point; returns the status code."""
+    """C_t = A_t B_t^T through the allocation-free entry point; returns the
+    status code.  A_t [M][K], B_t [N][K], C_t [M][N]: contiguous float64 CUDA
+    tensors on the current device (ValueError otherwise).  stream: a raw
+    cudaStream_t, default torch's current stream on that device."""
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t in (("A", A_t), ("B", B_t), ("C", C_t)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+            raise ValueError(f"{name} must be a float64 CUDA tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+        if t.dim() != 2 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous matrix")
     M, K = A_t.shape
     N = B_t.shape[0]
+    if B_t.shape[1] != K or tuple(C_t.shape) != (M, N):
+        raise ValueError(f"shapes A {tuple(A_t.shape)}, B {tuple(B_t.shape)}, C {tuple(C_t.shape)} "
+                         "do not form C = A B^T")
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
     return load().ris_gemm_tf32x3_noalloc(int(M), int(N), int(K), A_t.data_ptr(), B_t.data_ptr(),
                                           C_t.data_ptr(), stream)
+
+
+PROBE_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_mma_sync": 2, "tf32_tcgen05": 3,
+               "f16_tcgen05": 4}
+
+
+def debug_peak_probe(kind: str, reps: int = 3):
+    """Measured rate (TFLOP/s, ms of the best run) of one arithmetic pipe of
+    the current device (ris_debug_peak_probe)."""
+    r = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    st = load().ris_debug_peak_probe(PROBE_KINDS[kind], int(reps), ctypes.addressof(r),
+                                     ctypes.addressof(ms))
+    if st != 0:
+        raise RisError(st, f"ris_debug_peak_probe({kind}) failed")
+    return r.value, ms.value
+
+
+def debug_alloc_count() -> int:
+    """Device allocations the library has made since it was loaded."""
+    return int(load().ris_debug_alloc_count())
 
 
 def debug_dgemm(A, B, C, transA=False, transB=False, alpha=1.0, beta=0.0):

@@ -28,6 +28,23 @@ def test_noalloc_gemm_matches_allocating_entry():
         bound = np.abs(A) @ np.abs(B).T
         assert np.max(np.abs(C - ref) / bound) <= 2e-6
         assert np.max(np.abs(C - A @ B.T) / bound) <= 2e-6
+    # the split-K case above (M = 300, N = 200: six tiles, K split across CTAs)
+    # and repeated calls allocate nothing: the library's allocation counter
+    # does not move
+    A_t = torch.as_tensor(rng.standard_normal((300, 1000)), device="cuda")
+    B_t = torch.as_tensor(rng.standard_normal((200, 1000)), device="cuda")
+    C_t = torch.empty((300, 200), dtype=torch.float64, device="cuda")
+    n0 = ris.debug_alloc_count()
+    for _ in range(2):
+        assert ris.gemm_tf32x3_noalloc(A_t, B_t, C_t) == 0
+    assert ris.debug_alloc_count() == n0
+    # misuse is caught before the call: wrong dtype, transposed view, shape
+    with pytest.raises(ValueError):
+        ris.gemm_tf32x3_noalloc(A_t.float(), B_t, C_t)
+    with pytest.raises(ValueError):
+        ris.gemm_tf32x3_noalloc(A_t, B_t.t(), C_t)
+    with pytest.raises(ValueError):
+        ris.gemm_tf32x3_noalloc(A_t, B_t, C_t[:, :100])
     # repeated calls leave the device's free memory unchanged
     A_t = torch.as_tensor(rng.standard_normal((256, 512)), device="cuda")
     B_t = torch.as_tensor(rng.standard_normal((192, 512)), device="cuda")
