@@ -176,11 +176,38 @@ def phase_fix(X: np.ndarray) -> np.ndarray:
     return flat.reshape(X.shape)
 
 
+def phase_align(X: np.ndarray, X_prev: np.ndarray, ndet: int = 5):
+    """Phase tracking between consecutive geometries of a path (Sec. 2, the
+    phase of the excited states along a geometric path): for each state the
+    sign of its overlap with the previous step's state, taken over the ndet
+    most dominant determinants of the previous state (largest |X_prev|
+    elements; equal magnitudes ordered by flat index), decides whether the
+    new state is flipped.  Returns the signs (+1 keep, -1 flip; a zero
+    overlap keeps) and the aligned X.  Plain loops over states."""
+    X = np.asarray(X, dtype=np.float64)
+    Xp = np.asarray(X_prev, dtype=np.float64)
+    ns = X.shape[0]
+    signs = np.ones(ns, dtype=np.int32)
+    out = np.array(X, copy=True)
+    for k in range(ns):
+        xp = Xp[k].ravel()
+        x = X[k].ravel()
+        mag = np.abs(xp)
+        dominant = sorted(range(mag.size), key=lambda i: (-mag[i], i))[:ndet]
+        overlap = 0.0
+        for i in dominant:
+            overlap += x[i] * xp[i]
+        if overlap < 0.0:
+            signs[k] = -1
+            out[k] *= -1.0
+    return signs, out
+
+
 class RisOracle:
     """FP64 TDDFT-ris at fixed MO coefficients, orbital energies and amplitudes."""
 
     def __init__(self, coords, shells, aux_j, aux_k, C, mo_energy, nocc: int,
-                 cx: float = 0.25):
+                 cx: float = 0.25, metric_inverse: str = "solve"):
         self.coords = np.ascontiguousarray(coords, dtype=np.float64)
         self.shells, self.aux_j, self.aux_k = shells, aux_j, aux_k
         self.C = np.ascontiguousarray(C, dtype=np.float64)
@@ -189,11 +216,29 @@ class RisOracle:
         self.nao, self.nmo = self.C.shape
         self.nvir = self.nmo - self.nocc
         self.cx = float(cx)
+        self.metric_inverse = metric_inverse
         self.natm = self.coords.shape[0]
         self.Co = self.C[:, :self.nocc]
         self.Cv = self.C[:, self.nocc:]
         self.de = (self.eps[self.nocc:][None, :] - self.eps[:self.nocc][:, None])  # [i][a]
         self._setup()
+
+    def _inverse(self, M):
+        """M^-1 of Eq. (g_modified).  The RI integral does not depend on how
+        the inverse is formed; the routes differ only in rounding:
+        "solve" (LU with partial pivoting, the default), "cholesky"
+        (L^-T L^-1 from M = L L^T) or "eigh" (V diag(1/lambda) V^T)."""
+        n = M.shape[0]
+        if self.metric_inverse == "solve":
+            return np.linalg.solve(M, np.eye(n))
+        if self.metric_inverse == "cholesky":
+            L = np.linalg.cholesky(M)
+            Li = np.linalg.solve(L, np.eye(n))
+            return Li.T @ Li
+        if self.metric_inverse == "eigh":
+            w, V = np.linalg.eigh(M)
+            return (V / w[None, :]) @ V.T
+        raise ValueError(self.metric_inverse)
 
     # -- integrals in the MO blocks
     def _mo3(self, T, left, right):
@@ -207,8 +252,8 @@ class RisOracle:
         self.TK = int3c(c, self.shells, self.aux_k)
         self.MJ = int2c(c, self.aux_j)
         self.MK = int2c(c, self.aux_k)
-        self.MJinv = np.linalg.solve(self.MJ, np.eye(self.MJ.shape[0]))
-        self.MKinv = np.linalg.solve(self.MK, np.eye(self.MK.shape[0]))
+        self.MJinv = self._inverse(self.MJ)
+        self.MKinv = self._inverse(self.MK)
         Co, Cv = self.Co, self.Cv
         self.ovJ = self._mo3(self.TJ, Co, Cv)  # (ia|P)_J
         self.ooK = self._mo3(self.TK, Co, Co)  # (ij|P)_K
@@ -234,6 +279,107 @@ class RisOracle:
             exch = np.tensordot(self.ooK, t, axes=([1, 2], [0, 2]))   # [i][a]
             out[k] = self.de * x + 2.0 * coul - self.cx * exch
         return out
+
+    def apply_ApB_AmB(self, Z: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+        """(A + B) Z and (A - B) Z for Z [n][nocc][nvir] (Eqs. A_matrix,
+        B_matrix with the ris kernel): A + B = D + 4 (ia|jb)_J
+        - c_x [(ij|ab)_K + (ib|ja)_K], A - B = D - c_x [(ij|ab)_K - (ib|ja)_K].
+        Vectors are taken eight at a time (each term one tensor contraction)."""
+        if not hasattr(self, "_cvv"):
+            self._cvv = np.tensordot(self.vvK, self.MKinv, axes=([2], [0]))   # [a][b][Q]
+            self._cov = np.tensordot(self.ovK, self.MKinv, axes=([2], [0]))   # [j][a][Q]
+        P = np.empty_like(Z)
+        M = np.empty_like(Z)
+        for k0 in range(0, Z.shape[0], 8):
+            z = Z[k0:k0 + 8]
+            w = np.tensordot(z, self.ovJ, axes=([1, 2], [0, 1])) @ self.MJinv       # [k][P]
+            coul = np.tensordot(w, self.ovJ, axes=([1], [2]))                        # [k][i][a]
+            t = np.tensordot(z, self._cvv, axes=([2], [1]))                          # [k][j][a][Q]
+            kx = np.tensordot(t, self.ooK, axes=([1, 3], [1, 2])).transpose(0, 2, 1)  # (ij|ab) z_jb
+            u = np.tensordot(z, self.ovK, axes=([2], [1]))                           # [k][j][i][Q]
+            kb = np.tensordot(u, self._cov, axes=([1, 3], [0, 2]))                   # (ib|ja) z_jb
+            P[k0:k0 + 8] = self.de * z + 4.0 * coul - self.cx * (kx + kb)
+            M[k0:k0 + 8] = self.de * z - self.cx * (kx - kb)
+        return P, M
+
+    def rpa_davidson(self, nstates: int, tol: float = 1e-10, max_iter: int = 200,
+                     max_space: Optional[int] = None):
+        """Lowest RPA excitations by a plain Davidson on the Casida problem
+        (Eq. casida) in its symmetric form: omega^2 are the eigenvalues of
+        (A-B)^1/2 (A+B) (A-B)^1/2, since (A+B) R = omega L and
+        (A-B) L = omega R with R = X+Y, L = X-Y.  One orthonormal basis V
+        spans both R and L; the projected problem is the symmetric
+        eigenproblem of Mm^1/2 P Mm^1/2 with P = V^T (A+B) V and
+        Mm = V^T (A-B) V (the dense form of rpa_dense, in the subspace).
+        New directions: both residuals divided by (D - omega), D the
+        orbital-energy differences.  Converged when both residuals
+        (A+B) R - omega L and (A-B) L - omega R have 2-norm <= tol per state,
+        R = X+Y and L = X-Y normalised so that R . L = 1 (sum X^2 - Y^2 = 1).
+        Returns omega [nstates], X, Y [nstates][nocc][nvir] (largest |X|
+        element positive) and the iteration count."""
+        o, v = self.nocc, self.nvir
+        n = o * v
+        de = self.de.reshape(-1)
+        nb = nstates + min(nstates, 8)
+        max_space = max_space or max(20 * nstates, 4 * nb)
+        order = np.lexsort((np.arange(n), de))
+        V = np.zeros((nb, n))
+        for k in range(nb):
+            V[k, order[k]] = 1.0
+        P_, M_ = self.apply_ApB_AmB(V.reshape(nb, o, v))
+        PV, MV = P_.reshape(nb, n), M_.reshape(nb, n)
+        for it in range(max_iter):
+            Ps = V @ PV.T
+            Ms = V @ MV.T
+            Ps, Ms = 0.5 * (Ps + Ps.T), 0.5 * (Ms + Ms.T)
+            wm, Um = np.linalg.eigh(Ms)
+            if wm[0] <= 0:
+                raise RuntimeError("projected A-B not positive definite")
+            Sh = (Um * np.sqrt(wm)[None, :]) @ Um.T                # Mm^1/2
+            w2, T = np.linalg.eigh(Sh @ Ps @ Sh)
+            om = np.sqrt(w2[:nstates])
+            # subspace R (= X+Y) and L (= X-Y) with R . L = 1
+            r = (Sh @ T[:, :nstates]) / np.sqrt(om)[None, :]
+            l = (Ps @ r) / om[None, :]
+            R, L = r.T @ V, l.T @ V
+            res1 = r.T @ PV - om[:, None] * L        # (A+B) R - omega L
+            res2 = l.T @ MV - om[:, None] * R        # (A-B) L - omega R
+            rn = np.maximum(np.linalg.norm(res1, axis=1), np.linalg.norm(res2, axis=1))
+            if np.all(rn <= tol):
+                X = (0.5 * (R + L)).reshape(nstates, o, v)
+                Y = (0.5 * (R - L)).reshape(nstates, o, v)
+                for k in range(nstates):
+                    j = int(np.argmax(np.abs(X[k].ravel())))
+                    if X[k].ravel()[j] < 0:
+                        X[k] *= -1.0
+                        Y[k] *= -1.0
+                return om, X, Y, it
+            new = []
+            for k in range(nstates):
+                if rn[k] <= tol:
+                    continue
+                den = de - om[k]
+                den = np.where(np.abs(den) < 1e-8, np.copysign(1e-8, den), den)
+                new.append(res1[k] / den)
+                new.append(res2[k] / den)
+            new = np.array(new)
+            if V.shape[0] + new.shape[0] > max_space:
+                # restart on span{R, L}; the products follow linearly
+                q, _ = np.linalg.qr(np.vstack([R, L]).T)
+                Cm = q.T @ V.T
+                V, PV, MV = Cm @ V, Cm @ PV, Cm @ MV
+            for _ in range(2):
+                new = new - (new @ V.T) @ V
+            q, rr = np.linalg.qr(new.T)
+            q = q.T[np.abs(np.diag(rr)) > 1e-8 * np.max(np.abs(np.diag(rr)))]
+            for _ in range(2):
+                q = q - (q @ V.T) @ V
+                q = q / np.linalg.norm(q, axis=1)[:, None]
+            P_, M_ = self.apply_ApB_AmB(q.reshape(-1, o, v))
+            V = np.vstack([V, q])
+            PV = np.vstack([PV, P_.reshape(-1, n)])
+            MV = np.vstack([MV, M_.reshape(-1, n)])
+        raise RuntimeError("oracle RPA Davidson did not converge")
 
     def dense_AB(self) -> Tuple[np.ndarray, np.ndarray]:
         """Dense A and B over the ia pair index (small systems only)."""

@@ -1,5 +1,6 @@
 """The ris excitation energy as a torch.autograd.Function: backward against
-central finite differences of the re-solved energy and against the oracle."""
+central finite differences of the re-solved energy and against the oracle;
+integral reuse and recomputation under a memory budget."""
 import numpy as np
 import pytest
 
@@ -16,6 +17,10 @@ def torch_mod():
     from paper_2511_18233_gb300 import build
     build.build()
     return torch
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(np.asarray(b))))
 
 
 def _fd(model, coords, state, A, x, h, points=2):
@@ -57,31 +62,93 @@ def test_autograd_small_against_fd_and_oracle(torch_mod, oracle, rpa):
 
 
 @gpu
+def test_backward_reuses_or_recomputes(torch_mod):
+    """The backward reuses the context's integrals when it still holds the
+    forward's geometry, and recomputes them (same result) after they were
+    released over the memory budget or replaced by another geometry; device
+    coordinates go straight to the library."""
+    torch = torch_mod
+    from paper_2511_18233_gb300.autograd import RisModel
+    mol = synth.workload(0)
+    grads = []
+    for budget in (None, 0):
+        model = RisModel(mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc, 3,
+                         budget_bytes=budget)
+        R = torch.tensor(mol.coords, dtype=torch.float64, device="cuda", requires_grad=True)
+        model.energy(R, 1).backward()
+        assert model.recomputed == (0 if budget is None else 1)
+        grads.append(R.grad.cpu().numpy())
+        # another geometry in between: the backward rebuilds at the saved one
+        R2 = torch.tensor(mol.coords, dtype=torch.float64, device="cuda", requires_grad=True)
+        w2 = model.energy(R2, 1)
+        model.solve(R2.detach() + 0.01)
+        w2.backward()
+        assert _rel(R2.grad.cpu().numpy(), grads[-1]) <= 1e-12
+    assert _rel(grads[0], grads[1]) <= 1e-12
+
+
+@gpu
 @pytest.mark.slow
 def test_autograd_flake_rpa(torch_mod, oracle):
-    """C54H18 flake, RPA, 20 states: the state-1 energy's backward against
-    2-point central differences (step 1e-3 bohr) and the oracle (one atom)."""
+    """C54H18 flake, full RPA, 20 states.
+
+    * all 20 excitation energies against the oracle's RPA Davidson, 1e-9
+      relative;
+    * the derivative kernels at the oracle's amplitudes on three atoms
+      against the oracle's per-atom route, within the FP64 floor of this
+      system: the flake's Coulomb metric has cond ~6e8, and two FP64 routes
+      to M^-1 that are equal in exact arithmetic (LU solve and Cholesky) give
+      gradients differing by up to ~1e-4 of max|g| (pinned on the CPU by
+      tests/test_oracle_ris.py::test_flake_gradient_fp64_floor).  The bound
+      is twice that spread, measured here on the same atoms, plus 1e-9;
+    * the state-1 energy's autograd backward equal to the library gradient at
+      its own amplitudes, translation sum rule, and central differences of
+      the re-solved energy at step 1e-3 bohr: the 5-point stencil
+      (truncation ~1e-10 relative) within the same floor, the prescribed
+      2-point stencil within 1e-5 of max|g| (its O(h^2) truncation).
+    """
     torch = torch_mod
     from paper_2511_18233_gb300 import ris
     from paper_2511_18233_gb300.autograd import RisModel
     mol = synth.workload(2)
     assert mol.nao == 1134 and mol.nocc == 171
-    model = RisModel(mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc, 20, rpa=True,
+    NS = 20
+    orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc)
+    om_ref, Xo, Yo, _ = orc.rpa_davidson(NS, tol=1e-7)
+    model = RisModel(mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc, NS, rpa=True,
                      precision=ris.FP64)
     R = torch.tensor(mol.coords, dtype=torch.float64, device="cuda", requires_grad=True)
     w = model.energy(R, 0)
     w.backward()
     g = R.grad.cpu().numpy()
-    assert np.max(np.abs(g.sum(axis=0))) <= 1e-8
-    # the oracle's gradient of the same state (library amplitudes), one atom
-    out = model.solve(torch.as_tensor(mol.coords))
-    orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc)
-    ref = orc.gradients([0], out[1][:1], out[2][:1], atoms=[60])[0]
-    # cond(M_J) ~ 6e8 limits the agreement of two FP64 RI evaluations to ~1e-7
-    assert np.max(np.abs(g[60] - ref[60])) <= 1e-6 * np.max(np.abs(ref[60]))
-    # central differences, step 1e-3 bohr.  The flake's J metric has a
-    # condition number ~6e8, so each FP64 energy carries ~1e-8 Ha of rounding
-    # noise, i.e. ~1e-5 Ha/bohr in a 2-point difference at this step.
+    om, Xg, Yg = model.solve(R)
+    rel_om = float(np.max(np.abs(om - om_ref)) / np.max(np.abs(om_ref)))
+    # derivative kernels at the oracle's amplitudes
+    atoms = [0, 30, 60]
+    g_o = model.ctx.gradient([0], X=np.ascontiguousarray(Xo[:1]), Y=np.ascontiguousarray(Yo[:1]))[0]
+    ref = orc.gradients([0], Xo[:1], Yo[:1], atoms=atoms)[0][atoms]
+    orc_c = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy,
+                             mol.nocc, metric_inverse="cholesky")
+    ref_c = orc_c.gradients([0], Xo[:1], Yo[:1], atoms=atoms)[0][atoms]
+    floor = float(np.max(np.abs(ref - ref_c)))
+    scale = float(np.max(np.abs(ref)))
+    err_o = float(np.max(np.abs(g_o[atoms] - ref)))
+    # the backward is the library gradient at the forward's own amplitudes
+    g_lib = model.ctx.gradient([0], X=np.ascontiguousarray(Xg[:1]), Y=np.ascontiguousarray(Yg[:1]))[0]
+    fd_rows = []
     for (A, x) in [(0, 0), (60, 1)]:
-        fd = _fd(model, mol.coords, 0, A, x, 1e-3, 2)
-        assert abs(g[A, x] - fd) <= 5e-5
+        fd2 = _fd(model, mol.coords, 0, A, x, 1e-3, 2)
+        fd5 = _fd(model, mol.coords, 0, A, x, 1e-3, 5)
+        fd_rows.append((A, x, g[A, x], fd2, fd5))
+    print(f"\nflake: omega rel {rel_om:.2e}; kernels vs oracle {err_o:.2e} (floor {floor:.2e}, "
+          f"max|g| {scale:.2e}); FD " +
+          "; ".join(f"({A},{x}) g {gv:.6e} fd2-g {f2 - gv:.1e} fd5-g {f5 - gv:.1e}"
+                    for A, x, gv, f2, f5 in fd_rows))
+    assert rel_om <= 1e-9
+    assert err_o <= 2.0 * floor + 1e-9 * scale
+    assert _rel(g, g_lib) <= 1e-12
+    assert np.max(np.abs(g.sum(axis=0))) <= 1e-10 * np.max(np.abs(g))
+    gmax = float(np.max(np.abs(g)))
+    for A, x, gv, f2, f5 in fd_rows:
+        assert abs(gv - f5) <= 2.0 * floor + 1e-8 * gmax
+        assert abs(gv - f2) <= 1e-5 * gmax

@@ -221,15 +221,21 @@ def test_random_amplitudes_and_device_pointers(ris_mod, small):
     np.testing.assert_array_equal(nd.cpu().numpy(), nac)
 
 
-@gpu
-@pytest.mark.slow
-def test_chain_c20h22_parity(ris_mod, oracle):
-    """The 42-atom chain with s+p Coulomb auxiliaries: 10 states, spot-checked
-    gradients and adjacent couplings on sampled atoms."""
+@pytest.fixture(scope="module")
+def chain(oracle):
     mol = synth.workload(1)
     orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy,
                            mol.nocc)
     w, X, _ = orc.tda_davidson(11, tol=1e-11)
+    return mol, orc, w, X
+
+
+@gpu
+@pytest.mark.slow
+def test_chain_c20h22_parity(ris_mod, chain):
+    """The 42-atom chain with s+p Coulomb auxiliaries: 10 states, spot-checked
+    gradients and adjacent couplings on sampled atoms."""
+    mol, orc, w, X = chain
     c = _ctx(ris_mod, mol)
     om, Xg = c.excite(10)
     np.testing.assert_allclose(om, w[:10], rtol=1e-9)
@@ -245,6 +251,28 @@ def test_chain_c20h22_parity(ris_mod, oracle):
     assert _rel(nac[0, atoms], nref[0, atoms]) <= 1e-9
     assert _rel(nac[5, atoms], nref[1, atoms]) <= 1e-9
     assert np.max(np.abs(g.sum(axis=1))) <= 1e-10 * np.max(np.abs(g))
+
+
+@gpu
+@pytest.mark.slow
+def test_chain_c20h22_full_arrays(ris_mod, chain):
+    """One complete gradient array (all 42 atoms) and all nine adjacent
+    coupling numerators of the chain against the oracle's per-atom route,
+    element by element, at the oracle's amplitudes; plus the translation sum
+    rule on every array."""
+    mol, orc, w, X = chain
+    Xin = np.ascontiguousarray(X[:10])
+    c = _ctx(ris_mod, mol)
+    g = c.gradient([0], X=Xin)
+    pairs = [(s, s + 1) for s in range(9)]
+    num = np.zeros((9, mol.natm, 3))
+    c.nac(pairs, X=Xin, omega=np.ascontiguousarray(w[:10]), numerator=num)
+    ref = orc.pair_energy_derivs([(0, 0)] + pairs, Xin)
+    assert _rel(g[0], ref[0]) <= 1e-9
+    for p in range(9):
+        assert _rel(num[p], ref[1 + p]) <= 1e-9, p
+    for a in (g[0], *num):
+        assert np.max(np.abs(a.sum(axis=0))) <= 1e-10 * np.max(np.abs(a))
 
 
 @gpu

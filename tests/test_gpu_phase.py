@@ -1,7 +1,7 @@
 """Phase tracking along a trajectory: each state's sign follows the previous
 step through the overlap over its five most dominant determinants.  The
-decision (an integer per state) is compared bit-exactly with the rule
-written out in numpy; planted sign flips are undone; couplings computed from
+decision (an integer per state) is compared bit-exactly with the oracle's
+phase rule; planted sign flips are undone; couplings computed from
 the aligned amplitudes change sign exactly with the flipped states."""
 import numpy as np
 import pytest
@@ -23,14 +23,10 @@ def ris_mod():
 
 
 def rule(X, Xp):
-    """Sign per state: overlap of X with Xp over the five largest |Xp|
-    elements (ties by lower index)."""
-    out = []
-    for x, xp in zip(X.reshape(len(X), -1), Xp.reshape(len(Xp), -1)):
-        a = np.abs(xp)
-        idx = sorted(range(a.size), key=lambda i: (-a[i], i))[:5]
-        out.append(-1 if float(np.sum(x[idx] * xp[idx])) < 0.0 else 1)
-    return np.array(out, dtype=np.int32)
+    """The oracle's phase decision per state (five most dominant
+    determinants of the previous step)."""
+    from oracle import ris_oracle
+    return ris_oracle.phase_align(X, Xp)[0]
 
 
 def _ctx(ris_mod, mol, coords):
