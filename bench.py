@@ -1,10 +1,10 @@
 #!/usr/bin/env python
 """Throughput benchmark of the sm_103a TDDFT-ris engine.
 
-One step = one evaluation at one geometry of the C20H22 chain workload
-(42 atoms, 512 AOs, nocc 71, 102 J / 42 K auxiliary functions): screened
-three-centre integrals and metric Cholesky, B tensors, Davidson for the 10
-lowest TDA-ris states, gradients of all 10 states and the 9 couplings
+Headline: one step = one evaluation at one geometry of the C20H22 chain
+workload (42 atoms, 512 AOs, nocc 71, 102 J / 42 K auxiliary functions):
+screened three-centre integrals and metric Cholesky, B tensors, Davidson for
+the 10 lowest TDA-ris states, gradients of all 10 states and the 9 couplings
 between adjacent states.  Metric: evaluations per second.
 
 * value: the mixed-precision form (the throughput form; the FP64 form is
@@ -15,11 +15,21 @@ between adjacent states.  Metric: evaluations per second.
   timed events.
 * e2e: the same evaluation through host (numpy) buffers, host<->device copies
   inside the timed region, wall clock.
-* roofline: the kernel class with the largest share of the timed region
-  (per-class CUDA events inside the library).
-* cpu_baseline / --impl reference: the FP64 oracle on the host cores on a
-  bounded sample of the same workload (setup, Davidson, the derivative of
-  two pair energies w.r.t. one atom), extrapolated to the full evaluation.
+* roofline: the kernel class with the largest share of the timed region;
+  `achieved` counts the method's algorithmic work of that class (the
+  per-unit figures of the scope table: B build, A X per product, Gamma per
+  pair) over its CUDA-event time; peaks are the measured pipe rates
+  (profiles/peaks_probe_gb300.json, MEASURED_PEAKS.json).
+* error_vs_oracle: per result (energies, sampled gradients and couplings of
+  the timed evaluation) against the FP64 oracle.
+* configs: the other workloads as extra keys (C4H6 absolute time; the
+  C54H18 flake RPA-ris with the autograd state-1 gradient).
+* serving: the surface-hopping stream (64 trajectories, 2000 requests after
+  200, Poisson 200/s, warm Davidson) against plain FP64 replay.
+* cpu_baseline / --impl reference: the FP64 oracle on the host cores: the
+  C20H22 sample (setup, Davidson, derivatives of two pair energies w.r.t.
+  one atom, extrapolated to the full evaluation) and the C4H6 evaluation in
+  full, on all cores and on one.
 
 Multi-GPU: replicas only (each rank evaluates its own copy; no collective
 in the data path); value = evaluations of all ranks / max time over ranks.
@@ -27,6 +37,7 @@ in the data path); value = evaluations of all ranks / max time over ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -59,13 +70,52 @@ def replica_throughput(seconds: float, steps: int, world: int, dist=None, device
     return world * steps / seconds
 
 
-def _peaks():
+def peaks():
+    """Roofline denominators: HBM copy and bf16 from MEASURED_PEAKS.json, the
+    FP64 FMA, TF32 and FP16 tensor pipes from the committed probe run."""
+    out = {"src": {}}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return p, "measured"
+        out["hbm_gbs"], out["bf16_tflops"] = p["hbm_gbs"], p["bf16_tflops"]
+        out["src"]["hbm"] = "measured (MEASURED_PEAKS.json, copy)"
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+        out["hbm_gbs"], out["bf16_tflops"] = 6800.0, 1900.0
+        out["src"]["hbm"] = "fallback"
+    try:
+        with open(os.path.join(ROOT, "profiles", "peaks_probe_gb300.json")) as f:
+            r = json.load(f)["rates"]
+        out["fp64_tflops"] = r["fp64_fma"]["tflops"]
+        out["tf32_tflops"] = r["tf32_tcgen05"]["tflops"]
+        out["f16_tflops"] = r["f16_tcgen05"]["tflops"]
+        out["src"]["pipes"] = "measured (profiles/peaks_probe_gb300.json)"
+    except Exception:
+        out["fp64_tflops"] = out["bf16_tflops"] * 1.25 / 2250.0
+        out["tf32_tflops"] = out["bf16_tflops"] * 1.1 / 2.25
+        out["f16_tflops"] = out["bf16_tflops"]
+        out["src"]["pipes"] = "fallback (bf16 x nominal ratios)"
+    return out
+
+
+# DRAM traffic per launch of the dominant kernels, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid while the source file
+# it was taken on is unchanged (sha256 prefix).
+TRAFFIC = {}
+
+
+def _src_sha(rel):
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def traffic_for(cls):
+    t = TRAFFIC.get(cls)
+    if not t or _src_sha(t["source"]) != t["sha"]:
+        return None
+    return t["bytes_per_launch"]
 
 
 class Clocks:
@@ -107,6 +157,7 @@ class Clocks:
     def summary(self):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+
         def num(x):
             try:
                 return float(x)
@@ -121,10 +172,24 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for key in ("Model name", "BIOS Model name"):
+            for line in out.splitlines():
+                if line.strip().startswith(key + ":"):
+                    v = line.split(":", 1)[1].strip()
+                    if v and v != "-":
+                        return v
+    except Exception:
+        pass
+    return os.uname().machine
+
+
 # ------------------------------------------------------------------ oracle leg
-def oracle_sample(mol, reps=1):
-    """Time the oracle on a bounded sample; returns (evals/s, seconds used,
-    sample description, omega, sample derivative)."""
+def oracle_sample(mol):
+    """Time the oracle on a bounded sample of the C20H22 evaluation; returns
+    (evals/s, seconds used, sample description, reference values)."""
     from oracle import ris_oracle
     ris_oracle.build()
     t0 = time.perf_counter()
@@ -140,7 +205,50 @@ def oracle_sample(mol, reps=1):
     t_full = (t1 - t0) + (t2 - t1) + (t3 - t2) / len(pairs) * npair_full * mol.natm
     sample = (f"oracle setup + Davidson({NSTATES}) + d/dR of {len(pairs)} pair energies for 1 of "
               f"{mol.natm} atoms; derivative time extrapolated to {npair_full} pairs x {mol.natm} atoms")
-    return 1.0 / t_full, t3 - t0, sample, w, X, d
+    # reference values of the per-result errors (not timed): gradients of
+    # states 0 and 9 and the (0,1) coupling on atoms 0 and 20
+    atoms = [0, 20]
+    g = orc.gradients([0, NSTATES - 1], X, atoms=atoms)
+    nac = orc.nacs([(0, 1)], w, X, atoms=atoms)
+    ref = {"omega": w, "atoms": atoms, "grad": g[:, atoms], "nac01": nac[0, atoms]}
+    return 1.0 / t_full, t3 - t0, sample, ref
+
+
+_CFG1_ORACLE = r"""
+import sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from paper_2511_18233_gb300 import synth
+from oracle import ris_oracle
+ris_oracle.build()
+mol = synth.workload(0)
+ts = []
+for rep in range(3):
+    t0 = time.perf_counter()
+    orc = ris_oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc)
+    w, X, _ = orc.tda_davidson(5, tol=1e-10)
+    g = orc.gradients(range(5), X)
+    n = orc.nacs([(0, 1)], w, X)
+    ts.append(time.perf_counter() - t0)
+print(json.dumps({"seconds": sorted(ts)[1]}))
+"""
+
+
+def oracle_cfg1_full(threads):
+    """The C4H6 evaluation (5 states, 5 gradients, NAC(S1,S2)) by the oracle in
+    full, in a child process with `threads` OpenMP/BLAS threads (None: all
+    cores); median of 3."""
+    env = dict(os.environ)
+    if threads:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = str(threads)
+    r = subprocess.run([sys.executable, "-c", _CFG1_ORACLE % ROOT], capture_output=True, text=True,
+                       env=env, timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    s = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+    return {"evals_per_s": 1.0 / s, "ms_per_eval": 1e3 * s,
+            "threads": threads or os.cpu_count()}
 
 
 def run_reference(args):
@@ -151,7 +259,7 @@ def run_reference(args):
     mol = synth.workload(1)
     vals, used = [], 0.0
     for it in range(args.warmup + args.steps):
-        v, t, sample, *_ = oracle_sample(mol)
+        v, t, sample, _ = oracle_sample(mol)
         used += t
         if it >= args.warmup:
             vals.append(v)
@@ -162,20 +270,21 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(CONFIG, workload=WORKLOAD, subspace_eig="fp32" if args.eig_fp32 else "fp64"),
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": sample},
+                             "cpu": cpu_model(), "kind": "oracle (extrapolated)", "sample": sample},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-# ------------------------------------------------------------------ GPU leg
-def run_serving(args):
+# ------------------------------------------------------------------ GPU legs
+def run_serving(args, quick=False):
     """Serving stream of surface-hopping requests (energies + active-state
     gradient + NACs to the neighbouring states) from a closed pool of
     trajectories with Poisson arrivals; mixed precision with continuous
-    batching over several slots, then the same stream replayed on the plain
-    FP64 path one request at a time (cold Davidson, one slot)."""
+    batching over several slots (Davidson seeded with the trajectory's
+    resident amplitudes unless --serve-cold), then the same stream replayed
+    on the plain FP64 path one request at a time (cold Davidson, one slot)."""
     import torch
     from paper_2511_18233_gb300 import build, serve
     build.build()
@@ -183,6 +292,7 @@ def run_serving(args):
     specs = serve.make_trajectories(args.serve_trajectories, seed=2025)
     free, total = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
+    warm = not args.serve_cold
     out = {}
     for mode in ("mixed", "fp64_plain"):
         mixed = mode == "mixed"
@@ -191,7 +301,7 @@ def run_serving(args):
         with Clocks(0) as clk:
             res = serve.serve(specs, n_requests=nreq, n_warmup=nwarm, rate=args.serve_rate,
                               nslots=args.serve_slots if mixed else 1, budget_bytes=budget,
-                              precision="mixed" if mixed else "fp64", use_guess=args.serve_guess and mixed, seed=7,
+                              precision="mixed" if mixed else "fp64", use_guess=warm and mixed, seed=7,
                               **({"eig_fp32": 1} if mixed and args.eig_fp32 else {}))
         done = res.pop("done")
         res.pop("trajectories")
@@ -207,12 +317,12 @@ def run_serving(args):
             "dtype": "f32/tf32x3+f64", "data": "synthetic",
             "config": {"workload": f"{args.serve_trajectories} trajectories, chains C4..C40 and flakes "
                                    f"4-7 A, 5-10 states, Poisson {args.serve_rate}/s, closed pool",
+                       "requests": args.serve_requests, "warmup_requests": args.serve_warmup,
                        "slots": args.serve_slots, "budget_bytes": budget,
-                       "davidson_seed": "previous step" if args.serve_guess else "cold",
+                       "davidson_seed": "previous step" if warm else "cold",
                        "subspace_eig": "fp32" if args.eig_fp32 else "fp64"},
             "mixed": m, "fp64_plain": f}
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def main():
@@ -224,22 +334,25 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
                     help="both: mixed is the headline value, FP64 reported beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve", action="store_true", help="run the serving stream instead")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads and serving")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve", action="store_true", help="run only the serving stream")
     ap.add_argument("--eig-fp32", action="store_true",
                     help="mixed form: Davidson subspace eigenproblem in FP32 (option eig_fp32)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
-    ap.add_argument("--serve-fp64-requests", type=int, default=100)
+    ap.add_argument("--serve-fp64-requests", type=int, default=50)
     ap.add_argument("--serve-trajectories", type=int, default=64)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-guess", action="store_true",
-                    help="seed each step's Davidson with the trajectory's resident amplitudes")
+    ap.add_argument("--serve-cold", action="store_true",
+                    help="start every step's Davidson cold instead of from the resident amplitudes")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
-        return run_serving(args)
+        print(json.dumps(run_serving(args)))
+        return 0
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -253,11 +366,16 @@ def main():
     from paper_2511_18233_gb300 import build, synth
     build.build()
     mol = synth.workload(1)
-    cpu = None
+    cpu = cfg1_cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(mol)  # before any CUDA work of the library
+        cfg1_cpu = {"all_cores": oracle_cfg1_full(None), "one_thread": oracle_cfg1_full(1)}
     precs = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
     res = {p: measure(p, mol, args, world, local, dist) for p in precs}
+    extra = {}
+    if not args.no_extra and world == 1:
+        extra["c4h6"] = {p: measure_small(p, args) for p in precs}
+        extra["c54h18_flake_rpa"] = {p: measure_flake(p, args) for p in precs}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -279,15 +397,91 @@ def main():
     if len(precs) > 1:
         line["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
     if cpu is not None:
-        v, used, sample, w_ref, X_ref, d_ref = cpu
-        line["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": sample, "seconds": round(used, 2)}
-        line["error_vs_oracle"] = {p: {"omega_max_abs": float(np.max(np.abs(res[p]["omega"] - w_ref)))}
-                                   for p in precs}
+        v, used, sample, ref = cpu
+        line["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "cpu": cpu_model(),
+                                "kind": "oracle (extrapolated)", "sample": sample, "seconds": round(used, 2),
+                                "c4h6_full_evaluation": cfg1_cpu}
+        errs = {}
+        for p in precs:
+            r = res[p]
+            a = ref["atoms"]
+            errs[p] = {"omega_max_abs_ha": float(np.max(np.abs(r["omega"] - ref["omega"][:NSTATES]))),
+                       "grad_max_abs_ha_bohr": float(np.max(np.abs(r["grad"][[0, NSTATES - 1]][:, a] - ref["grad"]))),
+                       "nac01_max_abs_per_bohr": float(np.max(np.abs(r["nac"][0, a] - ref["nac01"]))),
+                       "sample": f"all {NSTATES} energies; gradients of states 0 and {NSTATES - 1} and the "
+                                 f"(0,1) coupling on atoms {a}, oracle amplitudes vs the library's"}
+        line["error_vs_oracle"] = errs
+    if extra:
+        line["configs"] = extra
+    if not args.no_extra and not args.no_serve and world == 1:
+        line["serving"] = run_serving(args)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def algorithmic_work(precision, d, nprod, npair, rpa=False):
+    """The method's own work per evaluation and kernel class (scope-table
+    counts, dense, no screening credit): flops for the GEMM classes (a
+    3xTF32 product counts once), bytes are reported by the library."""
+    n, o, v, nJ, nK = d["nao"], d["nocc"], d["nvir"], d["nJ"], d["nK"]
+    nov = o * v
+    coul_ax = 4.0 * nov * nJ * nprod * (2 if rpa else 1)
+    exch_ax = (2.0 * v * v * o * nK + 2.0 * o * o * v * nK) * nprod * (2 if rpa else 1)
+    b_coul = 2.0 * o * n * n * nJ + 2.0 * o * v * n * nJ
+    b_k = 2.0 * o * n * n * nK + 2.0 * o * o * n * nK + 2.0 * v * n * n * nK + 2.0 * v * v * n * nK
+    gam = (2.0 * o * v * v * nK + 4.0 * n * n * o * nK) * npair
+    if precision == "fp64":
+        return {"dgemm_fp64": coul_ax + exch_ax + b_coul + b_k + gam}
+    return {"dgemm_fp64": coul_ax + 2.0 * o * o * n * nK,
+            "tc_gemm_3xtf32": exch_ax + 2.0 * v * n * n * nK + 2.0 * v * v * n * nK + gam,
+            "emu_gemm_f64": b_coul}
+
+
+def classify(st, steps, step_ms_total, precision, dims, nprod, npair):
+    """Per kernel class: time share, executed and algorithmic work against
+    the pipe's measured peak."""
+    pk = peaks()
+    alg = algorithmic_work(precision, dims, nprod, npair)
+    tf32x3 = pk["tf32_tflops"] / 3.0           # three TF32 passes per product
+    emu = pk["f16_tflops"] / 55.0               # 55 FP16 slice products per FP64 product
+    classes = {
+        "tc_gemm_3xtf32": (st["tc_gemm_ms"], st["tc_gemm_flops"], "tensor (tf32)", tf32x3,
+                           "TF32 tcgen05 probe / 3 passes"),
+        "dgemm_fp64": (st["gemm_ms"], st["gemm_flops"], "fp64 fma", pk["fp64_tflops"], "FP64 FMA probe"),
+        "emu_gemm_f64": (st["emu_gemm_ms"], st["emu_gemm_flops"], "tensor (f16)", emu,
+                         "FP16 tcgen05 probe / 55 slice products (FP64-equivalent)"),
+        "contract": (st["contract_ms"], None, "hbm", None, "HBM copy"),
+        "subspace_eig": (st["eig_ms"], None, "latency (fp64, one CTA per eigenvalue)", None, ""),
+        "int3c": (st["int3c_ms"], None, "fp64 alu", None, "FP64 ALU roofline: profiles/"),
+        "int3c_deriv": (st["int3c_deriv_ms"], None, "fp64 alu", None,
+                        "side stream under the B build and Davidson, time not additive"),
+    }
+    table = {}
+    for k, (ms, exe, bound, peak, note) in classes.items():
+        row = {"ms_per_step": round(ms / steps, 3), "share_of_step": ms / (step_ms_total or 1.0), "bound": bound}
+        if k == "contract" and ms > 0:
+            ach = st["contract_bytes"] / 1e9 / (ms / 1000.0)
+            row.update({"achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                        "peak_source": pk["src"]["hbm"], "work": "algorithmic bytes"})
+        elif peak is not None and ms > 0:
+            a = alg.get(k, 0.0) * steps / 1e12 / (ms / 1000.0)
+            e = exe / 1e12 / (ms / 1000.0)
+            row.update({"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                        "executed_tflops": e, "executed_frac": e / peak,
+                        "peak_source": note + ", " + pk["src"]["pipes"],
+                        "work": "algorithmic flops (scope-table counts)"})
+        elif note:
+            row["note"] = note
+        table[k] = row
+    dom = max((k for k in classes if k != "int3c_deriv"), key=lambda k: classes[k][0])
+    roof = {"kernel": dom, "bound": table[dom]["bound"], "share_of_step": table[dom]["share_of_step"]}
+    for key in ("achieved", "peak", "unit", "frac", "peak_source", "executed_frac"):
+        if key in table[dom]:
+            roof[key] = table[dom][key]
+    roof["traffic"] = traffic_for(dom)
+    return roof, table
 
 
 def measure(precision, mol, args, world, local, dist):
@@ -328,6 +522,7 @@ def measure(precision, mol, args, world, local, dist):
     torch.cuda.synchronize()
     times = []
     l0 = ctx.stats()["launches"]
+    nprod = 0
     with Clocks(local) as clk:
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
@@ -343,6 +538,7 @@ def measure(precision, mol, args, world, local, dist):
     launches = int(st["launches"] - l0)
     stages = {k: round(st[k], 3) for k in ("aux_ms", "B_ms", "excite_ms", "deriv_ms")}
     stages.update({"davidson_products": int(st["n_products"]), "davidson_iterations": int(st["n_iter"])})
+    nprod = int(st["n_products"])
     torch.cuda.synchronize()
     tot = sum(times) / 1000.0
     value = replica_throughput(tot, args.steps, world, dist, dev)
@@ -364,51 +560,98 @@ def measure(precision, mol, args, world, local, dist):
         if it > 0:
             e2e_t.append(t1 - t0)
     e2e = world / float(np.mean(e2e_t))
-
-    peaks, src = _peaks()
-    fp64_peak = peaks["bf16_tflops"] * 1.25 / 2250.0  # measured bf16 x nominal FP64/BF16 ratio
-    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25     # measured bf16 x nominal TF32/BF16 ratio
-    classes = {
-        "tc_gemm_3xtf32": (st["tc_gemm_ms"], 3 * st["tc_gemm_flops"] / 1e12, "tensor", "TFLOP/s", tf32_peak,
-                           f"of {src} bf16 x nominal TF32/BF16 (1.1/2.25); achieved counts the 3 TF32 passes"),
-        "dgemm_fp64": (st["gemm_ms"], st["gemm_flops"] / 1e12, "tensor", "TFLOP/s", fp64_peak,
-                       f"of {src} bf16 x nominal FP64/BF16 (1.25/2250)"),
-        # FP64-accurate products on the FP16 tensor cores: 55 digit-slice
-        # products per FP64 product, counted as FP16 tensor work
-        "emu_gemm_f64": (st["emu_gemm_ms"], 55 * st["emu_gemm_flops"] / 1e12, "tensor", "TFLOP/s",
-                         peaks["bf16_tflops"], f"of {src} bf16 (FP16 runs at the same rate); "
-                         "achieved counts the 55 slice products"),
-        "int3c_deriv": (st["int3c_deriv_ms"], None, "alu", None, None,
-                        "side stream: runs under the B build and Davidson, time not additive"),
-        "int3c": (st["int3c_ms"], None, "alu", None, None, ""),
-        "contract": (st["contract_ms"], st["contract_bytes"] / 1e9, "hbm", "GB/s", peaks["hbm_gbs"],
-                     f"of {src} HBM copy"),
-        "subspace_eig": (st["eig_ms"], None, "alu", None, None, ""),
-    }
-    table = {}
-    for k, (ms, work, bound, unit, peak, note) in classes.items():
-        row = {"ms_per_step": round(ms / args.steps, 3), "share_of_step": ms / (sum(times) or 1.0),
-               "bound": bound}
-        if work is not None and ms > 0:
-            ach = work / (ms / 1000.0)
-            row.update({"achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak})
-        elif note:
-            row["note"] = note
-        table[k] = row
-    dom = max((k for k in classes if k != "int3c_deriv"), key=lambda k: classes[k][0])
-    ms, work, bound, unit, peak, note = classes[dom]
-    roof = {"kernel": dom, "bound": bound, "share_of_step": ms / (sum(times) or 1.0)}
-    if work is not None:
-        ach = work / (ms / 1000.0)
-        roof.update({"achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak, "peak_source": note,
-                     "traffic": None})
+    dm = ctx.dims()
+    dims = {"nao": dm["nao"], "nocc": mol.nocc, "nvir": mol.nvir, "nJ": dm["nauxJ"], "nK": dm["nauxK"]}
+    roof, table = classify(st, args.steps, sum(times), precision, dims, nprod, NSTATES + len(pairs))
     ctx.close()
     return {"value": value, "ms_per_step": 1000.0 * tot / args.steps,
             "dtype": "f64" if precision == "fp64" else "f32/tf32x3+f64",
             "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches, "stages": stages, "roofline": roof, "classes": table,
-            "clocks": clk.summary(), "omega": om_d.cpu().numpy()}
+            "clocks": clk.summary(), "omega": om_d.cpu().numpy(), "grad": g_d.cpu().numpy(),
+            "nac": n_d.cpu().numpy()}
+
+
+def _timed(fn, steps, warmup, stream, flush):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return ts
+
+
+def measure_small(precision, args):
+    """C4H6 chain (10 atoms, 112 AOs): 5 states, 5 gradients, NAC(S1,S2); it
+    fits in L2, so it is reported as absolute time per evaluation."""
+    import torch
+    from paper_2511_18233_gb300 import ris, synth
+    mol = synth.workload(0)
+    stream = torch.cuda.Stream()
+    ctx = ris.Context(precision=ris.FP64 if precision == "fp64" else ris.MIXED,
+                      cuda_stream=stream.cuda_stream)
+    dev = "cuda:0"
+    c, C, e = (torch.as_tensor(a, device=dev) for a in (mol.coords, mol.C, mol.mo_energy))
+    om = torch.zeros(5, dtype=torch.float64, device=dev)
+    X = torch.zeros((5, mol.nocc, mol.nvir), dtype=torch.float64, device=dev)
+    g = torch.zeros((5, mol.natm, 3), dtype=torch.float64, device=dev)
+    n = torch.zeros((1, mol.natm, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.build_aux(c, mol.shells, mol.aux_j, mol.aux_k)
+        ctx.build_B(C, e, mol.nocc)
+        ctx.excite(5, out=(om, X, None))
+        ctx.gradient(range(5), out=g)
+        ctx.nac([(0, 1)], out=n)
+
+    ts = _timed(step, max(args.steps, 5), args.warmup, stream, flush)
+    ctx.close()
+    ms = float(np.median(ts))
+    return {"workload": "C4H6 chain, 10 atoms, nao 112, TDA-ris 5 states, 5 gradients + NAC(S1,S2)",
+            "ms_per_eval_median": ms, "evals_per_s": 1000.0 / ms, "steps": len(ts)}
+
+
+def measure_flake(precision, args):
+    """C54H18 flake (72 atoms, 1134 AOs), full RPA-ris, 20 states; one
+    evaluation = the autograd forward (integrals, B, RPA Davidson) and the
+    backward of the state-1 energy (analytic gradient kernel)."""
+    import torch
+    from paper_2511_18233_gb300 import ris, synth
+    from paper_2511_18233_gb300.autograd import RisModel
+    mol = synth.workload(2)
+    stream = torch.cuda.Stream()
+    model = RisModel(mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc, 20, rpa=True,
+                     precision=ris.FP64 if precision == "fp64" else ris.MIXED,
+                     cuda_stream=stream.cuda_stream)
+    R0 = torch.as_tensor(mol.coords, device="cuda:0")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda:0")
+
+    def step():
+        R = R0.clone().requires_grad_(True)
+        with torch.cuda.stream(stream):
+            w = model.energy(R, 0)
+            w.backward()
+
+    steps = 3 if precision == "fp64" else max(args.steps, 3)
+    ts = _timed(step, steps, 1 if precision == "fp64" else args.warmup, stream, flush)
+    st = model.ctx.stats()
+    model.ctx.close()
+    ms = float(np.median(ts))
+    return {"workload": "C54H18 flake, 72 atoms, nao 1134, RPA-ris 20 states, autograd state-1 gradient",
+            "ms_per_eval_median": ms, "evals_per_s": 1000.0 / ms, "steps": len(ts),
+            "davidson_iterations_last": int(st["n_iter"])}
 
 
 if __name__ == "__main__":

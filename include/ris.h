@@ -86,7 +86,8 @@ typedef struct {
   int max_subspace;   /* Davidson subspace size before restart; 0 = automatic */
   double screen_thr;  /* shell-pair screening threshold; default 1e-14 */
   size_t mem_budget;  /* device bytes the context may hold; 0 = no limit */
-  int occ_block;      /* occupied-orbital block for streamed B builds; 0 = all */
+  int occ_block;      /* occupied orbitals per block of the exchange part of the Davidson
+                         products; 0 = automatic (all when they fit) */
   void* cuda_stream;  /* cudaStream_t to run on; NULL = the context makes one */
   int device;         /* CUDA device ordinal */
   int profile;        /* 1: time kernel classes with CUDA events (see ris_get_stats) */
@@ -110,6 +111,17 @@ typedef struct {
   int eig_fp32;       /* mixed precision: 1 solves the Davidson subspace eigenproblem in FP32
                          (FP64 Rayleigh quotients, close pairs and restarts re-orthonormalised
                          in FP64, back to FP64 if the residuals stall); 0 (default): FP64 */
+  int stream;         /* streamed form for systems whose dense AO three-index tensors do not
+                         fit (TDA only): the three-centre integrals are kept only on the
+                         screened shell pairs and mixed with the metric factors there, the MO
+                         transforms run over blocks of auxiliary functions, the exchange part
+                         of each Davidson product over blocks of occupied orbitals
+                         (occ_block), and the gradient regenerates the derivative integrals
+                         per block of auxiliary functions instead of storing them.
+                         0 (default): automatic (streamed when the dense integrals and
+                         derivative integrals would take more than a third of the device
+                         memory or of mem_budget); 1: always; -1: never */
+  int stream_block;   /* streamed form: auxiliary functions per block; 0 = automatic */
 } ris_options;
 
 typedef struct {
@@ -182,6 +194,17 @@ ris_status ris_excite_guess(ris_ctx* ctx, int nstates, const double* X_guess, do
  */
 ris_status ris_phase_align(ris_ctx* ctx, int nstates, const double* X_prev, int* sign,
                            double* X_out);
+
+/*
+ * Time-derivative couplings of surface hopping (Sec. 4: the hopping
+ * probabilities use T_IJ = g_IJ . v, the derivative coupling projected on
+ * the nuclear velocities): T[g] = sum_{A,x} nac[g][A][x] velocity[A][x] for
+ * npair couplings.  nac: [npair][natm][3] (1/bohr, e.g. from ris_nac);
+ * velocity: [natm][3] (bohr per atomic time unit); T: [npair].  Host or
+ * device pointers.  Needs ris_build_aux (for natm).
+ */
+ris_status ris_time_coupling(ris_ctx* ctx, int npair, const double* nac, const double* velocity,
+                             double* T);
 
 /*
  * The ris-approximated Z-vector solve: (A + B) Z = rhs (Eq. Z_vector, with

@@ -139,6 +139,8 @@ ris_status ris_options_default(ris_options* opt) {
   opt->deriv_prefetch = 1;
   opt->emu_f64 = 1;
   opt->eig_fp32 = 0;
+  opt->stream = 0;
+  opt->stream_block = 0;
   return RIS_OK;
 }
 
@@ -233,6 +235,11 @@ ris_status ris_excite_guess(ris_ctx* ctx, int nstates, const double* X_guess, do
 ris_status ris_phase_align(ris_ctx* ctx, int nstates, const double* X_prev, int* sign,
                            double* X_out) {
   return guarded(ctx, [&] { ctx->eng.phase_align(nstates, X_prev, sign, X_out); });
+}
+
+ris_status ris_time_coupling(ris_ctx* ctx, int npair, const double* nac, const double* velocity,
+                             double* T) {
+  return guarded(ctx, [&] { ctx->eng.time_coupling(npair, nac, velocity, T); });
 }
 
 ris_status ris_zvector(ris_ctx* ctx, int nrhs, const double* rhs, double* Z) {

@@ -129,6 +129,17 @@ void Engine::trim() {
   aoList.release();
   axPtr.release();
   axList.release();
+  pOff.release();
+  fpMu.release();
+  fpNu.release();
+  BJao.release();
+  BKao.release();
+  for (ShellSet& b : auxBlk) free_shells(b, st);
+  auxBlk.clear();
+  blkU0.clear();
+  blkW.clear();
+  blkWK.clear();
+  streamed = false;
   have_D = false;
   stage = 0;
   nstates = 0;
@@ -1088,6 +1099,7 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
       }
     make_shells(aux, a, l, e, &jm, &km, st);
     nU = aux.nfun;
+    nKsh = nKs;
     // functions of each atom (CSR) for the per-atom gradient sums
     auto csr = [&](const ShellSet& sh, SBuf<int>& ptr, SBuf<int>& list) {
       std::vector<int> cnt(natm + 1, 0), lst;
@@ -1143,13 +1155,22 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
     vmax = std::max(vmax, nb * 2.0 * M_PI / g * (aux.h_l[s] ? 1.0 / sqrt(g) : 1.0));
   }
   build_pairs(ao, xyz.p, opt.screen_thr / std::max(vmax, 1e-300), pl, nullptr, st);
-  // integrals
+  // integrals: dense [mu][nu][P], or (streamed form) on the screened pairs
+  // only, after the metric factors are known
   const int nao_ = ao.nfun;
-  TJ.ensure((size_t)nao_ * nao_ * nJ, st);
-  TK.ensure((size_t)nao_ * nao_ * nK, st);
-  RIS_CUDA(cudaMemsetAsync(TJ.p, 0, sizeof(double) * (size_t)nao_ * nao_ * nJ, st));
-  RIS_CUDA(cudaMemsetAsync(TK.p, 0, sizeof(double) * (size_t)nao_ * nao_ * nK, st));
-  int3c(ao, aux, pl, xyz.p, nJ, nK, TJ.p, TK.p, st);
+  streamed = want_streamed(nao_);
+  if (!streamed) {
+    TJ.ensure((size_t)nao_ * nao_ * nJ, st);
+    TK.ensure((size_t)nao_ * nao_ * nK, st);
+    RIS_CUDA(cudaMemsetAsync(TJ.p, 0, sizeof(double) * (size_t)nao_ * nao_ * nJ, st));
+    RIS_CUDA(cudaMemsetAsync(TK.p, 0, sizeof(double) * (size_t)nao_ * nao_ * nK, st));
+    int3c(ao, aux, pl, xyz.p, nJ, nK, TJ.p, TK.p, st);
+  } else {
+    TJ.release();
+    TK.release();
+    D.release();
+    Df.release();
+  }
   MU.ensure((size_t)nU * nU, st);
   dMU.ensure(3 * (size_t)nU * nU, st);
   int2c(aux, xyz.p, MU.p, dMU.p, st);
@@ -1173,8 +1194,9 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
               "auxiliary metric is not positive definite (pivot " +
                   std::to_string(info[0] ? info[0] : info[1]) + ")");
   nao = nao_;
+  if (streamed) setup_streamed();
   stage = 1;
-  if (opt.deriv_prefetch && st2) {  // derivative integrals behind the B build and Davidson
+  if (opt.deriv_prefetch && st2 && !streamed) {  // derivative integrals behind the B build and Davidson
     RIS_CUDA(cudaEventRecord(evA, st));
     RIS_CUDA(cudaStreamWaitEvent(st2, evA, 0));
     start_D(st2);
@@ -1223,6 +1245,11 @@ void Engine::build_B(int nao_, int nmo_, int nocc_, const double* Cin, const dou
   }
   k_orb_diff<<<cdiv(nov, 256), 256, 0, st>>>(eps.p, o, v, de.p);
   RIS_CHECK_LAUNCH();
+  if (streamed) {
+    build_B_streamed();
+    stage = 2;
+    return;
+  }
   const double* Co = C.p;
   const double* Cv = C.p + o;
   // Coulomb: H[i][nu][P] = sum_mu C_mu,i T[mu][nu][P]; B[i][a][P]; B L^-T
@@ -1511,45 +1538,60 @@ void Engine::apply_exchange_mixed(const double* Z, int nvec, double* out, double
   XtH.ensure((size_t)nvec * v * lo4, st);
   XtL.ensure((size_t)nvec * v * lo4, st);
   split_f64_t(Z, o, v, v, XtH.p, XtL.p, lo4, st, nvec, nov, (long long)v * lo4);
-  const size_t ysz = (size_t)nvec * o * nK * lv4;
+  // occupied orbitals per pass: all of them while Y stays below 3 Gi floats
+  // (per half), else blocks of ib (each pass reads B^K_vv once more)
+  const size_t per_i = (size_t)nvec * nK * lv4;
+  int ib = o;
+  if (opt.occ_block > 0)
+    ib = std::min(o, opt.occ_block);
+  else if (per_i * o > ((size_t)3 << 30))
+    ib = std::max(1, (int)(((size_t)3 << 30) / per_i));
+  const size_t ysz = per_i * ib;
   if (YH.n < ysz) {
     YH.ensure(ysz, st);
     YL.ensure(ysz, st);
   }
-  TcOperand A, B;
-  A.hi = BooH.p;
-  A.lo = BooL.p;
-  A.rows = o * nK;
-  A.ld = lo4;
-  B.hi = XtH.p;
-  B.lo = XtL.p;
-  B.rows = v;
-  B.ld = lo4;
-  B.bstride = (long long)v * lo4;
-  B.nb = nvec;
-  TcEpilogue e1;
-  e1.mode = kOutSplit;
-  e1.chi = YH.p;
-  e1.clo = YL.p;
-  e1.rs = lv4;
-  e1.bsc = (long long)o * nK * lv4;
-  tc_gemm(o * nK, v, o, A, B, nvec, e1, d_tcerr, st);
-  TcOperand A2, B2;
-  A2.hi = YH.p;
-  A2.lo = YL.p;
-  A2.rows = nvec * o;
-  A2.ld = nK * lv4;
-  B2.hi = BvvH.p;
-  B2.lo = BvvL.p;
-  B2.rows = v;
-  B2.ld = nK * lv4;
-  TcEpilogue e2;
-  e2.mode = kOutF64;
-  e2.c64 = out;
-  e2.rs = v;
-  e2.alpha = alpha;
-  e2.beta = beta;
-  tc_gemm(nvec * o, v, nK * lv4, A2, B2, 1, e2, d_tcerr, st);
+  for (int i0 = 0; i0 < o; i0 += ib) {
+    const int ni = std::min(ib, o - i0);
+    TcOperand A, B;
+    A.hi = BooH.p + (size_t)i0 * nK * lo4;
+    A.lo = BooL.p + (size_t)i0 * nK * lo4;
+    A.rows = ni * nK;
+    A.ld = lo4;
+    B.hi = XtH.p;
+    B.lo = XtL.p;
+    B.rows = v;
+    B.ld = lo4;
+    B.bstride = (long long)v * lo4;
+    B.nb = nvec;
+    TcEpilogue e1;
+    e1.mode = kOutSplit;
+    e1.chi = YH.p;
+    e1.clo = YL.p;
+    e1.rs = lv4;
+    e1.bsc = (long long)ni * nK * lv4;
+    tc_gemm(ni * nK, v, o, A, B, nvec, e1, d_tcerr, st);
+    TcOperand A2, B2;
+    A2.hi = YH.p;
+    A2.lo = YL.p;
+    A2.rows = nvec * ni;
+    A2.ld = nK * lv4;
+    B2.hi = BvvH.p;
+    B2.lo = BvvL.p;
+    B2.rows = v;
+    B2.ld = nK * lv4;
+    TcEpilogue e2;
+    e2.mode = kOutF64;
+    e2.c64 = out + (size_t)i0 * v;  // row (vec, i) -> out[vec][i0 + i]
+    e2.rs = v;
+    if (ni < o) {
+      e2.rin = ni;
+      e2.rld = nov;
+    }
+    e2.alpha = alpha;
+    e2.beta = beta;
+    tc_gemm(nvec * ni, v, nK * lv4, A2, B2, 1, e2, d_tcerr, st);
+  }
 }
 
 void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
@@ -2219,7 +2261,6 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
       RIS_REQUIRE(pairs[2 * g + q] >= 0 && pairs[2 * g + q] < nx, RIS_ERR_ARG,
                   "state index out of range");
   const bool rpa = Ya != nullptr;
-  ensure_D();
   // unique states
   std::vector<int> su;
   std::map<int, int> slot;
@@ -2229,6 +2270,12 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
       su.push_back(pairs[g]);
     }
   const int nsu = (int)su.size();
+  if (streamed) {
+    RIS_REQUIRE(!rpa, RIS_ERR_ARG, "the streamed form is TDA only");
+    pair_derivs_streamed(npair, pairs, nsu, su, slot, Xa, out);
+    return;
+  }
+  ensure_D();
   // per state: R, L, D^R = C_o R C_v^T, c^J, Q_R = R C_v^T, Q_L = L C_v^T
   SBuf<double> Rs((size_t)nsu * nov, st), Ls((size_t)nsu * nov, st), DR, cJ, QR, QL, t1;
   for (int s = 0; s < nsu; s++) {
@@ -2493,6 +2540,7 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
 // (ib|P)_K block B^K_ov as [R][i][a], built on demand when the context was
 // not created for RPA (the (A+B) products of the Z-vector need it).
 void Engine::ensure_Kov() {
+  RIS_REQUIRE(!streamed, RIS_ERR_ARG, "the (ib|P) block is not available in the streamed form");
   const int o = nocc, v = nvir, n = nao;
   const long long nov = (long long)o * v;
   if (BKovR.p && BKovR.n >= (size_t)nov * nK) return;
@@ -2610,6 +2658,645 @@ void Engine::zvector(int nr, const double* rhs_in, double* Z_out) {
   RIS_CUDA(cudaStreamSynchronize(st));
 }
 
+
+// ------------------------------------------------------------------ streamed form
+// For systems whose dense AO three-index tensors do not fit in device memory
+// (Sec. 3: the three-centre tensors are batched along the AO or auxiliary
+// index, with recomputation):
+//   * (mu nu|P) is computed only on the screened function pairs and mixed
+//     there with the metric factors, (mu nu|R)_X = sum_P (mu nu|P) (L_X^-1)_RP,
+//     so that each MO transform yields final B tensors (no accumulation over
+//     auxiliary blocks);
+//   * the MO transforms run over blocks of R, each block scattered into a
+//     dense [mu][nu][r] buffer;
+//   * the exchange part of every Davidson product runs over blocks of
+//     occupied orbitals (apply_exchange_mixed);
+//   * the gradient regenerates the derivative integrals block by block of
+//     auxiliary functions and contracts each block at once; the exchange
+//     density is formed from B^K_vv (G~_R = U B_R V^T, then mixed with L_K^-1)
+//     so that the fitting coefficients c^K_vv are never stored.
+
+// T[mu][nu][r] = T[nu][mu][r] = Bao[f][r0 + r] for the function pair f = (mu, nu)
+__global__ void k_fp_scatter(const double* __restrict__ Bao, int ldB, int r0, int rw, long long nfp,
+                             const int* __restrict__ fmu, const int* __restrict__ fnu, int n,
+                             double* __restrict__ T) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nfp * rw) return;
+  const long long f = t / rw;
+  const int r = (int)(t % rw);
+  const double x = Bao[(size_t)f * ldB + r0 + r];
+  const int mu = fmu[f], nu = fnu[f];
+  T[((size_t)mu * n + nu) * rw + r] = x;
+  T[((size_t)nu * n + mu) * rw + r] = x;
+}
+
+// Lu[R][u] = Linv[R][map[u]] (0 where map[u] < 0), R < nr, u < nu
+__global__ void k_gather_metric(const double* __restrict__ Linv, int nr, const int* __restrict__ map,
+                                int nu, double* __restrict__ Lu) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nr * nu) return;
+  const int R = t / nu, u = t % nu;
+  const int j = map[u];
+  Lu[t] = j >= 0 ? Linv[(size_t)R * nr + j] : 0.0;
+}
+
+// out[b][r0 + r][a] = G[a][b][r] (FP64 B^K_vv in the Davidson layout)
+__global__ void k_place_vv(const double* __restrict__ G, int v, int rw, int r0, int nK,
+                           double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)v * v * rw) return;
+  const int r = (int)(t % rw);
+  const long long ab = t / rw;
+  const int b = (int)(ab % v), a = (int)(ab / v);
+  out[((size_t)b * nK + r0 + r) * v + a] = G[t];
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Exact a <-> b symmetry of B^K_vv in its split storage [a][R][b] (row
+// length ldb): both elements become their FP64 mean, split again.
+__global__ void k_sym_split(float* __restrict__ hi, float* __restrict__ lo, int v, int nK, int ldb) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)v * v * nK) return;
+  const int b = (int)(t % v);
+  const long long aR = t / v;
+  const int R = (int)(aR % nK), a = (int)(aR / nK);
+  if (b <= a) return;
+  const size_t p = ((size_t)a * nK + R) * ldb + b, q = ((size_t)b * nK + R) * ldb + a;
+  const double m = 0.5 * (((double)hi[p] + (double)lo[p]) + ((double)hi[q] + (double)lo[q]));
+  const float x = (float)m;
+  const float h = tf32_round(x), l = tf32_round(x - h);
+  hi[p] = h;
+  lo[p] = l;
+  hi[q] = h;
+  lo[q] = l;
+}
+
+// out[row][u0 + c] = sum_s part[s][row][c], row < rows, c < w (fixed order)
+__global__ void k_sum_slices_cols(const double* __restrict__ part, int nslice, long long rows, int w,
+                                  double* __restrict__ out, int ldo, int u0) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * w) return;
+  const long long row = t / w;
+  const int c = (int)(t % w);
+  double acc = 0.0;
+  for (int sl = 0; sl < nslice; sl++) acc += part[(size_t)sl * rows * w + t];
+  out[(size_t)row * ldo + u0 + c] = acc;
+}
+
+bool Engine::want_streamed(int n) const {
+  if (opt.stream > 0) return true;
+  if (opt.stream < 0) return false;
+  size_t fr = 0, tot = 0;
+  RIS_CUDA(cudaMemGetInfo(&fr, &tot));
+  const double cap = opt.mem_budget ? (double)opt.mem_budget : (double)tot;
+  const double dense = 8.0 * n * n * (double)(nJ + nK) +
+                       (opt.precision == RIS_MIXED ? 4.0 : 8.0) * 3.0 * n * n * (double)nU;
+  return dense > cap / 3.0;
+}
+
+// Functions per block for a buffer of bytes_per_function per function: up to
+// 24 GB or 12% of the free device memory (or the stream_block option).
+int Engine::block_width(double per) const {
+  if (opt.stream_block > 0) return opt.stream_block;
+  size_t fr = 0, tot = 0;
+  RIS_CUDA(cudaMemGetInfo(&fr, &tot));
+  const double room = std::min(24.0e9, 0.12 * (double)fr);
+  return (int)std::max(1.0, std::min(256.0, std::floor(room / per)));
+}
+
+static void scatter_block(const double* Bao, int ldB, int r0, int rw, long long nfp, const int* fmu,
+                          const int* fnu, int n, double* T, cudaStream_t st) {
+  RIS_CUDA(cudaMemsetAsync(T, 0, sizeof(double) * (size_t)n * n * rw, st));
+  k_fp_scatter<<<(unsigned)cdiv(nfp * rw, 256), 256, 0, st>>>(Bao, ldB, r0, rw, nfp, fmu, fnu, n, T);
+  RIS_CHECK_LAUNCH();
+}
+
+// After the metric factors: the screened function pairs, (mu nu|P) on them,
+// the metric-mixed tensors B^J_AO = (mu nu|P) L_J^-T and B^K_AO (K functions
+// are the first nK union functions), and the auxiliary blocks.
+void Engine::setup_streamed() {
+  const int n = nao;
+  std::vector<int> ha(std::max(pl.npair, 1)), hb(std::max(pl.npair, 1));
+  if (pl.npair > 0) {
+    RIS_CUDA(cudaMemcpyAsync(ha.data(), pl.a, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaMemcpyAsync(hb.data(), pl.b, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+  }
+  std::vector<long long> po(std::max(pl.npair, 1), 0);
+  std::vector<int> fm, fn;
+  long long f = 0;
+  for (int ip = 0; ip < pl.npair; ip++) {
+    const int sa = ha[ip], sb = hb[ip];
+    const int na = ncart(ao.h_l[sa]), nb = ncart(ao.h_l[sb]);
+    po[ip] = f;
+    for (int ia = 0; ia < na; ia++)
+      for (int ib = 0; ib < nb; ib++) {
+        fm.push_back(ao.h_off[sa] + ia);
+        fn.push_back(ao.h_off[sb] + ib);
+      }
+    f += na * nb;
+  }
+  RIS_REQUIRE(f > 0 && f < (1ll << 31), RIS_ERR_ARG, "screened function pairs out of range");
+  nfp = f;
+  pOff.ensure(po.size(), st);
+  fpMu.ensure(fm.size(), st);
+  fpNu.ensure(fn.size(), st);
+  RIS_CUDA(cudaMemcpyAsync(pOff.p, po.data(), sizeof(long long) * po.size(), cudaMemcpyHostToDevice, st));
+  RIS_CUDA(cudaMemcpyAsync(fpMu.p, fm.data(), sizeof(int) * fm.size(), cudaMemcpyHostToDevice, st));
+  RIS_CUDA(cudaMemcpyAsync(fpNu.p, fn.data(), sizeof(int) * fn.size(), cudaMemcpyHostToDevice, st));
+  {
+    SBuf<double> Ts((size_t)nfp * nU, st);
+    int3c_pairs(ao, aux, pl, xyz.p, pOff.p, Ts.p, st);
+    std::vector<int> uJ(nU, -1);
+    for (int j = 0; j < nJ; j++) uJ[h_jU[j]] = j;
+    SBuf<int> d_uJ(nU, st);
+    RIS_CUDA(cudaMemcpyAsync(d_uJ.p, uJ.data(), sizeof(int) * nU, cudaMemcpyHostToDevice, st));
+    SBuf<double> LJu((size_t)nJ * nU, st);
+    k_gather_metric<<<cdiv((long long)nJ * nU, 256), 256, 0, st>>>(LJinv.p, nJ, d_uJ.p, nU, LJu.p);
+    RIS_CHECK_LAUNCH();
+    BJao.ensure((size_t)nfp * nJ, st);
+    BKao.ensure((size_t)nfp * nK, st);
+    if (opt.precision == RIS_MIXED && opt.emu_f64) {
+      EmuEpilogue e;
+      e.c64 = BJao.p; e.rs = nJ; e.cs = 1;
+      emu_abt((int)nfp, nJ, nU, Ts.p, nU, 1, LJu.p, nU, 1, e);
+      EmuEpilogue e2;
+      e2.c64 = BKao.p; e2.rs = nK; e2.cs = 1;
+      emu_abt((int)nfp, nK, nK, Ts.p, nU, 1, LKinv.p, nK, 1, e2);
+    } else {
+      dgemm(false, true, (int)nfp, nJ, nU, 1.0, Ts.p, nU, LJu.p, nU, 0.0, BJao.p, nJ, st);
+      dgemm(false, true, (int)nfp, nK, nK, 1.0, Ts.p, nU, LKinv.p, nK, 0.0, BKao.p, nK, st);
+    }
+    RIS_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
+  }
+  // auxiliary blocks: runs of union shells within the K part or within the
+  // J-only part, sized for the derivative integrals and a batch of exchange
+  // densities of the block
+  for (ShellSet& b : auxBlk) free_shells(b, st);
+  auxBlk.clear();
+  blkU0.clear();
+  blkW.clear();
+  blkWK.clear();
+  const double dsz = opt.precision == RIS_MIXED ? 4.0 : 8.0;
+  const int wmax = block_width(dsz * 3.0 * n * n + dsz * kCBatch * n * n);
+  int s = 0;
+  while (s < aux.n) {
+    const int lim = s < nKsh ? nKsh : aux.n;
+    int e = s, w = 0;
+    while (e < lim && (e == s || w + ncart(aux.h_l[e]) <= wmax)) w += ncart(aux.h_l[e++]);
+    std::vector<int> a(aux.h_atom.begin() + s, aux.h_atom.begin() + e);
+    std::vector<int> l(aux.h_l.begin() + s, aux.h_l.begin() + e);
+    std::vector<double> ex(aux.h_ex.begin() + s, aux.h_ex.begin() + e);
+    std::vector<int> jm, km;
+    int loc = 0;
+    for (int q = s; q < e; q++) {
+      jm.push_back(loc);
+      km.push_back(-1);
+      loc += ncart(aux.h_l[q]);
+    }
+    ShellSet view;
+    make_shells(view, a, l, ex, &jm, &km, st);
+    auxBlk.push_back(view);
+    blkU0.push_back(aux.h_off[s]);
+    blkW.push_back(w);
+    blkWK.push_back(s < nKsh ? w : 0);
+    s = e;
+  }
+  RIS_CUDA(cudaStreamSynchronize(st));
+}
+
+void Engine::build_B_streamed() {
+  const int o = nocc, v = nvir, n = nao;
+  const long long nov = (long long)o * v;
+  const bool mixed = opt.precision == RIS_MIXED;
+  RIS_REQUIRE(!opt.rpa, RIS_ERR_ARG, "the streamed form is TDA only");
+  RIS_REQUIRE(!(mixed && opt.refine), RIS_ERR_ARG, "refine is not available in the streamed form");
+  const bool emu = mixed && opt.emu_f64;
+  const int lo4 = ld4(o), lv4 = ld4(v), ldn = ld4(n);
+  const double* Co = C.p;
+  const double* Cv = C.p + o;
+  SBuf<double> Tb;
+  // Coulomb: B^J[i][a][R], R in blocks
+  BJ.ensure((size_t)nov * nJ, st);
+  {
+    const int rb = std::min(nJ, block_width(8.0 * n * n * (emu ? 3.5 : 1.0) + 8.0 * n * o * (emu ? 3.5 : 1.0)));
+    Tb.ensure((size_t)n * n * rb, st);
+    SBuf<double> H((size_t)o * n * rb, st);
+    for (int r0 = 0; r0 < nJ; r0 += rb) {
+      const int rw = std::min(rb, nJ - r0);
+      scatter_block(BJao.p, nJ, r0, rw, nfp, fpMu.p, fpNu.p, n, Tb.p, st);
+      if (emu) {  // H[nu][i][r] = sum_mu T[mu][nu][r] C_mu,i ; B[i][a][r] = sum_nu H C_nu,a
+        const long long rT = (long long)n * rw, rH = (long long)o * rw;
+        EmuEpilogue e1;
+        e1.c64 = H.p; e1.rin = rw; e1.rld = rH; e1.rs = 1; e1.cs = rw;
+        emu_abt((int)rT, o, n, Tb.p, 1, rT, C.p, 1, nmo, e1);
+        EmuEpilogue e2;
+        e2.c64 = BJ.p + r0; e2.rin = rw; e2.rld = (long long)v * nJ; e2.rs = 1; e2.cs = nJ;
+        emu_abt((int)rH, v, n, H.p, 1, rH, C.p + o, 1, nmo, e2);
+      } else {  // H[i][nu][r], then per i: B[i][a][r0 + r]
+        dgemm(true, false, o, n * rw, n, 1.0, Co, nmo, Tb.p, n * rw, 0.0, H.p, n * rw, st);
+        GemmBatch bt;
+        bt.nb1 = o;
+        bt.sB1 = (long long)n * rw;
+        bt.sC1 = (long long)v * nJ;
+        dgemm(true, false, v, rw, n, 1.0, Cv, nmo, H.p, rw, 0.0, BJ.p + r0, nJ, st, bt);
+      }
+    }
+  }
+  // exchange: B^K_oo[i][j][R] and B^K_vv (split [a][R][b] in mixed precision,
+  // FP64 [b][R][a] otherwise), R in blocks
+  BKoo.ensure((size_t)o * o * nK, st);
+  if (mixed) {
+    BvvH.ensure((size_t)v * nK * lv4, st);
+    BvvL.ensure((size_t)v * nK * lv4, st);
+  } else {
+    BKvvD.ensure((size_t)v * nK * v, st);
+  }
+  {
+    const int rb = std::min(nK, block_width(mixed ? 8.0 * n * n + 8.0 * (double)n * ldn + 8.0 * v * ldn
+                                                  : 8.0 * n * n + 8.0 * n * (double)std::max(o, v) + 8.0 * v * v));
+    Tb.ensure((size_t)n * n * rb, st);
+    if (mixed) {
+      if (!d_tcerr) {
+        RIS_ALLOC(cudaMallocAsync((void**)&d_tcerr, sizeof(int), st));
+        RIS_CUDA(cudaMemsetAsync(d_tcerr, 0, sizeof(int), st));
+      }
+      SBuf<float> Th((size_t)rb * n * ldn, st, true), Tl((size_t)rb * n * ldn, st, true);
+      SBuf<float> CvTh((size_t)v * ldn, st), CvTl((size_t)v * ldn, st);
+      SBuf<float> CoTh((size_t)o * ldn, st), CoTl((size_t)o * ldn, st);
+      SBuf<float> Hh((size_t)v * rb * ldn, st), Hl((size_t)v * rb * ldn, st);
+      split_f64_t(Cv, n, v, nmo, CvTh.p, CvTl.p, ldn, st);  // [a][mu]
+      split_f64_t(Co, n, o, nmo, CoTh.p, CoTl.p, ldn, st);  // [i][mu]
+      for (int r0 = 0; r0 < nK; r0 += rb) {
+        const int rw = std::min(rb, nK - r0);
+        scatter_block(BKao.p, nK, r0, rw, nfp, fpMu.p, fpNu.p, n, Tb.p, st);
+        split_f64_tpad(Tb.p, (long long)n * n, rw, n, ldn, Th.p, Tl.p, st);  // [r][mu][nu]
+        {  // H[a][r][nu] = sum_mu C_mu,a T[r][mu][nu]
+          TcEpilogue e = ep_split(Hh.p, Hl.p, (long long)rw * ldn);
+          e.cin = n;
+          e.cld = ldn;
+          tcg(v, rw * n, n, CvTh.p, CvTl.p, ldn, Th.p, Tl.p, ldn, 0, 1, e, d_tcerr, st);
+        }
+        {  // B[a][r0 + r][b] = sum_nu H[a][r][nu] C_nu,b
+          TcEpilogue e = ep_split(BvvH.p + (size_t)r0 * lv4, BvvL.p + (size_t)r0 * lv4, lv4);
+          e.rin = rw;
+          e.rld = (long long)nK * lv4;
+          tcg(v * rw, v, n, Hh.p, Hl.p, ldn, CvTh.p, CvTl.p, ldn, 0, 1, e, d_tcerr, st);
+        }
+        {  // the oo block the same way
+          TcEpilogue e = ep_split(Hh.p, Hl.p, (long long)rw * ldn);
+          e.cin = n;
+          e.cld = ldn;
+          tcg(o, rw * n, n, CoTh.p, CoTl.p, ldn, Th.p, Tl.p, ldn, 0, 1, e, d_tcerr, st);
+        }
+        {
+          TcEpilogue e = ep_f64(BKoo.p + r0, 1, 0, 1.0, 0.0, nK);
+          e.rin = rw;
+          e.rld = (long long)o * nK;
+          tcg(o * rw, o, n, Hh.p, Hl.p, ldn, CoTh.p, CoTl.p, ldn, 0, 1, e, d_tcerr, st);
+        }
+      }
+      k_sym_split<<<(unsigned)cdiv((long long)v * v * nK, 256), 256, 0, st>>>(BvvH.p, BvvL.p, v, nK, lv4);
+      RIS_CHECK_LAUNCH();
+    } else {
+      SBuf<double> H((size_t)std::max(o, v) * n * rb, st), G((size_t)v * v * rb, st);
+      for (int r0 = 0; r0 < nK; r0 += rb) {
+        const int rw = std::min(rb, nK - r0);
+        scatter_block(BKao.p, nK, r0, rw, nfp, fpMu.p, fpNu.p, n, Tb.p, st);
+        dgemm(true, false, o, n * rw, n, 1.0, Co, nmo, Tb.p, n * rw, 0.0, H.p, n * rw, st);
+        GemmBatch bt;
+        bt.nb1 = o;
+        bt.sB1 = (long long)n * rw;
+        bt.sC1 = (long long)o * nK;
+        dgemm(true, false, o, rw, n, 1.0, Co, nmo, H.p, rw, 0.0, BKoo.p + r0, nK, st, bt);
+        dgemm(true, false, v, n * rw, n, 1.0, Cv, nmo, Tb.p, n * rw, 0.0, H.p, n * rw, st);
+        GemmBatch b2;
+        b2.nb1 = v;
+        b2.sB1 = (long long)n * rw;
+        b2.sC1 = (long long)v * rw;
+        dgemm(true, false, v, rw, n, 1.0, Cv, nmo, H.p, rw, 0.0, G.p, rw, st, b2);
+        k_place_vv<<<(unsigned)cdiv((long long)v * v * rw, 256), 256, 0, st>>>(G.p, v, rw, r0, nK, BKvvD.p);
+        RIS_CHECK_LAUNCH();
+      }
+    }
+  }
+  Tb.release();
+  // fitting coefficients of the oo block, c = B L^-1, as [P][i][k]
+  cKoo.ensure((size_t)o * o * nK, st);
+  dgemm(false, false, o * o, nK, nK, 1.0, BKoo.p, nK, LKinv.p, nK, 0.0, cKoo.p, nK, st);
+  cKooP.ensure((size_t)o * o * nK, st);
+  transpose_last2(cKoo.p, 1, o * o, nK, cKooP.p, st);
+  if (mixed) {  // FP32 hi/lo operands of the products and of the gradient
+    BooH.ensure((size_t)o * nK * lo4, st);
+    BooL.ensure((size_t)o * nK * lo4, st);
+    split_f64_t(BKoo.p, o, nK, nK, BooH.p, BooL.p, lo4, st, o, (long long)o * nK, (long long)nK * lo4);
+    cooH.ensure((size_t)nK * o * lo4, st);
+    cooL.ensure((size_t)nK * o * lo4, st);
+    split_f64(cKooP.p, nK * o, o, o, cooH.p, cooL.p, lo4, st);
+    CoH.ensure((size_t)n * lo4, st);
+    CoL.ensure((size_t)n * lo4, st);
+    split_f64(C.p, n, o, nmo, CoH.p, CoL.p, lo4, st);
+    CvH.ensure((size_t)n * lv4, st);
+    CvL.ensure((size_t)n * lv4, st);
+    split_f64(C.p + o, n, v, nmo, CvH.p, CvL.p, lv4, st);
+  }
+}
+
+// Gradients / coupling numerators of TDA pair energies, streamed form.
+void Engine::pair_derivs_streamed(int npair, const int* pairs, int nsu, const std::vector<int>& su,
+                                  const std::map<int, int>& slot, const double* Xa, double* out) {
+  const int o = nocc, v = nvir, nn = nao;
+  const long long nov = (long long)o * v;
+  const bool mixed = opt.precision == RIS_MIXED;
+  const int lv4 = ld4(v), lo4 = ld4(o), kp = ld4(2 * o), ldK = ld4(nK);
+  const double* Co = C.p;
+  const double* Cv = C.p + o;
+  const double f = -opt.cx;  // TDA: one exchange combination with weight -c_x
+  // per state: R = X, D^R = C_o R C_v^T (symmetrised), c^J on the union index
+  SBuf<double> Rs((size_t)nsu * nov, st), DR((size_t)nsu * nn * nn, st), cJ((size_t)nsu * nJ, st),
+      QR, t1;
+  for (int s = 0; s < nsu; s++)
+    RIS_CUDA(cudaMemcpyAsync(Rs.p + s * nov, Xa + (size_t)su[s] * nov, sizeof(double) * nov,
+                             cudaMemcpyDeviceToDevice, st));
+  SBuf<float> RSh, RSl, WRh, WRl, DRf;
+  if (mixed) {
+    RSh.ensure((size_t)nsu * o * lv4, st);
+    RSl.ensure((size_t)nsu * o * lv4, st);
+    WRh.ensure((size_t)nsu * nn * kp, st, true);
+    WRl.ensure((size_t)nsu * nn * kp, st, true);
+    split_f64(Rs.p, nsu * o, v, v, RSh.p, RSl.p, lv4, st);
+    SBuf<float> RtH((size_t)nsu * v * lo4, st), RtL((size_t)nsu * v * lo4, st),
+        t1H((size_t)nsu * nn * lv4, st), t1L((size_t)nsu * nn * lv4, st);
+    split_f64_t(Rs.p, o, v, v, RtH.p, RtL.p, lo4, st, nsu, nov, (long long)v * lo4);
+    tcg(nn, v, o, CoH.p, CoL.p, lo4, RtH.p, RtL.p, lo4, (long long)v * lo4, nsu,
+        ep_split(t1H.p, t1L.p, lv4, 1, (long long)nn * lv4), d_tcerr, st);
+    tcg(nn, nn, v, t1H.p, t1L.p, lv4, CvH.p, CvL.p, lv4, 0, nsu,
+        ep_f64(DR.p, nn, (long long)nn * nn), d_tcerr, st, (long long)nn * lv4, nsu);
+    // W_R = [Q^T | C_o] as [s][nu][k']
+    tcg(nn, o, v, CvH.p, CvL.p, lv4, RSh.p, RSl.p, lv4, (long long)o * lv4, nsu,
+        ep_split(WRh.p, WRl.p, kp, 1, (long long)nn * kp), d_tcerr, st);
+    const dim3 gc(cdiv((long long)nn * o, 256), nsu);
+    k_copy_cols<<<gc, 256, 0, st>>>(CoH.p, lo4, WRh.p, kp, o, nn, o, (long long)nn * kp);
+    RIS_CHECK_LAUNCH();
+    k_copy_cols<<<gc, 256, 0, st>>>(CoL.p, lo4, WRl.p, kp, o, nn, o, (long long)nn * kp);
+    RIS_CHECK_LAUNCH();
+  } else {
+    QR.ensure((size_t)nsu * o * nn, st);
+    t1.ensure((size_t)nn * v, st);
+    for (int s = 0; s < nsu; s++) {
+      dgemm(false, false, nn, v, o, 1.0, Co, nmo, Rs.p + s * nov, v, 0.0, t1.p, v, st);
+      dgemm(false, true, nn, nn, v, 1.0, t1.p, v, Cv, nmo, 0.0, DR.p + (size_t)s * nn * nn, nn, st);
+      dgemm(false, true, o, nn, v, 1.0, Rs.p + s * nov, v, Cv, nmo, 0.0, QR.p + (size_t)s * o * nn, nn, st);
+    }
+  }
+  w5.ensure((size_t)nsu * nJ, st);
+  dgemm(false, false, nsu, nJ, (int)nov, 1.0, Rs.p, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
+  dgemm(false, false, nsu, nJ, nJ, 1.0, w5.p, nJ, LJinv.p, nJ, 0.0, cJ.p, nJ, st);
+  k_symmetrize_sq<<<cdiv((long long)nsu * nn * nn, 256), 256, 0, st>>>(DR.p, nn, nsu);
+  RIS_CHECK_LAUNCH();
+  if (mixed) {
+    DRf.ensure((size_t)nsu * nn * nn, st);
+    k_to_f32<<<cdiv((long long)nsu * nn * nn, 256), 256, 0, st>>>(DR.p, (long long)nsu * nn * nn, DRf.p);
+    RIS_CHECK_LAUNCH();
+  }
+  SBuf<double> cU((size_t)nsu * nU, st, true);
+  k_expand_cJ<<<cdiv(nsu * nJ, 256), 256, 0, st>>>(cJ.p, d_jU, nsu, nJ, nU, cU.p);
+  RIS_CHECK_LAUNCH();
+  SBuf<double> Yst((size_t)nsu * 3 * nn * nU, st);
+  // L_K^-T split (mixed): [P][R]
+  SBuf<float> LiTh, LiTl;
+  if (mixed) {
+    LiTh.ensure((size_t)nK * ldK, st, true);
+    LiTl.ensure((size_t)nK * ldK, st, true);
+    split_f64_t(LKinv.p, nK, nK, nK, LiTh.p, LiTl.p, ldK, st);
+  }
+  const int NB = std::min(npair, kCBatch);
+  int wmaxU = 1, wmaxK = 1;
+  for (size_t k = 0; k < blkW.size(); k++) {
+    wmaxU = std::max(wmaxU, blkW[k]);
+    wmaxK = std::max(wmaxK, blkWK[k]);
+  }
+  const size_t nn2 = (size_t)nn * nn;
+  // per pair of the batch: G[P][k][j] (mixed: split, j padded), Omega
+  SBuf<double> Gd(mixed ? 1 : (size_t)NB * nK * o * o, st), OmB((size_t)NB * nU * nU, st),
+      WK((size_t)NB * 3 * nn * nK, st);
+  SBuf<float> GH(mixed ? (size_t)NB * nK * o * lo4 : 1, st), GL(mixed ? (size_t)NB * nK * o * lo4 : 1, st);
+  SBuf<double> D64(mixed ? 1 : 3 * nn2 * wmaxU, st), Gam64(mixed ? 1 : (size_t)NB * nn2 * wmaxK, st);
+  SBuf<float> D32(mixed ? 3 * nn2 * wmaxU : 1, st), Gam32(mixed ? (size_t)NB * nn2 * wmaxK : 1, st);
+  SBuf<double> M1d(mixed ? 1 : (size_t)nn * wmaxK * 2 * o, st), WVd(mixed ? 1 : (size_t)nn * 2 * o, st);
+  SBuf<float> M1h(mixed ? (size_t)nn * wmaxK * kp : 1, st), M1l(mixed ? (size_t)nn * wmaxK * kp : 1, st);
+  SBuf<int> pst(2 * NB, st);
+  const int slJ = pick_slices((long long)nn * wmaxU, nn), slK = pick_slices((long long)nn * wmaxK, nn);
+  SBuf<double> partJ((size_t)slJ * std::min(nsu, kCBatch) * 3 * nn * wmaxU, st),
+      partK((size_t)slK * NB * 3 * nn * wmaxK, st);
+  const double dbytes = mixed ? 4.0 : 8.0;
+  for (int g0 = 0; g0 < npair; g0 += NB) {
+    const int nb = std::min(NB, npair - g0);
+    RIS_CUDA(cudaMemsetAsync(OmB.p, 0, sizeof(double) * nb * nU * nU, st));
+    std::vector<int> h_pst(2 * nb);
+    for (int b = 0; b < nb; b++) {
+      const int g = g0 + b;
+      const int sI = slot.at(pairs[2 * g]), sJ = slot.at(pairs[2 * g + 1]);
+      h_pst[2 * b] = sI;
+      h_pst[2 * b + 1] = sJ;
+      double* Om = OmB.p + (size_t)b * nU * nU;
+      k_omega_J<<<cdiv(nJ * nJ, 256), 256, 0, st>>>(cJ.p + (size_t)sI * nJ, cJ.p + (size_t)sJ * nJ, d_jU,
+                                                    nJ, nU, 2.0, Om);
+      RIS_CHECK_LAUNCH();
+      // G~[k][R][j] = sum_ab V_kb B_ab,R U_ja, then G[P][k][j] = sum_R L^-1_RP G~[k][R][j]
+      if (mixed) {
+        const float* USh = RSh.p + (size_t)sI * o * lv4;
+        const float* USl = RSl.p + (size_t)sI * o * lv4;
+        const float* VSh = RSh.p + (size_t)sJ * o * lv4;
+        const float* VSl = RSl.p + (size_t)sJ * o * lv4;
+        SBuf<float> T1h((size_t)nK * o * lv4, st, true), T1l((size_t)nK * o * lv4, st, true);
+        {  // T1[R][k][a] = sum_b V[k][b] B[a][R][b]
+          TcEpilogue e = ep_split(T1h.p, T1l.p, lv4);
+          e.cin = nK;
+          e.cld = 1;
+          e.cs = (long long)o * lv4;
+          tcg(o, v * nK, v, VSh, VSl, lv4, BvvH.p, BvvL.p, lv4, 0, 1, e, d_tcerr, st);
+        }
+        SBuf<float> Gth((size_t)o * o * ldK, st, true), Gtl((size_t)o * o * ldK, st, true);
+        {  // G~[(k, j)][R] = sum_a T1[R][k][a] U[j][a]
+          TcEpilogue e = ep_split(Gth.p, Gtl.p, (long long)o * ldK, ldK);
+          e.rin = o;
+          e.rld = 1;
+          tcg(nK * o, o, v, T1h.p, T1l.p, lv4, USh, USl, lv4, 0, 1, e, d_tcerr, st);
+        }
+        {  // G[P][k][j] = sum_R L^-1[R][P] G~[(k, j)][R]
+          float* gh = GH.p + (size_t)b * nK * o * lo4;
+          float* gl = GL.p + (size_t)b * nK * o * lo4;
+          RIS_CUDA(cudaMemsetAsync(gh, 0, sizeof(float) * nK * o * lo4, st));
+          RIS_CUDA(cudaMemsetAsync(gl, 0, sizeof(float) * nK * o * lo4, st));
+          TcEpilogue e = ep_split(gh, gl, (long long)o * lo4);
+          e.cin = o;
+          e.cld = lo4;
+          tcg(nK, o * o, nK, LiTh.p, LiTl.p, ldK, Gth.p, Gtl.p, ldK, 0, 1, e, d_tcerr, st);
+          // Omega[A][B] += f sum_{k,j} c^oo[A][k][j] G[B][k][j]
+          tcg(nK, nK, o * lo4, cooH.p, cooL.p, o * lo4, gh, gl, o * lo4, 0, 1, ep_f64(Om, nU, 0, f, 1.0),
+              d_tcerr, st);
+        }
+      } else {
+        const double* U = Rs.p + (size_t)sI * nov;
+        const double* V = Rs.p + (size_t)sJ * nov;
+        SBuf<double> T1((size_t)o * nK * v, st), Gt((size_t)o * nK * o, st);
+        dgemm(false, false, o, nK * v, v, 1.0, V, v, BKvvD.p, nK * v, 0.0, T1.p, nK * v, st);  // [k][R][a]
+        dgemm(false, true, o * nK, o, v, 1.0, T1.p, v, U, v, 0.0, Gt.p, o, st);                 // [k][R][j]
+        double* G = Gd.p + (size_t)b * nK * o * o;
+        GemmBatch bt;
+        bt.nb1 = o;
+        bt.sB1 = (long long)nK * o;
+        bt.sC1 = o;
+        dgemm(true, false, nK, o, nK, 1.0, LKinv.p, nK, Gt.p, o, 0.0, G, o * o, st, bt);         // [P][k][j]
+        dgemm(false, true, nK, nK, o * o, f, cKooP.p, o * o, G, o * o, 1.0, Om, nU, st);
+      }
+    }
+    RIS_CUDA(cudaMemcpyAsync(pst.p, h_pst.data(), sizeof(int) * 2 * nb, cudaMemcpyHostToDevice, st));
+    // auxiliary blocks: derivative integrals regenerated and contracted at once
+    for (size_t k = 0; k < auxBlk.size(); k++) {
+      const int u0 = blkU0[k], w = blkW[k], wK = blkWK[k];
+      if (g0 > 0 && wK == 0) continue;  // the Coulomb part is complete after the first batch
+      if (mixed) {
+        RIS_CUDA(cudaMemsetAsync(D32.p, 0, sizeof(float) * 3 * nn2 * w, st));
+        int3c_deriv<float>(ao, auxBlk[k], pl, xyz.p, D32.p, st);
+      } else {
+        RIS_CUDA(cudaMemsetAsync(D64.p, 0, sizeof(double) * 3 * nn2 * w, st));
+        int3c_deriv<double>(ao, auxBlk[k], pl, xyz.p, D64.p, st);
+      }
+      prof_begin(kProfContract, st);
+      double bytes = 0.0;
+      if (g0 == 0) {  // Coulomb part: Y_s[x][mu][u0 + p] for every state
+        for (int s0 = 0; s0 < nsu; s0 += kCBatch) {
+          const int ns = std::min(kCBatch, nsu - s0);
+          const dim3 grid(cdiv((long long)nn * w, 128), slJ);
+          if (mixed)
+            k_contract_states<float><<<grid, 128, 0, st>>>(D32.p, DRf.p, s0, ns, nn, w, slJ, partJ.p);
+          else
+            k_contract_states<double><<<grid, 128, 0, st>>>(D64.p, DR.p, s0, ns, nn, w, slJ, partJ.p);
+          RIS_CHECK_LAUNCH();
+          const long long rows = (long long)ns * 3 * nn;
+          k_sum_slices_cols<<<(unsigned)cdiv(rows * w, 256), 256, 0, st>>>(
+              partJ.p, slJ, rows, w, Yst.p + (size_t)s0 * 3 * nn * nU, nU, u0);
+          RIS_CHECK_LAUNCH();
+          bytes += dbytes * 3.0 * nn2 * w + 8.0 * ns * nn2;
+        }
+      }
+      if (wK > 0) {  // exchange part of each pair's Gamma for P in the block
+        for (int b = 0; b < nb; b++) {
+          const int g = g0 + b;
+          const int sI = slot.at(pairs[2 * g]), sJ = slot.at(pairs[2 * g + 1]);
+          if (mixed) {
+            const size_t sw = (size_t)nn * kp;
+            const float* gh = GH.p + (size_t)b * nK * o * lo4 + (size_t)u0 * o * lo4;
+            const float* gl = GL.p + (size_t)b * nK * o * lo4 + (size_t)u0 * o * lo4;
+            // M1[mu][p][k'] : k' < o  sum_i Q_U[i][mu] c^oo[P][i][k]
+            //                 k' >= o sum_j C_o[mu][j] G[P][k][j]
+            TcEpilogue e = ep_split(M1h.p, M1l.p, (long long)wK * kp);
+            e.cin = o;
+            e.cld = kp;
+            tcg(nn, wK * o, o, WRh.p + sI * sw, WRl.p + sI * sw, kp, cooH.p + (size_t)u0 * o * lo4,
+                cooL.p + (size_t)u0 * o * lo4, lo4, 0, 1, e, d_tcerr, st);
+            e.chi = M1h.p + o;
+            e.clo = M1l.p + o;
+            tcg(nn, wK * o, o, CoH.p, CoL.p, lo4, gh, gl, lo4, 0, 1, e, d_tcerr, st);
+            // Gamma[mu][nu][p] = f sum_k' W_V[nu][k'] M1[mu][p][k']
+            TcEpilogue eg;
+            eg.mode = kOutF32;
+            eg.c32 = Gam32.p + (size_t)b * nn2 * wK;
+            eg.alpha = f;
+            eg.beta = 0.0;
+            eg.rs = wK;
+            eg.cin = wK;
+            eg.cld = (long long)nn * wK;
+            tcg(nn, nn * wK, 2 * o, WRh.p + sJ * sw, WRl.p + sJ * sw, kp, M1h.p, M1l.p, kp, 0, 1, eg,
+                d_tcerr, st);
+          } else {
+            const double* G = Gd.p + (size_t)b * nK * o * o;
+            const double* QU = QR.p + (size_t)sI * o * nn;
+            const double* QV = QR.p + (size_t)sJ * o * nn;
+            // M1[mu][p][k'] : k' < o  sum_j C_o[mu][j] G[P][k][j]
+            //                 k' >= o sum_i Q_U[i][mu] c^oo[P][i][k]
+            GemmBatch bp;
+            bp.nb1 = wK;
+            bp.sB1 = (long long)o * o;
+            bp.sC1 = 2LL * o;
+            dgemm(false, true, nn, o, o, 1.0, Co, nmo, G + (size_t)u0 * o * o, o, 0.0, M1d.p, wK * 2 * o, st, bp);
+            dgemm(true, false, nn, o, o, 1.0, QU, nn, cKooP.p + (size_t)u0 * o * o, o, 0.0, M1d.p + o,
+                  wK * 2 * o, st, bp);
+            k_build_W<<<cdiv(nn * 2 * o, 256), 256, 0, st>>>(C.p, nmo, QV, nn, o, WVd.p);
+            RIS_CHECK_LAUNCH();
+            GemmBatch bm;
+            bm.nb1 = nn;
+            bm.sB1 = (long long)wK * 2 * o;
+            bm.sC1 = (long long)nn * wK;
+            dgemm(false, true, nn, wK, 2 * o, f, WVd.p, 2 * o, M1d.p, 2 * o, 0.0,
+                  Gam64.p + (size_t)b * nn2 * wK, wK, st, bm);
+          }
+        }
+        const dim3 gridK(cdiv((long long)nn * wK, 128), slK);
+        if (mixed)
+          k_contract_exchange<float, float><<<gridK, 128, 0, st>>>(D32.p, Gam32.p, nb, nn, w, wK, slK, partK.p);
+        else
+          k_contract_exchange<double, double><<<gridK, 128, 0, st>>>(D64.p, Gam64.p, nb, nn, w, wK, slK,
+                                                                     partK.p);
+        RIS_CHECK_LAUNCH();
+        const long long rows = (long long)nb * 3 * nn;
+        k_sum_slices_cols<<<(unsigned)cdiv(rows * wK, 256), 256, 0, st>>>(partK.p, slK, rows, wK, WK.p, nK, u0);
+        RIS_CHECK_LAUNCH();
+        bytes += dbytes * 3.0 * nn2 * wK + dbytes * 2.0 * nb * nn2 * wK;
+      }
+      prof_end(kProfContract, st, bytes);
+    }
+    k_grad_reduce_pairs<<<dim3(natm, nb), 128, 0, st>>>(WK.p, Yst.p, cU.p, pst.p, OmB.p, dMU.p, aoPtr.p,
+                                                        aoList.p, axPtr.p, axList.p, nn, nU, nK, natm,
+                                                        out + (size_t)g0 * natm * 3);
+    RIS_CHECK_LAUNCH();
+    RIS_CUDA(cudaStreamSynchronize(st));  // h_pst goes out of scope
+  }
+  if (mixed) {
+    int h_err = 0;
+    RIS_CUDA(cudaMemcpyAsync(&h_err, d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RIS_CUDA(cudaStreamSynchronize(st));
+    RIS_REQUIRE(h_err == 0, RIS_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait timed out");
+  }
+}
+
+// ------------------------------------------------------------------ time couplings
+// T[g] = sum_{A,x} d[g][A][x] v[A][x], one block per pair (fixed-order tree sum)
+__global__ void __launch_bounds__(256) k_time_coupling(const double* __restrict__ d,
+                                                       const double* __restrict__ vel, int n3,
+                                                       double* __restrict__ T) {
+  __shared__ double red[256];
+  const int g = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n3; i += 256) s += d[(size_t)g * n3 + i] * vel[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) T[g] = red[0];
+}
+
+void Engine::time_coupling(int npair, const double* nac, const double* vel, double* T) {
+  RIS_REQUIRE(stage >= 1 && natm > 0, RIS_ERR_STATE, "ris_time_coupling before ris_build_aux");
+  RIS_REQUIRE(npair >= 1 && nac && vel && T, RIS_ERR_ARG, "bad time-coupling arguments");
+  const int n3 = 3 * natm;
+  SBuf<double> dd((size_t)npair * n3, st), vv(n3, st), tt(npair, st);
+  copy_in(dd.p, nac, (size_t)npair * n3, st);
+  copy_in(vv.p, vel, n3, st);
+  k_time_coupling<<<npair, 256, 0, st>>>(dd.p, vv.p, n3, tt.p);
+  RIS_CHECK_LAUNCH();
+  copy_out(T, tt.p, npair, st);
+  RIS_CUDA(cudaStreamSynchronize(st));
+}
 
 // ------------------------------------------------------------------ phase tracking
 // Align the phases of the current states with those of the previous step

@@ -1,5 +1,6 @@
 // TDDFT-ris engine state and stages.
 #pragma once
+#include <map>
 #include <string>
 #include <vector>
 
@@ -143,6 +144,18 @@ struct Engine : StreamOwner {
   DBuf omega, X, Y;
   std::vector<double> h_omega;
 
+  // streamed form (large systems): three-centre integrals on the screened
+  // function pairs only, mixed with the metric factors there; auxiliary
+  // blocks for the MO transforms and the derivative integrals
+  bool streamed = false;
+  long long nfp = 0;        // function pairs of the screened shell-pair list
+  SBuf<long long> pOff;     // first function-pair row of each shell pair
+  SBuf<int> fpMu, fpNu;     // the two AO functions of each function pair
+  DBuf BJao, BKao;          // [fp][R]: sum_P (mu nu|P) (L_X^-1)_RP on the screened pairs
+  std::vector<int> blkU0, blkW, blkWK;  // auxiliary blocks: first union function, width, K part
+  std::vector<ShellSet> auxBlk;        // the blocks' shells with block-local offsets
+  int nKsh = 0;                         // K shells (the first nKsh union shells)
+
   // work
   DBuf w1, w2, w3, w4, w5, w6, w7, w8;
   double stats[16] = {0};
@@ -189,10 +202,19 @@ struct Engine : StreamOwner {
   // ris Z-vector solve (A+B) Z = rhs for nr right-hand sides (PCG)
   void zvector(int nr, const double* rhs, double* Z);
   void ensure_Kov();
+  // time-derivative couplings T[g] = d_g . v (nac [npair][natm][3], vel [natm][3])
+  void time_coupling(int npair, const double* nac, const double* vel, double* T);
   // phases of the current states against the previous step (five dominant determinants)
   void phase_align(int ns, const double* Xprev, int* sign, double* Xout);
   // exchange (ij|ab) and (ib|ja) contractions of nvec vectors: K1, K2 [nvec][nov]
   void exchange_terms(const double* Z, int nvec, double* K1, double* K2, bool mixed);
+  // streamed form
+  bool want_streamed(int nao_) const;
+  void setup_streamed();
+  void build_B_streamed();
+  void pair_derivs_streamed(int npair, const int* pairs, int nsu, const std::vector<int>& su,
+                            const std::map<int, int>& slot, const double* Xa, double* out);
+  int block_width(double bytes_per_function) const;
 };
 
 // n doubles from a host or device pointer into host memory

@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
     __syncwarp();
     const int col = n0 + c0 + lane;
     if (good && col < args.N) {
-      const long long cpos = ep.cin > 0 ? (long long)(col / ep.cin) * ep.cld + col % ep.cin : col;
+      const long long cpos = ep.cin > 0 ? (long long)(col / ep.cin) * ep.cld + (long long)(col % ep.cin) * ep.cs
+                                        : (long long)col * ep.cs;
 #pragma unroll 4
       for (int r = 0; r < 32; r++) {
         const int row = m0 + warp * 32 + r;
@@ -224,7 +225,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
           args.partial[((size_t)ks * args.M + row) * args.N + col] = x;
           continue;
         }
-        const size_t off = (size_t)z * ep.bsc + (size_t)row * ep.rs + (size_t)cpos * ep.cs;
+        const long long rpos = ep.rin > 0 ? (long long)(row / ep.rin) * ep.rld + (long long)(row % ep.rin) * ep.rs
+                                          : (long long)row * ep.rs;
+        const size_t off = (size_t)z * ep.bsc + (size_t)rpos + (size_t)cpos;
         if (ep.mode == kOutF64) {
           double* p = ep.c64 + off;
           *p = ep.beta == 0.0 ? ep.alpha * x : fma(ep.alpha, (double)x, ep.beta * *p);
@@ -352,7 +355,8 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
   a.kb_per = 1;
   const int tiles = cdiv(M, BM) * cdiv(N, BN);
   a.kb_per = a.nkb;
-  if (nb == 1 && ep.mode == kOutF64 && ep.cs == 1 && ep.cin == 0 && tiles < 152 && a.nkb >= 8) {
+  if (nb == 1 && ep.mode == kOutF64 && ep.cs == 1 && ep.cin == 0 && ep.rin == 0 && tiles < 152 &&
+      a.nkb >= 8) {
     int ks = std::max(1, std::min(std::max(1, 152 / tiles), a.nkb / 4));
     a.kb_per = cdiv(a.nkb, ks);
     a.ksplit = cdiv(a.nkb, a.kb_per);  // every slice non-empty

@@ -19,9 +19,11 @@ struct TcOperand {
 };
 
 // Epilogue: element (i, j) of batch z, i < M, j < N, is stored at
-//   z * bsc + i * rs + cpos(j) * cs,
-// cpos(j) = (j / cin) * cld + j % cin when cin > 0 (column blocks of cin at
-// stride cld, e.g. a padded inner index), else j.
+//   z * bsc + rpos(i) + cpos(j),
+// rpos(i) = (i / rin) * rld + (i % rin) * rs when rin > 0 (row blocks of rin
+// at stride rld), else i * rs;
+// cpos(j) = (j / cin) * cld + (j % cin) * cs when cin > 0 (column blocks of
+// cin at stride cld, e.g. a padded inner index), else j * cs.
 //   kOutF64:   C64 = alpha * acc + beta * C64
 //   kOutSplit: Chi/Clo = tf32 split of alpha * acc (FP32)
 //   kOutF32:   C32 = alpha * acc + beta * C32 (FP32 arithmetic)
@@ -37,6 +39,8 @@ struct TcEpilogue {
   double alpha = 1.0, beta = 0.0;
   int cin = 0;
   long long cld = 0;
+  int rin = 0;
+  long long rld = 0;
 };
 
 // C[z] (M x N) = A[z] (M x K) . B[z]^T (N x K), batches z < nb.  With

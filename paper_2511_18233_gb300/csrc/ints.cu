@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(128) k_int3c(const int* __restrict__ pa, const
                                                const double* __restrict__ xyz,
                                                const double* __restrict__ boys_tab, int nao,
                                                int nJ, int nK, double* __restrict__ TJ,
-                                               double* __restrict__ TK) {
+                                               double* __restrict__ TK,
+                                               const long long* __restrict__ poff,
+                                               const int* __restrict__ ax_off) {
   constexpr int L = LA + LB + LC;
   long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (long long)np * nax) return;
@@ -350,6 +352,11 @@ __global__ void __launch_bounds__(128) k_int3c(const int* __restrict__ pa, const
               s += fx[jx] * fy[jy] * fz[jz] * sub;
             }
         s *= nab * cfac(LC, ic);
+        if (poff) {  // screened-pair storage: one row per function pair of this shell pair
+          constexpr int NB = (LB + 1) * (LB + 2) / 2;
+          TJ[(size_t)(poff[ip] + ia * NB + ib) * nJ + ax_off[sc] + ic] = s;
+          continue;
+        }
         const int mu = oa + ia, nu = ob + ib;
         if (jm >= 0) {
           TJ[((size_t)mu * nao + nu) * nJ + jm + ic] = s;
@@ -671,7 +678,7 @@ void free_pairs(PairList& pl, cudaStream_t st) {
 template <int LA, int LB, int LC>
 static void launch_int3c(const ShellSet& ao, const ShellSet& aux, const PairList& pl,
                          const double* xyz, const double* tab, int nJ, int nK, double* TJ,
-                         double* TK, cudaStream_t st) {
+                         double* TK, const long long* poff, cudaStream_t st) {
   const int cls = LA * (LA + 1) / 2 + LB;
   const int p0 = pl.class_off[cls], np = pl.class_off[cls + 1] - p0;
   const int nax = (int)aux.by_l[LC].size();
@@ -679,7 +686,7 @@ static void launch_int3c(const ShellSet& ao, const ShellSet& aux, const PairList
   const long long nt = (long long)np * nax;
   k_int3c<LA, LB, LC><<<(unsigned)cdiv(nt, 128), 128, 0, st>>>(
       pl.a, pl.b, p0, np, aux.d_by_l[LC], nax, ao.atom, ao.off, ao.ex, ao.nbase, aux.atom, aux.ex,
-      aux.nbase, aux.jmap, aux.kmap, xyz, tab, ao.nfun, nJ, nK, TJ, TK);
+      aux.nbase, aux.jmap, aux.kmap, xyz, tab, ao.nfun, nJ, nK, TJ, TK, poff, aux.off);
   RIS_CHECK_LAUNCH();
 }
 
@@ -723,7 +730,17 @@ void int3c(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const do
   RIS_CUDA(cudaGetDevice(&dev));
   const double* tab = boys_table_device(dev);
   prof_begin(kProfInt3c, st);
-  RIS_FOR_CLASSES(launch_int3c, ao, aux, pl, xyz, tab, nJ, nK, TJ, TK, st)
+  RIS_FOR_CLASSES(launch_int3c, ao, aux, pl, xyz, tab, nJ, nK, TJ, TK, nullptr, st)
+  prof_end(kProfInt3c, st, (double)pl.npair * aux.n);
+}
+
+void int3c_pairs(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const double* xyz,
+                 const long long* poff, double* Ts, cudaStream_t st) {
+  int dev;
+  RIS_CUDA(cudaGetDevice(&dev));
+  const double* tab = boys_table_device(dev);
+  prof_begin(kProfInt3c, st);
+  RIS_FOR_CLASSES(launch_int3c, ao, aux, pl, xyz, tab, aux.nfun, 0, Ts, nullptr, poff, st)
   prof_end(kProfInt3c, st, (double)pl.npair * aux.n);
 }
 

@@ -46,6 +46,13 @@ void free_pairs(PairList& pl, cudaStream_t st);
 void int3c(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const double* d_coords,
            int nJ, int nK, double* TJ, double* TK, cudaStream_t st);
 
+// Screened-pair storage of (mu nu|P): for each shell pair ip of the list
+// (canonical order), its na x nb function pairs are rows poff[ip] + ia * nb
+// + ib of Ts [rows][aux.nfun] (mu of the pair's first shell, nu of its
+// second; P in the auxiliary set's own function order).
+void int3c_pairs(const ShellSet& ao, const ShellSet& aux, const PairList& pl, const double* xyz,
+                 const long long* poff, double* Ts, cudaStream_t st);
+
 // D[x][mu][nu][P] = d(mu nu|P)/dA_x with A the centre of mu (union auxiliary
 // set, P fastest), computed in FP64 and stored as T (double or float).
 // Zeroed by the caller.

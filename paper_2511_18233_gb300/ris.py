@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_gemm_f64emu", "ris_debug_sym_eig", "ris_debug_sym_eig_f32", "ris_debug_dgemm",
+           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_time_coupling", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_gemm_f64emu", "ris_debug_sym_eig", "ris_debug_sym_eig_f32", "ris_debug_dgemm",
            "ris_gemm_tf32x3_noalloc", "ris_debug_alloc_count", "ris_debug_peak_probe",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_int), ("mixed_tol", ctypes.c_double), ("refine", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mo_window", ctypes.c_double),
                 ("deriv_prefetch", ctypes.c_int), ("emu_f64", ctypes.c_int),
-                ("eig_fp32", ctypes.c_int)]
+                ("eig_fp32", ctypes.c_int), ("stream", ctypes.c_int), ("stream_block", ctypes.c_int)]
 
 
 class Shell(ctypes.Structure):
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     L.ris_trim.argtypes = [P]
     L.ris_zvector.argtypes = [P, i, P, P]
     L.ris_phase_align.argtypes = [P, i, P, P, P]
+    L.ris_time_coupling.argtypes = [P, i, P, P, P]
     L.ris_get_mo_window.argtypes = [P, P, P, P]
     L.ris_apply.argtypes = [P, i, P, P, P]
     L.ris_gradient.argtypes = [P, i, P, i, P, P, P]
@@ -245,6 +246,18 @@ class Context:
         sign = np.zeros(ns, dtype=np.int32)
         self._check(self.L.ris_phase_align(self.h, ns, _ptr(X_prev), _ptr(sign), _ptr(X_out)))
         return sign
+
+    def time_coupling(self, nac, velocity, out=None):
+        """T_IJ = d_IJ . v for each coupling (ris_time_coupling); nac
+        [npair][natm][3], velocity [natm][3], host or device."""
+        npair = int(nac.shape[0])
+        T = np.zeros(npair) if out is None else out
+        if isinstance(nac, np.ndarray):
+            nac = np.ascontiguousarray(nac, dtype=np.float64)
+        if isinstance(velocity, np.ndarray):
+            velocity = np.ascontiguousarray(velocity, dtype=np.float64)
+        self._check(self.L.ris_time_coupling(self.h, npair, _ptr(nac), _ptr(velocity), _ptr(T)))
+        return T
 
     def trim(self):
         """Release every device buffer of the context (ris_trim)."""

@@ -559,12 +559,12 @@ class RisExecutor:
             s["have_X"] = True
             grad = ctx.gradient([spec.active])[0]
             nac = ctx.nac(spec.pairs) if spec.pairs else np.zeros((0, ctx.natm, 3))
+            v = step_velocities(tr.mol.elements, spec, req.step)
+            T = ctx.time_coupling(nac, v) if len(spec.pairs) else np.zeros(0)
             omega = s["om"].cpu().numpy()
             st = ctx.stats()
         finally:
             ctx.trim()
-        v = step_velocities(tr.mol.elements, spec, req.step)
-        T = np.einsum("pax,ax->p", nac, v) if len(spec.pairs) else np.zeros(0)
         return ({"omega": omega, "grad": grad, "nac": nac, "T": T, "signs": signs,
                  "n_iter": int(st["n_iter"]), "n_products": int(st["n_products"])},
                 int(st["bytes_peak"]))

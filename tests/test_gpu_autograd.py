@@ -139,16 +139,23 @@ def test_autograd_flake_rpa(torch_mod, oracle):
     for (A, x) in [(0, 0), (60, 1)]:
         fd2 = _fd(model, mol.coords, 0, A, x, 1e-3, 2)
         fd5 = _fd(model, mol.coords, 0, A, x, 1e-3, 5)
-        fd_rows.append((A, x, g[A, x], fd2, fd5))
-    print(f"\nflake: omega rel {rel_om:.2e}; kernels vs oracle {err_o:.2e} (floor {floor:.2e}, "
-          f"max|g| {scale:.2e}); FD " +
-          "; ".join(f"({A},{x}) g {gv:.6e} fd2-g {f2 - gv:.1e} fd5-g {f5 - gv:.1e}"
-                    for A, x, gv, f2, f5 in fd_rows))
+        fd5h = _fd(model, mol.coords, 0, A, x, 5e-4, 5)
+        fd_rows.append((A, x, g[A, x], fd2, fd5, fd5h))
+    print(f"\nflake: omega rel {rel_om:.2e}; S1-S2 gap {om[1] - om[0]:.2e}; kernels vs oracle "
+          f"{err_o:.2e} (floor {floor:.2e}, max|g| {scale:.2e}); FD " +
+          "; ".join(f"({A},{x}) g {gv:.6e} fd2-g {f2 - gv:.1e} fd5-g {f5 - gv:.1e} fd5(h/2)-g {f5h - gv:.1e}"
+                    for A, x, gv, f2, f5, f5h in fd_rows))
     assert rel_om <= 1e-9
     assert err_o <= 2.0 * floor + 1e-9 * scale
     assert _rel(g, g_lib) <= 1e-12
     assert np.max(np.abs(g.sum(axis=0))) <= 1e-10 * np.max(np.abs(g))
     gmax = float(np.max(np.abs(g)))
-    for A, x, gv, f2, f5 in fd_rows:
-        assert abs(gv - f5) <= 2.0 * floor + 1e-8 * gmax
-        assert abs(gv - f2) <= 1e-5 * gmax
+    tol = 2.0 * floor + 1e-9 * gmax
+    for A, x, gv, f2, f5, f5h in fd_rows:
+        # S1 and S2 of the flake are only ~2e-4 Ha apart, so the state-1
+        # surface curves strongly near the avoided crossing and the stencils
+        # are truncation-limited.  Each stencil is held to its own truncation
+        # estimate: the 2-point one to its difference from the 5-point one,
+        # the 5-point one (O(h^4)) to a fifteenth of its change on halving h.
+        assert abs(gv - f2) <= 1.5 * abs(f2 - f5) + tol
+        assert abs(gv - f5h) <= 2.0 * abs(f5 - f5h) / 15.0 + tol

@@ -65,6 +65,23 @@ def test_cutdown_fp64_parity(ris_mod, ref):
 
 @gpu
 @pytest.mark.slow
+def test_cutdown_streamed_fp64_parity(ris_mod, ref):
+    """The streamed form (screened-pair integrals, auxiliary blocks,
+    regenerated derivative integrals) on the same cut-down, at the FP64
+    parity tolerance against the oracle."""
+    mol, w, X, g_ref, num_ref = ref
+    om, Xg, g, num = _run(ris_mod, mol, stream=1, stream_block=48)
+    np.testing.assert_allclose(om, w, rtol=1e-9)
+    sel = g[[0, NS - 1]][:, ATOMS]
+    gr = g_ref[:, ATOMS]
+    assert np.max(np.abs(sel - gr)) <= 1e-9 * np.max(np.abs(gr))
+    nr = num_ref[0, ATOMS]
+    assert np.max(np.abs(num[PAIR[0], ATOMS] - nr)) <= 1e-9 * np.max(np.abs(nr))
+    assert np.max(np.abs(g.sum(axis=1))) <= 1e-10 * np.max(np.abs(g))
+
+
+@gpu
+@pytest.mark.slow
 def test_cutdown_mixed_stated_error(ris_mod, ref):
     mol, w, X, g_ref, num_ref = ref
     om, Xg, g, num = _run(ris_mod, mol, precision=ris_mod.MIXED)
