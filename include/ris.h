@@ -91,7 +91,11 @@ typedef struct {
   void* cuda_stream;  /* cudaStream_t to run on; NULL = the context makes one */
   int device;         /* CUDA device ordinal */
   int profile;        /* 1: time kernel classes with CUDA events (see ris_get_stats) */
-  double mixed_tol;   /* RIS_MIXED: residual tolerance of the 3xTF32 Davidson phase; default 1e-6 */
+  double mixed_tol;   /* RIS_MIXED: residual tolerance of the 3xTF32 Davidson phase; default 1e-6.
+                         When the 3xTF32 products stall above it (eight iterations without a
+                         10% drop of the largest residual, within 100x the tolerance), TDA
+                         continues with FP64 products to the same tolerance (not available in
+                         the streamed form, which keeps no FP64 B^K_vv) */
   int refine;         /* RIS_MIXED: 1 = continue with FP64 products to conv_tol (the B
                          tensors are then built in FP64 throughout); default 0 */
   int precond;        /* TDA Davidson preconditioner: 0 (default) = (D - s + 2 B^J B^J^T)^-1
@@ -269,7 +273,8 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
  *       of the last call of each kind (CUDA events on the context's stream);
  *   [4] A-products and [5] Davidson iterations of the last excite (or the
  *   (A+B) products and CG iterations of the last Z-vector solve),
- *   [6] FP64 products of its refinement phase (mixed with refine), [7] the
+ *   [6] FP64 products of its refinement phase (mixed with refine, or the
+ *   FP64 continuation after the 3xTF32 products stalled above mixed_tol), [7] the
  *   largest residual norm |A x - omega x| at its last iteration (TDA);
  *   [15] kernels launched by the library since it was loaded (all contexts);
  *   with the profile option, per kernel class since the previous call:

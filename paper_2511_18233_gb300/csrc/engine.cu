@@ -465,14 +465,16 @@ __global__ void __launch_bounds__(1024) k_min(const double* __restrict__ x, long
 }
 
 // dinv = 1 / (de - s), s = min(de) - gap;  W[i][R] = dinv[i] BJ[i][R]
+// rows r0 .. r0 + nr - 1: dinv[i] = 1 / (de[i] - s), W[i - r0][P] = dinv[i] B^J[i][P]
 __global__ void k_precond_setup(const double* __restrict__ de, const double* __restrict__ dmin,
-                                long long n, double gap, const double* __restrict__ BJ, int nJ,
-                                double* __restrict__ dinv, double* __restrict__ W) {
+                                long long r0, long long nr, double gap,
+                                const double* __restrict__ BJ, int nJ, double* __restrict__ dinv,
+                                double* __restrict__ W) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * nJ) return;
-  const long long i = t / nJ;
+  if (t >= nr * nJ) return;
+  const long long i = r0 + t / nJ;
   const double d = 1.0 / (de[i] - (dmin[0] - gap));
-  W[t] = d * BJ[t];
+  W[t] = d * BJ[(size_t)r0 * nJ + t];
   if (t % nJ == 0) dinv[i] = d;
 }
 
@@ -1710,7 +1712,29 @@ void Engine::davidson_tda(int ns, const double* guess) {
     dav_core(ns, guess, guess ? ns : 0, false, opt.conv_tol, true);
     return;
   }
-  dav_core(ns, guess, guess ? ns : 0, true, std::max(opt.conv_tol, opt.mixed_tol), true);
+  bool ok = true;
+  const double tolm = std::max(opt.conv_tol, opt.mixed_tol);
+  struct ReleaseY {  // streamed form: the exchange work space is large; give it back
+    Engine& e;
+    ~ReleaseY() {
+      if (e.streamed) {
+        e.YH.release();
+        e.YL.release();
+      }
+    }
+  } release_y{*this};
+  dav_core(ns, guess, guess ? ns : 0, true, tolm, true, streamed ? nullptr : &ok);
+  if (!ok) {
+    // the 3xTF32 products stalled above the tolerance: continue from the
+    // current vectors with FP64 products to the same tolerance
+    SBuf<double> g((size_t)ns * nocc * nvir, st);
+    RIS_CUDA(cudaMemcpyAsync(g.p, X.p, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, st));
+    const double s4 = stats[4], s5 = stats[5];
+    dav_core(ns, g.p, ns, false, tolm);
+    stats[6] = stats[4];
+    stats[4] += s4;
+    stats[5] += s5;
+  }
   if (opt.refine) {
     SBuf<double> g((size_t)ns * nocc * nvir, st);
     RIS_CUDA(cudaMemcpyAsync(g.p, X.p, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, st));
@@ -1743,17 +1767,24 @@ void CoulPrecond::setup(Engine& e, bool shifted, double f_, int nmax) {
   pY.ensure((size_t)nmax * nJ, st);
   pZ.ensure((size_t)nmax * nJ, st);
   pP.ensure((size_t)nmax * n, st);
-  SBuf<double> W((size_t)n * nJ, st), cap((size_t)nJ * nJ, st), Li((size_t)nJ * nJ, st),
+  // the capacitance matrix B^T D'^-1 B over row blocks of at most 2^27
+  // elements of the scaled B (one block for all but the largest systems)
+  const long long rblk = std::max(1LL, std::min(n, (1LL << 27) / std::max(nJ, 1)));
+  SBuf<double> W((size_t)rblk * nJ, st), cap((size_t)nJ * nJ, st), Li((size_t)nJ * nJ, st),
       dm(1, st, true);
   SBuf<int> info(1, st);
   if (shifted) {
     k_min<<<1, 1024, 0, st>>>(e.de.p, n, dm.p);
     RIS_CHECK_LAUNCH();
   }
-  k_precond_setup<<<cdiv(n * nJ, 256), 256, 0, st>>>(e.de.p, dm.p, n, shifted ? kPrecondGap : 0.0,
-                                                      e.BJ.p, nJ, dinv.p, W.p);
-  RIS_CHECK_LAUNCH();
-  dgemm(true, false, nJ, nJ, (int)n, f, e.BJ.p, nJ, W.p, nJ, 0.0, cap.p, nJ, st);
+  for (long long r0 = 0; r0 < n; r0 += rblk) {
+    const long long nr = std::min(rblk, n - r0);
+    k_precond_setup<<<cdiv(nr * nJ, 256), 256, 0, st>>>(e.de.p, dm.p, r0, nr, shifted ? kPrecondGap : 0.0,
+                                                         e.BJ.p, nJ, dinv.p, W.p);
+    RIS_CHECK_LAUNCH();
+    dgemm(true, false, nJ, nJ, (int)nr, f, e.BJ.p + (size_t)r0 * nJ, nJ, W.p, nJ, r0 == 0 ? 0.0 : 1.0,
+          cap.p, nJ, st);
+  }
   k_add_identity<<<cdiv(nJ, 128), 128, 0, st>>>(cap.p, nJ);
   RIS_CHECK_LAUNCH();
   cholesky(cap.p, nJ, info.p, st);
@@ -1783,7 +1814,7 @@ void CoulPrecond::apply(Engine& e, const double* R, const int* idx, int nt, doub
 // given vectors (augment: plus unit vectors up to the usual block size);
 // products in FP64 or (mixed) with 3xTF32 exchange GEMMs.
 void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, double tol,
-                      bool augment) {
+                      bool augment, bool* ok) {
   const long long n = (long long)nocc * nvir;
   const int nb0 = (int)std::min<long long>(n, ns + std::min(ns, 8));
   int maxsp = opt.max_subspace > 0 ? opt.max_subspace : std::max(nb0 + 2 * ns, 8 * ns);
@@ -1865,6 +1896,7 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
   int nprod = m;
   dgemm(false, true, m, m, (int)n, 1.0, V.p, (int)n, AV.p, (int)n, 0.0, Hs.p, maxsp, st);
   std::vector<double> rn(ns);
+  std::vector<double> rhist;
   bool converged = false;
   int it = 0;
   double rmax = 0.0;
@@ -1895,6 +1927,13 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
       if (stall >= 3) eig32 = false;
     }
     rprev = rmax;
+    // mixed products: their rounding floor can lie just above the tolerance;
+    // eight iterations without a 10% drop of the largest residual, within
+    // 100x the tolerance, end the 3xTF32 phase (the caller finishes in FP64)
+    rhist.push_back(rmax);
+    if (ok && mixed && rhist.size() > 8 && rmax < 100.0 * tol &&
+        rmax > 0.9 * rhist[rhist.size() - 9])
+      break;
     int nt = (int)u.size();
     RIS_CUDA(cudaMemcpyAsync(d_idx, u.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
     precondition(nt);
@@ -1962,7 +2001,8 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
   stats[4] = nprod;
   stats[5] = it;
   stats[7] = rmax;
-  RIS_REQUIRE(converged, RIS_ERR_NOT_CONVERGED,
+  if (ok) *ok = converged;
+  RIS_REQUIRE(converged || ok, RIS_ERR_NOT_CONVERGED,
               "Davidson did not converge in " + std::to_string(it) + " iterations (largest residual " +
                   std::to_string(rmax) + ")");
   k_phase<<<ns, 256, 0, st>>>(Xr.p, nullptr, n);

@@ -194,8 +194,10 @@ struct Engine : StreamOwner {
   void gamma_K_mixed(const float* USh, const float* USl, const float* VSh, const float* VSl,
                      const float* WUh, const float* WUl, const float* WVh, const float* WVl,
                      double f, double* Gam, float* Gam32, double* Om);
+  // ok != nullptr: a mixed-precision run that stalls above the tolerance
+  // returns its current vectors with *ok = false instead of failing
   void dav_core(int ns, const double* guess, int nguess, bool mixed, double tol,
-                bool augment = false);
+                bool augment = false, bool* ok = nullptr);
   void apply_ApB_AmB(const double* Zin, int nvec, double* outP, double* outM);
   void davidson_tda(int ns, const double* guess = nullptr);
   void davidson_rpa(int ns);
