@@ -129,6 +129,8 @@ void Engine::trim() {
   aoList.release();
   axPtr.release();
   axList.release();
+  nbPtr.release();
+  nbCol.release();
   pOff.release();
   fpMu.release();
   fpNu.release();
@@ -691,8 +693,10 @@ __global__ void k_build_W(const double* __restrict__ C, int nmo, const double* _
 constexpr int kCBatch = 8;  // states (or pairs) sharing one pass over the derivative integrals
 
 // The contractions below run one thread per (mu, P, slice of nu): the sum
-// over nu is cut into nslice slices so that enough warps are in flight, each
-// slice writes its partial sums and k_sum_slices adds them in a fixed order.
+// over nu runs over mu's screened partners only (the derivative integrals
+// vanish elsewhere; CSR lists nbPtr / nbCol) and is cut into nslice slices so
+// that enough warps are in flight, each slice writes its partial sums and
+// k_sum_slices adds them in a fixed order.
 // With T = float (mixed precision: derivative integrals stored in FP32) the
 // products and runs of kChunk terms are summed in FP32 and the runs in FP64;
 // with T = double everything is FP64.
@@ -710,12 +714,16 @@ template <class T>
 __global__ void __launch_bounds__(128) k_contract_states(const T* __restrict__ D,
                                                          const T* __restrict__ DRs, int s0,
                                                          int ns, int nao, int nU, int nslice,
+                                                         const int* __restrict__ nbPtr,
+                                                         const int* __restrict__ nbCol,
                                                          double* __restrict__ part) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nao * nU) return;
   const int mu = (int)(idx / nU), P = (int)(idx % nU);
-  int nu0, nu1;
-  slice_range(nao, nslice, blockIdx.y, nu0, nu1);
+  int q0, q1;  // this slice of mu's screened partners nu
+  slice_range(nbPtr[mu + 1] - nbPtr[mu], nslice, blockIdx.y, q0, q1);
+  q0 += nbPtr[mu];
+  q1 += nbPtr[mu];
   const size_t nn2 = (size_t)nao * nao;
   const size_t plane = nn2 * nU;
   double y[kCBatch][3];
@@ -725,7 +733,8 @@ __global__ void __launch_bounds__(128) k_contract_states(const T* __restrict__ D
 #pragma unroll
     for (int x = 0; x < 3; x++) y[b][x] = 0.0, c[b][x] = (T)0;
   const T* dr = DRs + (size_t)s0 * nn2 + (size_t)mu * nao;
-  for (int nu = nu0; nu < nu1; nu++) {
+  for (int q = q0; q < q1; q++) {
+    const int nu = nbCol[q];
     const size_t a = ((size_t)mu * nao + nu) * nU + P;
     const T d0 = D[a], d1 = D[plane + a], d2 = D[2 * plane + a];
 #pragma unroll
@@ -736,7 +745,7 @@ __global__ void __launch_bounds__(128) k_contract_states(const T* __restrict__ D
       c[b][1] += d1 * w;
       c[b][2] += d2 * w;
     }
-    if (((nu - nu0) % kChunk) == kChunk - 1 || nu == nu1 - 1) {
+    if (((q - q0) % kChunk) == kChunk - 1 || q == q1 - 1) {
 #pragma unroll
       for (int b = 0; b < kCBatch; b++)
 #pragma unroll
@@ -759,12 +768,16 @@ template <class T, class G>
 __global__ void __launch_bounds__(128) k_contract_exchange(const T* __restrict__ D,
                                                            const G* __restrict__ GK, int nb,
                                                            int nao, int nU, int nK, int nslice,
+                                                           const int* __restrict__ nbPtr,
+                                                           const int* __restrict__ nbCol,
                                                            double* __restrict__ part) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nao * nK) return;
   const int mu = (int)(idx / nK), P = (int)(idx % nK);
-  int nu0, nu1;
-  slice_range(nao, nslice, blockIdx.y, nu0, nu1);
+  int q0, q1;  // this slice of mu's screened partners nu
+  slice_range(nbPtr[mu + 1] - nbPtr[mu], nslice, blockIdx.y, q0, q1);
+  q0 += nbPtr[mu];
+  q1 += nbPtr[mu];
   const size_t nn2 = (size_t)nao * nao;
   const size_t plane = nn2 * nU;
   const size_t gk = nn2 * nK;
@@ -774,7 +787,8 @@ __global__ void __launch_bounds__(128) k_contract_exchange(const T* __restrict__
   for (int b = 0; b < kCBatch; b++)
 #pragma unroll
     for (int x = 0; x < 3; x++) s[b][x] = 0.0, c[b][x] = (T)0;
-  for (int nu = nu0; nu < nu1; nu++) {
+  for (int q = q0; q < q1; q++) {
+    const int nu = nbCol[q];
     const size_t mn = (size_t)mu * nao + nu;
     const size_t a = mn * nU + P;
     const T d0 = D[a], d1 = D[plane + a], d2 = D[2 * plane + a];
@@ -787,7 +801,7 @@ __global__ void __launch_bounds__(128) k_contract_exchange(const T* __restrict__
       c[b][1] += d1 * g;
       c[b][2] += d2 * g;
     }
-    if (((nu - nu0) % kChunk) == kChunk - 1 || nu == nu1 - 1) {
+    if (((q - q0) % kChunk) == kChunk - 1 || q == q1 - 1) {
 #pragma unroll
       for (int b = 0; b < kCBatch; b++)
 #pragma unroll
@@ -814,9 +828,9 @@ __global__ void k_sum_slices(const double* __restrict__ part, int nslice, long l
 }
 
 // slices of the nu sum so that about eight blocks per SM are in flight
-static int pick_slices(long long threads, int nao) {
+static int pick_slices(long long threads, int partners) {
   const int base = cdiv(threads, 128);
-  return std::max(1, std::min({cdiv(8 * 152, base), nao / 16, 64}));
+  return std::max(1, std::min({cdiv(8 * 152, base), partners / 16, 64}));
 }
 
 // W_g[x][mu][P] of pair g = (I, J): exchange part plus the Coulomb part
@@ -1157,6 +1171,40 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
     vmax = std::max(vmax, nb * 2.0 * M_PI / g * (aux.h_l[s] ? 1.0 / sqrt(g) : 1.0));
   }
   build_pairs(ao, xyz.p, opt.screen_thr / std::max(vmax, 1e-300), pl, nullptr, st);
+  // the screened pairs on the host, and each AO function's screened partners
+  {
+    h_pa.assign(std::max(pl.npair, 1), 0);
+    h_pb.assign(std::max(pl.npair, 1), 0);
+    if (pl.npair > 0) {
+      RIS_CUDA(cudaMemcpyAsync(h_pa.data(), pl.a, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st));
+      RIS_CUDA(cudaMemcpyAsync(h_pb.data(), pl.b, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st));
+      RIS_CUDA(cudaStreamSynchronize(st));
+    }
+    const int nf = ao.nfun;
+    std::vector<std::vector<int>> nb(nf);
+    for (int ip = 0; ip < pl.npair; ip++) {
+      const int sa = h_pa[ip], sb = h_pb[ip];
+      for (int ia = 0; ia < ncart(ao.h_l[sa]); ia++)
+        for (int ib = 0; ib < ncart(ao.h_l[sb]); ib++) {
+          const int mu = ao.h_off[sa] + ia, nu = ao.h_off[sb] + ib;
+          nb[mu].push_back(nu);
+          if (sa != sb) nb[nu].push_back(mu);
+        }
+    }
+    std::vector<int> ptr(nf + 1, 0), col;
+    for (int mu = 0; mu < nf; mu++) {
+      std::sort(nb[mu].begin(), nb[mu].end());
+      ptr[mu + 1] = ptr[mu] + (int)nb[mu].size();
+      col.insert(col.end(), nb[mu].begin(), nb[mu].end());
+    }
+    nbAvg = std::max(1, ptr[nf] / std::max(nf, 1));
+    nbPtr.ensure(nf + 1, st);
+    nbCol.ensure(std::max<size_t>(col.size(), 1), st);
+    RIS_CUDA(cudaMemcpyAsync(nbPtr.p, ptr.data(), sizeof(int) * (nf + 1), cudaMemcpyHostToDevice, st));
+    if (!col.empty())
+      RIS_CUDA(cudaMemcpyAsync(nbCol.p, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, st));
+    RIS_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  }
   // integrals: dense [mu][nu][P], or (streamed form) on the screened pairs
   // only, after the metric factors are known
   const int nao_ = ao.nfun;
@@ -1769,7 +1817,8 @@ void CoulPrecond::setup(Engine& e, bool shifted, double f_, int nmax) {
   pP.ensure((size_t)nmax * n, st);
   // the capacitance matrix B^T D'^-1 B over row blocks of at most 2^27
   // elements of the scaled B (one block for all but the largest systems)
-  const long long rblk = std::max(1LL, std::min(n, (1LL << 27) / std::max(nJ, 1)));
+  const long long rblk = std::max(1LL, std::min(n, (1LL << (e.opt.precision == RIS_MIXED ? 26 : 27)) /
+                                                       std::max(nJ, 1)));
   SBuf<double> W((size_t)rblk * nJ, st), cap((size_t)nJ * nJ, st), Li((size_t)nJ * nJ, st),
       dm(1, st, true);
   SBuf<int> info(1, st);
@@ -1777,13 +1826,33 @@ void CoulPrecond::setup(Engine& e, bool shifted, double f_, int nmax) {
     k_min<<<1, 1024, 0, st>>>(e.de.p, n, dm.p);
     RIS_CHECK_LAUNCH();
   }
+  // mixed precision: the capacitance matrix only steers the preconditioner
+  // (never the converged pairs), so its long-K product runs as a 3xTF32
+  // tensor-core GEMM on transposed row blocks
+  const bool tc = e.opt.precision == RIS_MIXED && e.d_tcerr;
+  const int ldr = ld4((int)std::min(rblk, n));
+  SBuf<float> BTh, BTl, WTh, WTl;
+  if (tc) {
+    BTh.ensure((size_t)nJ * ldr, st);
+    BTl.ensure((size_t)nJ * ldr, st);
+    WTh.ensure((size_t)nJ * ldr, st);
+    WTl.ensure((size_t)nJ * ldr, st);
+  }
   for (long long r0 = 0; r0 < n; r0 += rblk) {
     const long long nr = std::min(rblk, n - r0);
     k_precond_setup<<<cdiv(nr * nJ, 256), 256, 0, st>>>(e.de.p, dm.p, r0, nr, shifted ? kPrecondGap : 0.0,
                                                          e.BJ.p, nJ, dinv.p, W.p);
     RIS_CHECK_LAUNCH();
-    dgemm(true, false, nJ, nJ, (int)nr, f, e.BJ.p + (size_t)r0 * nJ, nJ, W.p, nJ, r0 == 0 ? 0.0 : 1.0,
-          cap.p, nJ, st);
+    if (tc) {
+      const int lr = ld4((int)nr);
+      split_f64_t(e.BJ.p + (size_t)r0 * nJ, (int)nr, nJ, nJ, BTh.p, BTl.p, lr, st);  // [P][row]
+      split_f64_t(W.p, (int)nr, nJ, nJ, WTh.p, WTl.p, lr, st);
+      tcg(nJ, nJ, (int)nr, BTh.p, BTl.p, lr, WTh.p, WTl.p, lr, 0, 1,
+          ep_f64(cap.p, nJ, 0, f, r0 == 0 ? 0.0 : 1.0), e.d_tcerr, st);
+    } else {
+      dgemm(true, false, nJ, nJ, (int)nr, f, e.BJ.p + (size_t)r0 * nJ, nJ, W.p, nJ, r0 == 0 ? 0.0 : 1.0,
+            cap.p, nJ, st);
+    }
   }
   k_add_identity<<<cdiv(nJ, 128), 128, 0, st>>>(cap.p, nJ);
   RIS_CHECK_LAUNCH();
@@ -2402,15 +2471,17 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
                                                                   DRf.p);
     RIS_CHECK_LAUNCH();
   }
-  const int slJ = pick_slices((long long)nn * nU, nn);
+  const int slJ = pick_slices((long long)nn * nU, nbAvg);
   SBuf<double> partJ((size_t)slJ * std::min(nsu, kCBatch) * 3 * nn * nU, st);
   for (int s0 = 0; s0 < nsu; s0 += kCBatch) {
     const int ns = std::min(kCBatch, nsu - s0);
     const dim3 grid(cdiv((long long)nn * nU, 128), slJ);
     if (mixed)
-      k_contract_states<float><<<grid, 128, 0, st>>>(Df.p, DRf.p, s0, ns, nn, nU, slJ, partJ.p);
+      k_contract_states<float><<<grid, 128, 0, st>>>(Df.p, DRf.p, s0, ns, nn, nU, slJ, nbPtr.p,
+                                                     nbCol.p, partJ.p);
     else
-      k_contract_states<double><<<grid, 128, 0, st>>>(D.p, DR.p, s0, ns, nn, nU, slJ, partJ.p);
+      k_contract_states<double><<<grid, 128, 0, st>>>(D.p, DR.p, s0, ns, nn, nU, slJ, nbPtr.p,
+                                                      nbCol.p, partJ.p);
     RIS_CHECK_LAUNCH();
     const long long cnt = (long long)ns * 3 * nn * nU;
     k_sum_slices<<<cdiv(cnt, 256), 256, 0, st>>>(partJ.p, slJ, cnt,
@@ -2428,7 +2499,7 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
   SBuf<double> GK(gk32 ? 1 : (size_t)NB * gk, st), OmB((size_t)NB * nU * nU, st),
       WK((size_t)NB * 3 * nn * nK, st), Z, Goo, M1, WV;
   SBuf<float> GK32(gk32 ? (size_t)NB * gk : 1, st);
-  const int slK = pick_slices((long long)nn * nK, nn);
+  const int slK = pick_slices((long long)nn * nK, nbAvg);
   SBuf<double> partK((size_t)slK * NB * 3 * nn * nK, st);
   SBuf<int> pst(2 * NB, st);
   if (opt.precision != RIS_MIXED) {
@@ -2547,13 +2618,13 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
     const dim3 gridK(cdiv((long long)nn * nK, 128), slK);
     if (gk32)
       k_contract_exchange<float, float><<<gridK, 128, 0, st>>>(Df.p, GK32.p, nb, nn, nU, nK, slK,
-                                                              partK.p);
+                                                              nbPtr.p, nbCol.p, partK.p);
     else if (mixed)
       k_contract_exchange<float, double><<<gridK, 128, 0, st>>>(Df.p, GK.p, nb, nn, nU, nK, slK,
-                                                               partK.p);
+                                                               nbPtr.p, nbCol.p, partK.p);
     else
       k_contract_exchange<double, double><<<gridK, 128, 0, st>>>(D.p, GK.p, nb, nn, nU, nK, slK,
-                                                                partK.p);
+                                                                nbPtr.p, nbCol.p, partK.p);
     RIS_CHECK_LAUNCH();
     const long long cntK = (long long)nb * 3 * nn * nK;
     k_sum_slices<<<cdiv(cntK, 256), 256, 0, st>>>(partK.p, slK, cntK, WK.p);
@@ -2821,12 +2892,8 @@ static void scatter_block(const double* Bao, int ldB, int r0, int rw, long long 
 // are the first nK union functions), and the auxiliary blocks.
 void Engine::setup_streamed() {
   const int n = nao;
-  std::vector<int> ha(std::max(pl.npair, 1)), hb(std::max(pl.npair, 1));
-  if (pl.npair > 0) {
-    RIS_CUDA(cudaMemcpyAsync(ha.data(), pl.a, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st));
-    RIS_CUDA(cudaMemcpyAsync(hb.data(), pl.b, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st));
-    RIS_CUDA(cudaStreamSynchronize(st));
-  }
+  const std::vector<int>& ha = h_pa;
+  const std::vector<int>& hb = h_pb;
   std::vector<long long> po(std::max(pl.npair, 1), 0);
   std::vector<int> fm, fn;
   long long f = 0;
@@ -3131,7 +3198,7 @@ void Engine::pair_derivs_streamed(int npair, const int* pairs, int nsu, const st
   SBuf<double> M1d(mixed ? 1 : (size_t)nn * wmaxK * 2 * o, st), WVd(mixed ? 1 : (size_t)nn * 2 * o, st);
   SBuf<float> M1h(mixed ? (size_t)nn * wmaxK * kp : 1, st), M1l(mixed ? (size_t)nn * wmaxK * kp : 1, st);
   SBuf<int> pst(2 * NB, st);
-  const int slJ = pick_slices((long long)nn * wmaxU, nn), slK = pick_slices((long long)nn * wmaxK, nn);
+  const int slJ = pick_slices((long long)nn * wmaxU, nbAvg), slK = pick_slices((long long)nn * wmaxK, nbAvg);
   SBuf<double> partJ((size_t)slJ * std::min(nsu, kCBatch) * 3 * nn * wmaxU, st),
       partK((size_t)slK * NB * 3 * nn * wmaxK, st);
   const double dbytes = mixed ? 4.0 : 8.0;
@@ -3216,9 +3283,11 @@ void Engine::pair_derivs_streamed(int npair, const int* pairs, int nsu, const st
           const int ns = std::min(kCBatch, nsu - s0);
           const dim3 grid(cdiv((long long)nn * w, 128), slJ);
           if (mixed)
-            k_contract_states<float><<<grid, 128, 0, st>>>(D32.p, DRf.p, s0, ns, nn, w, slJ, partJ.p);
+            k_contract_states<float><<<grid, 128, 0, st>>>(D32.p, DRf.p, s0, ns, nn, w, slJ, nbPtr.p,
+                                                           nbCol.p, partJ.p);
           else
-            k_contract_states<double><<<grid, 128, 0, st>>>(D64.p, DR.p, s0, ns, nn, w, slJ, partJ.p);
+            k_contract_states<double><<<grid, 128, 0, st>>>(D64.p, DR.p, s0, ns, nn, w, slJ, nbPtr.p,
+                                                            nbCol.p, partJ.p);
           RIS_CHECK_LAUNCH();
           const long long rows = (long long)ns * 3 * nn;
           k_sum_slices_cols<<<(unsigned)cdiv(rows * w, 256), 256, 0, st>>>(
@@ -3281,10 +3350,11 @@ void Engine::pair_derivs_streamed(int npair, const int* pairs, int nsu, const st
         }
         const dim3 gridK(cdiv((long long)nn * wK, 128), slK);
         if (mixed)
-          k_contract_exchange<float, float><<<gridK, 128, 0, st>>>(D32.p, Gam32.p, nb, nn, w, wK, slK, partK.p);
+          k_contract_exchange<float, float><<<gridK, 128, 0, st>>>(D32.p, Gam32.p, nb, nn, w, wK, slK,
+                                                                   nbPtr.p, nbCol.p, partK.p);
         else
           k_contract_exchange<double, double><<<gridK, 128, 0, st>>>(D64.p, Gam64.p, nb, nn, w, wK, slK,
-                                                                     partK.p);
+                                                                     nbPtr.p, nbCol.p, partK.p);
         RIS_CHECK_LAUNCH();
         const long long rows = (long long)nb * 3 * nn;
         k_sum_slices_cols<<<(unsigned)cdiv(rows * wK, 256), 256, 0, st>>>(partK.p, slK, rows, wK, WK.p, nK, u0);

@@ -144,6 +144,11 @@ struct Engine : StreamOwner {
   DBuf omega, X, Y;
   std::vector<double> h_omega;
 
+  // screened partners of each AO function (CSR over the screened shell-pair
+  // list), the nu range of the derivative contractions
+  SBuf<int> nbPtr, nbCol;
+  int nbAvg = 1;
+  std::vector<int> h_pa, h_pb;  // the screened shell pairs on the host
   // streamed form (large systems): three-centre integrals on the screened
   // function pairs only, mixed with the metric factors there; auxiliary
   // blocks for the MO transforms and the derivative integrals
