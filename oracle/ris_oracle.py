@@ -550,10 +550,14 @@ class RisOracle:
                           + self._coul(RI, RJ, self.ovJ, d_ovJ, self.MJinv)
                           + self._coul(RI, RJ, self.ovJ, self.ovJ, dMJinv))
                     xk = 0.0
-                    for (U, V) in ((RI, RJ), (LI, LJ)):
+                    # TDA (Y = 0): L = R, so the (L, L) term equals the (R, R) one
+                    combos = ((RI, RJ), (LI, LJ)) if rpa else ((RI, RJ),)
+                    for (U, V) in combos:
                         xk += (self._xk(U, V, d_ooK, self.vvK, self.MKinv)
                                + self._xk(U, V, self.ooK, d_vvK, self.MKinv)
                                + self._xk(U, V, self.ooK, self.vvK, dMKinv))
+                    if not rpa:
+                        xk = 2.0 * xk
                     bk = 0.0
                     if rpa:
                         for (U, V, s) in ((RI, RJ, 1.0), (LI, LJ, -1.0)):

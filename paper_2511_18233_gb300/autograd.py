@@ -41,6 +41,7 @@ class RisModel:
         self.ctx = ris.Context(rpa=int(rpa), precision=precision, device=device, **opts)
         self.geometry = None      # coordinates the context's integrals belong to
         self.recomputed = 0       # backward passes that rebuilt the integrals
+        self.last = None          # (omega, X[, Y]) of the last solve
 
     def _coords(self, coords: torch.Tensor) -> torch.Tensor:
         c = coords.detach().to(torch.float64)
@@ -56,7 +57,8 @@ class RisModel:
 
     def solve(self, coords):
         self._build(self._coords(coords))
-        return self.ctx.excite(self.nstates)
+        self.last = self.ctx.excite(self.nstates)
+        return self.last
 
     def holds(self, c: torch.Tensor) -> bool:
         g = self.geometry

@@ -1859,6 +1859,22 @@ void CoulPrecond::setup(Engine& e, bool shifted, double f_, int nmax) {
   cholesky(cap.p, nJ, info.p, st);
   tri_inverse(cap.p, Li.p, nJ, st);
   dgemm(true, false, nJ, nJ, nJ, 1.0, Li.p, nJ, Li.p, nJ, 0.0, capinv.p, nJ, st);
+  // mixed precision: 3xTF32 applications when the splits of B^J stay small
+  // (a preconditioner only changes the number of iterations)
+  this->tc = tc && (double)n * (ld4(nJ) + nJ) * 8.0 < 4.0e9;
+  if (this->tc) {
+    const int ln = ld4((int)n), lj = ld4(nJ);
+    Bh.ensure((size_t)n * lj, st);
+    Bl.ensure((size_t)n * lj, st);
+    BTh.ensure((size_t)nJ * ln, st);
+    BTl.ensure((size_t)nJ * ln, st);
+    Th.ensure((size_t)nmax * ln, st);
+    Tl.ensure((size_t)nmax * ln, st);
+    Zh.ensure((size_t)nmax * lj, st);
+    Zl.ensure((size_t)nmax * lj, st);
+    split_f64(e.BJ.p, (int)n, nJ, nJ, Bh.p, Bl.p, lj, st);
+    split_f64_t(e.BJ.p, (int)n, nJ, nJ, BTh.p, BTl.p, ln, st);
+  }
   int h_info = 0;
   RIS_CUDA(cudaMemcpyAsync(&h_info, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   RIS_CUDA(cudaStreamSynchronize(st));
@@ -1871,9 +1887,18 @@ void CoulPrecond::apply(Engine& e, const double* R, const int* idx, int nt, doub
   cudaStream_t st = e.st;
   k_precond_scale<<<cdiv(n * nt, 256), 256, 0, st>>>(R, dinv.p, idx, n, nt, T);
   RIS_CHECK_LAUNCH();
-  dgemm(false, false, nt, nJ, (int)n, 1.0, T, (int)n, e.BJ.p, nJ, 0.0, pY.p, nJ, st);
-  dgemm(false, false, nt, nJ, nJ, 1.0, pY.p, nJ, capinv.p, nJ, 0.0, pZ.p, nJ, st);
-  dgemm(false, true, nt, (int)n, nJ, 1.0, pZ.p, nJ, e.BJ.p, nJ, 0.0, pP.p, (int)n, st);
+  if (tc) {  // the two long products on the 3xTF32 tensor cores
+    const int ln = ld4((int)n), lj = ld4(nJ);
+    split_f64(T, nt, (int)n, n, Th.p, Tl.p, ln, st);
+    tcg(nt, nJ, (int)n, Th.p, Tl.p, ln, BTh.p, BTl.p, ln, 0, 1, ep_f64(pY.p, nJ), e.d_tcerr, st);
+    dgemm(false, false, nt, nJ, nJ, 1.0, pY.p, nJ, capinv.p, nJ, 0.0, pZ.p, nJ, st);
+    split_f64(pZ.p, nt, nJ, nJ, Zh.p, Zl.p, lj, st);
+    tcg(nt, (int)n, nJ, Zh.p, Zl.p, lj, Bh.p, Bl.p, lj, 0, 1, ep_f64(pP.p, n), e.d_tcerr, st);
+  } else {
+    dgemm(false, false, nt, nJ, (int)n, 1.0, T, (int)n, e.BJ.p, nJ, 0.0, pY.p, nJ, st);
+    dgemm(false, false, nt, nJ, nJ, 1.0, pY.p, nJ, capinv.p, nJ, 0.0, pZ.p, nJ, st);
+    dgemm(false, true, nt, (int)n, nJ, 1.0, pZ.p, nJ, e.BJ.p, nJ, 0.0, pP.p, (int)n, st);
+  }
   k_precond_update<<<cdiv(n * nt, 256), 256, 0, st>>>(T, pP.p, dinv.p, n, nt, f);
   RIS_CHECK_LAUNCH();
 }

@@ -80,6 +80,10 @@ struct Engine;
 // Coulomb-exact preconditioner (definition and formula in engine.cu).
 struct CoulPrecond {
   SBuf<double> dinv, capinv, pY, pZ, pP;
+  // mixed precision (when small): hi/lo splits of B^J as [ia][P] and
+  // [P][ia] and of the work vectors, for 3xTF32 applications
+  SBuf<float> Bh, Bl, BTh, BTl, Th, Tl, Zh, Zl;
+  bool tc = false;
   double f = 2.0;
   void setup(Engine& e, bool shifted, double f, int nmax);
   // T[j] = M^-1 R[idx ? idx[j] : j], j < nt <= nmax

@@ -114,14 +114,16 @@ def test_autograd_flake_rpa(torch_mod, oracle):
     assert mol.nao == 1134 and mol.nocc == 171
     NS = 20
     orc = oracle.RisOracle(mol.coords, mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc)
-    om_ref, Xo, Yo, _ = orc.rpa_davidson(NS, tol=1e-7)
+    # residual 1e-6: eigenvalue error ~ r^2, far below the 1e-9 bound; the
+    # amplitudes are passed to both sides below, so their accuracy is moot
+    om_ref, Xo, Yo, _ = orc.rpa_davidson(NS, tol=1e-6)
     model = RisModel(mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc, NS, rpa=True,
                      precision=ris.FP64)
     R = torch.tensor(mol.coords, dtype=torch.float64, device="cuda", requires_grad=True)
     w = model.energy(R, 0)
+    om, Xg, Yg = model.last  # the forward's 20 states
     w.backward()
     g = R.grad.cpu().numpy()
-    om, Xg, Yg = model.solve(R)
     rel_om = float(np.max(np.abs(om - om_ref)) / np.max(np.abs(om_ref)))
     # derivative kernels at the oracle's amplitudes
     atoms = [0, 30, 60]
@@ -135,11 +137,15 @@ def test_autograd_flake_rpa(torch_mod, oracle):
     err_o = float(np.max(np.abs(g_o[atoms] - ref)))
     # the backward is the library gradient at the forward's own amplitudes
     g_lib = model.ctx.gradient([0], X=np.ascontiguousarray(Xg[:1]), Y=np.ascontiguousarray(Yg[:1]))[0]
+    # finite differences of the re-solved S1 energy; the three lowest states
+    # are enough for it (a Davidson block of 6 instead of 28)
+    low = RisModel(mol.shells, mol.aux_j, mol.aux_k, mol.C, mol.mo_energy, mol.nocc, 3, rpa=True,
+                   precision=ris.FP64)
     fd_rows = []
     for (A, x) in [(0, 0), (60, 1)]:
-        fd2 = _fd(model, mol.coords, 0, A, x, 1e-3, 2)
-        fd5 = _fd(model, mol.coords, 0, A, x, 1e-3, 5)
-        fd5h = _fd(model, mol.coords, 0, A, x, 5e-4, 5)
+        fd2 = _fd(low, mol.coords, 0, A, x, 1e-3, 2)
+        fd5 = _fd(low, mol.coords, 0, A, x, 1e-3, 5)
+        fd5h = _fd(low, mol.coords, 0, A, x, 5e-4, 5)
         fd_rows.append((A, x, g[A, x], fd2, fd5, fd5h))
     print(f"\nflake: omega rel {rel_om:.2e}; S1-S2 gap {om[1] - om[0]:.2e}; kernels vs oracle "
           f"{err_o:.2e} (floor {floor:.2e}, max|g| {scale:.2e}); FD " +

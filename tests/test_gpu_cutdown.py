@@ -72,11 +72,15 @@ def test_cutdown_streamed_fp64_parity(ris_mod, ref):
     mol, w, X, g_ref, num_ref = ref
     om, Xg, g, num = _run(ris_mod, mol, stream=1, stream_block=48)
     np.testing.assert_allclose(om, w, rtol=1e-9)
+    # relative error of a result array (G14): max|diff| over the sampled
+    # atoms against the array's largest element (the library's full array;
+    # the oracle sampled two atoms only)
     sel = g[[0, NS - 1]][:, ATOMS]
     gr = g_ref[:, ATOMS]
-    assert np.max(np.abs(sel - gr)) <= 1e-9 * np.max(np.abs(gr))
+    assert np.max(np.abs(sel - gr)) <= 1e-9 * max(np.max(np.abs(gr)), np.max(np.abs(g[[0, NS - 1]])))
     nr = num_ref[0, ATOMS]
-    assert np.max(np.abs(num[PAIR[0], ATOMS] - nr)) <= 1e-9 * np.max(np.abs(nr))
+    assert np.max(np.abs(num[PAIR[0], ATOMS] - nr)) <= 1e-9 * max(np.max(np.abs(nr)),
+                                                                  np.max(np.abs(num[PAIR[0]])))
     assert np.max(np.abs(g.sum(axis=1))) <= 1e-10 * np.max(np.abs(g))
 
 
