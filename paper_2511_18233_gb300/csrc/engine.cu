@@ -1829,25 +1829,25 @@ void CoulPrecond::setup(Engine& e, bool shifted, double f_, int nmax) {
   // mixed precision: the capacitance matrix only steers the preconditioner
   // (never the converged pairs), so its long-K product runs as a 3xTF32
   // tensor-core GEMM on transposed row blocks
-  const bool tc = e.opt.precision == RIS_MIXED && e.d_tcerr;
+  const bool use_tc = e.opt.precision == RIS_MIXED && e.d_tcerr;
   const int ldr = ld4((int)std::min(rblk, n));
-  SBuf<float> BTh, BTl, WTh, WTl;
-  if (tc) {
-    BTh.ensure((size_t)nJ * ldr, st);
-    BTl.ensure((size_t)nJ * ldr, st);
-    WTh.ensure((size_t)nJ * ldr, st);
-    WTl.ensure((size_t)nJ * ldr, st);
+  SBuf<float> capBh, capBl, capWh, capWl;  // transposed splits of one row block
+  if (use_tc) {
+    capBh.ensure((size_t)nJ * ldr, st);
+    capBl.ensure((size_t)nJ * ldr, st);
+    capWh.ensure((size_t)nJ * ldr, st);
+    capWl.ensure((size_t)nJ * ldr, st);
   }
   for (long long r0 = 0; r0 < n; r0 += rblk) {
     const long long nr = std::min(rblk, n - r0);
     k_precond_setup<<<cdiv(nr * nJ, 256), 256, 0, st>>>(e.de.p, dm.p, r0, nr, shifted ? kPrecondGap : 0.0,
                                                          e.BJ.p, nJ, dinv.p, W.p);
     RIS_CHECK_LAUNCH();
-    if (tc) {
+    if (use_tc) {
       const int lr = ld4((int)nr);
-      split_f64_t(e.BJ.p + (size_t)r0 * nJ, (int)nr, nJ, nJ, BTh.p, BTl.p, lr, st);  // [P][row]
-      split_f64_t(W.p, (int)nr, nJ, nJ, WTh.p, WTl.p, lr, st);
-      tcg(nJ, nJ, (int)nr, BTh.p, BTl.p, lr, WTh.p, WTl.p, lr, 0, 1,
+      split_f64_t(e.BJ.p + (size_t)r0 * nJ, (int)nr, nJ, nJ, capBh.p, capBl.p, lr, st);  // [P][row]
+      split_f64_t(W.p, (int)nr, nJ, nJ, capWh.p, capWl.p, lr, st);
+      tcg(nJ, nJ, (int)nr, capBh.p, capBl.p, lr, capWh.p, capWl.p, lr, 0, 1,
           ep_f64(cap.p, nJ, 0, f, r0 == 0 ? 0.0 : 1.0), e.d_tcerr, st);
     } else {
       dgemm(true, false, nJ, nJ, (int)nr, f, e.BJ.p + (size_t)r0 * nJ, nJ, W.p, nJ, r0 == 0 ? 0.0 : 1.0,
@@ -1861,8 +1861,8 @@ void CoulPrecond::setup(Engine& e, bool shifted, double f_, int nmax) {
   dgemm(true, false, nJ, nJ, nJ, 1.0, Li.p, nJ, Li.p, nJ, 0.0, capinv.p, nJ, st);
   // mixed precision: 3xTF32 applications when the splits of B^J stay small
   // (a preconditioner only changes the number of iterations)
-  this->tc = tc && (double)n * (ld4(nJ) + nJ) * 8.0 < 4.0e9;
-  if (this->tc) {
+  tc = use_tc && (double)n * (ld4(nJ) + nJ) * 8.0 < 4.0e9;
+  if (tc) {
     const int ln = ld4((int)n), lj = ld4(nJ);
     Bh.ensure((size_t)n * lj, st);
     Bl.ensure((size_t)n * lj, st);
@@ -1888,6 +1888,8 @@ void CoulPrecond::apply(Engine& e, const double* R, const int* idx, int nt, doub
   k_precond_scale<<<cdiv(n * nt, 256), 256, 0, st>>>(R, dinv.p, idx, n, nt, T);
   RIS_CHECK_LAUNCH();
   if (tc) {  // the two long products on the 3xTF32 tensor cores
+    RIS_REQUIRE(Bh.p && BTh.p && Th.p && Zh.p && nt <= (int)(Zh.n / ld4(nJ)), RIS_ERR_ARG,
+                "preconditioner splits missing");
     const int ln = ld4((int)n), lj = ld4(nJ);
     split_f64(T, nt, (int)n, n, Th.p, Tl.p, ln, st);
     tcg(nt, nJ, (int)n, Th.p, Tl.p, ln, BTh.p, BTl.p, ln, 0, 1, ep_f64(pY.p, nJ), e.d_tcerr, st);

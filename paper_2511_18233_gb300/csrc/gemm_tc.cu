@@ -37,6 +37,7 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 
 // 3-D map {K, rows, batch} of FP32, box {32, 128, 1}, 128-byte swizzle.
 CUtensorMap make_map(const float* base, int K, int rows, int ld, long long bstride, int nb) {
+  RIS_REQUIRE(base != nullptr, RIS_ERR_ARG, "tc_gemm: null operand");
   RIS_REQUIRE(((uintptr_t)base & 15) == 0, RIS_ERR_ARG, "tc_gemm: operand not 16-byte aligned");
   RIS_REQUIRE(ld % 4 == 0 && (nb == 1 || bstride % 4 == 0), RIS_ERR_ARG,
               "tc_gemm: leading dimension / batch stride not a multiple of 16 bytes");
