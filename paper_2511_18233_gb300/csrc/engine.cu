@@ -733,24 +733,28 @@ __global__ void __launch_bounds__(128) k_contract_states(const T* __restrict__ D
 #pragma unroll
     for (int x = 0; x < 3; x++) y[b][x] = 0.0, c[b][x] = (T)0;
   const T* dr = DRs + (size_t)s0 * nn2 + (size_t)mu * nao;
-  for (int q = q0; q < q1; q++) {
-    const int nu = nbCol[q];
-    const size_t a = ((size_t)mu * nao + nu) * nU + P;
-    const T d0 = D[a], d1 = D[plane + a], d2 = D[2 * plane + a];
+  // runs of kChunk partners: products summed in T, runs in FP64; the inner
+  // loop is unrolled so that several partners' loads are in flight
+  for (int qc = q0; qc < q1; qc += kChunk) {
+    const int qe = min(qc + kChunk, q1);
+#pragma unroll 4
+    for (int q = qc; q < qe; q++) {
+      const int nu = nbCol[q];
+      const size_t a = ((size_t)mu * nao + nu) * nU + P;
+      const T d0 = D[a], d1 = D[plane + a], d2 = D[2 * plane + a];
 #pragma unroll
-    for (int b = 0; b < kCBatch; b++) {
-      if (b >= ns) break;
-      const T w = dr[(size_t)b * nn2 + nu];
-      c[b][0] += d0 * w;
-      c[b][1] += d1 * w;
-      c[b][2] += d2 * w;
+      for (int b = 0; b < kCBatch; b++) {
+        if (b >= ns) break;
+        const T w = dr[(size_t)b * nn2 + nu];
+        c[b][0] += d0 * w;
+        c[b][1] += d1 * w;
+        c[b][2] += d2 * w;
+      }
     }
-    if (((q - q0) % kChunk) == kChunk - 1 || q == q1 - 1) {
 #pragma unroll
-      for (int b = 0; b < kCBatch; b++)
+    for (int b = 0; b < kCBatch; b++)
 #pragma unroll
-        for (int x = 0; x < 3; x++) y[b][x] += (double)c[b][x], c[b][x] = (T)0;
-    }
+      for (int x = 0; x < 3; x++) y[b][x] += (double)c[b][x], c[b][x] = (T)0;
   }
   double* ps = part + (size_t)blockIdx.y * ns * 3 * nao * nU;
 #pragma unroll
@@ -787,26 +791,28 @@ __global__ void __launch_bounds__(128) k_contract_exchange(const T* __restrict__
   for (int b = 0; b < kCBatch; b++)
 #pragma unroll
     for (int x = 0; x < 3; x++) s[b][x] = 0.0, c[b][x] = (T)0;
-  for (int q = q0; q < q1; q++) {
-    const int nu = nbCol[q];
-    const size_t mn = (size_t)mu * nao + nu;
-    const size_t a = mn * nU + P;
-    const T d0 = D[a], d1 = D[plane + a], d2 = D[2 * plane + a];
-    const size_t k1 = mn * nK + P, k2 = ((size_t)nu * nao + mu) * nK + P;
+  for (int qc = q0; qc < q1; qc += kChunk) {
+    const int qe = min(qc + kChunk, q1);
+#pragma unroll 2
+    for (int q = qc; q < qe; q++) {
+      const int nu = nbCol[q];
+      const size_t mn = (size_t)mu * nao + nu;
+      const size_t a = mn * nU + P;
+      const T d0 = D[a], d1 = D[plane + a], d2 = D[2 * plane + a];
+      const size_t k1 = mn * nK + P, k2 = ((size_t)nu * nao + mu) * nK + P;
 #pragma unroll
-    for (int b = 0; b < kCBatch; b++) {
-      if (b >= nb) break;
-      const T g = (T)0.5 * ((T)GK[b * gk + k1] + (T)GK[b * gk + k2]);
-      c[b][0] += d0 * g;
-      c[b][1] += d1 * g;
-      c[b][2] += d2 * g;
+      for (int b = 0; b < kCBatch; b++) {
+        if (b >= nb) break;
+        const T g = (T)0.5 * ((T)GK[b * gk + k1] + (T)GK[b * gk + k2]);
+        c[b][0] += d0 * g;
+        c[b][1] += d1 * g;
+        c[b][2] += d2 * g;
+      }
     }
-    if (((q - q0) % kChunk) == kChunk - 1 || q == q1 - 1) {
 #pragma unroll
-      for (int b = 0; b < kCBatch; b++)
+    for (int b = 0; b < kCBatch; b++)
 #pragma unroll
-        for (int x = 0; x < 3; x++) s[b][x] += (double)c[b][x], c[b][x] = (T)0;
-    }
+      for (int x = 0; x < 3; x++) s[b][x] += (double)c[b][x], c[b][x] = (T)0;
   }
   double* ps = part + (size_t)blockIdx.y * nb * 3 * nao * nK;
 #pragma unroll
