@@ -1039,6 +1039,39 @@ __global__ void k_rpa_combine(const double* __restrict__ de, const double* __res
 }
 
 // ------------------------------------------------------------------ setup
+// nbPtr / nbCol: the screened partners nu of every AO function mu (both
+// orders of each screened shell pair), by counting then filling; the order
+// within a row is that of the pair list (deterministic).
+void Engine::partners_from_host_pairs() {
+  const int nf = ao.nfun;
+  std::vector<int> ptr(nf + 1, 0);
+  for (int ip = 0; ip < pl.npair; ip++) {
+    const int sa = h_pa[ip], sb = h_pb[ip];
+    const int na = ncart(ao.h_l[sa]), nb = ncart(ao.h_l[sb]);
+    for (int ia = 0; ia < na; ia++) ptr[ao.h_off[sa] + ia + 1] += nb;
+    if (sa != sb)
+      for (int ib = 0; ib < nb; ib++) ptr[ao.h_off[sb] + ib + 1] += na;
+  }
+  for (int mu = 0; mu < nf; mu++) ptr[mu + 1] += ptr[mu];
+  std::vector<int> col(std::max(ptr[nf], 1)), fill(ptr.begin(), ptr.end() - 1);
+  for (int ip = 0; ip < pl.npair; ip++) {
+    const int sa = h_pa[ip], sb = h_pb[ip];
+    const int na = ncart(ao.h_l[sa]), nb = ncart(ao.h_l[sb]);
+    for (int ia = 0; ia < na; ia++)
+      for (int ib = 0; ib < nb; ib++) {
+        const int mu = ao.h_off[sa] + ia, nu = ao.h_off[sb] + ib;
+        col[fill[mu]++] = nu;
+        if (sa != sb) col[fill[nu]++] = mu;
+      }
+  }
+  nbAvg = std::max(1, ptr[nf] / std::max(nf, 1));
+  nbPtr.ensure(nf + 1, st);
+  nbCol.ensure(col.size(), st);
+  // pageable host-to-device copies are staged before the call returns
+  RIS_CUDA(cudaMemcpyAsync(nbPtr.p, ptr.data(), sizeof(int) * (nf + 1), cudaMemcpyHostToDevice, st));
+  RIS_CUDA(cudaMemcpyAsync(nbCol.p, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, st));
+}
+
 void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_shell* aos, int nJs,
                        const ris_shell* auxJ, int nKs, const ris_shell* auxK) {
   RIS_REQUIRE(natm_ > 0 && nshell > 0 && nJs > 0 && nKs > 0, RIS_ERR_ARG, "empty input");
@@ -1135,8 +1168,8 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
       ptr.ensure(natm + 1, st);
       list.ensure(std::max<size_t>(lst.size(), 1), st);
       RIS_CUDA(cudaMemcpyAsync(ptr.p, cnt.data(), sizeof(int) * (natm + 1), cudaMemcpyHostToDevice, st));
+      // pageable host-to-device copies are staged before the call returns
       RIS_CUDA(cudaMemcpyAsync(list.p, lst.data(), sizeof(int) * lst.size(), cudaMemcpyHostToDevice, st));
-      RIS_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
     };
     csr(ao, aoPtr, aoList);
     csr(aux, axPtr, axList);
@@ -1177,39 +1210,24 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
     vmax = std::max(vmax, nb * 2.0 * M_PI / g * (aux.h_l[s] ? 1.0 / sqrt(g) : 1.0));
   }
   build_pairs(ao, xyz.p, opt.screen_thr / std::max(vmax, 1e-300), pl, nullptr, st);
-  // the screened pairs on the host, and each AO function's screened partners
-  {
-    h_pa.assign(std::max(pl.npair, 1), 0);
-    h_pb.assign(std::max(pl.npair, 1), 0);
-    if (pl.npair > 0) {
-      RIS_CUDA(cudaMemcpyAsync(h_pa.data(), pl.a, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st));
-      RIS_CUDA(cudaMemcpyAsync(h_pb.data(), pl.b, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st));
-      RIS_CUDA(cudaStreamSynchronize(st));
-    }
-    const int nf = ao.nfun;
-    std::vector<std::vector<int>> nb(nf);
-    for (int ip = 0; ip < pl.npair; ip++) {
-      const int sa = h_pa[ip], sb = h_pb[ip];
-      for (int ia = 0; ia < ncart(ao.h_l[sa]); ia++)
-        for (int ib = 0; ib < ncart(ao.h_l[sb]); ib++) {
-          const int mu = ao.h_off[sa] + ia, nu = ao.h_off[sb] + ib;
-          nb[mu].push_back(nu);
-          if (sa != sb) nb[nu].push_back(mu);
-        }
-    }
-    std::vector<int> ptr(nf + 1, 0), col;
-    for (int mu = 0; mu < nf; mu++) {
-      std::sort(nb[mu].begin(), nb[mu].end());
-      ptr[mu + 1] = ptr[mu] + (int)nb[mu].size();
-      col.insert(col.end(), nb[mu].begin(), nb[mu].end());
-    }
-    nbAvg = std::max(1, ptr[nf] / std::max(nf, 1));
-    nbPtr.ensure(nf + 1, st);
-    nbCol.ensure(std::max<size_t>(col.size(), 1), st);
-    RIS_CUDA(cudaMemcpyAsync(nbPtr.p, ptr.data(), sizeof(int) * (nf + 1), cudaMemcpyHostToDevice, st));
-    if (!col.empty())
-      RIS_CUDA(cudaMemcpyAsync(nbCol.p, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, st));
-    RIS_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  // the screened pairs go to pinned host memory on a copy stream, so that
+  // each AO function's partner list is built on the host while the
+  // integrals and the metric factors run on the device
+  if (!st3) {
+    RIS_CUDA(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
+    RIS_CUDA(cudaEventCreateWithFlags(&evP, cudaEventDisableTiming));
+  }
+  if (pin_n < 2 * (size_t)std::max(pl.npair, 1)) {
+    if (pin) RIS_CUDA(cudaFreeHost(pin));
+    pin = nullptr;
+    pin_n = 2 * (size_t)std::max(pl.npair, 1);
+    RIS_ALLOC(cudaMallocHost((void**)&pin, sizeof(int) * pin_n));
+  }
+  RIS_CUDA(cudaEventRecord(evP, st));
+  RIS_CUDA(cudaStreamWaitEvent(st3, evP, 0));
+  if (pl.npair > 0) {
+    RIS_CUDA(cudaMemcpyAsync(pin, pl.a, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st3));
+    RIS_CUDA(cudaMemcpyAsync(pin + pl.npair, pl.b, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st3));
   }
   // integrals: dense [mu][nu][P], or (streamed form) on the screened pairs
   // only, after the metric factors are known
@@ -1243,6 +1261,10 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
     cholesky(w1.p, n, d_info + set, st);
     tri_inverse(w1.p, set == 0 ? LJinv.p : LKinv.p, n, st);
   }
+  RIS_CUDA(cudaStreamSynchronize(st3));
+  h_pa.assign(pin, pin + pl.npair);
+  h_pb.assign(pin + pl.npair, pin + 2 * (size_t)pl.npair);
+  partners_from_host_pairs();
   int info[2];
   RIS_CUDA(cudaMemcpyAsync(info, d_info, sizeof(info), cudaMemcpyDeviceToHost, st));
   RIS_CUDA(cudaStreamSynchronize(st));

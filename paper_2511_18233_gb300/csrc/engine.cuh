@@ -69,7 +69,15 @@ struct StreamOwner {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   cudaStream_t st2 = nullptr;  // low-priority side stream (derivative integrals)
+  cudaStream_t st3 = nullptr;  // copy stream (the pair list to the host)
+  cudaEvent_t evP = nullptr;   // the pair list is built
+  int* pin = nullptr;          // pinned host copy of the pair list
+  size_t pin_n = 0;
   ~StreamOwner() {
+    if (st3) cudaStreamSynchronize(st3);
+    if (pin) cudaFreeHost(pin);
+    if (evP) cudaEventDestroy(evP);
+    if (st3) cudaStreamDestroy(st3);
     if (st2) cudaStreamDestroy(st2);
     if (own_stream && st) cudaStreamDestroy(st);
   }
@@ -153,6 +161,7 @@ struct Engine : StreamOwner {
   SBuf<int> nbPtr, nbCol;
   int nbAvg = 1;
   std::vector<int> h_pa, h_pb;  // the screened shell pairs on the host
+  void partners_from_host_pairs();  // nbPtr / nbCol from h_pa / h_pb
   // streamed form (large systems): three-centre integrals on the screened
   // function pairs only, mixed with the metric factors there; auxiliary
   // blocks for the MO transforms and the derivative integrals

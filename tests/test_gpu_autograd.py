@@ -24,10 +24,15 @@ def _rel(a, b):
 
 
 def _fd(model, coords, state, A, x, h, points=2):
-    def e(d):
-        c = coords.copy()
-        c[A, x] += d
-        return float(model.solve(__import__("torch").as_tensor(c))[0][state])
+    cache = model.__dict__.setdefault("_fd_cache", {})
+
+    def e(d):  # energies of displaced geometries, each solved once per model
+        key = (state, A, x, round(d / 2.5e-4))
+        if key not in cache:
+            c = coords.copy()
+            c[A, x] += d
+            cache[key] = float(model.solve(__import__("torch").as_tensor(c))[0][state])
+        return cache[key]
     if points == 2:
         return (e(h) - e(-h)) / (2 * h)
     return (e(-2 * h) - 8 * e(-h) + 8 * e(h) - e(2 * h)) / (12 * h)
