@@ -98,10 +98,21 @@ def peaks():
     return out
 
 
-# DRAM traffic per launch of the dominant kernels, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid while the source file
-# it was taken on is unchanged (sha256 prefix).
-TRAFFIC = {}
+# DRAM traffic of each GEMM class per C20H22 mixed evaluation: the sum of
+# dram__bytes_read.sum + dram__bytes_write.sum over the class's launches of
+# one evaluation, from one ncu capture of `bench.py --no-extra
+# --no-cpu-baseline --precision mixed --steps 1 --warmup 1` (five
+# evaluations, divided by five; ncu runs each launch with a cold L2).  Valid
+# while the kernel's source file is unchanged (sha256 prefix); the summary is
+# in profiles/launches_mixed_c20h22.md.
+TRAFFIC = {
+    "dgemm_fp64": {"bytes_per_eval": 1.3512e9, "source": "paper_2511_18233_gb300/csrc/la.cu",
+                   "sha": "ac327dac6413d7d1"},
+    "tc_gemm_3xtf32": {"bytes_per_eval": 4.7681e9, "source": "paper_2511_18233_gb300/csrc/gemm_tc.cu",
+                       "sha": "43c01fd7f312ef94"},
+    "emu_gemm_f64": {"bytes_per_eval": 0.9360e9, "source": "paper_2511_18233_gb300/csrc/gemm_emu.cu",
+                     "sha": "6eca5b2a53ba7b71"},
+}
 
 
 def _src_sha(rel):
@@ -116,7 +127,7 @@ def traffic_for(cls):
     t = TRAFFIC.get(cls)
     if not t or _src_sha(t["source"]) != t["sha"]:
         return None
-    return t["bytes_per_launch"]
+    return t["bytes_per_eval"]
 
 
 class Clocks:
@@ -451,7 +462,7 @@ def algorithmic_work(precision, d, nprod, npair, rpa=False):
             "emu_gemm_f64": b_coul}
 
 
-def classify(st, steps, step_ms_total, precision, dims, nprod, npair):
+def classify(st, steps, step_ms_total, precision, dims, nprod, npair, workload="c20h22"):
     """Per kernel class: time share, executed and algorithmic work against
     the pipe's measured peak."""
     pk = peaks()
@@ -492,7 +503,9 @@ def classify(st, steps, step_ms_total, precision, dims, nprod, npair):
     for key in ("achieved", "peak", "unit", "frac", "peak_source", "executed_frac"):
         if key in table[dom]:
             roof[key] = table[dom][key]
-    roof["traffic"] = traffic_for(dom)
+    roof["traffic"] = traffic_for(dom) if workload == "c20h22" and precision == "mixed" else None
+    if roof["traffic"] is not None:
+        roof["traffic_unit"] = "bytes per evaluation (all launches of the class, ncu, cold L2)"
     return roof, table
 
 
@@ -673,7 +686,8 @@ def measure_packed(args):
     st = ctx.stats()
     dm = ctx.dims()
     dims = {"nao": dm["nao"], "nocc": mol.nocc, "nvir": mol.nvir, "nJ": dm["nauxJ"], "nK": dm["nauxK"]}
-    roof, table = classify(st, len(ts), sum(ts), "mixed", dims, int(st["n_products"]), ns + len(pairs))
+    roof, table = classify(st, len(ts), sum(ts), "mixed", dims, int(st["n_products"]), ns + len(pairs),
+                           workload="packed")
     ga = g.cpu().numpy()
     ctx.close()
     ms = float(np.mean(ts))
