@@ -26,7 +26,8 @@ between adjacent states.  Metric: evaluations per second.
   C54H18 flake RPA-ris with the autograd state-1 gradient; the packed
   12 x C20H22 workload in the streamed mixed form).
 * serving: the surface-hopping stream (64 trajectories, 2000 requests after
-  200, Poisson 200/s, warm Davidson) against plain FP64 replay.
+  200, Poisson 200/s, Davidson seeded with the trajectory's resident
+  amplitudes) against a shorter cold-Davidson stream and plain FP64 replay.
 * cpu_baseline / --impl reference: the FP64 oracle on the host cores: the
   C20H22 sample (setup, Davidson, derivatives of two pair energies w.r.t.
   one atom, extrapolated to the full evaluation) and the C4H6 evaluation in
@@ -306,14 +307,20 @@ def run_serving(args, quick=False):
     budget = int(0.8 * free)
     warm = not args.serve_cold
     out = {}
-    for mode in ("mixed", "fp64_plain"):
-        mixed = mode == "mixed"
-        nreq = args.serve_requests if mixed else args.serve_fp64_requests
-        nwarm = args.serve_warmup if mixed else max(2, args.serve_warmup // 20)
+    modes = ["mixed", "fp64_plain"]
+    if warm and args.serve_cold_requests > 0:
+        modes.insert(1, "mixed_cold")  # the same stream with every Davidson started cold
+    for mode in modes:
+        mixed = mode.startswith("mixed")
+        nreq = {"mixed": args.serve_requests, "mixed_cold": args.serve_cold_requests,
+                "fp64_plain": args.serve_fp64_requests}[mode]
+        nwarm = {"mixed": args.serve_warmup, "mixed_cold": max(2, args.serve_warmup // 5),
+                 "fp64_plain": max(2, args.serve_warmup // 20)}[mode]
+        seeded = warm and mode == "mixed"
         with Clocks(0) as clk:
             res = serve.serve(specs, n_requests=nreq, n_warmup=nwarm, rate=args.serve_rate,
                               nslots=args.serve_slots if mixed else 1, budget_bytes=budget,
-                              precision="mixed" if mixed else "fp64", use_guess=warm and mixed, seed=7,
+                              precision="mixed" if mixed else "fp64", use_guess=seeded, seed=7,
                               **({"eig_fp32": 1} if mixed and args.eig_fp32 else {}))
         done = res.pop("done")
         res.pop("trajectories")
@@ -334,6 +341,9 @@ def run_serving(args, quick=False):
                        "davidson_seed": "previous step" if warm else "cold",
                        "subspace_eig": "fp32" if args.eig_fp32 else "fp64"},
             "mixed": m, "fp64_plain": f}
+    if "mixed_cold" in out:
+        line["mixed_cold"] = out["mixed_cold"]
+        line["warm_over_cold"] = m["throughput_per_s"] / out["mixed_cold"]["throughput_per_s"]
     return line
 
 
@@ -355,6 +365,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-fp64-requests", type=int, default=30)
+    ap.add_argument("--serve-cold-requests", type=int, default=400,
+                    help="requests of the cold-Davidson comparison stream (0: skip)")
     ap.add_argument("--serve-trajectories", type=int, default=64)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-rate", type=float, default=200.0)
