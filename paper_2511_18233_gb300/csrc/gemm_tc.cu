@@ -331,10 +331,30 @@ void split_f64_t(const double* src, int rows, int cols, long long lds, float* hi
   RIS_CHECK_LAUNCH();
 }
 
+// Longest contraction accumulated in one TMEM accumulator.  The tensor
+// core's FP32 accumulation loses precision with every MMA it adds (its
+// error grows about linearly with the number of K steps), so longer
+// contractions with an FP64 output run as chunks of at most this length
+// whose results are summed in FP64 by the epilogue.
+constexpr int kTcKChunk = 16384;
+
 void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb, const TcEpilogue& ep,
              int* d_err, cudaStream_t st, float* ws, size_t ws_floats, bool allow_alloc) {
   if (M <= 0 || N <= 0 || nb <= 0) return;
   RIS_REQUIRE(K > 0, RIS_ERR_ARG, "tc_gemm: K must be positive");
+  if (ep.mode == kOutF64 && K > kTcKChunk) {
+    for (int k0 = 0; k0 < K; k0 += kTcKChunk) {
+      TcOperand a = A, b = B;
+      a.hi += k0;
+      a.lo += k0;
+      b.hi += k0;
+      b.lo += k0;
+      TcEpilogue e = ep;
+      if (k0 > 0) e.beta = 1.0;
+      tc_gemm(M, N, std::min(kTcKChunk, K - k0), a, b, nb, e, d_err, st, ws, ws_floats, allow_alloc);
+    }
+    return;
+  }
   RIS_REQUIRE(A.rows >= M && B.rows >= N, RIS_ERR_ARG, "tc_gemm: operand rows");
   RIS_REQUIRE(nb <= 65535, RIS_ERR_ARG, "tc_gemm: batch too large");
   ensure_smem_attr((const void*)k_tc_gemm, SMEM_BYTES);

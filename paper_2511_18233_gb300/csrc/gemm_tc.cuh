@@ -45,7 +45,9 @@ struct TcEpilogue {
 
 // C[z] (M x N) = A[z] (M x K) . B[z]^T (N x K), batches z < nb.  With
 // kOutF64 and nb == 1 the K range may be split across CTAs (deterministic
-// two-pass reduction).  *d_err (device int) is set non-zero if a pipeline
+// two-pass reduction); with kOutF64 a K longer than 16384 runs as chunks
+// whose results the epilogue sums in FP64 (the tensor core's FP32
+// accumulation error grows with the number of K steps).  *d_err (device int) is set non-zero if a pipeline
 // wait timed out.
 // ws / ws_floats: optional caller-owned FP32 workspace for the split-K
 // partial sums; with allow_alloc false the GEMM never allocates (it splits K
