@@ -28,7 +28,7 @@ def ris_mod():
 
 @gpu
 @pytest.mark.parametrize("M,N,K", [(128, 128, 32), (200, 130, 71), (7, 300, 1000), (1278, 441, 18648),
-                                   (2982, 441, 71), (64, 64, 4)])
+                                   (2982, 441, 71), (64, 64, 4), (96, 160, 131072)])
 def test_tc_gemm_against_fp64(ris_mod, M, N, K):
     rng = np.random.default_rng(M + 7 * N + 13 * K)
     A = rng.standard_normal((M, K))
@@ -37,6 +37,8 @@ def test_tc_gemm_against_fp64(ris_mod, M, N, K):
     ref = A @ B.T
     bound = np.abs(A) @ np.abs(B).T
     tol = 2e-6 if K <= 2048 else 1e-5
+    print(f"\ntc_gemm {M}x{N}x{K}: max err / sum|a||b| {np.max(np.abs(C - ref) / bound):.1e}, "
+          f"/ max|ref| {np.max(np.abs(C - ref)) / np.max(np.abs(ref)):.1e}")
     assert np.max(np.abs(C - ref) / bound) <= tol
     # and far below a single TF32 product's error (2^-11 relative per operand)
 
