@@ -6,7 +6,8 @@ Ha/bohr (absolute, per component), so a coupling itself is within
 1e-5/|omega_J - omega_I| 1/bohr.  The GEMM itself: 3xTF32 with FP32
 accumulation in tensor memory keeps |C - A B^T| <= 2e-6 (|A| |B|^T)
 elementwise up to K ~ 2000 and <= 1e-5 (|A| |B|^T) at K ~ 2e4, where the
-FP32 accumulator's rounding grows with the number of terms.
+FP32 accumulator's rounding grows with the number of terms; beyond K = 16384
+the library runs the product in chunks whose results it sums in FP64.
 """
 import numpy as np
 import pytest
