@@ -90,11 +90,13 @@ def peaks():
         out["fp64_tflops"] = r["fp64_fma"]["tflops"]
         out["tf32_tflops"] = r["tf32_tcgen05"]["tflops"]
         out["f16_tflops"] = r["f16_tcgen05"]["tflops"]
+        out["fp32_tflops"] = r["fp32_fma"]["tflops"]
         out["src"]["pipes"] = "measured (profiles/peaks_probe_gb300.json)"
     except Exception:
         out["fp64_tflops"] = out["bf16_tflops"] * 1.25 / 2250.0
         out["tf32_tflops"] = out["bf16_tflops"] * 1.1 / 2.25
         out["f16_tflops"] = out["bf16_tflops"]
+        out["fp32_tflops"] = out["bf16_tflops"] * 80.0 / 2250.0
         out["src"]["pipes"] = "fallback (bf16 x nominal ratios)"
     return out
 
@@ -456,10 +458,12 @@ def main():
     return 0
 
 
-def algorithmic_work(precision, d, nprod, npair, rpa=False):
+def algorithmic_work(precision, d, nprod, npair, rpa=False, ff=True):
     """The method's own work per evaluation and kernel class (scope-table
     counts, dense, no screening credit): flops for the GEMM classes (a
-    3xTF32 product counts once), bytes are reported by the library."""
+    3xTF32 or double-FP32 product counts once), bytes are reported by the
+    library.  In the mixed form the Coulomb part of A.X runs as double-FP32
+    products (option subspace_ff, on by default)."""
     n, o, v, nJ, nK = d["nao"], d["nocc"], d["nvir"], d["nJ"], d["nK"]
     nov = o * v
     coul_ax = 4.0 * nov * nJ * nprod * (2 if rpa else 1)
@@ -469,7 +473,8 @@ def algorithmic_work(precision, d, nprod, npair, rpa=False):
     gam = (2.0 * o * v * v * nK + 4.0 * n * n * o * nK) * npair
     if precision == "fp64":
         return {"dgemm_fp64": coul_ax + exch_ax + b_coul + b_k + gam}
-    return {"dgemm_fp64": coul_ax + 2.0 * o * o * n * nK,
+    return {"dgemm_fp64": (0.0 if ff else coul_ax) + 2.0 * o * o * n * nK,
+            "ff_gemm_f64x": coul_ax if ff else 0.0,
             "tc_gemm_3xtf32": exch_ax + 2.0 * v * n * n * nK + 2.0 * v * v * n * nK + gam,
             "emu_gemm_f64": b_coul}
 
@@ -481,12 +486,15 @@ def classify(st, steps, step_ms_total, precision, dims, nprod, npair, workload="
     alg = algorithmic_work(precision, dims, nprod, npair)
     tf32x3 = pk["tf32_tflops"] / 3.0           # three TF32 passes per product
     emu = pk["f16_tflops"] / 55.0               # 55 FP16 slice products per FP64 product
+    ffx = pk["fp32_tflops"] / 12.0              # 12 FP32 instructions per double-FP32 multiply-add
     classes = {
         "tc_gemm_3xtf32": (st["tc_gemm_ms"], st["tc_gemm_flops"], "tensor (tf32)", tf32x3,
                            "TF32 tcgen05 probe / 3 passes"),
         "dgemm_fp64": (st["gemm_ms"], st["gemm_flops"], "fp64 fma", pk["fp64_tflops"], "FP64 FMA probe"),
         "emu_gemm_f64": (st["emu_gemm_ms"], st["emu_gemm_flops"], "tensor (f16)", emu,
                          "FP16 tcgen05 probe / 55 slice products (FP64-equivalent)"),
+        "ff_gemm_f64x": (st.get("ff_gemm_ms", 0.0), st.get("ff_gemm_flops", 0.0), "fp32 fma (double-FP32)",
+                         ffx, "FP32 FMA probe / 12 instructions per multiply-add"),
         "contract": (st["contract_ms"], None, "hbm", None, "HBM copy"),
         "subspace_eig": (st["eig_ms"], None, "latency (fp64, one CTA per eigenvalue)", None, ""),
         "int3c": (st["int3c_ms"], None, "fp64 alu", None, "FP64 ALU roofline: profiles/"),

@@ -126,6 +126,11 @@ typedef struct {
                          derivative integrals would take more than a third of the device
                          memory or of mem_budget); 1: always; -1: never */
   int stream_block;   /* streamed form: auxiliary functions per block; 0 = automatic */
+  int subspace_ff;    /* mixed precision: 1 (default) forms the Davidson Ritz vectors X = S V,
+                         A X = S (A V) and the Coulomb part of the A products as double-FP32
+                         products on the FP32 pipe (error per element at most about 3e-11 of
+                         sum |a||b|, see ris_debug_gemm_ff); the orthogonalisation and the
+                         projected matrix V^T A V stay FP64.  0: all FP64 */
 } ris_options;
 
 typedef struct {
@@ -268,7 +273,7 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
                         int* nauxK, int* npairs_screened);
 
 /*
- * Statistics, copied into out[0..n-1] (n <= 32):
+ * Statistics, copied into out[0..n-1] (n <= 34):
  *   [0] aux, [1] B, [2] excite (or Z-vector), [3] gradient/nac: milliseconds
  *       of the last call of each kind (CUDA events on the context's stream);
  *   [4] A-products and [5] Davidson iterations of the last excite (or the
@@ -286,7 +291,8 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
  *   [28] device bytes the context holds now, [29] the most it has held
  *   since it was created or last trimmed (its HBM footprint);
  *   [30] FP64-emulating tensor-core GEMM ms, [31] its algorithmic FP64
- *   flops (profile option, as [16]..[27]).
+ *   flops, [32] double-FP32 GEMM ms, [33] its flops (profile option, as
+ *   [16]..[27]).
  */
 ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n);
 
@@ -360,6 +366,23 @@ int ris_debug_gemm_tf32x3(int M, int N, int K, const double* A, const double* B,
  * RIS_ERR_TIMEOUT if a pipeline wait timed out, or another ris_status.
  */
 int ris_debug_gemm_f64emu(int M, int N, int K, const double* A, const double* B, double* C);
+
+/*
+ * Test hook: C = alpha A op(B) + beta C with the library's double-FP32 GEMM
+ * (the kernel behind the mixed form's subspace products): FP64 operands cut
+ * into pairs of FP32 numbers, products accumulated by the compensated dot
+ * product of Ogita, Rump and Oishi on the FP32 pipe.  Error per element at
+ * most about 3e-11 sum_k |A_ik| |op(B)_kj| plus FP64 rounding of the result;
+ * values of magnitude below 2^-126 count as zero, at or above 2^128 as
+ * infinite.  A: [M][K]; B: [N][K] if transB else [K][N]; C: [M][N] (read
+ * when beta != 0); FP64 DEVICE pointers on the current device.  Shapes:
+ * M <= 32 and either K <= 256 with N >= 128, or K >= 512 with N <= 512;
+ * *kind (if not null) receives 1 (long-K kernel), 2 (short-K kernel) or 0
+ * (shape not handled: RIS_ERR_ARG, nothing launched).  Synchronises the
+ * device; returns 0 or a ris_status.
+ */
+int ris_debug_gemm_ff(int transB, int M, int N, int K, double alpha, const double* A,
+                      const double* B, double beta, double* C, int* kind);
 
 /*
  * Allocation-free 3xTF32 GEMM: C = A . B^T computed exactly like

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libris.so")
-UNITS = ["ints.cu", "la.cu", "gemm_tc.cu", "gemm_emu.cu", "engine.cu", "capi.cu", "probe.cu"]
+UNITS = ["ints.cu", "la.cu", "gemm_tc.cu", "gemm_emu.cu", "gemm_ff.cu", "engine.cu", "capi.cu",
+         "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -18,13 +18,16 @@ std::atomic<long long> g_allocs{0};
 namespace {
 struct Rec {
   int cls;
+  cudaStream_t st;
   cudaEvent_t a, b;
   double work;
 };
-// Profiling is process-wide (one context at a time); the mutex only keeps
-// concurrent contexts from corrupting the record list.
+// Profiling is per context: a context created with the profile option
+// registers the streams it launches on, kernel classes are timed only on
+// registered streams, and a context collects only its own streams' records.
 std::mutex g_prof_mu;
-bool g_prof_on = false;
+std::atomic<int> g_prof_n{0};  // registered streams
+std::vector<cudaStream_t> g_prof_streams;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 cudaEvent_t take_event() {
@@ -37,42 +40,81 @@ cudaEvent_t take_event() {
   RIS_CUDA(cudaEventCreate(&e));
   return e;
 }
+bool profiled(cudaStream_t st) {
+  for (cudaStream_t s : g_prof_streams)
+    if (s == st) return true;
+  return false;
+}
+// Takes the records of the given streams out of the list (events waited on).
+void take_recs(const cudaStream_t* sts, int n, double* ms, double* work) {
+  std::vector<Rec> keep;
+  for (auto& r : g_recs) {
+    bool mine = false;
+    for (int i = 0; i < n; i++) mine = mine || (sts[i] && r.st == sts[i]);
+    if (!mine) {
+      keep.push_back(r);
+      continue;
+    }
+    RIS_CUDA(cudaEventSynchronize(r.a));
+    if (r.b) {
+      RIS_CUDA(cudaEventSynchronize(r.b));
+      float t = 0.f;
+      RIS_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+      if (ms) ms[r.cls] += t;
+      if (work) work[r.cls] += r.work;
+      g_pool.push_back(r.b);
+    }
+    g_pool.push_back(r.a);
+  }
+  g_recs.swap(keep);
+}
 }  // namespace
 
-void prof_enable(bool on) { g_prof_on = on; }
-void prof_begin(int cls, cudaStream_t st) {
-  if (!g_prof_on) return;
+void prof_attach(cudaStream_t st) {
+  if (!st) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  Rec r{cls, take_event(), nullptr, 0.0};
+  g_prof_streams.push_back(st);
+  ++g_prof_n;
+}
+void prof_detach(cudaStream_t st) {
+  if (!st) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto it = g_prof_streams.begin(); it != g_prof_streams.end(); ++it)
+    if (*it == st) {
+      g_prof_streams.erase(it);
+      --g_prof_n;
+      break;
+    }
+  if (!profiled(st)) {
+    try {
+      take_recs(&st, 1, nullptr, nullptr);
+    } catch (const Error&) {
+    }
+  }
+}
+void prof_begin(int cls, cudaStream_t st) {
+  if (g_prof_n.load() == 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!profiled(st)) return;
+  Rec r{cls, st, take_event(), nullptr, 0.0};
   RIS_CUDA(cudaEventRecord(r.a, st));
   g_recs.push_back(r);
 }
 void prof_end(int cls, cudaStream_t st, double work) {
-  if (!g_prof_on) return;
+  if (g_prof_n.load() == 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   for (auto it = g_recs.rbegin(); it != g_recs.rend(); ++it)
-    if (it->cls == cls && it->b == nullptr) {
+    if (it->cls == cls && it->st == st && it->b == nullptr) {
       it->b = take_event();
       it->work = work;
       RIS_CUDA(cudaEventRecord(it->b, st));
       return;
     }
 }
-void prof_collect(double* ms, double* work) {
+void prof_collect(const cudaStream_t* sts, int n, double* ms, double* work) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   for (int c = 0; c < kProfN; c++) ms[c] = work[c] = 0.0;
-  for (auto& r : g_recs) {
-    if (r.b) {
-      RIS_CUDA(cudaEventSynchronize(r.b));
-      float t = 0.f;
-      RIS_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
-      ms[r.cls] += t;
-      work[r.cls] += r.work;
-      g_pool.push_back(r.b);
-    }
-    g_pool.push_back(r.a);
-  }
-  g_recs.clear();
+  take_recs(sts, n, ms, work);
 }
 }  // namespace ris
 
@@ -141,6 +183,7 @@ ris_status ris_options_default(ris_options* opt) {
   opt->eig_fp32 = 0;
   opt->stream = 0;
   opt->stream_block = 0;
+  opt->subspace_ff = 1;
   return RIS_OK;
 }
 
@@ -162,7 +205,6 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
   if (o.eig_fp32 != 0 && o.eig_fp32 != 1) return RIS_ERR_ARG;
   c->eng.opt = o;
   c->eng.device = o.device;
-  if (o.profile) ris::prof_enable(true);
   ris_status s = guarded(c.get(), [&] {
     if (o.cuda_stream) {
       c->eng.st = (cudaStream_t)o.cuda_stream;
@@ -184,6 +226,10 @@ ris_status ris_create(ris_ctx** out, const ris_options* opt) {
       RIS_CUDA(cudaStreamCreateWithPriority(&c->eng.st2, cudaStreamNonBlocking, lo));
       RIS_CUDA(cudaEventCreateWithFlags(&c->eng.evA, cudaEventDisableTiming));
       RIS_CUDA(cudaEventCreateWithFlags(&c->eng.evD, cudaEventDisableTiming));
+    }
+    if (o.profile) {
+      ris::prof_attach(c->eng.st);
+      ris::prof_attach(c->eng.st2);
     }
   });
   if (s != RIS_OK) return s;
@@ -331,21 +377,23 @@ ris_status ris_get_dims(const ris_ctx* ctx, int* natm, int* nao, int* nocc, int*
 }
 
 ris_status ris_get_stats(const ris_ctx* ctx, double* out, int n) {
-  if (!ctx || !out || n < 0 || n > 32) return RIS_ERR_ARG;
-  double all[32] = {0};
+  if (!ctx || !out || n < 0 || n > 34) return RIS_ERR_ARG;
+  double all[34] = {0};
   for (int i = 0; i < 16; i++) all[i] = ctx->eng.stats[i];
   all[15] = (double)ris::g_launches.load();
   try {
-    cudaSetDevice(ctx->eng.device);
+    RIS_CUDA(cudaSetDevice(ctx->eng.device));
     double ms[ris::kProfN], work[ris::kProfN];
-    ris::prof_collect(ms, work);
+    const cudaStream_t sts[2] = {ctx->eng.st, ctx->eng.st2};
+    ris::prof_collect(sts, 2, ms, work);
     for (int c = 0; c < ris::kProfN; c++) {
-      const int slot = c == ris::kProfEmuGemm ? 30 : 16 + 2 * c;
+      const int slot = c == ris::kProfEmuGemm ? 30 : c == ris::kProfFF ? 32 : 16 + 2 * c;
       all[slot] = ms[c];
       all[slot + 1] = work[c];
     }
-  } catch (const ris::Error&) {
-    return RIS_ERR_CUDA;
+  } catch (const ris::Error& e) {
+    ctx->eng.err = e.msg;
+    return e.code;
   }
   all[28] = (double)ctx->eng.mem.cur;
   all[29] = (double)ctx->eng.mem.peak;
@@ -368,6 +416,10 @@ void ris_destroy(ris_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->eng.device);
   if (ctx->eng.st) cudaStreamSynchronize(ctx->eng.st);
+  if (ctx->eng.opt.profile) {
+    ris::prof_detach(ctx->eng.st);
+    ris::prof_detach(ctx->eng.st2);
+  }
   delete ctx;
 }
 

@@ -53,12 +53,15 @@ extern std::atomic<long long> g_allocs;
 // Optional per-kernel-class timing with CUDA events on the launching stream
 // (enabled by the profile option; off by default).
 enum ProfClass {
-  kProfGemm = 0, kProfInt3c, kProfInt3cDeriv, kProfContract, kProfEig, kProfTcGemm, kProfEmuGemm, kProfN
+  kProfGemm = 0, kProfInt3c, kProfInt3cDeriv, kProfContract, kProfEig, kProfTcGemm, kProfEmuGemm,
+  kProfFF, kProfN
 };
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st, double work);
-void prof_enable(bool on);
-void prof_collect(double* ms, double* work);  // sums per class since the last collect
+void prof_attach(cudaStream_t st);  // time the classes launched on st
+void prof_detach(cudaStream_t st);
+// sums per class of the records on the given streams since their last collect
+void prof_collect(const cudaStream_t* sts, int n, double* ms, double* work);
 
 #define RIS_REQUIRE(cond, code, text)                    \
   do {                                                   \

@@ -31,6 +31,7 @@
 #include <set>
 
 #include "engine.cuh"
+#include "gemm_ff.cuh"
 
 namespace ris {
 
@@ -513,60 +514,74 @@ __global__ void k_scale_rows(double* __restrict__ X, long long n, int nrow, cons
 // Cholesky of the Gram matrix G (nt x nt, unit diagonal expected) with
 // dropping of (near-)dependent rows; P[i][c] such that the kept rows
 // Tnew_i = sum_c P[i][c] T_c are orthonormal.  *nkeep = number kept.
-__global__ void k_cholqr_small(const double* G, int nt, double drop, double* P, int* nkeep,
-                               double* work) {
-  // G, R and P live in shared memory (nt <= 64); one thread runs the
-  // factorisation, the block loads and stores.
+// One warp: right-looking factorisation G = R^T R over the pivots in order
+// (a pivot whose remaining diagonal is not above drop * G_jj is skipped and
+// updates nothing), lanes over the columns of each update; then P = R^-T
+// restricted to the kept pivots, lane q solving R^T y = e_q.
+__global__ void __launch_bounds__(32) k_cholqr_small(const double* G, int nt, double drop,
+                                                     double* P, int* nkeep) {
   extern __shared__ double sh[];
-  double* Gs = sh;
-  double* R = Gs + nt * nt;
+  double* A = sh;            // working copy, upper triangle updated
+  double* R = A + nt * nt;   // row j: row of R for kept pivot j
   double* Ps = R + nt * nt;
-  int* keep = (int*)(Ps + nt * nt);
-  (void)work;
-  for (int i = threadIdx.x; i < nt * nt; i += blockDim.x) {
-    Gs[i] = G[i];
+  double* rinv = Ps + nt * nt;
+  int* keep = (int*)(rinv + nt);
+  const int lane = threadIdx.x;
+  for (int i = lane; i < nt * nt; i += 32) {
+    A[i] = G[i];
+    R[i] = 0.0;
     Ps[i] = 0.0;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int r = 0;
-    for (int j = 0; j < nt; j++) {
-      double d = Gs[j * nt + j];
-      for (int q = 0; q < r; q++) {
-        const int i = keep[q];
-        double s = Gs[i * nt + j];
-        for (int q2 = 0; q2 < q; q2++) s -= R[keep[q2] * nt + i] * R[keep[q2] * nt + j];
-        R[i * nt + j] = s / R[i * nt + i];
-        d -= R[i * nt + j] * R[i * nt + j];
-      }
-      if (d > drop * Gs[j * nt + j] && d > 0) {
-        R[j * nt + j] = sqrt(d);
-        keep[r++] = j;
-      }
+  __syncwarp();
+  int r = 0;
+  for (int j = 0; j < nt; j++) {
+    const double d = A[j * nt + j];
+    if (!(d > drop * G[j * nt + j] && d > 0)) continue;  // warp-uniform
+    const double rjj = sqrt(d), ri = 1.0 / rjj;
+    for (int l = j + 1 + lane; l < nt; l += 32) R[j * nt + l] = A[j * nt + l] * ri;
+    if (lane == 0) {
+      R[j * nt + j] = rjj;
+      rinv[r] = ri;
+      keep[r] = j;
     }
-    // P = R^{-T} over the kept indices: Tnew_s = sum_q (R^{-T})_sq T_keep[q];
-    // column q of R^{-T} solves R^T y = e_q (forward substitution).
-    for (int q = 0; q < r; q++) {
-      double y[64];
-      for (int s = 0; s < r; s++) {
-        double acc = (s == q) ? 1.0 : 0.0;
-        for (int s2 = 0; s2 < s; s2++) acc -= R[keep[s2] * nt + keep[s]] * y[s2];
-        y[s] = acc / R[keep[s] * nt + keep[s]];
-      }
-      for (int s = 0; s < r; s++) Ps[s * nt + keep[q]] = y[s];
+    __syncwarp();
+    for (int l2 = j + 1 + lane; l2 < nt; l2 += 32) {
+      const double b = R[j * nt + l2];
+      for (int l = j + 1; l <= l2; l++) A[l * nt + l2] -= R[j * nt + l] * b;
     }
-    *nkeep = r;
+    __syncwarp();
+    r++;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nt * nt; i += blockDim.x) P[i] = Ps[i];
+  // column keep[q] of P: y_s = (delta_sq - sum_{q <= s2 < s} R[keep s2][keep s] y_s2) / R_ss
+  for (int q = lane; q < r; q += 32) {
+    const int cq = keep[q];
+    for (int s = q; s < r; s++) {
+      double acc = s == q ? 1.0 : 0.0;
+      const int ks = keep[s];
+      for (int s2 = q; s2 < s; s2++) acc -= R[keep[s2] * nt + ks] * Ps[s2 * nt + cq];
+      Ps[s * nt + cq] = acc * rinv[s];
+    }
+  }
+  __syncwarp();
+  if (lane == 0) *nkeep = r;
+  for (int i = lane; i < nt * nt; i += 32) P[i] = Ps[i];
+}
+
+// FP64 GEMM, or the double-FP32 one (gemm_ff.cu) when ff is set and the
+// shape is one of its skinny forms.
+static void gemm_sub(bool ff, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+                     int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                     cudaStream_t st) {
+  if (!(ff && ffgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st)))
+    dgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st);
 }
 
 static void cholqr_small(const double* G, int nt, double drop, double* P, int* nkeep,
                          cudaStream_t st) {
   RIS_REQUIRE(nt >= 1 && nt <= 64, RIS_ERR_ARG, "cholqr_small: block of 1..64 vectors");
-  const size_t smem = 3 * (size_t)nt * nt * sizeof(double) + nt * sizeof(int) + 16;
-  ensure_smem_attr((const void*)k_cholqr_small, (int)(3 * 64 * 64 * sizeof(double) + 64 * sizeof(int) + 16));
-  k_cholqr_small<<<1, 32, smem, st>>>(G, nt, drop, P, nkeep, nullptr);
+  const size_t smem = (3 * (size_t)nt * nt + nt) * sizeof(double) + nt * sizeof(int);
+  ensure_smem_attr((const void*)k_cholqr_small, (int)((3 * 64 * 64 + 64) * sizeof(double) + 64 * sizeof(int)));
+  k_cholqr_small<<<1, 32, smem, st>>>(G, nt, drop, P, nkeep);
   RIS_CHECK_LAUNCH();
 }
 
@@ -1674,10 +1689,11 @@ void Engine::apply_exchange_mixed(const double* Z, int nvec, double* out, double
 
 void Engine::apply_A_mixed(const double* Xin, int nvec, double* out) {
   const long long nov = (long long)nocc * nvir;
-  // Coulomb in FP64: out = 2 (X B^J) B^J^T
+  // Coulomb, FP64-accurate: out = 2 (X B^J) B^J^T (double-FP32 with subspace_ff)
   w5.ensure((size_t)nvec * std::max(nJ, 1), st);
-  dgemm(false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
-  dgemm(false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
+  const bool ff = opt.subspace_ff != 0;
+  gemm_sub(ff, false, false, nvec, nJ, (int)nov, 1.0, Xin, (int)nov, BJ.p, nJ, 0.0, w5.p, nJ, st);
+  gemm_sub(ff, false, true, nvec, (int)nov, nJ, 2.0, w5.p, nJ, BJ.p, nJ, 0.0, out, (int)nov, st);
   apply_exchange_mixed(Xin, nvec, out, -opt.cx, 1.0);
   k_add_diag<<<cdiv(nov * nvec, 256), 256, 0, st>>>(de.p, Xin, nov, nvec, out);
   RIS_CHECK_LAUNCH();
@@ -1959,6 +1975,14 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
   bool s32 = false;  // S came from the FP32 solver
   int stall = 0;
   double rprev = 0.0;
+  // Ritz vectors X = S V and A X = S (A V) as double-FP32 products in the
+  // mixed form (subspace_ff); the orthogonalisation, the restart basis and the
+  // projected matrix V^T A V stay FP64
+  const bool ffs = mixed && opt.subspace_ff;
+  auto sgemm = [&](bool ta, bool tb, int m_, int n_, int k_, double al, const double* A_, int la,
+                   const double* B_, int lb, double be, double* C_, int lc) {
+    gemm_sub(ffs, ta, tb, m_, n_, k_, al, A_, la, B_, lb, be, C_, lc, st);
+  };
   auto product = [&](const double* x, int nv, double* y) {
     if (mixed)
       apply_A_mixed(x, nv, y);
@@ -2029,8 +2053,8 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
     const int nk = std::min(m, std::max(ns, kkeep));
     s32 = eig32 && sym_eig_lowest_f32(Hs.p, maxsp, m, nk, w.p, S.p, ework.p, st);
     if (!s32) sym_eig_lowest(Hs.p, maxsp, m, nk, w.p, S.p, ework.p, st);
-    dgemm(false, false, ns, (int)n, m, 1.0, S.p, m, V.p, (int)n, 0.0, Xr.p, (int)n, st);
-    dgemm(false, false, ns, (int)n, m, 1.0, S.p, m, AV.p, (int)n, 0.0, AXr.p, (int)n, st);
+    sgemm(false, false, ns, (int)n, m, 1.0, S.p, m, V.p, (int)n, 0.0, Xr.p, (int)n);
+    sgemm(false, false, ns, (int)n, m, 1.0, S.p, m, AV.p, (int)n, 0.0, AXr.p, (int)n);
     k_residual<<<cdiv(n * ns, 256), 256, 0, st>>>(AXr.p, Xr.p, w.p, n, ns, Rr.p);
     RIS_CHECK_LAUNCH();
     row_norms(Rr.p, ns, n, G.p, st);

@@ -102,7 +102,7 @@ struct Engine : StreamOwner {
   ris_options opt{};
   int device = 0;
   MemTrack mem;
-  std::string err;
+  mutable std::string err;  // last error message (also set by the const statistics call)
   int stage = 0;  // 0 created, 1 aux built, 2 B built, 3 excited
 
   // geometry / basis

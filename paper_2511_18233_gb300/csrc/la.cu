@@ -132,13 +132,25 @@ __global__ void __launch_bounds__(256) k_dgemm(int m, int n, int k, double alpha
   }
 }
 
-__global__ void k_splitk_reduce(int m, int n, int ksplit, const double* __restrict__ ws,
-                                double alpha, double beta, double* __restrict__ C, int ldc) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)m * n) return;
-  const int i = (int)(t / n), j = (int)(t % n);
+// 32 outputs per CTA; warp g adds the slices g, g + 8, ... in order, then
+// warp 0 adds the eight sums in order (the FP64 adds of a skinny product's
+// many slices spread over many SMs; same result every run).
+__global__ void __launch_bounds__(256) k_splitk_reduce(int m, int n, int ksplit,
+                                                       const double* __restrict__ ws, double alpha,
+                                                       double beta, double* __restrict__ C, int ldc) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const long long mn = (long long)m * n;
+  const long long t = (long long)blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int z = 0; z < ksplit; z++) s += ws[(size_t)z * m * n + t];
+  if (t < mn)
+    for (int z = g; z < ksplit; z += 8) s += ws[(size_t)z * mn + t];
+  red[g][lane] = s;
+  __syncthreads();
+  if (g != 0 || t >= mn) return;
+#pragma unroll
+  for (int h = 1; h < 8; h++) s += red[h][lane];
+  const int i = (int)(t / n), j = (int)(t % n);
   double* p = C + (size_t)i * ldc + j;
   *p = beta == 0.0 ? alpha * s : fma(alpha, s, beta * *p);
 }
@@ -233,7 +245,7 @@ void dgemm(bool transA, bool transB, int m, int n, int k, double alpha, const do
     launch_t<true, true>(sh, grid, st, m, n, k, alpha, A, lda, B, ldb, beta, Cout, ldc, bt, ksplit, kchunk);
   RIS_CHECK_LAUNCH();
   if (ksplit > 1) {
-    k_splitk_reduce<<<cdiv((long long)m * n, 256), 256, 0, st>>>(m, n, ksplit, ws, alpha, beta, C, ldc);
+    k_splitk_reduce<<<cdiv((long long)m * n, 32), 256, 0, st>>>(m, n, ksplit, ws, alpha, beta, C, ldc);
     RIS_CHECK_LAUNCH();
     dev_free(ws, sizeof(double) * (size_t)ksplit * m * n, st, ws_tr);
   }
@@ -1184,16 +1196,56 @@ __global__ void k_row_dot(const double* __restrict__ V, long long ncol, const do
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-void row_norms(const double* X, int nrow, long long ncol, double* out, cudaStream_t st) {
+// Long rows: nsplit CTAs per row write partial sums, k_row_dot_fin adds them
+// in order (spreads the FP64 work over the SMs; same result every run).
+__global__ void k_row_dot_part(const double* __restrict__ V, long long ncol,
+                               const double* __restrict__ x, int nsplit, double* __restrict__ part) {
+  __shared__ double red[33];
+  const int row = blockIdx.y, sp = blockIdx.x;
+  const double* v = V + (size_t)row * ncol;
+  const double* y = x ? x : v;
+  const long long per = (ncol + nsplit - 1) / nsplit;
+  const long long b = (long long)sp * per, e = min(ncol, b + per);
+  double s = 0.0;
+  for (long long i = b + threadIdx.x; i < e; i += 256) s += v[i] * y[i];
+  s = block_sum<256>(s, red);
+  if (threadIdx.x == 0) part[(size_t)row * nsplit + sp] = s;
+}
+
+__global__ void k_row_dot_fin(const double* __restrict__ part, int nrow, int nsplit,
+                              double* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  double s = 0.0;
+  for (int z = 0; z < nsplit; z++) s += part[(size_t)r * nsplit + z];
+  out[r] = s;
+}
+
+static void row_dots(const double* V, int nrow, long long ncol, const double* x, double* out,
+                     cudaStream_t st) {
   if (nrow <= 0) return;
-  k_row_dot<<<nrow, 256, 0, st>>>(X, ncol, nullptr, out);
+  const int nsplit = (int)std::min<long long>(32, ncol / 4096);
+  if (nsplit < 2 || nrow > 65535) {
+    k_row_dot<<<nrow, 256, 0, st>>>(V, ncol, x, out);
+    RIS_CHECK_LAUNCH();
+    return;
+  }
+  MemTrack* tr = nullptr;
+  const size_t b = sizeof(double) * (size_t)nrow * nsplit;
+  double* part = (double*)dev_alloc(b, st, &tr);
+  k_row_dot_part<<<dim3(nsplit, nrow), 256, 0, st>>>(V, ncol, x, nsplit, part);
   RIS_CHECK_LAUNCH();
+  k_row_dot_fin<<<cdiv(nrow, 64), 64, 0, st>>>(part, nrow, nsplit, out);
+  RIS_CHECK_LAUNCH();
+  dev_free(part, b, st, tr);
+}
+
+void row_norms(const double* X, int nrow, long long ncol, double* out, cudaStream_t st) {
+  row_dots(X, nrow, ncol, nullptr, out, st);
 }
 void gemv_rows(const double* V, int nrow, long long ncol, const double* x, double* out,
                cudaStream_t st) {
-  if (nrow <= 0) return;
-  k_row_dot<<<nrow, 256, 0, st>>>(V, ncol, x, out);
-  RIS_CHECK_LAUNCH();
+  row_dots(V, nrow, ncol, x, out, st);
 }
 
 }  // namespace ris

@@ -23,7 +23,7 @@ STATUS = {0: "RIS_OK", -1: "RIS_ERR_ARG", -2: "RIS_ERR_OOM", -3: "RIS_ERR_METRIC
 FP64, MIXED = 0, 1
 
 EXPORTS = ["ris_options_default", "ris_create", "ris_build_aux", "ris_build_B", "ris_excite",
-           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_time_coupling", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_gemm_f64emu", "ris_debug_sym_eig", "ris_debug_sym_eig_f32", "ris_debug_dgemm",
+           "ris_apply", "ris_excite_guess", "ris_trim", "ris_zvector", "ris_phase_align", "ris_time_coupling", "ris_get_mo_window", "ris_debug_gemm_tf32x3", "ris_debug_gemm_f64emu", "ris_debug_gemm_ff", "ris_debug_sym_eig", "ris_debug_sym_eig_f32", "ris_debug_dgemm",
            "ris_gemm_tf32x3_noalloc", "ris_debug_alloc_count", "ris_debug_peak_probe",
            "ris_gradient", "ris_nac", "ris_get_dims", "ris_get_stats", "ris_debug_boys",
            "ris_last_error", "ris_destroy"]
@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_int), ("mixed_tol", ctypes.c_double), ("refine", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mo_window", ctypes.c_double),
                 ("deriv_prefetch", ctypes.c_int), ("emu_f64", ctypes.c_int),
-                ("eig_fp32", ctypes.c_int), ("stream", ctypes.c_int), ("stream_block", ctypes.c_int)]
+                ("eig_fp32", ctypes.c_int), ("stream", ctypes.c_int), ("stream_block", ctypes.c_int),
+                ("subspace_ff", ctypes.c_int)]
 
 
 class Shell(ctypes.Structure):
@@ -83,6 +84,8 @@ def load(path: str = LIB_PATH):
     L.ris_debug_boys.argtypes = [i, P, P, P]
     L.ris_debug_gemm_tf32x3.argtypes = [i, i, i, P, P, P]
     L.ris_debug_gemm_f64emu.argtypes = [i, i, i, P, P, P]
+    L.ris_debug_gemm_ff.argtypes = [i, i, i, i, ctypes.c_double, P, P, ctypes.c_double, P,
+                                    ctypes.POINTER(i)]
     L.ris_debug_sym_eig.argtypes = [i, i, P, P, P]
     L.ris_debug_sym_eig_f32.argtypes = [i, i, P, P, P]
     d = ctypes.c_double
@@ -275,11 +278,11 @@ class Context:
                  22: "contract_ms", 23: "contract_bytes", 24: "eig_ms", 25: "eig_calls",
                  26: "tc_gemm_ms", 27: "tc_gemm_flops", 6: "refine_products",
                  28: "bytes_held", 29: "bytes_peak", 7: "residual_max", 30: "emu_gemm_ms",
-                 31: "emu_gemm_flops"}
+                 31: "emu_gemm_flops", 32: "ff_gemm_ms", 33: "ff_gemm_flops"}
 
     def stats(self):
-        out = (ctypes.c_double * 32)()
-        self._check(self.L.ris_get_stats(self.h, out, 32))
+        out = (ctypes.c_double * 34)()
+        self._check(self.L.ris_get_stats(self.h, out, 34))
         return {k: out[i] for i, k in self.STAT_KEYS.items()}
 
 
@@ -324,6 +327,30 @@ def debug_gemm_f64emu(A, B):
     if st != 0:
         raise RisError(st, "ris_debug_gemm_f64emu failed")
     return C_t.cpu().numpy()
+
+
+def debug_gemm_ff(A, B, transB=True, alpha=1.0, beta=0.0, C=None):
+    """C = alpha A op(B) + beta C through the library's double-FP32 GEMM
+    (numpy in/out); op(B) = B^T (B [N][K]) when transB, else B ([K][N]).
+    Returns (C, kind) with kind 1 (long-K kernel) or 2 (short-K kernel)."""
+    import torch
+    A_t = torch.as_tensor(np.ascontiguousarray(A, dtype=np.float64), device="cuda")
+    B_t = torch.as_tensor(np.ascontiguousarray(B, dtype=np.float64), device="cuda")
+    M, K = A_t.shape
+    N = B_t.shape[0] if transB else B_t.shape[1]
+    if (B_t.shape[1] if transB else B_t.shape[0]) != K:
+        raise ValueError("debug_gemm_ff: inner dimensions differ")
+    if C is None:
+        C_t = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    else:
+        C_t = torch.as_tensor(np.ascontiguousarray(C, dtype=np.float64), device="cuda").clone()
+    kind = ctypes.c_int(-1)
+    st = load().ris_debug_gemm_ff(int(bool(transB)), M, N, K, float(alpha), A_t.data_ptr(),
+                                  B_t.data_ptr(), float(beta), C_t.data_ptr(), ctypes.byref(kind))
+    torch.cuda.synchronize()
+    if st != 0:
+        raise RisError(st, f"ris_debug_gemm_ff failed (shape kind {kind.value})")
+    return C_t.cpu().numpy(), kind.value
 
 
 def gemm_tf32x3_noalloc(A_t, B_t, C_t, stream=None) -> int:

@@ -47,6 +47,7 @@ def test_options_defaults(lib):
     assert o.precond == 0 and o.mo_window == 0.0 and o.deriv_prefetch == 1
     assert o.emu_f64 == 1 and o.eig_fp32 == 0
     assert o.stream == 0 and o.stream_block == 0 and o.occ_block == 0
+    assert o.subspace_ff == 1
 
 
 def test_create_rejects_bad_options(lib):

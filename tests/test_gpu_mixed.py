@@ -127,3 +127,23 @@ def test_mixed_chain_stated_error(ris_mod, chain, eig32):
     c.nac([(s, s + 1) for s in range(9)], numerator=num)
     nref = orc.pair_energy_derivs([(2, 3)], X[:10], atoms=atoms)
     assert np.max(np.abs(num[2, atoms] - nref[0, atoms])) <= 1e-5
+
+
+@gpu
+def test_subspace_ff_same_states(ris_mod):
+    """The double-FP32 subspace products (option subspace_ff, default on)
+    against FP64 ones on the C20H22 chain: the same excitation energies to
+    well below the stated error, and the double-FP32 kernels actually ran."""
+    mol = synth.workload(1)
+    out = {}
+    for ff in (0, 1):
+        c = _ctx(ris_mod, mol, precision=ris_mod.MIXED, subspace_ff=ff, profile=1)
+        c.stats()  # reset the per-class timers
+        om, X = c.excite(10)
+        out[ff] = (om, c.stats())
+        c.close()
+    assert out[1][1]["ff_gemm_ms"] > 0 and out[0][1]["ff_gemm_ms"] == 0
+    print(f"\nsubspace products: FP64 {out[0][1]['gemm_ms']:.2f} ms; double-FP32 "
+          f"{out[1][1]['ff_gemm_ms']:.2f} ms + FP64 {out[1][1]['gemm_ms']:.2f} ms")
+    assert np.max(np.abs(out[1][0] - out[0][0])) <= 1e-8
+    assert out[1][1]["residual_max"] <= 1e-6
