@@ -1228,9 +1228,13 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
   // the screened pairs go to pinned host memory on a copy stream, so that
   // each AO function's partner list is built on the host while the
   // integrals and the metric factors run on the device
-  if (!st3) {
-    RIS_CUDA(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
+  if (!st3) {  // high priority: its single-CTA metric factorisations run beside the integrals
+    int lo = 0, hi = 0;
+    RIS_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    RIS_CUDA(cudaStreamCreateWithPriority(&st3, cudaStreamNonBlocking, hi));
     RIS_CUDA(cudaEventCreateWithFlags(&evP, cudaEventDisableTiming));
+    RIS_CUDA(cudaEventCreateWithFlags(&evC, cudaEventDisableTiming));
+    RIS_CUDA(cudaEventCreateWithFlags(&evM, cudaEventDisableTiming));
   }
   if (pin_n < 2 * (size_t)std::max(pl.npair, 1)) {
     if (pin) RIS_CUDA(cudaFreeHost(pin));
@@ -1238,12 +1242,32 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
     pin_n = 2 * (size_t)std::max(pl.npair, 1);
     RIS_ALLOC(cudaMallocHost((void**)&pin, sizeof(int) * pin_n));
   }
+  // the metric factors (two-centre integrals, Cholesky, inverse) depend on
+  // the auxiliary shells only: they run on st3 beside the three-centre
+  // integrals (buffers allocated on st first)
+  MU.ensure((size_t)nU * nU, st);
+  dMU.ensure(3 * (size_t)nU * nU, st);
+  if (!d_info) RIS_ALLOC(cudaMallocAsync((void**)&d_info, sizeof(int) * 2, st));
+  LJinv.ensure((size_t)nJ * nJ, st);
+  LKinv.ensure((size_t)nK * nK, st);
+  w1.ensure((size_t)std::max(nJ, nK) * std::max(nJ, nK), st);
   RIS_CUDA(cudaEventRecord(evP, st));
   RIS_CUDA(cudaStreamWaitEvent(st3, evP, 0));
   if (pl.npair > 0) {
     RIS_CUDA(cudaMemcpyAsync(pin, pl.a, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st3));
     RIS_CUDA(cudaMemcpyAsync(pin + pl.npair, pl.b, sizeof(int) * pl.npair, cudaMemcpyDeviceToHost, st3));
   }
+  RIS_CUDA(cudaEventRecord(evC, st3));
+  int2c(aux, xyz.p, MU.p, dMU.p, st3);
+  for (int set = 0; set < 2; set++) {
+    const int n = set == 0 ? nJ : nK;
+    const int* map = set == 0 ? d_jU : d_kU;
+    k_gather_sq<<<cdiv(n * n, 256), 256, 0, st3>>>(MU.p, nU, map, n, w1.p);
+    RIS_CHECK_LAUNCH();
+    cholesky(w1.p, n, d_info + set, st3);
+    tri_inverse(w1.p, set == 0 ? LJinv.p : LKinv.p, n, st3);
+  }
+  RIS_CUDA(cudaEventRecord(evM, st3));
   // integrals: dense [mu][nu][P], or (streamed form) on the screened pairs
   // only, after the metric factors are known
   const int nao_ = ao.nfun;
@@ -1260,23 +1284,8 @@ void Engine::build_aux(int natm_, const double* coords, int nshell, const ris_sh
     D.release();
     Df.release();
   }
-  MU.ensure((size_t)nU * nU, st);
-  dMU.ensure(3 * (size_t)nU * nU, st);
-  int2c(aux, xyz.p, MU.p, dMU.p, st);
-  // metric factors
-  if (!d_info) RIS_ALLOC(cudaMallocAsync((void**)&d_info, sizeof(int) * 2, st));
-  LJinv.ensure((size_t)nJ * nJ, st);
-  LKinv.ensure((size_t)nK * nK, st);
-  w1.ensure((size_t)std::max(nJ, nK) * std::max(nJ, nK), st);
-  for (int set = 0; set < 2; set++) {
-    const int n = set == 0 ? nJ : nK;
-    const int* map = set == 0 ? d_jU : d_kU;
-    k_gather_sq<<<cdiv(n * n, 256), 256, 0, st>>>(MU.p, nU, map, n, w1.p);
-    RIS_CHECK_LAUNCH();
-    cholesky(w1.p, n, d_info + set, st);
-    tri_inverse(w1.p, set == 0 ? LJinv.p : LKinv.p, n, st);
-  }
-  RIS_CUDA(cudaStreamSynchronize(st3));
+  RIS_CUDA(cudaStreamWaitEvent(st, evM, 0));
+  RIS_CUDA(cudaEventSynchronize(evC));
   h_pa.assign(pin, pin + pl.npair);
   h_pb.assign(pin + pl.npair, pin + 2 * (size_t)pl.npair);
   partners_from_host_pairs();

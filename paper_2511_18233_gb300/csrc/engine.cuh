@@ -69,14 +69,18 @@ struct StreamOwner {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   cudaStream_t st2 = nullptr;  // low-priority side stream (derivative integrals)
-  cudaStream_t st3 = nullptr;  // copy stream (the pair list to the host)
+  cudaStream_t st3 = nullptr;  // side stream: the pair list to the host, the metric factors
   cudaEvent_t evP = nullptr;   // the pair list is built
+  cudaEvent_t evC = nullptr;   // its host copy is done
+  cudaEvent_t evM = nullptr;   // the metric factors are done (st3)
   int* pin = nullptr;          // pinned host copy of the pair list
   size_t pin_n = 0;
   ~StreamOwner() {
     if (st3) cudaStreamSynchronize(st3);
     if (pin) cudaFreeHost(pin);
     if (evP) cudaEventDestroy(evP);
+    if (evC) cudaEventDestroy(evC);
+    if (evM) cudaEventDestroy(evM);
     if (st3) cudaStreamDestroy(st3);
     if (st2) cudaStreamDestroy(st2);
     if (own_stream && st) cudaStreamDestroy(st);

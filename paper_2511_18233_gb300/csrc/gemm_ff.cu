@@ -34,82 +34,19 @@
 // * k_ff_rows (k <= 256, n large, m <= 32): a CTA owns 32 output columns,
 //   its four warps split k and combine through shared memory; A is split
 //   once per CTA into shared memory (broadcast reads), B is streamed once.
-// * k_ff_long (k large, m <= 32, n <= 512): warp r of a CTA owns output row
-//   r and each lane TN columns; k is cut into chunks over CTAs, 32-deep
+// * k_ff_long (k large, m <= 32, n <= 512): warp w of a CTA owns output rows
+//   w, w + 8, ... and each lane TN columns; k is cut into chunks over CTAs, 32-deep
 //   slices of A and B are split into shared memory, and every chunk writes
 //   its (S, C) pairs; k_ff_reduce adds the chunks in a fixed order (the
 //   result does not depend on scheduling).
 #include "gemm_ff.cuh"
+#include "ff_arith.cuh"
 
 #include <algorithm>
 
 namespace ris {
 
 namespace {
-
-__device__ __forceinline__ void ff_split(double x, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7ff) - 1023;
-  const unsigned long long f = b & 0xfffffffffffffULL;
-  if (e < -126) {  // zero, FP64 subnormal, or below the FP32 normal range
-    hi = 0.f;
-    lo = 0.f;
-    return;
-  }
-  if (e > 127) {  // beyond the FP32 range (or inf / nan)
-    hi = __uint_as_float(sgn | 0x7f800000u);
-    lo = 0.f;
-    return;
-  }
-  hi = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (unsigned)(f >> 29));
-  const unsigned r = (unsigned)(f & 0x1fffffffu);  // value r * 2^(e-52)
-  if (r == 0u || e < -74) {  // 2^(e-52) below the FP32 normal range: lo < 2^-97, dropped
-    lo = 0.f;
-    return;
-  }
-  const float sc = __uint_as_float((unsigned)(e + 75) << 23);  // 2^(e-52)
-  lo = __uint_as_float(__float_as_uint(__fmul_rn(__uint2float_rn(r), sc)) | sgn);
-}
-
-// FP32 -> FP64 by the bit pattern (FP32 subnormals flush to zero).
-__device__ __forceinline__ double ff_widen(float v) {
-  const unsigned u = __float_as_uint(v);
-  const unsigned ex = (u >> 23) & 0xffu;
-  if (ex == 0u) return 0.0;
-  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned long long e64 = ex == 0xffu ? 0x7ffULL : (unsigned long long)(ex + 896u);
-  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
-  return __longlong_as_double((long long)(s | (e64 << 52) | m));
-}
-
-// (s, c) += (ah + al) (bh + bl)
-__device__ __forceinline__ void ff_term(float ah, float al, float bh, float bl, float& s, float& c) {
-  const float p = __fmul_rn(ah, bh);
-  const float e = __fmaf_rn(ah, bh, -p);
-  const float t = __fadd_rn(s, p);
-  const float z = __fsub_rn(t, s);
-  const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(q, __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e))));
-}
-
-// (s, c) <- TwoSum(s, c) + c's remainder
-__device__ __forceinline__ void ff_renorm(float& s, float& c) {
-  const float t = __fadd_rn(s, c);
-  const float z = __fsub_rn(t, s);
-  c = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(c, z));
-  s = t;
-}
-
-// (S, C) += (s, c)
-__device__ __forceinline__ void ff_add(float& S, float& C, float s, float c) {
-  const float t = __fadd_rn(S, s);
-  const float z = __fsub_rn(t, S);
-  const float q = __fadd_rn(__fsub_rn(S, __fsub_rn(t, z)), __fsub_rn(s, z));
-  S = t;
-  C = __fadd_rn(C, __fadd_rn(q, c));
-}
 
 __device__ __forceinline__ void ff_store(double* p, float s, float c, double alpha, double beta) {
   const double y = ff_widen(s) + ff_widen(c);
@@ -148,13 +85,28 @@ __global__ void __launch_bounds__(32 * kRowsKG) k_ff_rows(int m, int n, int k, d
     sA[e] = make_float2(h, l);
   }
   if (TB) {
-    // consecutive threads read consecutive k of one row of B (coalesced)
-    for (int e = threadIdx.x; e < 32 * k; e += 32 * kRowsKG) {
-      const int jj = e / k, kk = e - jj * k;
-      float h = 0.f, l = 0.f;
-      if (j0 + jj < n) ff_split(B[(size_t)(j0 + jj) * ldb + kk], h, l);
-      sBh[kk * 33 + jj] = h;
-      sBl[kk * 33 + jj] = l;
+    // consecutive threads read consecutive k of one row of B (coalesced),
+    // four loads in flight per thread before the splits
+    constexpr int NT = 32 * kRowsKG;
+    for (int e0 = threadIdx.x; e0 < 32 * k; e0 += 4 * NT) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int e = e0 + u * NT;
+        const int jj = e / k, kk = e - jj * k;
+        v[u] = e < 32 * k && j0 + jj < n ? B[(size_t)(j0 + jj) * ldb + kk] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int e = e0 + u * NT;
+        const int jj = e / k, kk = e - jj * k;
+        float h, l;
+        ff_split(v[u], h, l);
+        if (e < 32 * k) {
+          sBh[kk * 33 + jj] = h;
+          sBl[kk * 33 + jj] = l;
+        }
+      }
     }
   }
   __syncthreads();
@@ -166,7 +118,7 @@ __global__ void __launch_bounds__(32 * kRowsKG) k_ff_rows(int m, int n, int k, d
   if (TB || j < n) {
     for (int k0 = kb; k0 < ke; k0 += 32) {
       const int k1 = min(ke, k0 + 32);
-#pragma unroll 2
+#pragma unroll 4
       for (int kk = k0; kk < k1; kk++) {
         float bh, bl;
         if (TB) {
@@ -203,65 +155,103 @@ __global__ void __launch_bounds__(32 * kRowsKG) k_ff_rows(int m, int n, int k, d
 }
 
 // ------------------------------------------------------------------ long k
-// Grid (n tiles of 32*TN columns, k chunks); CTA of 32*m threads, warp r =
-// output row r.  ws[chunk][m][n] receives the chunk's (S, C) pairs.
-template <int TN, bool TB>
-__global__ void __launch_bounds__(1024) k_ff_long(int m, int n, int k, int kchunk,
-                                                  const double* __restrict__ A, int lda,
-                                                  const double* __restrict__ B, int ldb,
-                                                  float2* __restrict__ ws) {
+// Grid (n tiles of 32*TN columns, k chunks); CTA of 256 threads: warp w owns
+// output rows w, w + 8, ... (RW of them, m <= 8 RW), each lane TN columns,
+// so that all eight warps stage the operands whatever m is.  ws[chunk][m][n]
+// receives the chunk's (S, C) pairs.
+constexpr int kLongT = 256;
+template <int TN, int RW, bool TB>
+__global__ void __launch_bounds__(kLongT) k_ff_long(int m, int n, int k, int kchunk,
+                                                    const double* __restrict__ A, int lda,
+                                                    const double* __restrict__ B, int ldb,
+                                                    float2* __restrict__ ws) {
   constexpr int BN = 32 * TN;
   __shared__ float2 sA[32][33];      // [k][row]
   __shared__ float sBh[32][BN + 1];  // [k][column]
   __shared__ float sBl[32][BN + 1];
-  const int nth = blockDim.x;
-  const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0 = blockIdx.x * BN;
   const int kb = blockIdx.y * kchunk, ke = min(k, kb + kchunk);
-  float S[TN], Cc[TN];
+  float S[RW][TN], Cc[RW][TN];
 #pragma unroll
-  for (int t = 0; t < TN; t++) S[t] = Cc[t] = 0.f;
+  for (int i = 0; i < RW; i++)
+#pragma unroll
+    for (int t = 0; t < TN; t++) S[i][t] = Cc[i][t] = 0.f;
   for (int k0 = kb; k0 < ke; k0 += 32) {
     const int kn = min(32, ke - k0);
     __syncthreads();
-    for (int e = threadIdx.x; e < m * 32; e += nth) {
+    for (int e = threadIdx.x; e < m * 32; e += kLongT) {
       const int rr = e >> 5, kk = e & 31;
       float h = 0.f, l = 0.f;
       if (kk < kn) ff_split(A[(size_t)rr * lda + k0 + kk], h, l);
       sA[kk][rr] = make_float2(h, l);
     }
-    for (int e = threadIdx.x; e < BN * 32; e += nth) {
-      int jj, kk;
-      if (TB) {  // B [n][k]: consecutive threads along k
-        jj = e >> 5;
-        kk = e & 31;
-      } else {   // B [k][n]: consecutive threads along n
-        kk = e / BN;
-        jj = e - kk * BN;
+    // B: four loads in flight per thread before the splits
+    for (int e0 = threadIdx.x; e0 < BN * 32; e0 += 4 * kLongT) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int e = e0 + u * kLongT;
+        int jj, kk;
+        if (TB) {  // B [n][k]: consecutive threads along k
+          jj = e >> 5;
+          kk = e & 31;
+        } else {   // B [k][n]: consecutive threads along n
+          kk = e / BN;
+          jj = e - kk * BN;
+        }
+        v[u] = 0.0;
+        if (e < BN * 32 && kk < kn && c0 + jj < n)
+          v[u] = TB ? B[(size_t)(c0 + jj) * ldb + k0 + kk] : B[(size_t)(k0 + kk) * ldb + c0 + jj];
       }
-      float h = 0.f, l = 0.f;
-      if (kk < kn && c0 + jj < n)
-        ff_split(TB ? B[(size_t)(c0 + jj) * ldb + k0 + kk] : B[(size_t)(k0 + kk) * ldb + c0 + jj], h, l);
-      sBh[kk][jj] = h;
-      sBl[kk][jj] = l;
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int e = e0 + u * kLongT;
+        const int jj = TB ? e >> 5 : e % BN, kk = TB ? e & 31 : e / BN;
+        float h, l;
+        ff_split(v[u], h, l);
+        if (e < BN * 32) {
+          sBh[kk][jj] = h;
+          sBl[kk][jj] = l;
+        }
+      }
     }
     __syncthreads();
-    float s[TN], c[TN];
+    float s[RW][TN], c[RW][TN];
 #pragma unroll
-    for (int t = 0; t < TN; t++) s[t] = c[t] = 0.f;
-#pragma unroll 4
+    for (int i = 0; i < RW; i++)
+#pragma unroll
+      for (int t = 0; t < TN; t++) s[i][t] = c[i][t] = 0.f;
+#pragma unroll 2
     for (int kk = 0; kk < 32; kk++) {  // rows past kn are zero
-      const float2 a = sA[kk][r];
+      float bh[TN], bl[TN];
 #pragma unroll
-      for (int t = 0; t < TN; t++) ff_term(a.x, a.y, sBh[kk][lane + 32 * t], sBl[kk][lane + 32 * t], s[t], c[t]);
+      for (int t = 0; t < TN; t++) {
+        bh[t] = sBh[kk][lane + 32 * t];
+        bl[t] = sBl[kk][lane + 32 * t];
+      }
+#pragma unroll
+      for (int i = 0; i < RW; i++) {
+        if (w + 8 * i < m) {  // warp-uniform
+          const float2 a = sA[kk][w + 8 * i];
+#pragma unroll
+          for (int t = 0; t < TN; t++) ff_term(a.x, a.y, bh[t], bl[t], s[i][t], c[i][t]);
+        }
+      }
     }
 #pragma unroll
-    for (int t = 0; t < TN; t++) ff_add(S[t], Cc[t], s[t], c[t]);
+    for (int i = 0; i < RW; i++)
+#pragma unroll
+      for (int t = 0; t < TN; t++) ff_add(S[i][t], Cc[i][t], s[i][t], c[i][t]);
   }
 #pragma unroll
-  for (int t = 0; t < TN; t++) {
-    const int col = c0 + lane + 32 * t;
-    if (col < n) ws[((size_t)blockIdx.y * m + r) * n + col] = make_float2(S[t], Cc[t]);
+  for (int i = 0; i < RW; i++) {
+    const int r = w + 8 * i;
+#pragma unroll
+    for (int t = 0; t < TN; t++) {
+      const int col = c0 + lane + 32 * t;
+      if (r < m && col < n) ws[((size_t)blockIdx.y * m + r) * n + col] = make_float2(S[i][t], Cc[i][t]);
+    }
   }
 }
 
@@ -314,19 +304,27 @@ void rows_dispatch(int m, int n, int k, double alpha, const double* A, int lda, 
 #undef RIS_FF_RM
 }
 
-template <int TN, bool TB>
+template <int TN, int RW, bool TB>
 void launch_long(dim3 grid, int m, int n, int k, int kchunk, const double* A, int lda,
                  const double* B, int ldb, float2* ws, cudaStream_t st) {
-  k_ff_long<TN, TB><<<grid, 32 * m, 0, st>>>(m, n, k, kchunk, A, lda, B, ldb, ws);
+  k_ff_long<TN, RW, TB><<<grid, kLongT, 0, st>>>(m, n, k, kchunk, A, lda, B, ldb, ws);
+}
+
+template <int TN, bool TB>
+void long_rows(dim3 grid, int m, int n, int k, int kchunk, const double* A, int lda,
+               const double* B, int ldb, float2* ws, cudaStream_t st) {
+  if (m <= 8) return launch_long<TN, 1, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
+  if (m <= 16) return launch_long<TN, 2, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
+  return launch_long<TN, 4, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
 }
 
 template <bool TB>
 void long_dispatch(int tn, dim3 grid, int m, int n, int k, int kchunk, const double* A, int lda,
                    const double* B, int ldb, float2* ws, cudaStream_t st) {
-  if (tn == 1) return launch_long<1, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
-  if (tn == 2) return launch_long<2, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
-  if (tn == 3) return launch_long<3, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
-  return launch_long<4, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
+  if (tn == 1) return long_rows<1, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
+  if (tn == 2) return long_rows<2, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
+  if (tn == 3) return long_rows<3, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
+  return long_rows<4, TB>(grid, m, n, k, kchunk, A, lda, B, ldb, ws, st);
 }
 
 }  // namespace

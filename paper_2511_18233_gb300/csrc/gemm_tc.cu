@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "gemm_tc.cuh"
+#include "ff_arith.cuh"
 #include "tc_ptx.cuh"
 
 namespace ris {
@@ -253,13 +254,28 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ CUte
   }
 }
 
-__global__ void k_tc_reduce(int M, int N, int ksplit, const float* __restrict__ part, double alpha,
-                            double beta, double* __restrict__ C, int ldc) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)M * N) return;
+// The FP32 partial sums of the K slices are added in double-FP32 (TwoSum on
+// the FP32 pipe, as exact as an FP64 sum) and widened once, so the FP64 pipe
+// only applies alpha and beta.  32 outputs per CTA: warp g adds the slices
+// g, g + 8, ... in order, then warp 0 the eight sums in order (a skinny
+// product's many slices spread over many SMs; same result every run).
+__global__ void __launch_bounds__(256) k_tc_reduce(int M, int N, int ksplit,
+                                                   const float* __restrict__ part, double alpha,
+                                                   double beta, double* __restrict__ C, int ldc) {
+  __shared__ float2 red[8][32];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const long long mn = (long long)M * N;
+  const long long t = (long long)blockIdx.x * 32 + lane;
+  float S = 0.f, Cc = 0.f;
+  if (t < mn)
+    for (int z = g; z < ksplit; z += 8) ff_add(S, Cc, part[(size_t)z * mn + t], 0.f);
+  red[g][lane] = make_float2(S, Cc);
+  __syncthreads();
+  if (g != 0 || t >= mn) return;
+#pragma unroll
+  for (int h = 1; h < 8; h++) ff_add(S, Cc, red[h][lane].x, red[h][lane].y);
   const int i = (int)(t / N), j = (int)(t % N);
-  double s = 0.0;
-  for (int z = 0; z < ksplit; z++) s += (double)part[(size_t)z * M * N + t];
+  const double s = ff_widen(S) + ff_widen(Cc);
   double* p = C + (size_t)i * ldc + j;
   *p = beta == 0.0 ? alpha * s : fma(alpha, s, beta * *p);
 }
@@ -403,8 +419,8 @@ void tc_gemm(int M, int N, int K, const TcOperand& A, const TcOperand& B, int nb
   k_tc_gemm<<<grid, 128, SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a);
   RIS_CHECK_LAUNCH();
   if (a.ksplit > 1) {
-    k_tc_reduce<<<cdiv((long long)M * N, 256), 256, 0, st>>>(M, N, a.ksplit, part, ep.alpha, ep.beta,
-                                                             ep.c64, (int)ep.rs);
+    k_tc_reduce<<<cdiv((long long)M * N, 32), 256, 0, st>>>(M, N, a.ksplit, part, ep.alpha, ep.beta,
+                                                            ep.c64, (int)ep.rs);
     RIS_CHECK_LAUNCH();
     if (own_part) dev_free(part, sizeof(float) * (size_t)a.ksplit * M * N, st, part_tr);
   }

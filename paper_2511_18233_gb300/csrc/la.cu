@@ -4,8 +4,9 @@
 //   problem, up to 4x4 per thread), batched over two strided levels,
 //   transposes folded into the tile loads, split along k for few tiles.
 // * cholesky / tri_inverse: the metric factor M = L L^T of Eq. (g_modified)
-//   and L^{-1}; left-looking, one CTA (the metric is at most a few thousand
-//   functions for one molecule of the ris basis).
+//   and L^{-1}; the factorisation on one CTA (the metric is at most a few
+//   thousand functions for one molecule of the ris basis), the inverse one
+//   warp per column over many CTAs.
 // * sym_eig_lowest: lowest k eigenpairs of a small symmetric matrix (the
 //   Davidson subspace problem): Householder reduction to tridiagonal form
 //   (one CTA), then one CTA per eigenvalue for Sturm-sequence multisection,
@@ -344,10 +345,10 @@ __global__ void __launch_bounds__(1024) k_cholesky_smem(double* A, int n, int* i
     for (int i = j + 1 + tid; i < n; i += 1024) S[(size_t)i * n + j] /= pj;
     __syncthreads();
     // trailing lower triangle: S[i][k] -= S[i][j] S[k][j], j < k <= i
-    const int m = n - j - 1;
-    for (long long t = tid; t < (long long)m * m; t += 1024) {
-      const int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
-      if (k <= i) S[(size_t)i * n + k] -= S[(size_t)i * n + j] * S[(size_t)k * n + j];
+    // (warps over rows, lanes over columns)
+    for (int i = j + 1 + (tid >> 5); i < n; i += 32) {
+      const double sij = S[(size_t)i * n + j];
+      for (int k = j + 1 + (tid & 31); k <= i; k += 32) S[(size_t)i * n + k] -= sij * S[(size_t)k * n + j];
     }
     __syncthreads();
   }
@@ -383,39 +384,55 @@ __global__ void k_tri_inverse(const double* __restrict__ L, double* __restrict__
   }
 }
 
-// Shared-memory form for n <= kSmemChol: L staged once, one thread per
-// column j of X = L^-1.  Thread j keeps X[k][j] (k > j) in the upper
-// triangle of its own row of the staged copy (Ls[j][k], zero in L), which no
-// other thread reads; two partial sums shorten the dependent chain.
-__global__ void __launch_bounds__(kSmemChol) k_tri_inverse_smem(const double* __restrict__ L,
-                                                                double* __restrict__ X, int n) {
-  extern __shared__ double Ls[];
-  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) Ls[e] = L[e];
+// One warp per column j of X = L^-1 (four per CTA, CTAs over the columns):
+// column-oriented forward substitution of L x = e_j.  Lane l holds the
+// right-hand side of rows l, l + 32, ...; at step k the owner of row k
+// forms x_k = b_k / L_kk (reciprocals of the diagonal formed once per CTA)
+// and broadcasts it, and every lane updates its rows below k.  L is staged
+// transposed in shared memory so that a step's reads are consecutive.
+constexpr int kTriRB = 5;  // rows per lane: n <= 160
+__global__ void __launch_bounds__(128) k_tri_inverse_cols(const double* __restrict__ L,
+                                                          double* __restrict__ X, int n) {
+  extern __shared__ double tri_sh[];
+  double* Lt = tri_sh;  // Lt[k][i] = L[i][k]
+  double* rd = Lt + (size_t)n * n;
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), k = (int)(e % n);
+    Lt[(size_t)k * n + i] = L[e];
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rd[i] = 1.0 / L[(size_t)i * n + i];
   __syncthreads();
-  const int j = threadIdx.x;
-  if (j >= n) return;
-  for (int i = 0; i < j; i++) X[(size_t)i * n + j] = 0.0;
-  const double xj = 1.0 / Ls[(size_t)j * n + j];
-  X[(size_t)j * n + j] = xj;
-  for (int i = j + 1; i < n; i++) {
-    double a0 = Ls[(size_t)i * n + j] * xj, a1 = 0.0;
-    int k = j + 1;
-    for (; k + 1 < i; k += 2) {
-      a0 += Ls[(size_t)i * n + k] * Ls[(size_t)j * n + k];
-      a1 += Ls[(size_t)i * n + k + 1] * Ls[(size_t)j * n + k + 1];
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (j >= n) return;  // whole warp
+  double b[kTriRB];
+#pragma unroll
+  for (int r = 0; r < kTriRB; r++) b[r] = 32 * r + lane == j ? 1.0 : 0.0;
+  for (int i = lane; i < j; i += 32) X[(size_t)i * n + j] = 0.0;
+#pragma unroll
+  for (int r = 0; r < kTriRB; r++) {
+    for (int kk = 0; kk < 32; kk++) {
+      const int k = 32 * r + kk;
+      if (k >= n) break;
+      if (k < j) continue;
+      const double xk = __shfl_sync(0xffffffffu, b[r], kk) * rd[k];
+      if (lane == kk) X[(size_t)k * n + j] = xk;
+      const double* lk = Lt + (size_t)k * n;
+#pragma unroll
+      for (int r2 = r; r2 < kTriRB; r2++) {
+        const int i = 32 * r2 + lane;
+        if (i > k && i < n) b[r2] = fma(-lk[i], xk, b[r2]);
+      }
     }
-    if (k < i) a0 += Ls[(size_t)i * n + k] * Ls[(size_t)j * n + k];
-    const double v = -(a0 + a1) / Ls[(size_t)i * n + i];
-    Ls[(size_t)j * n + i] = v;
-    X[(size_t)i * n + j] = v;
   }
 }
 
 void tri_inverse(const double* L, double* Linv, int n, cudaStream_t st) {
-  if (n <= kSmemChol) {
-    const size_t smem = (size_t)n * n * sizeof(double);
-    ensure_smem_attr((const void*)k_tri_inverse_smem, (int)((size_t)kSmemChol * kSmemChol * sizeof(double)));
-    k_tri_inverse_smem<<<1, kSmemChol, smem, st>>>(L, Linv, n);
+  if (n <= 32 * kTriRB) {
+    const size_t smem = ((size_t)n * n + n) * sizeof(double);
+    ensure_smem_attr((const void*)k_tri_inverse_cols,
+                     (int)(((size_t)32 * kTriRB * 32 * kTriRB + 32 * kTriRB) * sizeof(double)));
+    k_tri_inverse_cols<<<cdiv(n, 4), 128, smem, st>>>(L, Linv, n);
   } else {
     k_tri_inverse<<<cdiv(n, 32), 32, 0, st>>>(L, Linv, n);
   }
@@ -502,7 +519,8 @@ __global__ void __launch_bounds__(kEigT) k_eig_tridiag(const double* H, int ldH,
   extern __shared__ double sm_A[];
   __shared__ double red[33];
   __shared__ double sh_alpha, sh_tau;
-  __shared__ double p[kEigMaxM];  // A_sub v of the current step
+  __shared__ double p[kEigMaxM];   // A_sub v of the current step
+  __shared__ double vc[kEigMaxM];  // the current Householder vector (column c below the diagonal)
   EigWork W(work, m);
   double* A = use_smem ? sm_A : W.A;
   double* d = W.d;
@@ -539,22 +557,30 @@ __global__ void __launch_bounds__(kEigT) k_eig_tridiag(const double* H, int ldH,
     __syncthreads();
     const double t = sh_tau;
     if (t == 0.0) continue;
-    // p = t * A_sub v, using symmetry for coalesced reads
+    for (int i = c + 1 + tid; i < m; i += kEigT) vc[i] = A[(size_t)i * m + c];
+    __syncthreads();
+    // p = t * A_sub v, using symmetry for coalesced reads (two partial sums
+    // shorten the dependent FP64 chain)
     for (int i = c + 1 + tid; i < m; i += kEigT) {
-      double acc = 0.0;
-      for (int j = c + 1; j < m; j++) acc += A[(size_t)j * m + i] * A[(size_t)j * m + c];
-      p[i] = t * acc;
+      double a0 = 0.0, a1 = 0.0;
+      int j = c + 1;
+      for (; j + 1 < m; j += 2) {
+        a0 += A[(size_t)j * m + i] * vc[j];
+        a1 += A[(size_t)(j + 1) * m + i] * vc[j + 1];
+      }
+      if (j < m) a0 += A[(size_t)j * m + i] * vc[j];
+      p[i] = t * (a0 + a1);
     }
     __syncthreads();
     part = 0.0;
-    for (int i = c + 1 + tid; i < m; i += kEigT) part += p[i] * A[(size_t)i * m + c];
+    for (int i = c + 1 + tid; i < m; i += kEigT) part += p[i] * vc[i];
     const double K = 0.5 * t * block_sum<kEigT>(part, red);
-    for (int i = c + 1 + tid; i < m; i += kEigT) p[i] -= K * A[(size_t)i * m + c];
+    for (int i = c + 1 + tid; i < m; i += kEigT) p[i] -= K * vc[i];
     __syncthreads();
-    const int ms = m - c - 1;
-    for (size_t ij = tid; ij < (size_t)ms * ms; ij += kEigT) {
-      const int i = c + 1 + (int)(ij / ms), j = c + 1 + (int)(ij % ms);
-      A[(size_t)i * m + j] -= A[(size_t)i * m + c] * p[j] + p[i] * A[(size_t)j * m + c];
+    // rank-2 update of the trailing block: warps over rows, lanes over columns
+    for (int i = c + 1 + (tid >> 5); i < m; i += kEigT / 32) {
+      const double vi = vc[i], pi = p[i];
+      for (int j = c + 1 + (tid & 31); j < m; j += 32) A[(size_t)i * m + j] -= vi * p[j] + pi * vc[j];
     }
     __syncthreads();
   }
@@ -787,6 +813,7 @@ __global__ void __launch_bounds__(kEigT) k_eig_tridiag32(const double* H, int ld
   __shared__ float red[33];
   __shared__ float sh_alpha, sh_tau;
   __shared__ float p[kEigMaxM];
+  __shared__ float vc[kEigMaxM];
   EigWork W(work, m);
   float* A = sA32;
   const int tid = threadIdx.x;
@@ -820,21 +847,22 @@ __global__ void __launch_bounds__(kEigT) k_eig_tridiag32(const double* H, int ld
     __syncthreads();
     const float tt = sh_tau;
     if (tt == 0.f) continue;
+    for (int i = c + 1 + tid; i < m; i += kEigT) vc[i] = A[(size_t)i * m + c];
+    __syncthreads();
     for (int i = c + 1 + tid; i < m; i += kEigT) {
       float acc = 0.f;
-      for (int j = c + 1; j < m; j++) acc += A[(size_t)j * m + i] * A[(size_t)j * m + c];
+      for (int j = c + 1; j < m; j++) acc += A[(size_t)j * m + i] * vc[j];
       p[i] = tt * acc;
     }
     __syncthreads();
     part = 0.f;
-    for (int i = c + 1 + tid; i < m; i += kEigT) part += p[i] * A[(size_t)i * m + c];
+    for (int i = c + 1 + tid; i < m; i += kEigT) part += p[i] * vc[i];
     const float K = 0.5f * tt * block_sum<kEigT>(part, red);
-    for (int i = c + 1 + tid; i < m; i += kEigT) p[i] -= K * A[(size_t)i * m + c];
+    for (int i = c + 1 + tid; i < m; i += kEigT) p[i] -= K * vc[i];
     __syncthreads();
-    const int ms = m - c - 1;
-    for (size_t ij = tid; ij < (size_t)ms * ms; ij += kEigT) {
-      const int i = c + 1 + (int)(ij / ms), j = c + 1 + (int)(ij % ms);
-      A[(size_t)i * m + j] -= A[(size_t)i * m + c] * p[j] + p[i] * A[(size_t)j * m + c];
+    for (int i = c + 1 + (tid >> 5); i < m; i += kEigT / 32) {
+      const float vi = vc[i], pi = p[i];
+      for (int j = c + 1 + (tid & 31); j < m; j += 32) A[(size_t)i * m + j] -= vi * p[j] + pi * vc[j];
     }
     __syncthreads();
   }
