@@ -1542,10 +1542,11 @@ void Engine::emu_abt(int M, int N, int K, const double* A, long long rsA, long l
 }
 
 // Mixed precision: (ab|P)_K = sum_mu,nu C_mu,a C_nu,b (mu nu|P) by two
-// 3xTF32 tensor-core transforms, then B = (ab|P) L_K^-T in FP64 (out
-// [a][b][R]).  Half transform 1: H[a][P][nu] = sum_mu C_v^T[a][mu] T[(P,nu)][mu]
+// 3xTF32 tensor-core transforms, then B = (ab|P) L_K^-T by a third (out
+// [a][b][R]; the K metric is well conditioned, its smallest eigenvalue about
+// 0.05).  Half transform 1: H[a][P][nu] = sum_mu C_v^T[a][mu] T[(P,nu)][mu]
 // with T[(P,nu)][mu] = (nu mu|P) (symmetric in mu, nu); transform 2:
-// G[(a,P)][b] = sum_nu H[(a,P)][nu] C_v^T[b][nu].
+// G[a][b][P] = sum_nu C_v^T[b][nu] H[(a,P)][nu].
 void Engine::build_Kvv_tc(double* out) {
   const int o = nocc, v = nvir, n = nao;
   const int ldn = ld4(n);
@@ -1564,14 +1565,21 @@ void Engine::build_Kvv_tc(double* out) {
     e.cld = ldn;
     tcg(v, nK * n, n, CvTh.p, CvTl.p, ldn, Th.p, Tl.p, ldn, 0, 1, e, d_tcerr, st);
   }
-  SBuf<double> G((size_t)v * nK * v, st);
-  tcg(v * nK, v, n, Hh.p, Hl.p, ldn, CvTh.p, CvTl.p, ldn, 0, 1, ep_f64(G.p, v), d_tcerr, st);
-  // out[a][b][R] = sum_P G[a][P][b] L^-1[R][P]
-  GemmBatch bt;
-  bt.nb1 = v;
-  bt.sA1 = (long long)nK * v;
-  bt.sC1 = (long long)v * nK;
-  dgemm(true, true, v, nK, nK, 1.0, G.p, v, LKinv.p, nK, 0.0, out, nK, st, bt);
+  // G[b][(a,P)] = sum_nu C_v^T[b][nu] H[(a,P)][nu], stored split as
+  // [a][b][P] (P padded to lk, zero) so that it is the K-major operand of the
+  // metric product; consecutive lanes of the epilogue write consecutive P
+  const int lk = ld4(nK);
+  SBuf<float> Gh((size_t)v * v * lk, st, true), Gl((size_t)v * v * lk, st, true);
+  {
+    TcEpilogue e = ep_split(Gh.p, Gl.p, lk);
+    e.cin = nK;
+    e.cld = (long long)v * lk;
+    tcg(v, v * nK, n, CvTh.p, CvTl.p, ldn, Hh.p, Hl.p, ldn, 0, 1, e, d_tcerr, st);
+  }
+  // out[(a,b)][R] = sum_P G[a][b][P] L^-1[R][P] (3xTF32, one GEMM over every (a, b))
+  SBuf<float> Lh((size_t)nK * lk, st), Ll((size_t)nK * lk, st);
+  split_f64(LKinv.p, nK, nK, nK, Lh.p, Ll.p, lk, st);
+  tcg(v * v, nK, nK, Gh.p, Gl.p, lk, Lh.p, Ll.p, lk, 0, 1, ep_f64(out, nK), d_tcerr, st);
   // restore the exact a <-> b symmetry that rounding broke (A must stay symmetric)
   k_sym_pairs<<<cdiv((long long)v * v * nK, 256), 256, 0, st>>>(out, v, nK);
   RIS_CHECK_LAUNCH();

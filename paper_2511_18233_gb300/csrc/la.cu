@@ -486,6 +486,40 @@ __device__ int sturm_count(const double* d, const double* e2, int m, double x) {
   return c;
 }
 
+// The same count from the signs of the leading principal minors
+// p_i = det(T_i - x I): p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}, one
+// sign change per eigenvalue below x (p_i / p_{i-1} is the pivot above; a
+// zero minor counts as a change, as a zero pivot taken negative).  No
+// division: per step one subtraction, one product and one FMA on the FP64
+// pipe, the dependent chain a single FMA (against a reciprocal and three
+// operations for the pivots, which matters on this part's narrow FP64
+// pipe); signs and exponents are read from the bit patterns.  The pair
+// (p_{i-1}, p_i) is rescaled by a power of two when the larger leaves
+// [2^-500, 2^500] (exact; the signs are unchanged).
+__device__ __forceinline__ int dexp(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+}
+__device__ int sturm_count_minors(const double* d, const double* e2, int m, double x) {
+  double p0 = 1.0, p1 = d[0] - x;
+  if (dexp(p1) == 0) p1 = -1e-300;  // zero (or subnormal): a change
+  int c = __double_as_longlong(p1) < 0 ? 1 : 0;
+  for (int i = 1; i < m; i++) {
+    double p2 = fma(d[i] - x, p1, -(e2[i - 1] * p0));
+    const long long b1 = __double_as_longlong(p1);
+    if (dexp(p2) == 0) p2 = b1 < 0 ? 1e-300 : -1e-300;  // a zero minor: a change
+    c += (__double_as_longlong(p2) < 0) != (b1 < 0);
+    const int ex = max(dexp(p1), dexp(p2));
+    if (ex > 1023 + 500 || ex < 1023 - 500) {
+      const double sc = __longlong_as_double((long long)(2046 - ex) << 52);  // 2^(1023 - ex)
+      p2 *= sc;
+      p1 *= sc;
+    }
+    p0 = p1;
+    p1 = p2;
+  }
+  return c;
+}
+
 // The work array holds A (m x m: Householder vectors below the diagonal),
 // d, e, tau (m each), the eigenvalues (64) and the eigenvectors (k x m).
 struct EigWork {
@@ -559,17 +593,23 @@ __global__ void __launch_bounds__(kEigT) k_eig_tridiag(const double* H, int ldH,
     if (t == 0.0) continue;
     for (int i = c + 1 + tid; i < m; i += kEigT) vc[i] = A[(size_t)i * m + c];
     __syncthreads();
-    // p = t * A_sub v, using symmetry for coalesced reads (two partial sums
-    // shorten the dependent FP64 chain)
-    for (int i = c + 1 + tid; i < m; i += kEigT) {
+    // p = t * A_sub v, using symmetry for coalesced reads: two threads per
+    // row (alternate j), two partial sums each, so that the dependent FP64
+    // chains are a quarter of the row long
+    for (int i0 = c + 1; i0 < m; i0 += kEigT / 2) {  // uniform: the shuffle needs every lane
+      const int i = i0 + (tid >> 1), h = tid & 1;
       double a0 = 0.0, a1 = 0.0;
-      int j = c + 1;
-      for (; j + 1 < m; j += 2) {
-        a0 += A[(size_t)j * m + i] * vc[j];
-        a1 += A[(size_t)(j + 1) * m + i] * vc[j + 1];
+      if (i < m) {
+        int j = c + 1 + h;
+        for (; j + 2 < m; j += 4) {
+          a0 += A[(size_t)j * m + i] * vc[j];
+          a1 += A[(size_t)(j + 2) * m + i] * vc[j + 2];
+        }
+        if (j < m) a0 += A[(size_t)j * m + i] * vc[j];
       }
-      if (j < m) a0 += A[(size_t)j * m + i] * vc[j];
-      p[i] = t * (a0 + a1);
+      double acc = a0 + a1;
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (i < m && h == 0) p[i] = t * acc;
     }
     __syncthreads();
     part = 0.0;
@@ -605,7 +645,7 @@ constexpr int kEigVecT = 128;
 // eigenvalues runs on as many SMs): lambda_j by multisection on Sturm
 // counts, 32 points per step (33-fold shrink): FP32 counts down to a
 // bracket of 1e-5 ||T||, widened by 1e-5 ||T|| on each side (over 100 times
-// the FP32 count error), then FP64 counts to full precision; the
+// the FP32 count error), then FP64 counts down to 3e-14 ||T||; the
 // eigenvector of T by inverse iteration (Gaussian elimination with partial
 // pivoting of T - lambda_j I, three solves), and its back-transformation
 // x = H_0 ... H_{m-3} z.  Householder vectors in shared memory when
@@ -663,12 +703,14 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work, int a
     }
     lo = fmax(lo - coarse, glo - 1e-12 * tnorm);
     hi = fmin(hi + coarse, ghi + 1e-12 * tnorm);
-    // fine: FP64 counts (the counts that decide the final bracket)
+    // fine: FP64 counts (the counts that decide the final bracket), down to
+    // a bracket of 3e-14 ||T|| (the midpoint then within 1.5e-14 ||T||, far
+    // below what the Davidson residuals resolve) or the FP64 resolution
     for (int it = 0; it < 40; it++) {
       const double h = (hi - lo) / 33.0;
-      if (!(h > 0.0) || lo + h <= lo) break;
+      if (!(h > 0.0) || lo + h <= lo || hi - lo <= 3e-14 * tnorm) break;
       const double x = lo + h * (lane + 1);
-      const bool above = sturm_count(d, e2, m, x) > j;  // lambda_j < x
+      const bool above = sturm_count_minors(d, e2, m, x) > j;  // lambda_j < x
       const unsigned mask = __ballot_sync(0xffffffffu, above);
       const int f = mask ? __ffs(mask) - 1 : 32;  // first point above lambda_j
       const double nlo = f == 0 ? lo : lo + h * f;
