@@ -673,11 +673,6 @@ __global__ void k_symmetrize_sq(double* __restrict__ X, int n, int nb) {
   M[(size_t)j * n + i] = m;
 }
 
-__global__ void k_to_f32(const double* __restrict__ x, long long n, float* __restrict__ y) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) y[t] = (float)x[t];
-}
-
 // cU[s][jU[Q]] = cJ[s][Q] (union index), zero elsewhere (cU zeroed by the caller)
 __global__ void k_expand_cJ(const double* __restrict__ cJ, const int* __restrict__ jU, int ns,
                             int nJ, int nU, double* __restrict__ cU) {
@@ -722,13 +717,47 @@ __host__ __device__ inline void slice_range(int nao, int nslice, int s, int& lo,
   hi = (int)((long long)nao * (s + 1) / nslice);
 }
 
+// State densities regrouped for the contraction: DRt[batch][mu][nu][b] =
+// DR_{8 batch + b}[mu][nu] (zero past the last state), so that a partner's
+// eight weights are two (FP32) or four (FP64) vector loads.
+template <class T>
+__global__ void k_states_t(const double* __restrict__ DR, int nsu, int nao, T* __restrict__ out) {
+  const long long nn2 = (long long)nao * nao;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nn2) return;
+  const int batch = blockIdx.y;
+  T v[kCBatch];
+#pragma unroll
+  for (int b = 0; b < kCBatch; b++) {
+    const int s = batch * kCBatch + b;
+    v[b] = s < nsu ? (T)DR[(size_t)s * nn2 + t] : (T)0;
+  }
+  T* o = out + ((size_t)batch * nn2 + t) * kCBatch;
+#pragma unroll
+  for (int b = 0; b < kCBatch; b++) o[b] = v[b];
+}
+
+__device__ __forceinline__ void load_w8(const float* p, float (&w)[kCBatch]) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+}
+__device__ __forceinline__ void load_w8(const double* p, double (&w)[kCBatch]) {
+#pragma unroll
+  for (int h = 0; h < 4; h++) {
+    const double2 a = *reinterpret_cast<const double2*>(p + 2 * h);
+    w[2 * h] = a.x;
+    w[2 * h + 1] = a.y;
+  }
+}
+
 // Coulomb part, per state (the pair densities are linear in the per-state
 // transition densities): part[slice][b][x][mu][P] = sum_{nu in slice}
-// D[x][mu][nu][P] DRs_{s0+b}[mu][nu], b < ns <= kCBatch, DRs symmetrised.
+// D[x][mu][nu][P] DRt[mu][nu][b], b < ns <= kCBatch, DRt the batch's
+// symmetrised state densities regrouped by k_states_t.
 template <class T>
 __global__ void __launch_bounds__(128) k_contract_states(const T* __restrict__ D,
-                                                         const T* __restrict__ DRs, int s0,
-                                                         int ns, int nao, int nU, int nslice,
+                                                         const T* __restrict__ DRt, int ns,
+                                                         int nao, int nU, int nslice,
                                                          const int* __restrict__ nbPtr,
                                                          const int* __restrict__ nbCol,
                                                          double* __restrict__ part) {
@@ -747,7 +776,7 @@ __global__ void __launch_bounds__(128) k_contract_states(const T* __restrict__ D
   for (int b = 0; b < kCBatch; b++)
 #pragma unroll
     for (int x = 0; x < 3; x++) y[b][x] = 0.0, c[b][x] = (T)0;
-  const T* dr = DRs + (size_t)s0 * nn2 + (size_t)mu * nao;
+  const T* dr = DRt + (size_t)mu * nao * kCBatch;
   // runs of kChunk partners: products summed in T, runs in FP64; the inner
   // loop is unrolled so that several partners' loads are in flight
   for (int qc = q0; qc < q1; qc += kChunk) {
@@ -757,13 +786,14 @@ __global__ void __launch_bounds__(128) k_contract_states(const T* __restrict__ D
       const int nu = nbCol[q];
       const size_t a = ((size_t)mu * nao + nu) * nU + P;
       const T d0 = D[a], d1 = D[plane + a], d2 = D[2 * plane + a];
+      T w[kCBatch];
+      load_w8(dr + (size_t)nu * kCBatch, w);
 #pragma unroll
       for (int b = 0; b < kCBatch; b++) {
         if (b >= ns) break;
-        const T w = dr[(size_t)b * nn2 + nu];
-        c[b][0] += d0 * w;
-        c[b][1] += d1 * w;
-        c[b][2] += d2 * w;
+        c[b][0] += d0 * w[b];
+        c[b][1] += d1 * w[b];
+        c[b][2] += d2 * w[b];
       }
     }
 #pragma unroll
@@ -2560,23 +2590,26 @@ void Engine::pair_derivs(int npair, const int* pairs, int nx, const double* X_in
   SBuf<double> Yst((size_t)nsu * 3 * nn * nU, st);
   prof_begin(kProfContract, st);
   const double dbytes = mixed ? 4.0 : 8.0;  // derivative integrals in FP32 / FP64
-  SBuf<float> DRf;
-  if (mixed) {
-    DRf.ensure((size_t)nsu * nn * nn, st);
-    k_to_f32<<<cdiv((long long)nsu * nn * nn, 256), 256, 0, st>>>(DR.p, (long long)nsu * nn * nn,
-                                                                  DRf.p);
-    RIS_CHECK_LAUNCH();
-  }
+  const int nbat = cdiv(nsu, kCBatch);
+  const size_t dtb = (size_t)nn * nn * kCBatch;  // one batch of regrouped densities
+  SBuf<float> DRf(mixed ? nbat * dtb : 1, st);
+  SBuf<double> DRd(mixed ? 1 : nbat * dtb, st);
+  if (mixed)
+    k_states_t<float><<<dim3(cdiv((long long)nn * nn, 256), nbat), 256, 0, st>>>(DR.p, nsu, nn, DRf.p);
+  else
+    k_states_t<double><<<dim3(cdiv((long long)nn * nn, 256), nbat), 256, 0, st>>>(DR.p, nsu, nn, DRd.p);
+  RIS_CHECK_LAUNCH();
   const int slJ = pick_slices((long long)nn * nU, nbAvg);
   SBuf<double> partJ((size_t)slJ * std::min(nsu, kCBatch) * 3 * nn * nU, st);
   for (int s0 = 0; s0 < nsu; s0 += kCBatch) {
     const int ns = std::min(kCBatch, nsu - s0);
     const dim3 grid(cdiv((long long)nn * nU, 128), slJ);
+    const size_t bo = (size_t)(s0 / kCBatch) * dtb;
     if (mixed)
-      k_contract_states<float><<<grid, 128, 0, st>>>(Df.p, DRf.p, s0, ns, nn, nU, slJ, nbPtr.p,
+      k_contract_states<float><<<grid, 128, 0, st>>>(Df.p, DRf.p + bo, ns, nn, nU, slJ, nbPtr.p,
                                                      nbCol.p, partJ.p);
     else
-      k_contract_states<double><<<grid, 128, 0, st>>>(D.p, DR.p, s0, ns, nn, nU, slJ, nbPtr.p,
+      k_contract_states<double><<<grid, 128, 0, st>>>(D.p, DRd.p + bo, ns, nn, nU, slJ, nbPtr.p,
                                                       nbCol.p, partJ.p);
     RIS_CHECK_LAUNCH();
     const long long cnt = (long long)ns * 3 * nn * nU;
@@ -3262,11 +3295,17 @@ void Engine::pair_derivs_streamed(int npair, const int* pairs, int nsu, const st
   dgemm(false, false, nsu, nJ, nJ, 1.0, w5.p, nJ, LJinv.p, nJ, 0.0, cJ.p, nJ, st);
   k_symmetrize_sq<<<cdiv((long long)nsu * nn * nn, 256), 256, 0, st>>>(DR.p, nn, nsu);
   RIS_CHECK_LAUNCH();
+  // state densities regrouped [batch][mu][nu][b] for the contraction
+  const int nbat = cdiv(nsu, kCBatch);
+  const size_t dtb = (size_t)nn * nn * kCBatch;
+  SBuf<double> DRd(mixed ? 1 : nbat * dtb, st);
   if (mixed) {
-    DRf.ensure((size_t)nsu * nn * nn, st);
-    k_to_f32<<<cdiv((long long)nsu * nn * nn, 256), 256, 0, st>>>(DR.p, (long long)nsu * nn * nn, DRf.p);
-    RIS_CHECK_LAUNCH();
+    DRf.ensure(nbat * dtb, st);
+    k_states_t<float><<<dim3(cdiv((long long)nn * nn, 256), nbat), 256, 0, st>>>(DR.p, nsu, nn, DRf.p);
+  } else {
+    k_states_t<double><<<dim3(cdiv((long long)nn * nn, 256), nbat), 256, 0, st>>>(DR.p, nsu, nn, DRd.p);
   }
+  RIS_CHECK_LAUNCH();
   SBuf<double> cU((size_t)nsu * nU, st, true);
   k_expand_cJ<<<cdiv(nsu * nJ, 256), 256, 0, st>>>(cJ.p, d_jU, nsu, nJ, nU, cU.p);
   RIS_CHECK_LAUNCH();
@@ -3378,11 +3417,12 @@ void Engine::pair_derivs_streamed(int npair, const int* pairs, int nsu, const st
         for (int s0 = 0; s0 < nsu; s0 += kCBatch) {
           const int ns = std::min(kCBatch, nsu - s0);
           const dim3 grid(cdiv((long long)nn * w, 128), slJ);
+          const size_t bo = (size_t)(s0 / kCBatch) * dtb;
           if (mixed)
-            k_contract_states<float><<<grid, 128, 0, st>>>(D32.p, DRf.p, s0, ns, nn, w, slJ, nbPtr.p,
+            k_contract_states<float><<<grid, 128, 0, st>>>(D32.p, DRf.p + bo, ns, nn, w, slJ, nbPtr.p,
                                                            nbCol.p, partJ.p);
           else
-            k_contract_states<double><<<grid, 128, 0, st>>>(D64.p, DR.p, s0, ns, nn, w, slJ, nbPtr.p,
+            k_contract_states<double><<<grid, 128, 0, st>>>(D64.p, DRd.p + bo, ns, nn, w, slJ, nbPtr.p,
                                                             nbCol.p, partJ.p);
           RIS_CHECK_LAUNCH();
           const long long rows = (long long)ns * 3 * nn;
