@@ -83,7 +83,9 @@ typedef struct {
   double cx;          /* fraction of exact exchange c_x (Eq. g_integral); default 0.25 */
   double conv_tol;    /* Davidson residual 2-norm per state; default 1e-10 */
   int max_iter;       /* Davidson iterations; default 100 */
-  int max_subspace;   /* Davidson subspace size before restart; 0 = automatic */
+  int max_subspace;   /* Davidson subspace size before restart; 0 = automatic: max(initial
+                         block + 2 nstates, 8 nstates), 4 nstates instead of 8 in the mixed
+                         phase when nocc*nvir <= 2^20 (TDA) */
   double screen_thr;  /* shell-pair screening threshold; default 1e-14 */
   size_t mem_budget;  /* device bytes the context may hold; 0 = no limit */
   int occ_block;      /* occupied orbitals per block of the exchange part of the Davidson

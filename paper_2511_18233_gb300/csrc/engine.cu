@@ -2004,7 +2004,12 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
                       bool augment, bool* ok) {
   const long long n = (long long)nocc * nvir;
   const int nb0 = (int)std::min<long long>(n, ns + std::min(ns, 8));
-  int maxsp = opt.max_subspace > 0 ? opt.max_subspace : std::max(nb0 + 2 * ns, 8 * ns);
+  // automatic size: 8 ns, or 4 ns for the mixed phase when the products are
+  // cheap (nov <= 2^20): its looser tolerance converges in as many
+  // iterations from the smaller subspace, whose FP64 eigensolve (latency-
+  // bound, about m^3) then costs far less
+  const int mult = mixed && n <= (1LL << 20) ? 4 : 8;
+  int maxsp = opt.max_subspace > 0 ? opt.max_subspace : std::max(nb0 + 2 * ns, mult * ns);
   maxsp = (int)std::min<long long>(std::min(maxsp, 256), n);
   RIS_REQUIRE(maxsp >= nb0, RIS_ERR_ARG, "max_subspace smaller than the initial block");
   const int kkeep = std::min(2 * ns, 64);
