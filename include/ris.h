@@ -92,7 +92,8 @@ typedef struct {
                          products; 0 = automatic (all when they fit) */
   void* cuda_stream;  /* cudaStream_t to run on; NULL = the context makes one */
   int device;         /* CUDA device ordinal */
-  int profile;        /* 1: time kernel classes with CUDA events (see ris_get_stats) */
+  int profile;        /* 1: time the kernel classes this context launches with CUDA events on
+                         its streams (see ris_get_stats; other contexts are not counted) */
   double mixed_tol;   /* RIS_MIXED: residual tolerance of the 3xTF32 Davidson phase; default 1e-6.
                          When the 3xTF32 products stall above it (eight iterations without a
                          10% drop of the largest residual, within 100x the tolerance), TDA
