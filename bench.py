@@ -109,12 +109,14 @@ def peaks():
 # while the kernel's source file is unchanged (sha256 prefix); the summary is
 # in profiles/launches_mixed_c20h22.md.
 TRAFFIC = {
-    "dgemm_fp64": {"bytes_per_eval": 1.3512e9, "source": "paper_2511_18233_gb300/csrc/la.cu",
-                   "sha": "ac327dac6413d7d1"},
-    "tc_gemm_3xtf32": {"bytes_per_eval": 4.7681e9, "source": "paper_2511_18233_gb300/csrc/gemm_tc.cu",
-                       "sha": "43c01fd7f312ef94"},
-    "emu_gemm_f64": {"bytes_per_eval": 0.9360e9, "source": "paper_2511_18233_gb300/csrc/gemm_emu.cu",
+    "dgemm_fp64": {"bytes_per_eval": 0.4933e9, "source": "paper_2511_18233_gb300/csrc/la.cu",
+                   "sha": "507661db5d6a9971"},
+    "tc_gemm_3xtf32": {"bytes_per_eval": 5.1348e9, "source": "paper_2511_18233_gb300/csrc/gemm_tc.cu",
+                       "sha": "80f44d6f789f2b89"},
+    "emu_gemm_f64": {"bytes_per_eval": 0.9350e9, "source": "paper_2511_18233_gb300/csrc/gemm_emu.cu",
                      "sha": "6eca5b2a53ba7b71"},
+    "ff_gemm_f64x": {"bytes_per_eval": 0.5702e9, "source": "paper_2511_18233_gb300/csrc/gemm_ff.cu",
+                     "sha": "dadb56aa86262bbf"},
 }
 
 

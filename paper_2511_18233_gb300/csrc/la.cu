@@ -682,8 +682,17 @@ __global__ void __launch_bounds__(kEigVecT) k_eig_vec(int m, double* work, int a
     for (size_t t = tid; t < (size_t)m * m; t += kEigVecT) As[t] = W.A[t];
   const double* A = a_smem ? As : W.A;
   __syncthreads();
-  double glo = 0.0, ghi = 0.0;
-  tri_bounds(d, e, m, glo, ghi);
+  // Gershgorin bounds by one thread (every thread repeating the FP64 scan
+  // would load the SM's narrow FP64 pipe 128-fold)
+  if (tid == 0) {
+    double lo0 = 0.0, hi0 = 0.0;
+    tri_bounds(d, e, m, lo0, hi0);
+    sh_lo = lo0;
+    sh_hi = hi0;
+  }
+  __syncthreads();
+  const double glo = sh_lo, ghi = sh_hi;
+  __syncthreads();  // sh_lo / sh_hi are reused for the bracket below
   const double tnorm = fmax(fmax(fabs(glo), fabs(ghi)), 1e-300);
   if (tid < 32) {
     const int lane = tid;
@@ -817,10 +826,22 @@ __global__ void __launch_bounds__(kEigT) k_eig_finish(int m, int k, double* w, d
   __syncthreads();
   const double tnorm = fmax(fmax(fabs(bnd[0]), fabs(bnd[1])), 1e-300);
   const double gap_tol = 1e-7 * tnorm;
+  // close[j] bit i (i < j): lambda_i within gap_tol of lambda_j, one thread
+  // per j (the test repeated by every thread would load the narrow FP64 pipe)
+  __shared__ unsigned long long close[64];
+  if (tid < k) {
+    unsigned long long msk = 0ull;
+    for (int i = 0; i < tid; i++)
+      if (!(fabs(lam[tid] - lam[i]) > gap_tol)) msk |= 1ull << i;
+    close[tid] = msk;
+  }
+  __syncthreads();
   double* Z = W.Z;
   for (int j = 1; j < k; j++) {
+    const unsigned long long msk = close[j];
+    if (!msk) continue;
     for (int i = 0; i < j; i++) {
-      if (fabs(lam[j] - lam[i]) > gap_tol) continue;
+      if (!((msk >> i) & 1ull)) continue;
       double part = 0.0;
       for (int q = tid; q < m; q += kEigT) part += Z[(size_t)i * m + q] * Z[(size_t)j * m + q];
       const double s = block_sum<kEigT>(part, red);
