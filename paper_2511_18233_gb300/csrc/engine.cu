@@ -24,6 +24,7 @@
 // the symmetrised Gamma; the auxiliary-centre and metric derivatives follow
 // from translational invariance.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <map>
@@ -504,11 +505,23 @@ __global__ void k_precond_update(double* __restrict__ T, const double* __restric
   T[t] -= f * dinv[t % n] * P[t];
 }
 
-__global__ void k_scale_rows(double* __restrict__ X, long long n, int nrow, const double* __restrict__ nrm2) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// X[r] /= sqrt(nrm2[r]) (rows of zero norm zeroed); 256 threads per block,
+// each block forms the reciprocal norms of the rows it touches once (an FP64
+// square root and division per element would load the narrow FP64 pipe).
+__global__ void __launch_bounds__(256) k_scale_rows(double* __restrict__ X, long long n, int nrow,
+                                                    const double* __restrict__ nrm2) {
+  __shared__ double inv[256];
+  const long long t0 = (long long)blockIdx.x * 256;
+  const long long r0 = t0 / n;
+  const long long r1 = min((long long)nrow - 1, (t0 + 255) / n);
+  if ((long long)threadIdx.x <= r1 - r0) {
+    const double s = nrm2[r0 + threadIdx.x];
+    inv[threadIdx.x] = s > 0 ? 1.0 / sqrt(s) : 0.0;
+  }
+  __syncthreads();
+  const long long t = t0 + threadIdx.x;
   if (t >= n * nrow) return;
-  const double s = nrm2[t / n];
-  X[t] *= s > 0 ? 1.0 / sqrt(s) : 0.0;
+  X[t] *= inv[t / n - r0];
 }
 
 // Cholesky of the Gram matrix G (nt x nt, unit diagonal expected) with
@@ -519,7 +532,7 @@ __global__ void k_scale_rows(double* __restrict__ X, long long n, int nrow, cons
 // updates nothing), lanes over the columns of each update; then P = R^-T
 // restricted to the kept pivots, lane q solving R^T y = e_q.
 __global__ void __launch_bounds__(32) k_cholqr_small(const double* G, int nt, double drop,
-                                                     double* P, int* nkeep) {
+                                                     double* P, int* nkeep, double* pivmin) {
   extern __shared__ double sh[];
   double* A = sh;            // working copy, upper triangle updated
   double* R = A + nt * nt;   // row j: row of R for kept pivot j
@@ -534,9 +547,11 @@ __global__ void __launch_bounds__(32) k_cholqr_small(const double* G, int nt, do
   }
   __syncwarp();
   int r = 0;
+  double dmin = 1.0;  // smallest kept pivot relative to its diagonal
   for (int j = 0; j < nt; j++) {
     const double d = A[j * nt + j];
     if (!(d > drop * G[j * nt + j] && d > 0)) continue;  // warp-uniform
+    dmin = fmin(dmin, d / G[j * nt + j]);
     const double rjj = sqrt(d), ri = 1.0 / rjj;
     for (int l = j + 1 + lane; l < nt; l += 32) R[j * nt + l] = A[j * nt + l] * ri;
     if (lane == 0) {
@@ -563,7 +578,10 @@ __global__ void __launch_bounds__(32) k_cholqr_small(const double* G, int nt, do
     }
   }
   __syncwarp();
-  if (lane == 0) *nkeep = r;
+  if (lane == 0) {
+    *nkeep = r;
+    if (pivmin) *pivmin = dmin;
+  }
   for (int i = lane; i < nt * nt; i += 32) P[i] = Ps[i];
 }
 
@@ -577,11 +595,11 @@ static void gemm_sub(bool ff, bool ta, bool tb, int m, int n, int k, double alph
 }
 
 static void cholqr_small(const double* G, int nt, double drop, double* P, int* nkeep,
-                         cudaStream_t st) {
+                         cudaStream_t st, double* pivmin = nullptr) {
   RIS_REQUIRE(nt >= 1 && nt <= 64, RIS_ERR_ARG, "cholqr_small: block of 1..64 vectors");
   const size_t smem = (3 * (size_t)nt * nt + nt) * sizeof(double) + nt * sizeof(int);
   ensure_smem_attr((const void*)k_cholqr_small, (int)((3 * 64 * 64 + 64) * sizeof(double) + 64 * sizeof(int)));
-  k_cholqr_small<<<1, 32, smem, st>>>(G, nt, drop, P, nkeep);
+  k_cholqr_small<<<1, 32, smem, st>>>(G, nt, drop, P, nkeep, pivmin);
   RIS_CHECK_LAUNCH();
 }
 
@@ -602,22 +620,24 @@ __global__ void k_mirror(double* __restrict__ H, int ld, int m0, int m1) {
 
 // Sign of each row so that its largest-magnitude element is positive
 // (ties: smallest index); the same sign is applied to Y when given.
+// |x| compared as the integer bit pattern of the magnitude (same order for
+// non-negative doubles) so that the scan stays off the FP64 pipe.
 __global__ void k_phase(double* __restrict__ X, double* __restrict__ Y, long long n) {
-  __shared__ double bv[32];
+  __shared__ unsigned long long bv[32];
   __shared__ long long bi[32];
   __shared__ double sgn;
   double* x = X + (size_t)blockIdx.x * n;
-  double best = -1.0;
+  unsigned long long best = 0ull;
   long long besti = 0x7fffffffffffffffLL;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    const double v = fabs(x[i]);
+    const unsigned long long v = (unsigned long long)__double_as_longlong(x[i]) & 0x7fffffffffffffffull;
     if (v > best || (v == best && i < besti)) {
       best = v;
       besti = i;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const unsigned long long ov = __shfl_xor_sync(0xffffffffu, best, o);
     const long long oi = __shfl_xor_sync(0xffffffffu, besti, o);
     if (ov > best || (ov == best && oi < besti)) {
       best = ov;
@@ -2016,7 +2036,7 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
   SBuf<double> V((size_t)maxsp * n, st), AV((size_t)maxsp * n, st), Hs((size_t)maxsp * maxsp, st),
       S((size_t)64 * maxsp, st), w(64, st), Xr((size_t)ns * n, st), AXr((size_t)ns * n, st),
       Rr((size_t)ns * n, st), T((size_t)ns * n, st), tmp((size_t)std::max(ns, kkeep) * n, st),
-      Cc((size_t)ns * maxsp, st), G((size_t)ns * ns, st), Pm((size_t)ns * ns + 64, st),
+      Cc((size_t)ns * maxsp, st), G((size_t)ns * ns, st), Pm((size_t)ns * ns + 2 * ns + 72, st),
       ework(eig_work_size(maxsp), st);
   SBuf<int> idxbuf((size_t)std::max(nb0, ns) + 8, st);
   int* d_idx = idxbuf.p;
@@ -2170,22 +2190,38 @@ void Engine::dav_core(int ns, const double* guess, int nguess, bool mixed, doubl
       }
       m = keep;
     }
-    // two rounds of (project out V, orthonormalise within the block)
+    // up to two rounds of (project out V, orthonormalise within the block).
+    // The mixed phase stops after the first when it lost little (every
+    // vector keeps at least half its norm under the projection, no vector
+    // dropped, smallest CholQR pivot >= 1e-4 of its diagonal): then the
+    // vectors are orthogonal to V and to each other to ~1e-14, far below its
+    // 1e-6 tolerance ("twice is enough" with the test of Daniel, Gragg,
+    // Kaufman and Stewart).  The FP64 form always takes both.
     int nkeep = nt;
+    // info block: [0] nkeep (int), [1] smallest pivot, [2, 2 + ns) squared
+    // norms before the projection, [2 + ns, 2 + 2 ns) after it
+    double* info = Pm.p + (size_t)ns * ns + 8;
+    std::vector<double> hinfo(2 + 2 * (size_t)ns);
+    row_norms(T.p, nt, n, info + 2, st);
     for (int pass = 0; pass < 2 && nkeep > 0; pass++) {
       dgemm(false, true, nt, m, (int)n, 1.0, T.p, (int)n, V.p, (int)n, 0.0, Cc.p, m, st);
       dgemm(false, false, nt, (int)n, m, -1.0, Cc.p, m, V.p, (int)n, 1.0, T.p, (int)n, st);
-      row_norms(T.p, nt, n, G.p, st);
-      k_scale_rows<<<cdiv(n * nt, 256), 256, 0, st>>>(T.p, n, nt, G.p);
+      row_norms(T.p, nt, n, info + 2 + ns, st);
+      k_scale_rows<<<cdiv(n * nt, 256), 256, 0, st>>>(T.p, n, nt, info + 2 + ns);
       RIS_CHECK_LAUNCH();
       dgemm(false, true, nt, nt, (int)n, 1.0, T.p, (int)n, T.p, (int)n, 0.0, G.p, nt, st);
-      cholqr_small(G.p, nt, drop, Pm.p, (int*)(Pm.p + nt * nt), st);
-      RIS_CUDA(cudaMemcpyAsync(&nkeep, Pm.p + nt * nt, sizeof(int), cudaMemcpyDeviceToHost, st));
+      cholqr_small(G.p, nt, drop, Pm.p, (int*)info, st, info + 1);
+      RIS_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(double) * (2 + 2 * (size_t)ns),
+                               cudaMemcpyDeviceToHost, st));
       RIS_CUDA(cudaStreamSynchronize(st));
+      memcpy(&nkeep, hinfo.data(), sizeof(int));
       if (nkeep == 0) break;
+      bool one_pass = mixed && pass == 0 && nkeep == nt && hinfo[1] >= 1e-4;
+      for (int j = 0; j < nt && one_pass; j++) one_pass = hinfo[2 + ns + j] >= 0.25 * hinfo[2 + j];
       dgemm(false, false, nkeep, (int)n, nt, 1.0, Pm.p, nt, T.p, (int)n, 0.0, tmp.p, (int)n, st);
       RIS_CUDA(cudaMemcpyAsync(T.p, tmp.p, sizeof(double) * nkeep * n, cudaMemcpyDeviceToDevice, st));
       nt = nkeep;
+      if (one_pass) break;
     }
     if (nkeep == 0) break;
     RIS_CUDA(cudaMemcpyAsync(V.p + (size_t)m * n, T.p, sizeof(double) * nt * n,
