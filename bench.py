@@ -499,7 +499,8 @@ def classify(st, steps, step_ms_total, precision, dims, nprod, npair, workload="
                          ffx, "FP32 FMA probe / 12 instructions per multiply-add"),
         "contract": (st["contract_ms"], None, "hbm", None, "HBM copy"),
         "subspace_eig": (st["eig_ms"], None, "latency (fp64, one CTA per eigenvalue)", None, ""),
-        "int3c": (st["int3c_ms"], None, "fp64 alu", None, "FP64 ALU roofline: profiles/"),
+        "int3c": (st["int3c_ms"], None, "fp64 alu", None,
+                  "McMurchie-Davidson recursion on the FP64 pipe; executed FP64 operations not counted, no achieved/peak"),
         "int3c_deriv": (st["int3c_deriv_ms"], None, "fp64 alu", None,
                         "side stream under the B build and Davidson, time not additive"),
     }
