@@ -116,7 +116,7 @@ TRAFFIC = {
     "emu_gemm_f64": {"bytes_per_eval": 0.9350e9, "source": "paper_2511_18233_gb300/csrc/gemm_emu.cu",
                      "sha": "6eca5b2a53ba7b71"},
     "ff_gemm_f64x": {"bytes_per_eval": 0.5702e9, "source": "paper_2511_18233_gb300/csrc/gemm_ff.cu",
-                     "sha": "dadb56aa86262bbf"},
+                     "sha": "66a9f1945925d817"},
 }
 
 

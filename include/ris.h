@@ -375,9 +375,10 @@ int ris_debug_gemm_f64emu(int M, int N, int K, const double* A, const double* B,
  * (the kernel behind the mixed form's subspace products): FP64 operands cut
  * into pairs of FP32 numbers, products accumulated by the compensated dot
  * product of Ogita, Rump and Oishi on the FP32 pipe.  Error per element at
- * most about 3e-11 sum_k |A_ik| |op(B)_kj| plus FP64 rounding of the result;
- * values of magnitude below 2^-126 count as zero; values at or above 2^128
- * and non-finite values (inf, nan) count as infinite.  A: [M][K]; B: [N][K] if transB else [K][N]; C: [M][N] (read
+ * most about 3e-11 sum_k |A_ik| |op(B)_kj| plus FP64 rounding of the result,
+ * for operands of magnitude 2^-74 and above; smaller values keep 24
+ * significant bits, below 2^-126 they count as zero; values at or above
+ * 2^128 and non-finite values (inf, nan) count as infinite.  A: [M][K]; B: [N][K] if transB else [K][N]; C: [M][N] (read
  * when beta != 0); FP64 DEVICE pointers on the current device.  Shapes:
  * M <= 32 and either K <= 256 with N >= 128, or K >= 512 with N <= 512;
  * *kind (if not null) receives 1 (long-K kernel), 2 (short-K kernel) or 0

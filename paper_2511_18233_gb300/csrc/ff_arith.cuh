@@ -11,8 +11,9 @@ namespace ris {
 
 // x = hi + lo + r: hi the leading 24 significand bits of x and lo the next
 // 29 rounded to 24, by integer operations on the bit pattern (no FP64
-// instruction); |r| <= 2^-47 |x|.  |x| < 2^-126 flushes to zero and
-// |x| >= 2^128 becomes +-inf.
+// instruction); |r| <= 2^-47 |x| for |x| >= 2^-74.  Below that lo would
+// leave the FP32 normal range and is dropped (|r| < 2^-97); |x| < 2^-126
+// flushes to zero and |x| >= 2^128 becomes +-inf.
 __device__ __forceinline__ void ff_split(double x, float& hi, float& lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;

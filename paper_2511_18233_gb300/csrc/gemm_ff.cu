@@ -12,8 +12,9 @@
 // Arithmetic (all FP32 operations round to nearest and are never contracted):
 // * Split.  An FP64 element x becomes hi + lo with hi its leading 24
 //   significand bits and lo the next 29 rounded to 24, by integer operations
-//   on the bit pattern (no FP64 instruction); |x - hi - lo| <= 2^-47 |x|.
-//   |x| < 2^-126 flushes to zero and |x| >= 2^128 becomes +-inf.
+//   on the bit pattern (no FP64 instruction); |x - hi - lo| <= 2^-47 |x|
+//   for |x| >= 2^-74 (below, lo is dropped: error < 2^-97); |x| < 2^-126
+//   flushes to zero and |x| >= 2^128 becomes +-inf.
 // * Term.  a*b ~ ah*bh + (ah*bl + al*bh) (al*bl < 2^-46 |a b| dropped).  The
 //   leading product is made exact as p + e with an FMA (e = ah*bh - p, the
 //   "TwoProduct" of Dekker 1971); p is added to the running sum s by Knuth's
