@@ -522,7 +522,12 @@ def classify(st, steps, step_ms_total, precision, dims, nprod, npair, workload="
             row["note"] = note
         table[k] = row
     dom = max((k for k in classes if k != "int3c_deriv"), key=lambda k: classes[k][0])
-    roof = {"kernel": dom, "bound": table[dom]["bound"], "share_of_step": table[dom]["share_of_step"]}
+    # the contract's vocabulary (hbm | tensor | alu), the pipe itself under "pipe"
+    kind = {"tensor (tf32)": "tensor", "tensor (f16)": "tensor", "fp64 fma": "alu",
+            "fp32 fma (double-FP32)": "alu", "hbm": "hbm", "fp64 alu": "alu"}
+    pipe = table[dom]["bound"]
+    roof = {"kernel": dom, "bound": kind.get(pipe, pipe), "pipe": pipe,
+            "share_of_step": table[dom]["share_of_step"]}
     for key in ("achieved", "peak", "unit", "frac", "peak_source", "executed_frac"):
         if key in table[dom]:
             roof[key] = table[dom][key]
