@@ -110,7 +110,7 @@ def peaks():
 # in profiles/launches_mixed_c20h22.md.
 TRAFFIC = {
     "dgemm_fp64": {"bytes_per_eval": 0.4933e9, "source": "paper_2511_18233_gb300/csrc/la.cu",
-                   "sha": "507661db5d6a9971"},
+                   "sha": "5d8e96e3ff2bf3cb"},
     "tc_gemm_3xtf32": {"bytes_per_eval": 5.1348e9, "source": "paper_2511_18233_gb300/csrc/gemm_tc.cu",
                        "sha": "80f44d6f789f2b89"},
     "emu_gemm_f64": {"bytes_per_eval": 0.9350e9, "source": "paper_2511_18233_gb300/csrc/gemm_emu.cu",

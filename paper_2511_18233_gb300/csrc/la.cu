@@ -472,28 +472,16 @@ __device__ int sturm_count_f(const float* d, const float* e2, int m, float x) {
   return c;
 }
 
-// Number of eigenvalues of the tridiagonal (d, e) below x: negative pivots of
-// the LDL^T factorisation of T - x I.  e2 holds e[i]^2.
-__device__ int sturm_count(const double* d, const double* e2, int m, double x) {
-  int c = 0;
-  double q = d[0] - x;
-  if (q < 0) c++;
-  for (int i = 1; i < m; i++) {
-    if (q == 0.0) q = -1e-300;
-    q = d[i] - x - e2[i - 1] * rcp64(q);
-    if (q < 0) c++;
-  }
-  return c;
-}
-
-// The same count from the signs of the leading principal minors
-// p_i = det(T_i - x I): p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}, one
-// sign change per eigenvalue below x (p_i / p_{i-1} is the pivot above; a
-// zero minor counts as a change, as a zero pivot taken negative).  No
-// division: per step one subtraction, one product and one FMA on the FP64
-// pipe, the dependent chain a single FMA (against a reciprocal and three
-// operations for the pivots, which matters on this part's narrow FP64
-// pipe); signs and exponents are read from the bit patterns.  The pair
+// Number of eigenvalues of the tridiagonal (d, e) below x (e2 holds e[i]^2)
+// from the signs of the leading principal minors p_i = det(T_i - x I):
+// p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}, one sign change per
+// eigenvalue below x (p_i / p_{i-1} is the i-th pivot of the LDL^T
+// factorisation of T - x I; a zero minor counts as a change, as a zero pivot
+// taken negative).  No division: per step one subtraction, one product and
+// one FMA on the FP64 pipe, the dependent chain a single FMA (the pivot
+// recurrence needs a reciprocal and three operations per step, which
+// matters on this part's narrow FP64 pipe); signs and exponents are read
+// from the bit patterns.  The pair
 // (p_{i-1}, p_i) is rescaled by a power of two when the larger leaves
 // [2^-500, 2^500] (exact; the signs are unchanged).
 __device__ __forceinline__ int dexp(double v) {
